@@ -1,0 +1,248 @@
+"""Dense finite-difference oracle for the discretised Fokker-Planck equation.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import or run this
+module.  The product path (the CUDA library and its Python binding) never
+calls it, and the two share no code.
+
+What it computes (plain FP64 numpy, no blocking or fusion):
+
+* The PDF f(phi1, phi2; x1, x2, x3) on the full tensor grid, stored as the
+  row-major array ``f[i1, i2, j1, j2, j3]`` (paper: "Matrix product state
+  encoding" fixes the dimension order phi1, phi2, x1, x2, x3).
+* Grids (paper: "Finite-difference discretisation"): x_j = j * 2pi/M,
+  periodic; phi_i = (i + 1/2)/M, cell-centred, so that the zero-sum ghost
+  rules of Eq. compBCs put the wall half a cell outside the first and last
+  nodes.
+* Right-hand side of Eq. FP2 (the discretised Eq. FP0 with the artificial
+  composition-space dissipation):
+      L(f) = - sum_i u_i D1x_i f + gamma sum_i D2x_i f
+             + sum_a D1phi_a [ (Omega (phi_a - <Phi_a>(x)) + Da phi1 phi2) f ]
+             + D_phi sum_a D2phi_a f
+  with S_1 = S_2 = -Da phi1 phi2, so that -d/dphi_a (S_a f) = +D1phi_a(Da phi1 phi2 f).
+  D1/D2 are the second-order central differences (CFD2).  In x they are
+  periodic.  In phi the ghost points follow Eq. compBCs: g_{-1} = -g_0,
+  g_M = -g_{M-1} for a first derivative (applied to the drift flux g) and
+  f_{-1} = f_0, f_M = f_{M-1} for the second derivative.
+* The conditional mean <Phi_a>(x) = h_phi1 h_phi2 sum_{i1,i2} phi_a f
+  (Eq. 2, unnormalised as printed).
+* Explicit two-stage Runge-Kutta in time ("Finite-difference discretisation"):
+  Heun  f* = f + dt L(f);  f_{n+1} = (f + f* + dt L(f*)) / 2   (default)
+  midpoint  f_h = f + dt/2 L(f);  f_{n+1} = f + dt L(f_h)    (rk_variant 1)
+* Integrated statistics (Eqs. spaceAvg, RACov, SGSCov) with the space average
+  normalised by the domain volume, so that the mean of <1> is one.
+* The moment equation Eq. FPMoms for Da = 0 (a separate 3-D RK2-CFD2 solver),
+  used as an independent check of the composition-space operators.
+* The NVPP count of Eq. MPSdofs.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(closed forms, Fourier-exact solutions, conservation laws, the moment
+equation, brute-force sums and the paper's NVPP values).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "Grid", "make_grid", "velocity_field", "initial_pdf", "d1_periodic",
+    "d2_periodic", "d1_zero_sum", "d2_zero_sum", "conditional_means", "rhs",
+    "rk2_step", "solve", "observables", "moment_rhs", "moment_step", "nvpp",
+    "bond_profile",
+]
+
+
+class Grid:
+    """Tensor grid: bits per dimension in the order phi1, phi2, x1, x2, x3."""
+
+    def __init__(self, bits):
+        self.bits = [int(b) for b in bits]
+        self.M = [2 ** b for b in self.bits]
+        self.h_phi = [1.0 / m for m in self.M[:2]]
+        self.h_x = [2.0 * math.pi / m for m in self.M[2:]]
+        self.phi = [(np.arange(m) + 0.5) / m for m in self.M[:2]]
+        self.x = [np.arange(m) * (2.0 * math.pi / m) for m in self.M[2:]]
+
+    @property
+    def shape(self):
+        return tuple(self.M)
+
+
+def make_grid(bits) -> Grid:
+    return Grid(bits)
+
+
+def velocity_field(params, grid: Grid):
+    """u_i(x) = shear_amp * tanh(x2 - pi) [i = 1] + sum of modes
+    a * sin(k . x + theta) added to component c."""
+    X1, X2, X3 = np.meshgrid(*grid.x, indexing="ij")
+    u = [np.zeros(grid.M[2:]), np.zeros(grid.M[2:]), np.zeros(grid.M[2:])]
+    u[0] += params["shear_amp"] * np.tanh(X2 - math.pi)
+    for m in params["umodes"]:
+        k = m["k"]
+        u[m["comp"]] += m["amp"] * np.sin(k[0] * X1 + k[1] * X2 + k[2] * X3 + m["phase"])
+    return u
+
+
+def _gaussian2(grid: Grid, centre, sigma):
+    P1, P2 = np.meshgrid(grid.phi[0], grid.phi[1], indexing="ij")
+    g = np.exp(-((P1 - centre[0]) ** 2 + (P2 - centre[1]) ** 2) / (2.0 * sigma * sigma))
+    return g / (g.sum() * grid.h_phi[0] * grid.h_phi[1])
+
+
+def initial_pdf(params, grid: Grid):
+    """f0 = w(x2) G_hi(phi) + (1 - w(x2)) G_lo(phi), w = (1 + tanh((x2 - pi)/width))/2,
+    G normalised so that h_phi1 h_phi2 sum G = 1; optionally multiplied by
+    (1 + sum_m b_m cos(q_m . x + psi_m))."""
+    g_hi = _gaussian2(grid, params["ic_c_hi"], params["ic_sigma"])
+    g_lo = _gaussian2(grid, params["ic_c_lo"], params["ic_sigma"])
+    w = 0.5 * (1.0 + np.tanh((grid.x[1] - math.pi) / params["ic_blend_width"]))
+    wx = np.broadcast_to(w[None, :, None], grid.M[2:])
+    f = g_hi[:, :, None, None, None] * wx[None, None] + g_lo[:, :, None, None, None] * (1.0 - wx)[None, None]
+    if params.get("icmodes"):
+        X1, X2, X3 = np.meshgrid(*grid.x, indexing="ij")
+        mod = np.ones(grid.M[2:])
+        for m in params["icmodes"]:
+            q = m["k"]
+            mod += m["amp"] * np.cos(q[0] * X1 + q[1] * X2 + q[2] * X3 + m["phase"])
+        f = f * mod[None, None]
+    return np.ascontiguousarray(f)
+
+
+def d1_periodic(f, axis, h):
+    return (np.roll(f, -1, axis) - np.roll(f, 1, axis)) / (2.0 * h)
+
+
+def d2_periodic(f, axis, h):
+    return (np.roll(f, -1, axis) - 2.0 * f + np.roll(f, 1, axis)) / (h * h)
+
+
+def _pad(f, axis, lo, hi):
+    return np.concatenate([lo, f, hi], axis=axis)
+
+
+def d1_zero_sum(g, axis, h):
+    """CFD2 first derivative with ghosts g_{-1} = -g_0, g_M = -g_{M-1} (Eq. compBCs, n = 1)."""
+    first = np.take(g, [0], axis=axis)
+    last = np.take(g, [-1], axis=axis)
+    gp = _pad(g, axis, -first, -last)
+    n = g.shape[axis]
+    return (np.take(gp, np.arange(2, n + 2), axis=axis) - np.take(gp, np.arange(0, n), axis=axis)) / (2.0 * h)
+
+
+def d2_zero_sum(f, axis, h):
+    """CFD2 second derivative with ghosts f_{-1} = f_0, f_M = f_{M-1} (Eq. compBCs, n = 2)."""
+    first = np.take(f, [0], axis=axis)
+    last = np.take(f, [-1], axis=axis)
+    fp = _pad(f, axis, first, last)
+    n = f.shape[axis]
+    return (np.take(fp, np.arange(2, n + 2), axis=axis) - 2.0 * f
+            + np.take(fp, np.arange(0, n), axis=axis)) / (h * h)
+
+
+def conditional_means(f, grid: Grid):
+    """<Phi_a>(x) = h1 h2 sum_{i1,i2} phi_a f  (Eq. 2, unnormalised)."""
+    w = grid.h_phi[0] * grid.h_phi[1]
+    m1 = w * np.tensordot(grid.phi[0], f.sum(axis=1), axes=(0, 0))
+    m2 = w * np.tensordot(grid.phi[1], f.sum(axis=0), axes=(0, 0))
+    return m1, m2
+
+
+def rhs(f, grid: Grid, u, params):
+    """L(f) of Eq. FP2 (see the module docstring)."""
+    om, da, gam, dphi = params["omega"], params["da"], params["gamma"], params["d_phi"]
+    out = np.zeros_like(f)
+    for i in range(3):
+        ax = 2 + i
+        hx = grid.h_x[i]
+        out -= u[i][None, None] * d1_periodic(f, ax, hx)
+        if gam != 0.0:
+            out += gam * d2_periodic(f, ax, hx)
+    m1, m2 = conditional_means(f, grid)
+    P1 = grid.phi[0][:, None, None, None, None]
+    P2 = grid.phi[1][None, :, None, None, None]
+    react = da * P1 * P2
+    g1 = (om * (P1 - m1[None, None]) + react) * f
+    g2 = (om * (P2 - m2[None, None]) + react) * f
+    out += d1_zero_sum(g1, 0, grid.h_phi[0])
+    out += d1_zero_sum(g2, 1, grid.h_phi[1])
+    if dphi != 0.0:
+        out += dphi * d2_zero_sum(f, 0, grid.h_phi[0])
+        out += dphi * d2_zero_sum(f, 1, grid.h_phi[1])
+    return out
+
+
+def rk2_step(f, grid: Grid, u, params):
+    dt = params["dt"]
+    if params.get("rk_variant", 0) == 1:
+        fh = f + 0.5 * dt * rhs(f, grid, u, params)
+        return f + dt * rhs(fh, grid, u, params)
+    fs = f + dt * rhs(f, grid, u, params)
+    return 0.5 * (f + fs + dt * rhs(fs, grid, u, params))
+
+
+def solve(params, nsteps, f0=None, u=None):
+    """Advance the initial PDF (or f0) by nsteps RK2 steps; returns the dense array."""
+    grid = make_grid(params["bits"])
+    if u is None:
+        u = velocity_field(params, grid)
+    f = initial_pdf(params, grid) if f0 is None else np.array(f0, dtype=np.float64)
+    for _ in range(int(nsteps)):
+        f = rk2_step(f, grid, u, params)
+    return f
+
+
+def observables(f, grid: Grid):
+    """Point-wise moments and their space averages (Eqs. 2, spaceAvg, RACov, SGSCov).
+
+    Returns a dict with the fields norm(x) = <1>, mean1/mean2 = <Phi_a>,
+    and the scalars norm_avg, mean1_avg, mean2_avg, phi11_avg, phi22_avg,
+    phi12_avg (space averages of <Phi_a Phi_b>), R12, Y12 and product_J
+    (the space average of <1 - phi1 - phi2>)."""
+    w = grid.h_phi[0] * grid.h_phi[1]
+    P1 = grid.phi[0][:, None, None, None, None]
+    P2 = grid.phi[1][None, :, None, None, None]
+    norm = w * f.sum(axis=(0, 1))
+    m1, m2 = conditional_means(f, grid)
+    s11 = w * (P1 * P1 * f).sum(axis=(0, 1))
+    s22 = w * (P2 * P2 * f).sum(axis=(0, 1))
+    s12 = w * (P1 * P2 * f).sum(axis=(0, 1))
+    avg = lambda a: float(a.mean())
+    out = dict(norm=norm, mean1=m1, mean2=m2,
+               norm_avg=avg(norm), mean1_avg=avg(m1), mean2_avg=avg(m2),
+               phi11_avg=avg(s11), phi22_avg=avg(s22), phi12_avg=avg(s12))
+    out["R12"] = avg(m1 * m2) - out["mean1_avg"] * out["mean2_avg"]
+    out["Y12"] = avg(s12 - m1 * m2)
+    out["product_J"] = out["norm_avg"] - out["mean1_avg"] - out["mean2_avg"]
+    return out
+
+
+def moment_rhs(m, grid: Grid, u, gamma):
+    """Eq. FPMoms with S = 0 on the 3-D grid: -u . D1x m + gamma sum_i D2x_i m."""
+    out = np.zeros_like(m)
+    for i in range(3):
+        out -= u[i] * d1_periodic(m, i, grid.h_x[i])
+        if gamma != 0.0:
+            out += gamma * d2_periodic(m, i, grid.h_x[i])
+    return out
+
+
+def moment_step(m, grid: Grid, u, params):
+    dt, gam = params["dt"], params["gamma"]
+    if params.get("rk_variant", 0) == 1:
+        mh = m + 0.5 * dt * moment_rhs(m, grid, u, gam)
+        return m + dt * moment_rhs(mh, grid, u, gam)
+    ms = m + dt * moment_rhs(m, grid, u, gam)
+    return 0.5 * (m + ms + dt * moment_rhs(ms, grid, u, gam))
+
+
+def bond_profile(N, chi):
+    """p(n) = min(2^n, 2^(N-n), chi) for n = 0..N (Eq. MPSdofs)."""
+    return [min(2 ** n, 2 ** (N - n), chi) for n in range(N + 1)]
+
+
+def nvpp(N, chi):
+    """Number of variables parameterising the PDF, Eq. MPSdofs."""
+    p = bond_profile(N, chi)
+    return 2 * sum(p[n - 1] * p[n] for n in range(1, N + 1)) - sum(p[n] ** 2 for n in range(1, N))

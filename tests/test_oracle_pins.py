@@ -1,0 +1,284 @@
+"""Pins for the CPU oracle: each check compares the oracle with something other
+than itself (a Fourier-exact solution, a closed-form variance law, conservation
+laws that follow from Eq. compBCs, the separate moment equation Eq. FPMoms,
+characteristic solutions of the reaction drift, the paper's NVPP values).
+A dropped term, a wrong sign or a wrong ghost rule in the oracle fails at
+least one of them."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _params(bits, **kw):
+    p = workload.make_params("small", **kw)
+    p["bits"] = list(bits)
+    if "dt" not in kw:
+        ub = abs(p["shear_amp"]) + sum(abs(m["amp"]) for m in p["umodes"])
+        p["dt"] = workload.cfl_dt(p["bits"], p["omega"], p["da"], p["gamma"], p["d_phi"], ub)
+    return p
+
+
+# ---------------------------------------------------------------- stencils (P2)
+@pytest.mark.parametrize("M", [2, 4, 8, 16, 32])
+def test_phi_stencils_zero_column_sums(M):
+    """Eq. compBCs: the sum over the lattice of any discrete phi-derivative is zero."""
+    h = 1.0 / M
+    I = np.eye(M)
+    D1 = np.stack([oracle.d1_zero_sum(I[:, j], 0, h) for j in range(M)], axis=1)
+    D2 = np.stack([oracle.d2_zero_sum(I[:, j], 0, h) for j in range(M)], axis=1)
+    assert np.abs(D1.sum(axis=0)).max() < 1e-12 * M
+    assert np.abs(D2.sum(axis=0)).max() < 1e-12 * M * M
+    # interior rows are the CFD2 stencils: exact on linear / quadratic data
+    phi = (np.arange(M) + 0.5) * h
+    if M >= 3:
+        assert np.allclose((D1 @ phi)[1:-1], 1.0, atol=1e-12)
+        assert np.allclose((D2 @ phi ** 2)[1:-1], 2.0, atol=1e-9)
+
+
+def test_phi_stencil_ghost_values():
+    """First derivative: antisymmetric ghosts make row 0 read (g1 + g0)/2h and the
+    last row -(g_{M-1} + g_{M-2})/2h; second derivative: symmetric ghosts make
+    the end rows one-sided differences (values fixed by Eq. compBCs)."""
+    M, h = 8, 1.0 / 8
+    rng = np.random.default_rng(1)
+    g = rng.standard_normal(M)
+    d1 = oracle.d1_zero_sum(g, 0, h)
+    assert math.isclose(d1[0], (g[1] + g[0]) / (2 * h), rel_tol=1e-14)
+    assert math.isclose(d1[-1], -(g[-1] + g[-2]) / (2 * h), rel_tol=1e-14)
+    d2 = oracle.d2_zero_sum(g, 0, h)
+    assert math.isclose(d2[0], (g[1] - g[0]) / h ** 2, rel_tol=1e-13)
+    assert math.isclose(d2[-1], (g[-2] - g[-1]) / h ** 2, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("M", [4, 16, 64])
+def test_periodic_stencils_fourier_symbols(M):
+    """On e^{ikx} the periodic CFD2 operators act as i sin(kh)/h and -2(1-cos kh)/h^2."""
+    h = 2 * math.pi / M
+    x = np.arange(M) * h
+    for k in range(M):
+        e = np.exp(1j * k * x)
+        assert np.allclose(oracle.d1_periodic(e, 0, h), 1j * math.sin(k * h) / h * e, atol=1e-12)
+        assert np.allclose(oracle.d2_periodic(e, 0, h), -2 * (1 - math.cos(k * h)) / h ** 2 * e, atol=1e-10)
+
+
+# ------------------------------------------------------ Fourier-exact transport (P1)
+@pytest.mark.parametrize("rk", [0, 1])
+def test_constant_velocity_transport_is_fourier_exact(rk):
+    """For constant u and gamma, each Fourier mode of the discrete solution is
+    multiplied per step by R(dt*lam), R(z) = 1 + z + z^2/2 (every two-stage RK2),
+    lam = sum_i [-i u_i sin(k_i h_i)/h_i - 2 gamma (1 - cos k_i h_i)/h_i^2]."""
+    bits = [1, 1, 3, 4, 2]
+    p = _params(bits, omega=0.0, da=0.0, d_phi=0.0, gamma=0.07, rk_variant=rk, dt=0.05)
+    g = oracle.make_grid(bits)
+    uc = [0.7, -0.3, 1.1]
+    u = [np.full(g.M[2:], c) for c in uc]
+    f0 = np.random.default_rng(3).standard_normal(g.shape)
+    n = 9
+    f = oracle.solve(p, n, f0=f0, u=u)
+    F = np.fft.fftn(f0, axes=(2, 3, 4))
+    lam = np.zeros(g.M[2:], dtype=complex)
+    for i in range(3):
+        k = np.fft.fftfreq(g.M[2 + i]) * g.M[2 + i]
+        kh = k * g.h_x[i]
+        sym = -1j * uc[i] * np.sin(kh) / g.h_x[i] - 2 * p["gamma"] * (1 - np.cos(kh)) / g.h_x[i] ** 2
+        shape = [1, 1, 1]
+        shape[i] = -1
+        lam = lam + sym.reshape(shape)
+    z = p["dt"] * lam
+    R = 1 + z + z * z / 2
+    ref = np.real(np.fft.ifftn(F * R[None, None] ** n, axes=(2, 3, 4)))
+    assert np.abs(f - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_gaussian_advection_diffusion_second_order():
+    """Continuous check: a periodic Gaussian advected and diffused in x1 at
+    constant speed; the error against the exact (image-summed) solution falls
+    by ~4x per grid doubling (CFD2 in space, dt ~ h^2)."""
+    errs = []
+    for K in (5, 6, 7):
+        bits = [1, 1, K, 1, 1]
+        M = 2 ** K
+        h = 2 * math.pi / M
+        gam, c, s0, T = 0.05, 0.8, 0.4, 0.2
+        nsteps = int(round(T / (0.05 * h * h / gam)))
+        dt = T / nsteps
+        p = _params(bits, omega=0.0, da=0.0, d_phi=0.0, gamma=gam, dt=dt)
+        g = oracle.make_grid(bits)
+        u = [np.full(g.M[2:], c), np.zeros(g.M[2:]), np.zeros(g.M[2:])]
+
+        def exact(t):
+            s2 = s0 * s0 + 2 * gam * t
+            x = g.x[0]
+            val = sum(np.exp(-(x - math.pi - c * t + 2 * math.pi * j) ** 2 / (2 * s2)) for j in range(-3, 4))
+            return val * s0 / math.sqrt(s2)
+
+        f0 = np.broadcast_to(exact(0.0)[None, None, :, None, None], g.shape).copy()
+        f = oracle.solve(p, nsteps, f0=f0, u=u)
+        errs.append(np.abs(f[0, 0, :, 0, 0] - exact(T)).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < o < 2.3 for o in orders), (errs, orders)
+
+
+# --------------------------------------------------------------- mass (P3)
+def test_norm_conserved_pointwise_full_rhs():
+    """<1>(x) stays 1 under the full operator (zero column sums in phi, D.1 = 0 in x)."""
+    p = _params([4, 4, 3, 3, 3])
+    g = oracle.make_grid(p["bits"])
+    f = oracle.initial_pdf(p, g)
+    o0 = oracle.observables(f, g)
+    assert np.abs(o0["norm"] - 1).max() < 1e-13
+    f = oracle.solve(p, 6)
+    o = oracle.observables(f, g)
+    assert np.abs(o["norm"] - 1).max() < 1e-12
+
+
+# ------------------------------------------------ mixing + dissipation (P4)
+@pytest.mark.parametrize("rk", [0, 1])
+def test_variance_closed_form(rk):
+    """Spatially uniform PDF, u = 0, Da = 0, interior Gaussian: the discrete
+    variance obeys Var' = -2 Omega Var + 2 D_phi exactly, so under RK2
+    Var_n - Var_inf = (1 - 2 Omega dt + 2 Omega^2 dt^2)^n (Var_0 - Var_inf),
+    Var_inf = D_phi / Omega, and the mean stays put."""
+    om, dphi = 1.3, 4e-3
+    p = _params([6, 6, 1, 1, 1], omega=om, da=0.0, d_phi=dphi, gamma=0.0, shear_amp=0.0,
+                umodes=[], ic_c_hi=[0.5, 0.45], ic_c_lo=[0.5, 0.45], rk_variant=rk)
+    g = oracle.make_grid(p["bits"])
+    f = oracle.initial_pdf(p, g)
+
+    def stats(f):
+        o = oracle.observables(f, g)
+        return o["mean1_avg"], o["phi11_avg"] - o["mean1_avg"] ** 2, o["mean2_avg"], o["phi22_avg"] - o["mean2_avg"] ** 2
+
+    m10, v10, m20, v20 = stats(f)
+    n = 40
+    f = oracle.solve(p, n, f0=f)
+    m1, v1, m2, v2 = stats(f)
+    dt = p["dt"]
+    R = 1 - 2 * om * dt + 2 * om * om * dt * dt
+    vinf = dphi / om
+    assert abs(m1 - m10) < 1e-13 and abs(m2 - m20) < 1e-13
+    assert abs(v1 - (vinf + (v10 - vinf) * R ** n)) < 1e-13
+    assert abs(v2 - (vinf + (v20 - vinf) * R ** n)) < 1e-13
+    assert abs(v1 - v10) > 1e-5  # the law is exercised, not trivially satisfied
+
+
+# ------------------------------------ interior IC: means, species difference (P5-P7)
+def _interior(**kw):
+    return _params([5, 5, 3, 3, 3], ic_c_hi=[0.62, 0.4], ic_c_lo=[0.38, 0.6], **kw)
+
+
+def test_initial_conditional_mean_follows_blend():
+    """Interior Gaussians: <Phi_1>(x) = 0.62 w(x2) + 0.38 (1 - w(x2)) with the
+    tanh blend (discrete Gaussian means are exact to e^{-2 pi^2 sigma^2/h^2})."""
+    p = _interior()
+    g = oracle.make_grid(p["bits"])
+    o = oracle.observables(oracle.initial_pdf(p, g), g)
+    w = 0.5 * (1 + np.tanh((g.x[1] - math.pi) / 0.2))
+    exp1 = 0.62 * w + 0.38 * (1 - w)
+    assert np.abs(o["mean1"] - exp1[None, :, None]).max() < 1e-12
+
+
+def test_velocity_divergence_free():
+    p = _params([1, 1, 4, 4, 4])
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    div = sum(oracle.d1_periodic(u[i], i, g.h_x[i]) for i in range(3))
+    assert np.abs(div).max() < 1e-13
+    assert np.abs(u[0]).max() > 0.5
+
+
+def test_moment_equation_da0():
+    """Da = 0: <Phi_a>(x, t) of the 5-D scheme equals the 3-D RK2-CFD2 solution of
+    Eq. FPMoms started from <Phi_a>(x, 0); the spatial means are conserved."""
+    p = _interior(da=0.0)
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    f = oracle.initial_pdf(p, g)
+    m1, m2 = oracle.conditional_means(f, g)
+    o0 = oracle.observables(f, g)
+    n = 8
+    for _ in range(n):
+        f = oracle.rk2_step(f, g, u, p)
+        m1 = oracle.moment_step(m1, g, u, p)
+        m2 = oracle.moment_step(m2, g, u, p)
+    f1, f2 = oracle.conditional_means(f, g)
+    assert np.abs(f1 - m1).max() < 1e-12
+    assert np.abs(f2 - m2).max() < 1e-12
+    o = oracle.observables(f, g)
+    assert abs(o["mean1_avg"] - o0["mean1_avg"]) < 1e-13
+    assert np.abs(m1 - oracle.conditional_means(oracle.initial_pdf(p, g), g)[0]).max() > 1e-4
+
+
+def test_species_difference_follows_moment_equation():
+    """Da > 0: S_1 = S_2, so <Phi_1> - <Phi_2> obeys the linear moment equation
+    point-wise, and its space average is conserved (paper: the difference in
+    consumption must stay zero for symmetric initial data)."""
+    p = _interior(da=1.5)
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    f = oracle.initial_pdf(p, g)
+    a, b = oracle.conditional_means(f, g)
+    d = a - b
+    o0 = oracle.observables(f, g)
+    for _ in range(8):
+        f = oracle.rk2_step(f, g, u, p)
+        d = oracle.moment_step(d, g, u, p)
+    a, b = oracle.conditional_means(f, g)
+    assert np.abs((a - b) - d).max() < 1e-12
+    o = oracle.observables(f, g)
+    assert abs((o["mean1_avg"] - o["mean2_avg"]) - (o0["mean1_avg"] - o0["mean2_avg"])) < 1e-13
+    assert o["mean1_avg"] < o0["mean1_avg"] - 1e-4  # reaction consumes
+
+
+def test_reaction_characteristic_logistic():
+    """u = 0, Omega = 0: a narrow PDF moves along the characteristic of
+    phi_a' = S_a = -Da phi1 phi2, i.e. phi1 - phi2 = c and
+    phi1(t) = c / (1 + (c/phi1_0 - 1) exp(-Da c t)); mean error O(sigma^2 Da t)."""
+    da, T = 1.0, 0.5
+    p = _params([7, 7, 1, 1, 1], omega=0.0, da=da, d_phi=0.0, gamma=0.0, shear_amp=0.0, umodes=[],
+                ic_sigma=0.015, ic_c_hi=[0.6, 0.35], ic_c_lo=[0.6, 0.35])
+    n = int(math.ceil(T / p["dt"]))
+    p["dt"] = T / n
+    g = oracle.make_grid(p["bits"])
+    f0 = oracle.initial_pdf(p, g)
+    o0 = oracle.observables(f0, g)
+    f = oracle.solve(p, n, f0=f0)
+    o = oracle.observables(f, g)
+    a0, b0 = o0["mean1_avg"], o0["mean2_avg"]
+    c = a0 - b0
+    a_ex = c / (1 + (c / a0 - 1) * math.exp(-da * c * T))
+    assert abs(o["mean1_avg"] - a_ex) < 1e-3
+    assert abs((o["mean1_avg"] - o["mean2_avg"]) - c) < 1e-12
+    assert o["mean1_avg"] < a0 - 0.05
+
+
+# --------------------------------------------------------------------- NVPP (P8)
+def test_nvpp_paper_values():
+    with open(os.path.join(GOLDEN, "nvpp.json")) as fh:
+        gold = json.load(fh)
+    for case in gold["maximal"]:
+        assert oracle.nvpp(case["N"], case["chi"]) == case["nvpp"] == 2 ** case["N"]
+    o = {c.get("fraction_order", c.get("reduction_order")): c for c in gold["orders"]}
+    frac = oracle.nvpp(35, 128) / 2 ** 35
+    assert round(math.log10(frac)) == o[-5]["fraction_order"]
+    red = 2 ** 35 / oracle.nvpp(35, 32)
+    assert round(math.log10(red)) == o[6]["reduction_order"]
+
+
+def test_nvpp_brute_force_small():
+    """Brute force: count the entries of an MPS with the profile p(n) minus the
+    gauge dimension sum p(n)^2, for tiny chains."""
+    for N in range(1, 9):
+        for chi in (1, 2, 3, 4, 8, 16):
+            p = oracle.bond_profile(N, chi)
+            entries = sum(p[n] * 2 * p[n + 1] for n in range(N))
+            gauge = sum(p[n] ** 2 for n in range(1, N))
+            assert oracle.nvpp(N, chi) == entries - gauge

@@ -1,0 +1,99 @@
+"""Seeded synthetic workloads for the Fokker-Planck QTT solver.
+
+This module only draws and packs input parameters (grid bits, coefficients,
+random velocity-mode wavevectors/phases, the time step).  It holds none of
+the method's arithmetic: both the CUDA library and the CPU oracle receive the
+same parameter dictionary and evaluate the velocity field, the initial PDF and
+the operators themselves.
+
+Workloads (one PDF f(phi1, phi2; x1, x2, x3) on [0,1]^2 x [0, 2pi)^3):
+  small   2^4 points per dimension (20 QTT sites, 2^20 cells), chi_max 32, 50 steps
+  medium  2^6 points per dimension (30 sites, 2^30 cells), chi_max 64, 200 steps
+  large   2^8 points per dimension (40 sites, 2^40 cells), chi_max 128, 500 steps
+Velocity: u1 = tanh(x2 - pi) plus 4 random Fourier modes of amplitude 0.1,
+each mode adding a*sin(k.x + theta) to one component c with k_c = 0 (so the
+field is divergence-free).  Diffusivity 1e-2, Omega = 1, Da = 1, artificial
+composition-space dissipation D_phi = 4e-3 * Omega.
+Initial PDF: normalised Gaussian of standard deviation 0.05 centred at
+(phi1, phi2) = (1, 0) for x2 > pi and at (0, 1) otherwise, blended by
+w(x2) = (1 + tanh((x2 - pi)/0.2))/2.
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
+
+WORKLOADS = {
+    "small": dict(bits=4, chi_max=32, steps=50),
+    "medium": dict(bits=6, chi_max=64, steps=200),
+    "large": dict(bits=8, chi_max=128, steps=500),
+}
+
+
+def draw_velocity_modes(seed: int, n_modes: int = 4, amp: float = 0.1, kmax: int = 2):
+    """Random Fourier modes: component c, integer wavevector k with k[c] = 0 and
+    the other two entries in [-kmax, kmax], not both zero; phase ~ U[0, 2pi)."""
+    rng = np.random.default_rng(seed)
+    modes = []
+    for _ in range(n_modes):
+        c = int(rng.integers(0, 3))
+        while True:
+            k = [int(v) for v in rng.integers(-kmax, kmax + 1, size=3)]
+            k[c] = 0
+            if any(k):
+                break
+        theta = float(rng.uniform(0.0, 2.0 * math.pi))
+        modes.append(dict(comp=c, k=k, phase=theta, amp=float(amp)))
+    return modes
+
+
+def cfl_dt(bits, omega, da, gamma, d_phi, u_bound, cfl=0.2):
+    """Time step from the stability limits of the explicit scheme, using the
+    bound u_bound >= max_x sum_i |u_i| (advection), Omega + Da (composition
+    drift speed on [0,1]^2) and the two diffusion numbers."""
+    hx = min(2.0 * math.pi / 2 ** b for b in bits[2:])
+    hp = min(1.0 / 2 ** b for b in bits[:2])
+    lims = [hp / max(omega + da, 1e-300)]
+    if u_bound > 0:
+        lims.append(hx / u_bound)
+    if gamma > 0:
+        lims.append(hx * hx / (6.0 * gamma))
+    if d_phi > 0:
+        lims.append(hp * hp / (4.0 * d_phi))
+    return cfl * min(lims)
+
+
+def make_params(workload: str = "small", seed: int = 0, precision: str = "fp64",
+                **overrides) -> dict:
+    """Parameter dictionary for one PDF.  Keys mirror the C struct qtt_params."""
+    w = WORKLOADS[workload] if isinstance(workload, str) else dict(workload)
+    K = w["bits"]
+    p = dict(
+        bits=[K] * 5,
+        chi_max=w["chi_max"],
+        svd_rel_tol=1e-14 if precision == "fp64" else 1e-7,
+        precision=PRECISIONS[precision],
+        omega=1.0,
+        da=1.0,
+        gamma=1e-2,
+        d_phi=4e-3,
+        shear_amp=1.0,
+        umodes=draw_velocity_modes(seed),
+        ic_sigma=0.05,
+        ic_blend_width=0.2,
+        ic_c_hi=[1.0, 0.0],
+        ic_c_lo=[0.0, 1.0],
+        icmodes=[],
+        rk_variant=0,
+        steps=w.get("steps", 1),
+        seed=seed,
+    )
+    p.update(copy.deepcopy(overrides))
+    if "dt" not in overrides:
+        ub = abs(p["shear_amp"]) + sum(abs(m["amp"]) for m in p["umodes"])
+        p["dt"] = cfl_dt(p["bits"], p["omega"], p["da"], p["gamma"], p["d_phi"], ub)
+    return p
