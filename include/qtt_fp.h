@@ -1,0 +1,162 @@
+/*
+ * qtt_fp.h -- C ABI of the GB300 QTT Fokker-Planck solver.
+ *
+ * The library time-steps the joint PDF f(phi1, phi2; x1, x2, x3) of the
+ * reactive-scalar Fokker-Planck equation (paper: Eq. FP0, discretised as
+ * Eq. FP2 with the zero-sum composition-space ghost rules of Eq. compBCs)
+ * on a 2^K1 x ... x 2^K5 grid.  f is stored as a quantics tensor train
+ * (matrix product state, paper: "Matrix product state encoding"): N = sum K_d
+ * sites of physical dimension 2, dimension order phi1, phi2, x1, x2, x3, bits
+ * of each dimension most significant first.  Finite-difference operators are
+ * matrix product operators (paper: "Matrix product state algorithm").
+ *
+ * Conventions for every entry point:
+ *   - Calls never abort or trap.  Each returns a qtt_status; on failure the
+ *     context's last-error string (qtt_last_error) says why.
+ *   - Host arrays passed in are owned by the caller and only read during the
+ *     call (parameters are copied at init).  Output arrays are host FP64
+ *     memory owned by the caller, written after the library's stream has
+ *     been synchronised.
+ *   - The library owns all device memory of a context.  A context is not
+ *     thread-safe; use one context per host thread / stream.
+ *   - All device work of a context runs on params.stream (NULL = the legacy
+ *     default stream of the current device).
+ */
+#ifndef QTT_FP_H
+#define QTT_FP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtt_ctx qtt_ctx; /* opaque */
+
+typedef enum {
+  QTT_OK = 0,
+  QTT_EINVAL = 1,   /* invalid argument or parameter */
+  QTT_ENOMEM = 2,   /* device or host allocation failed */
+  QTT_ECUDA = 3,    /* a CUDA runtime call failed */
+  QTT_ENOCONV = 4,  /* an eigen / QR iteration hit its sweep cap */
+  QTT_ETIMEOUT = 5, /* a bounded device wait gave up */
+  QTT_ENAN = 6,     /* a non-finite value appeared in the state */
+  QTT_ESTATE = 7,   /* call not valid in the context's current state */
+  QTT_EIO = 8       /* checkpoint file error */
+} qtt_status;
+
+/* Arithmetic of the core contractions (MPO x MPS, Hadamard, sketches).
+ * FP64: everything in FP64.  The reduced forms keep FP64 for the Gram
+ * matrices and eigensolves of the SVD truncation and for all norm / mass
+ * accumulation; their QR factorisations run in FP32. */
+typedef enum { QTT_FP64 = 0, QTT_FP32 = 1, QTT_TF32 = 2, QTT_BF16X3 = 3 } qtt_precision;
+
+typedef struct {
+  int32_t bits[5];       /* K per dimension, order phi1, phi2, x1, x2, x3; 1..12 */
+  int32_t chi_max;       /* maximum bond dimension chi (paper: Eq. MPSdofs) */
+  double svd_rel_tol;    /* also drop singular values below tol * sigma_1 (0 = cap only) */
+  int32_t precision;     /* qtt_precision */
+  int32_t oversample;    /* extra sketch columns of the randomized rounding (<= 0: default 8) */
+  int32_t exact;         /* 1: no truncation at all (requires chi_max >= 2^(N/2) and tol = 0) */
+  uint64_t seed;         /* seed of the Gaussian sketches of the randomized rounding */
+  double omega;          /* Omega_mix (constant) */
+  double da;             /* Damkohler number: S_1 = S_2 = -da * phi1 * phi2 */
+  double gamma;          /* diffusivity in x */
+  double d_phi;          /* artificial composition-space dissipation (Eq. FP2) */
+  double dt;             /* time step */
+  double shear_amp;      /* u1 += shear_amp * tanh(x2 - pi) */
+  int32_t n_umodes;      /* velocity Fourier modes: u_c += a sin(k . x + theta), k_c = 0 */
+  const int32_t* umode_comp;   /* [n_umodes] component c in 0..2 */
+  const int32_t* umode_k;      /* [3 * n_umodes] integer wavevectors */
+  const double* umode_phase;   /* [n_umodes] */
+  const double* umode_amp;     /* [n_umodes] */
+  double ic_sigma;       /* std of the two composition-space Gaussians */
+  double ic_blend_width; /* w(x2) = (1 + tanh((x2 - pi) / width)) / 2 */
+  double ic_c_hi[2];     /* Gaussian centre used where w -> 1 (x2 > pi) */
+  double ic_c_lo[2];     /* Gaussian centre used where w -> 0 */
+  int32_t n_icmodes;     /* optional modulation f0 *= 1 + sum b cos(q . x + psi) */
+  const int32_t* icmode_k;     /* [3 * n_icmodes] */
+  const double* icmode_phase;  /* [n_icmodes] */
+  const double* icmode_amp;    /* [n_icmodes] */
+  int32_t rk_variant;    /* 0 = Heun (default), 1 = midpoint */
+  void* stream;          /* cudaStream_t or NULL */
+} qtt_params;
+
+/* What qtt_observe returns (all FP64, space averages normalised by the
+ * number of x points; paper Eqs. 2, spaceAvg, RACov, SGSCov). */
+typedef enum {
+  QTT_OBS_SCALARS = 0,   /* 12 values: time, norm_avg, mean1_avg, mean2_avg,
+                            phi11_avg, phi22_avg, phi12_avg, R12, Y12,
+                            product_J, discarded_weight (last step), steps */
+  QTT_OBS_BONDS = 1,     /* N+1 values: bond dimensions b_0..b_N (b_0 = b_N = 1) */
+  QTT_OBS_DENSE = 2,     /* 2^N values: f[i1][i2][j1][j2][j3] row-major; N <= 26 */
+  QTT_OBS_MEANS = 3,     /* 3 * 2^(K3+K4+K5) values: <1>(x), <Phi_1>(x), <Phi_2>(x); x row-major */
+  QTT_OBS_POINTS = 4,    /* f at given multi-indices: pass in `out` n groups of N bits
+                            (as doubles 0/1, MSB first per dimension), cap = n * N;
+                            the first n entries are overwritten with the values */
+  QTT_OBS_NVPP = 5,      /* 1 value: number of variables parameterising f (Eq. MPSdofs) */
+  QTT_OBS_TIMINGS = 6    /* per kernel class: launches, total ms (profiling builds) */
+} qtt_observable;
+
+/* Build the initial PDF, velocity and operators (paper: "Flow case
+ * definition"; encodings of "Matrix product state algorithm") and upload
+ * them.  *out receives a new context (NULL on failure). */
+qtt_status qtt_init(const qtt_params* params, qtt_ctx** out);
+
+/* Advance nsteps explicit RK2 steps of Eq. FP2 in MPS form.  Each stage
+ * forms f + dt L(f) as a sum of MPO x MPS products (linear operator) and a
+ * Hadamard product with the conditional means (mixing drift), compresses it
+ * by randomized rounding and truncates it by an SVD sweep to chi_max. */
+qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps);
+
+/* Extract observables (see qtt_observable).  `out` has room for `cap`
+ * doubles; *written receives the number written.  Returns QTT_EINVAL when
+ * cap is too small. */
+qtt_status qtt_observe(qtt_ctx* ctx, int32_t what, double* out, int64_t cap, int64_t* written);
+
+/* Relative L2 distance ||a - b|| / ||b|| of the two states (same grid),
+ * from FP64 overlaps <a|a>, <b|b>, <a|b>. */
+qtt_status qtt_compare(qtt_ctx* a, qtt_ctx* b, double* rel_l2);
+
+/* Checkpoint: cores, bonds, time and step count, with a header and an
+ * FNV-1a checksum.  Load requires a context initialised with the same grid. */
+qtt_status qtt_save(qtt_ctx* ctx, const char* path);
+qtt_status qtt_load(qtt_ctx* ctx, const char* path);
+
+void qtt_destroy(qtt_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed qtt_init when ctx is NULL). */
+const char* qtt_last_error(const qtt_ctx* ctx);
+
+/* Library version string. */
+const char* qtt_version(void);
+
+/* ---------------------------------------------------------------------
+ * Host-side verification entry points.  They run the initialisation's
+ * encoders on the CPU only (no GPU, no context) so that the operator and
+ * state encodings can be checked against independent dense constructions.
+ *
+ * qtt_host_dense writes a dense expansion of one object built from params:
+ *   0        initial PDF f0 (paper: "Flow case definition" with the workload's
+ *            initial condition), 2^N values, N <= 26
+ *   1, 2, 3  velocity component u_1, u_2, u_3 over x, 2^(K3+K4+K5) values
+ *   10 + d   first-derivative operator of dimension d (0..4) as a row-major
+ *            M_d x M_d matrix: zero-sum ghosts of Eq. compBCs for d < 2,
+ *            periodic CFD2 for d >= 2
+ *   20 + d   second-derivative operator of dimension d, same conventions
+ *   30       W_lin, the linear part of the right-hand side of Eq. FP2
+ *            (2^N x 2^N, N <= 12)
+ *   31       the stage operator I + dt W_lin (2^N x 2^N, N <= 12)
+ *   32       the composition-space factor of the mixing term,
+ *            -dt Omega D1phi_a, for a = 1, 2: 2 x (M1 M2)^2 values
+ *   40       bond dimensions of the stage operator (N + 1 values)
+ *   41       bond dimensions of the encoded initial PDF (N + 1 values)
+ * Returns QTT_EINVAL for an unknown `which`, invalid params or cap too small.
+ * ------------------------------------------------------------------- */
+qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, int64_t cap, int64_t* written);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTT_FP_H */

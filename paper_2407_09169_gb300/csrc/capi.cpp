@@ -1,0 +1,493 @@
+// C ABI of the QTT Fokker-Planck solver (declared in include/qtt_fp.h).
+// Every entry point catches all exceptions and reports a status; nothing
+// aborts.  Device work runs in the Engine (engine.cu); this file converts
+// parameters, dispatches and formats outputs.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/qtt_fp.h"
+#include "engine.hpp"
+#include "host_tt.hpp"
+#include "model.hpp"
+
+struct qtt_ctx {
+  std::unique_ptr<qtt::Engine> eng;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+qtt_status classify(const std::string& m) {
+  if (m.rfind("EINVAL", 0) == 0) return QTT_EINVAL;
+  if (m.rfind("ENOMEM", 0) == 0) return QTT_ENOMEM;
+  if (m.rfind("EIO", 0) == 0) return QTT_EIO;
+  if (m.rfind("CUDA", 0) == 0) return QTT_ECUDA;
+  return QTT_ESTATE;
+}
+
+bool to_params(const qtt_params* in, qtt::Params& p, std::string& err) {
+  if (!in) {
+    err = "EINVAL: params is NULL";
+    return false;
+  }
+  for (int d = 0; d < 5; ++d) p.bits[d] = in->bits[d];
+  p.chi_max = in->chi_max;
+  p.svd_rel_tol = in->svd_rel_tol;
+  p.precision = in->precision;
+  p.oversample = in->oversample > 0 ? in->oversample : 8;
+  p.exact = in->exact;
+  p.seed = in->seed;
+  p.omega = in->omega;
+  p.da = in->da;
+  p.gamma = in->gamma;
+  p.d_phi = in->d_phi;
+  p.dt = in->dt;
+  p.shear_amp = in->shear_amp;
+  if (in->n_umodes < 0 || in->n_umodes > 4096 || in->n_icmodes < 0 || in->n_icmodes > 4096) {
+    err = "EINVAL: mode counts out of range";
+    return false;
+  }
+  if (in->n_umodes > 0 && (!in->umode_comp || !in->umode_k || !in->umode_phase || !in->umode_amp)) {
+    err = "EINVAL: velocity mode arrays are NULL";
+    return false;
+  }
+  if (in->n_icmodes > 0 && (!in->icmode_k || !in->icmode_phase || !in->icmode_amp)) {
+    err = "EINVAL: initial-condition mode arrays are NULL";
+    return false;
+  }
+  p.umodes.clear();
+  for (int m = 0; m < in->n_umodes; ++m) {
+    qtt::Mode md;
+    md.comp = in->umode_comp[m];
+    for (int i = 0; i < 3; ++i) md.k[i] = in->umode_k[3 * m + i];
+    md.phase = in->umode_phase[m];
+    md.amp = in->umode_amp[m];
+    p.umodes.push_back(md);
+  }
+  p.icmodes.clear();
+  for (int m = 0; m < in->n_icmodes; ++m) {
+    qtt::Mode md;
+    for (int i = 0; i < 3; ++i) md.k[i] = in->icmode_k[3 * m + i];
+    md.phase = in->icmode_phase[m];
+    md.amp = in->icmode_amp[m];
+    p.icmodes.push_back(md);
+  }
+  p.ic_sigma = in->ic_sigma;
+  p.ic_blend_width = in->ic_blend_width;
+  for (int i = 0; i < 2; ++i) {
+    p.ic_c_hi[i] = in->ic_c_hi[i];
+    p.ic_c_lo[i] = in->ic_c_lo[i];
+  }
+  p.rk_variant = in->rk_variant;
+  std::string why = qtt::validate(p);
+  if (!why.empty()) {
+    err = "EINVAL: " + why;
+    return false;
+  }
+  return true;
+}
+
+// Dense matrix [row bits][col bits] of an operator train (d = 4).
+std::vector<double> op_matrix(const qtt::TT& t) {
+  const int N = t.N();
+  const size_t M = (size_t)1 << N;
+  std::vector<double> raw = qtt::tt_dense(t), out(M * M, 0.0);
+  for (size_t idx = 0; idx < raw.size(); ++idx) {
+    size_t row = 0, col = 0, x = idx;
+    for (int n = N - 1; n >= 0; --n) {
+      const size_t i = x & 3;
+      x >>= 2;
+      row |= (i >> 1) << (N - 1 - n);
+      col |= (i & 1) << (N - 1 - n);
+    }
+    out[row * M + col] = raw[idx];
+  }
+  return out;
+}
+
+qtt_status put(const std::vector<double>& v, double* out, int64_t cap, int64_t* written) {
+  if (written) *written = 0;
+  if (!out || cap < (int64_t)v.size()) return QTT_EINVAL;
+  std::memcpy(out, v.data(), v.size() * sizeof(double));
+  if (written) *written = (int64_t)v.size();
+  return QTT_OK;
+}
+
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ULL) {
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qtt_version(void) { return "qtt-fp-gb300 0.1 (sm_103a)"; }
+
+const char* qtt_last_error(const qtt_ctx* ctx) {
+  if (!ctx) return g_init_err.c_str();
+  return ctx->err.c_str();
+}
+
+qtt_status qtt_init(const qtt_params* params, qtt_ctx** out) {
+  if (!out) {
+    g_init_err = "EINVAL: out is NULL";
+    return QTT_EINVAL;
+  }
+  *out = nullptr;
+  try {
+    qtt::Params p;
+    std::string err;
+    if (!to_params(params, p, err)) {
+      g_init_err = err;
+      return QTT_EINVAL;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      g_init_err = std::string("CUDA: no usable CUDA device (") + cudaGetErrorString(e) + ")";
+      return QTT_ECUDA;
+    }
+    std::unique_ptr<qtt_ctx> ctx(new qtt_ctx());
+    ctx->eng.reset(new qtt::Engine(p, (cudaStream_t)params->stream));
+    ctx->eng->init();
+    *out = ctx.release();
+    g_init_err.clear();
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    g_init_err = ex.what();
+    return classify(g_init_err);
+  } catch (...) {
+    g_init_err = "unknown failure in qtt_init";
+    return QTT_ESTATE;
+  }
+}
+
+qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps) {
+  if (!ctx || !ctx->eng) return QTT_EINVAL;
+  if (nsteps < 0) {
+    ctx->err = "EINVAL: nsteps < 0";
+    return QTT_EINVAL;
+  }
+  try {
+    ctx->eng->step(nsteps);
+    std::string msg;
+    const int st = ctx->eng->check_status(msg);
+    if (st != 0) {
+      ctx->err = msg;
+      return (qtt_status)st;
+    }
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return classify(ctx->err);
+  }
+}
+
+qtt_status qtt_observe(qtt_ctx* ctx, int32_t what, double* out, int64_t cap, int64_t* written) {
+  if (written) *written = 0;
+  if (!ctx || !ctx->eng) return QTT_EINVAL;
+  if (!out) {
+    ctx->err = "EINVAL: out is NULL";
+    return QTT_EINVAL;
+  }
+  try {
+    qtt::Engine& E = *ctx->eng;
+    const qtt::Params& p = E.params();
+    const int N = E.N();
+    const int Kx = p.bits[2] + p.bits[3] + p.bits[4];
+    switch (what) {
+      case QTT_OBS_SCALARS: {
+        std::vector<double> v(12);
+        E.scalars(v.data());
+        return put(v, out, cap, written);
+      }
+      case QTT_OBS_BONDS: {
+        std::vector<int> b = E.bonds();
+        return put(std::vector<double>(b.begin(), b.end()), out, cap, written);
+      }
+      case QTT_OBS_DENSE: {
+        if (N > 26) {
+          ctx->err = "EINVAL: dense output needs N <= 26";
+          return QTT_EINVAL;
+        }
+        const int64_t need = (int64_t)1 << N;
+        if (cap < need) {
+          ctx->err = "EINVAL: cap < 2^N";
+          return QTT_EINVAL;
+        }
+        E.dense(out);
+        if (written) *written = need;
+        return QTT_OK;
+      }
+      case QTT_OBS_MEANS: {
+        if (Kx > 26) {
+          ctx->err = "EINVAL: mean fields need K3+K4+K5 <= 26";
+          return QTT_EINVAL;
+        }
+        const int64_t need = 3 * ((int64_t)1 << Kx);
+        if (cap < need) {
+          ctx->err = "EINVAL: cap < 3 * 2^(K3+K4+K5)";
+          return QTT_EINVAL;
+        }
+        E.means(out);
+        if (written) *written = need;
+        return QTT_OK;
+      }
+      case QTT_OBS_POINTS: {
+        if (cap < N || cap % N != 0) {
+          ctx->err = "EINVAL: cap must be a positive multiple of N";
+          return QTT_EINVAL;
+        }
+        const int npts = (int)(cap / N);
+        std::vector<unsigned char> bits((size_t)cap);
+        for (int64_t i = 0; i < cap; ++i) bits[i] = out[i] != 0.0 ? 1 : 0;
+        std::vector<double> vals(npts);
+        E.points(bits, npts, vals.data());
+        std::memcpy(out, vals.data(), sizeof(double) * npts);
+        if (written) *written = npts;
+        return QTT_OK;
+      }
+      case QTT_OBS_NVPP: {
+        std::vector<int> b = E.bonds();
+        double s1 = 0, s2 = 0;
+        for (int n = 1; n <= N; ++n) s1 += 2.0 * b[n - 1] * b[n];
+        for (int n = 1; n < N; ++n) s2 += (double)b[n] * b[n];
+        return put(std::vector<double>{s1 - s2}, out, cap, written);
+      }
+      case QTT_OBS_TIMINGS:
+        return put(E.timings(), out, cap, written);
+      default:
+        ctx->err = "EINVAL: unknown observable";
+        return QTT_EINVAL;
+    }
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return classify(ctx->err);
+  }
+}
+
+qtt_status qtt_compare(qtt_ctx* a, qtt_ctx* b, double* rel_l2) {
+  if (!a || !b || !a->eng || !b->eng || !rel_l2) return QTT_EINVAL;
+  try {
+    const double aa = a->eng->overlap(*a->eng);
+    const double bb = b->eng->overlap(*b->eng);
+    const double ab = a->eng->overlap(*b->eng);
+    const double d2 = aa + bb - 2.0 * ab;
+    *rel_l2 = std::sqrt(d2 > 0 ? d2 : 0.0) / std::sqrt(bb > 0 ? bb : 1e-300);
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    a->err = ex.what();
+    return classify(a->err);
+  }
+}
+
+qtt_status qtt_save(qtt_ctx* ctx, const char* path) {
+  if (!ctx || !ctx->eng || !path) return QTT_EINVAL;
+  try {
+    qtt::Engine& E = *ctx->eng;
+    std::vector<double> data = E.download_state();
+    std::vector<int> b = E.bonds();
+    std::vector<unsigned char> buf;
+    auto app = [&](const void* p, size_t n) {
+      const unsigned char* c = (const unsigned char*)p;
+      buf.insert(buf.end(), c, c + n);
+    };
+    const char magic[8] = {'Q', 'T', 'T', 'F', 'P', '0', '0', '1'};
+    app(magic, 8);
+    const int32_t N = E.N();
+    app(&N, 4);
+    for (int d = 0; d < 5; ++d) app(&E.params().bits[d], 4);
+    const double t = E.time();
+    const int64_t st = E.steps();
+    app(&t, 8);
+    app(&st, 8);
+    for (int v : b) app(&v, 4);
+    const uint64_t cnt = data.size();
+    app(&cnt, 8);
+    app(data.data(), data.size() * sizeof(double));
+    const uint64_t h = fnv1a(buf.data(), buf.size());
+    app(&h, 8);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) {
+      ctx->err = std::string("EIO: cannot open ") + path;
+      return QTT_EIO;
+    }
+    const size_t wr = std::fwrite(buf.data(), 1, buf.size(), f);
+    const int cl = std::fclose(f);
+    if (wr != buf.size() || cl != 0) {
+      ctx->err = "EIO: short write";
+      return QTT_EIO;
+    }
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return classify(ctx->err);
+  }
+}
+
+qtt_status qtt_load(qtt_ctx* ctx, const char* path) {
+  if (!ctx || !ctx->eng || !path) return QTT_EINVAL;
+  try {
+    FILE* f = std::fopen(path, "rb");
+    if (!f) {
+      ctx->err = std::string("EIO: cannot open ") + path;
+      return QTT_EIO;
+    }
+    std::vector<unsigned char> buf;
+    unsigned char tmp[65536];
+    size_t got;
+    while ((got = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + got);
+    std::fclose(f);
+    qtt::Engine& E = *ctx->eng;
+    const int N = E.N();
+    const size_t head = 8 + 4 + 20 + 8 + 8 + 4 * (size_t)(N + 1) + 8;
+    if (buf.size() < head + 8 || std::memcmp(buf.data(), "QTTFP001", 8) != 0) {
+      ctx->err = "EIO: not a checkpoint of this library";
+      return QTT_EIO;
+    }
+    uint64_t hstored;
+    std::memcpy(&hstored, buf.data() + buf.size() - 8, 8);
+    if (fnv1a(buf.data(), buf.size() - 8) != hstored) {
+      ctx->err = "EIO: checksum mismatch (truncated or corrupted checkpoint)";
+      return QTT_EIO;
+    }
+    size_t o = 8;
+    int32_t Nf;
+    std::memcpy(&Nf, buf.data() + o, 4);
+    o += 4;
+    if (Nf != N) {
+      ctx->err = "EIO: checkpoint has a different number of sites";
+      return QTT_EIO;
+    }
+    for (int d = 0; d < 5; ++d) {
+      int32_t bd;
+      std::memcpy(&bd, buf.data() + o, 4);
+      o += 4;
+      if (bd != E.params().bits[d]) {
+        ctx->err = "EIO: checkpoint grid differs";
+        return QTT_EIO;
+      }
+    }
+    double t;
+    int64_t st;
+    std::memcpy(&t, buf.data() + o, 8);
+    o += 8;
+    std::memcpy(&st, buf.data() + o, 8);
+    o += 8;
+    std::vector<int> b = E.bonds();
+    for (int n = 0; n <= N; ++n) {
+      int32_t v;
+      std::memcpy(&v, buf.data() + o, 4);
+      o += 4;
+      if (v != b[n]) {
+        ctx->err = "EIO: checkpoint bond profile differs (chi_max mismatch)";
+        return QTT_EIO;
+      }
+    }
+    uint64_t cnt;
+    std::memcpy(&cnt, buf.data() + o, 8);
+    o += 8;
+    if (buf.size() != o + cnt * sizeof(double) + 8) {
+      ctx->err = "EIO: checkpoint size mismatch";
+      return QTT_EIO;
+    }
+    std::vector<double> data(cnt);
+    std::memcpy(data.data(), buf.data() + o, cnt * sizeof(double));
+    E.upload_state(data);
+    E.set_time(t, st);
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return classify(ctx->err);
+  }
+}
+
+void qtt_destroy(qtt_ctx* ctx) {
+  if (!ctx) return;
+  try {
+    if (ctx->eng) cudaStreamSynchronize(ctx->eng->stream());
+  } catch (...) {
+  }
+  delete ctx;
+}
+
+qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, int64_t cap, int64_t* written) {
+  if (written) *written = 0;
+  try {
+    qtt::Params p;
+    std::string err;
+    if (!to_params(params, p, err)) {
+      g_init_err = err;
+      return QTT_EINVAL;
+    }
+    const int N = p.N();
+    if (which == 0) {
+      if (N > 26) return QTT_EINVAL;
+      qtt::Model m = qtt::build_model(p);
+      return put(qtt::tt_dense(m.f0), out, cap, written);
+    }
+    if (which >= 1 && which <= 3) {
+      if (p.bits[2] + p.bits[3] + p.bits[4] > 26) return QTT_EINVAL;
+      return put(qtt::tt_dense(qtt::velocity_tt(p, which - 1)), out, cap, written);
+    }
+    if ((which >= 10 && which <= 14) || (which >= 20 && which <= 24)) {
+      const int d = which % 10;
+      const int K = p.bits[d];
+      const double h = d < 2 ? 1.0 / (double)(1 << K) : 2.0 * 3.14159265358979323846 / (double)(1 << K);
+      qtt::TT op;
+      if (which < 20) op = d < 2 ? qtt::op_d1_zero_sum(K, h) : qtt::op_d1_periodic(K, h);
+      else op = d < 2 ? qtt::op_d2_zero_sum(K, h) : qtt::op_d2_periodic(K, h);
+      return put(op_matrix(op), out, cap, written);
+    }
+    if (which == 30 || which == 31 || which == 40) {
+      if (which != 40 && N > 12) return QTT_EINVAL;
+      qtt::Model m = qtt::build_model(p);
+      if (which == 40) return put(std::vector<double>(m.op_lin.r.begin(), m.op_lin.r.end()), out, cap, written);
+      qtt::TT W = which == 30 ? qtt::linear_operator(p, m.u) : m.op_lin;
+      return put(op_matrix(W), out, cap, written);
+    }
+    if (which == 32) {
+      if (p.Kphi() > 12) return QTT_EINVAL;
+      qtt::Model m = qtt::build_model(p);
+      std::vector<double> res;
+      for (int a = 0; a < 2; ++a) {
+        qtt::TT t = m.had_phi;
+        const int L = t.N() - 1;
+        // select the open-bond column a of the last core
+        std::vector<double> c((size_t)t.r[L] * 4, 0.0);
+        for (int x = 0; x < t.r[L]; ++x)
+          for (int i = 0; i < 4; ++i) c[(size_t)x * 4 + i] = t.at(L, x, i, a);
+        t.c[L] = c;
+        t.r[L + 1] = 1;
+        std::vector<double> mtx = op_matrix(t);
+        res.insert(res.end(), mtx.begin(), mtx.end());
+      }
+      return put(res, out, cap, written);
+    }
+    if (which == 41) {
+      qtt::Model m = qtt::build_model(p);
+      return put(std::vector<double>(m.f0.r.begin(), m.f0.r.end()), out, cap, written);
+    }
+    return QTT_EINVAL;
+  } catch (const std::exception& ex) {
+    g_init_err = ex.what();
+    return classify(g_init_err);
+  }
+}
+
+}  // extern "C"

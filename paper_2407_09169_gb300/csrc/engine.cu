@@ -1,0 +1,795 @@
+// Device engine of the QTT Fokker-Planck solver.
+//
+// One explicit RK2 stage (paper: "Finite-difference discretisation" -- RK2
+// in time; "Matrix product state algorithm" -- the scheme run on the MPS
+// manifold with MPO x MPS products, Hadamard products and SVD truncation)
+// computes a sum of terms  g = sum_t c_t Op_t f_t, where Op_t is either
+//   * the linear stage operator I + dt W_lin (transport, diffusion, the
+//     linear composition drift Omega phi_a + reaction, dissipation), or
+//   * the mixing term -dt Omega D1phi_a (<Phi_a>(x) f), an element-wise
+//     (Hadamard) product of f with the conditional means, whose x-part cores
+//     are f's own x cores with the conditional-mean vectors absorbed into the
+//     first one (paper: "Computational complexity" -- the element-wise
+//     product is the O(chi^4) operation), or
+//   * a multiple of the identity (RK combinations).
+// The exact sum has bond dimension ~ chi * (w + chi) on the x sites; it is
+// never formed.  Instead:
+//   1. a right-to-left sketch pass contracts the terms with a Gaussian
+//      random MPS of bond ell = chi + oversample (W_n, right environments);
+//   2. a left-to-right pass forms each site tensor T = C * (Op core x f core),
+//      orthonormalises the sketch Y = T W_{n+1} by Householder QR, keeps
+//      Q as the left-orthonormal core and carries C = Q^T T to the next site
+//      (randomized "orthogonalise the sketch" rounding of tensor trains);
+//   3. a right-to-left sweep truncates every bond to chi with the SVD,
+//      obtained from the FP64 Gram matrix M M^T of the bond matrix and its
+//      eigen-decomposition, leaving the state right-canonical.
+// Exact mode (no truncation, for parity with the finite-difference oracle):
+// step 1 uses identity cores instead of random ones up to the centre of the
+// chain, step 2 keeps identity cores (no QR) up to the centre and writes the
+// centre core as T W, so the whole stage is a chain of exact contractions.
+#include "engine.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+
+namespace qtt {
+
+#define QTT_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t _e = (call);                                                                   \
+    if (_e != cudaSuccess)                                                                     \
+      throw std::runtime_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + " at " + \
+                               __FILE__ + ":" + std::to_string(__LINE__));                     \
+  } while (0)
+
+struct KernelTimer {
+  bool on = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double ms[8] = {0}, launches[8] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void flush() {
+    for (auto& r : recs) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.cls] += t;
+        launches[r.cls] += 1;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  ~KernelTimer() {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+enum { TM_GEMM = 0, TM_QR = 1, TM_EIG = 2, TM_OTHER = 3 };
+
+struct TimeScope {
+  KernelTimer* t;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t b = nullptr;
+  TimeScope(KernelTimer* tm, int c, cudaStream_t s) : t(tm), cls(c), st(s) {
+    if (t && t->on) {
+      cudaEvent_t a = t->get();
+      b = t->get();
+      cudaEventRecord(a, st);
+      t->recs.push_back({cls, a, b});
+    }
+  }
+  ~TimeScope() {
+    if (t && t->on && b) cudaEventRecord(b, st);
+  }
+};
+
+Chain DevMps::chain() const {
+  Chain c;
+  std::memset(&c, 0, sizeof(c));
+  c.n = N;
+  for (int n = 0; n < N; ++n) c.core[n] = core(n);
+  for (int n = 0; n <= N; ++n) c.bond[n] = b[n];
+  return c;
+}
+
+static long long pow2(int e) { return e >= 62 ? (1LL << 62) : (1LL << e); }
+
+Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
+  N_ = p.N();
+  kphi_ = p.Kphi();
+  exact_ = p.exact != 0;
+  prec_bits_ = (p.precision == 0) ? 64 : 32;
+  timer_ = new KernelTimer();
+  if (const char* e = std::getenv("QTT_KERNEL_TIMING")) timer_->on = (e[0] == '1');
+}
+
+Engine::~Engine() {
+  for (void* a : allocs_) cudaFree(a);
+  delete timer_;
+}
+
+void* Engine::dalloc(size_t bytes) {
+  void* ptr = nullptr;
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw std::runtime_error("ENOMEM: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  allocs_.push_back(ptr);
+  return ptr;
+}
+
+void Engine::alloc_mps(DevMps& m, const std::vector<int>& bonds) {
+  m.N = (int)bonds.size() - 1;
+  m.b = bonds;
+  m.off.assign(m.N, 0);
+  size_t tot = 0;
+  for (int n = 0; n < m.N; ++n) {
+    m.off[n] = tot;
+    tot += (size_t)bonds[n] * 2 * bonds[n + 1];
+  }
+  m.total = tot;
+  m.data = (double*)dalloc(tot * sizeof(double));
+  QTT_CUDA(cudaMemsetAsync(m.data, 0, tot * sizeof(double), st_));
+}
+
+void Engine::upload_tt_mps(DevMps& m, const TT& t, const std::vector<int>& bonds) {
+  // zero-padded copy of a host train into the static profile
+  std::vector<double> h(m.total, 0.0);
+  for (int n = 0; n < t.N(); ++n) {
+    if (t.r[n] > bonds[n] || t.r[n + 1] > bonds[n + 1])
+      throw std::runtime_error("EINVAL: host train exceeds the static bond profile");
+    for (int a = 0; a < t.r[n]; ++a)
+      for (int s = 0; s < 2; ++s)
+        for (int c = 0; c < t.r[n + 1]; ++c)
+          h[m.off[n] + ((size_t)a * 2 + s) * bonds[n + 1] + c] = t.at(n, a, s, c);
+  }
+  QTT_CUDA(cudaMemcpy(m.data, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+}
+
+void Engine::upload_op(DevOp& op, const TT& t) {
+  op.N = t.N();
+  op.w = t.r;
+  op.off_t.assign(op.N, 0);
+  op.off_ss.assign(op.N, 0);
+  size_t tot = 0;
+  for (int n = 0; n < op.N; ++n) {
+    const size_t sz = (size_t)t.r[n] * 4 * t.r[n + 1];
+    op.off_t[n] = tot;
+    tot += sz;
+    op.off_ss[n] = tot;
+    tot += sz;
+  }
+  std::vector<double> h(tot, 0.0);
+  for (int n = 0; n < op.N; ++n) {
+    const int wl = t.r[n], wr = t.r[n + 1];
+    for (int w = 0; w < wl; ++w)
+      for (int s = 0; s < 2; ++s)
+        for (int sp = 0; sp < 2; ++sp)
+          for (int w2 = 0; w2 < wr; ++w2) {
+            const double v = t.at(n, w, s * 2 + sp, w2);
+            h[op.off_t[n] + ((size_t)s * wr + w2) * 2 * wl + w * 2 + sp] = v;
+            h[op.off_ss[n] + ((size_t)(s * 2 + sp) * wl + w) * wr + w2] = v;
+          }
+  }
+  op.data = (double*)dalloc(tot * sizeof(double));
+  QTT_CUDA(cudaMemcpy(op.data, h.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
+}
+
+void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
+                  OutView C) {
+  TimeScope ts(timer_, TM_GEMM, st_);
+  gemm_f64(st_, M, N, K, outer, inner, alpha, A, B, beta, C, ws_, ws_elems_);
+}
+
+static MatView mv(const double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
+  MatView v;
+  v.p = p;
+  v.rs = rs;
+  v.cs = cs;
+  v.so = so;
+  v.si = si;
+  return v;
+}
+static OutView ov(double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
+  OutView v;
+  v.p = p;
+  v.rs = rs;
+  v.cs = cs;
+  v.so = so;
+  v.si = si;
+  return v;
+}
+
+void Engine::init() {
+  std::string why = validate(p_);
+  if (!why.empty()) throw std::runtime_error("EINVAL: " + why);
+  if (N_ > kMaxSites) throw std::runtime_error("EINVAL: too many sites");
+  if (p_.precision != 0) throw std::runtime_error("EINVAL: reduced-precision contraction forms are not built yet");
+  model_ = build_model(p_);
+  const int N = N_;
+  // static bond profiles
+  D_.assign(N + 1, 1);
+  for (int n = 1; n < N; ++n) D_[n] = (int)std::min<long long>({pow2(n), pow2(N - n), (long long)p_.chi_max});
+  ell_.assign(N + 1, 1);
+  rz_.assign(N + 1, 1);
+  if (exact_) {
+    nc_ = N / 2;
+    for (int n = nc_ + 1; n <= N; ++n) ell_[n] = (int)pow2(N - n);
+    for (int n = 0; n <= N; ++n) rz_[n] = (int)(n <= nc_ ? pow2(n) : pow2(N - n));
+  } else {
+    nc_ = N - 1;
+    const int lmax = p_.chi_max + (p_.oversample > 0 ? p_.oversample : 8);
+    for (int n = 1; n <= N; ++n) ell_[n] = (int)std::min<long long>((long long)lmax, pow2(N - n));
+    rz_[0] = 1;
+    for (int n = 0; n + 1 < N; ++n) rz_[n + 1] = std::min(2 * rz_[n], ell_[n + 1]);
+    rz_[N] = 1;
+  }
+  max_bond_ = 1;
+  for (int n = 0; n <= N; ++n) max_bond_ = std::max({max_bond_, D_[n], ell_[n], rz_[n]});
+
+  // state
+  TT f0 = tt_round(model_.f0, 1e-14, p_.chi_max);
+  alloc_mps(f_, D_);
+  alloc_mps(fs_, D_);
+  alloc_mps(g_, D_);
+  upload_tt_mps(f_, f0, D_);
+  if (!exact_) {
+    alloc_mps(mid_, rz_);
+    std::vector<int> ob(N + 1, 1);
+    for (int n = 1; n <= N; ++n) ob[n] = ell_[n];
+    alloc_mps(omega_, ob);
+  }
+  // operators
+  upload_op(op_lin_, model_.op_lin);
+  upload_op(had_, model_.had_phi);
+  {
+    TT id;
+    id.d = 4;
+    id.r.assign(N + 1, 1);
+    id.c.assign(N, std::vector<double>{1.0, 0.0, 0.0, 1.0});
+    upload_op(ident_, id);
+  }
+  for (int w = 0; w < 6; ++w) {
+    alloc_mps(wphi_[w], model_.wphi[w].r);
+    upload_tt_mps(wphi_[w], model_.wphi[w], model_.wphi[w].r);
+  }
+
+  // per-slot product bonds: slot 0, 3 identity, slot 1 linear, slot 2 mixing
+  auto wslot = [&](int slot, int n) -> size_t {
+    if (slot == 1) return (size_t)op_lin_.w[n];
+    if (slot == 2) return (size_t)(n <= kphi_ ? had_.w[n] : D_[n]);
+    return 1;
+  };
+  const int nlo = exact_ ? nc_ + 1 : 1;
+  size_t x1 = 1, x2 = 1, pp = 1, yy = 1, mb = 1, gg = 1;
+  for (int slot = 0; slot < 4; ++slot) {
+    Woff_[slot].assign(N + 1, 0);
+    size_t tot = 0;
+    for (int n = nlo; n <= N; ++n) {
+      Woff_[slot][n] = tot;
+      tot += (size_t)wslot(slot, n) * D_[n] * ell_[n];
+    }
+    Wslot_[slot] = (double*)dalloc(tot * sizeof(double));
+    size_t cmax = 1, tmax = 1;
+    for (int n = 0; n < N; ++n) {
+      const bool zipped = exact_ ? (n <= nc_) : true;
+      if (zipped) {
+        cmax = std::max(cmax, (size_t)rz_[n] * wslot(slot, n) * D_[n]);
+        tmax = std::max(tmax, (size_t)2 * rz_[n] * wslot(slot, n + 1) * D_[n + 1]);
+        pp = std::max(pp, (size_t)rz_[n] * wslot(slot, n) * 2 * D_[n + 1]);
+      }
+      if (n >= nlo) {
+        x1 = std::max(x1, (size_t)wslot(slot, n + 1) * D_[n + 1] * 2 * ell_[n]);
+        x2 = std::max(x2, (size_t)wslot(slot, n + 1) * 2 * D_[n] * 2 * ell_[n]);
+      }
+    }
+    C_[slot] = (double*)dalloc(std::max(cmax, tmax) * sizeof(double));
+    T_[slot] = (double*)dalloc(std::max(cmax, tmax) * sizeof(double));
+  }
+  for (int n = 0; n < N; ++n) {
+    yy = std::max(yy, (size_t)2 * rz_[n] * ell_[n + 1]);
+    mb = std::max(mb, (size_t)2 * rz_[n] * std::max(D_[n + 1], rz_[n + 1]));
+    gg = std::max(gg, (size_t)rz_[n] * rz_[n]);
+  }
+  P_ = (double*)dalloc(pp * sizeof(double));
+  X1_ = (double*)dalloc(x1 * sizeof(double));
+  X2_ = (double*)dalloc(x2 * sizeof(double));
+  Y_ = (double*)dalloc(yy * sizeof(double));
+  for (int i = 0; i < 3; ++i) Mb_[i] = (double*)dalloc(mb * sizeof(double));
+  G_ = (double*)dalloc(gg * sizeof(double));
+  U_ = (double*)dalloc(gg * sizeof(double));
+  Us_ = (double*)dalloc((size_t)max_bond_ * max_bond_ * sizeof(double));
+  lam_ = (double*)dalloc((size_t)max_bond_ * sizeof(double));
+  const size_t rmax = (size_t)max_bond_;
+  eigwork_ = (double*)dalloc((3 * rmax * rmax + 3 * rmax) * sizeof(double));
+  qrwork_ = (double*)dalloc((2 * (2 * rmax) * rmax + rmax) * sizeof(double));
+  ws_elems_ = (size_t)8 << 20;
+  ws_ = (double*)dalloc(ws_elems_ * sizeof(double));
+  for (int i = 0; i < 2; ++i) {
+    v_[i] = (double*)dalloc((size_t)2 * D_[kphi_] * sizeof(double));
+    hf_[i] = (double*)dalloc((size_t)4 * D_[kphi_ + 1] * sizeof(double));
+  }
+  envw_ = (double*)dalloc((size_t)16 * max_bond_ * sizeof(double) + 64);
+  envout_ = (double*)dalloc((size_t)(8 * max_bond_ + (size_t)max_bond_ * max_bond_ + 64) * sizeof(double));
+  disc_ = (double*)dalloc(sizeof(double) * 4);
+  obsA_ = (double*)dalloc((size_t)2 * max_bond_ * max_bond_ * sizeof(double) + 64);
+  obsB_ = (double*)dalloc((size_t)2 * max_bond_ * max_bond_ * sizeof(double) + 64);
+  obsX_ = (double*)dalloc((size_t)2 * max_bond_ * max_bond_ * sizeof(double) + 64);
+  status_ = (int*)dalloc(sizeof(int) * 4);
+  ranks_ = (int*)dalloc(sizeof(int) * (N + 1));
+  QTT_CUDA(cudaMemsetAsync(disc_, 0, sizeof(double) * 4, st_));
+  QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int) * 4, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+}
+
+void Engine::cond_means(const DevMps& f, double* v) {
+  // v[a][b] = h1 h2 sum over phi indices of phi_a f(..)[b] at the phi/x cut (Eq. 2)
+  TimeScope ts(timer_, TM_OTHER, st_);
+  const Chain fc = f.chain();
+  for (int a = 0; a < 2; ++a)
+    left_weight_env(st_, fc, wphi_[1 + a].chain(), kphi_, max_bond_, v + (size_t)a * D_[kphi_], D_[kphi_], envw_);
+}
+
+void Engine::make_hfirst(const DevMps& f, double* v, double* hf) {
+  // first x core of diag(<Phi_a>(x)): hf[a][s][b'] = sum_b v[a][b] A_kphi[b][s][b']
+  const int bl = D_[kphi_], br = D_[kphi_ + 1];
+  gemm(2, 2 * br, bl, 1, 1, 1.0, mv(v, bl, 1), mv(f.core(kphi_), 2 * br, 1), 0.0, ov(hf, 2 * br, 1));
+}
+
+void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr) {
+  const int bl = t.f->b[n], br = t.f->b[n + 1];
+  const int wl = t.w(n), wr = t.w(n + 1);
+  const double* A = t.f->core(n);
+  // X1[(w',a')][s][l] = sum_l' W_{n+1}[(w',a')][l'] Om[l][s][l']
+  gemm(wr * br, Ll, Lr, 1, 2, 1.0, mv(Wn1, Lr, 1), mv(Om, 1, 2LL * Lr, 0, Lr), 0.0, ov(X1_, 2LL * Ll, 1, 0, Ll));
+  if (!t.diag(n)) {
+    // X2[w'][(a,s')][(s,l)] = sum_a' A[(a,s')][a'] X1[(w',a')][(s,l)]
+    gemm(2 * bl, 2 * Ll, br, wr, 1, 1.0, mv(A, br, 1), mv(X1_, 2LL * Ll, 1, (long long)br * 2 * Ll), 0.0,
+         ov(X2_, 2LL * Ll, 1, 4LL * bl * Ll));
+    // W_n[(w,a)][l] = sum_{s,s',w'} W[w][s*2+s'][w'] X2[w'][(a,s')][(s,l)]
+    const double* Wss = t.op->Wss(n);
+    for (int ss = 0; ss < 4; ++ss) {
+      const int s = ss >> 1, sp = ss & 1;
+      gemm(wl, Ll, wr, bl, 1, 1.0, mv(Wss + (size_t)ss * wl * wr, wr, 1),
+           mv(X2_ + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll), ss == 0 ? 0.0 : 1.0,
+           ov(Wn, (long long)bl * Ll, 1, Ll));
+    }
+  } else {
+    const double* H = t.H(n);
+    // X2[h'][a][s][l] = sum_a' A[a][s][a'] X1[(h',a')][s][l]
+    gemm(bl, Ll, br, wr, 2, 1.0, mv(A, 2LL * br, 1, 0, br), mv(X1_, 2LL * Ll, 1, (long long)br * 2 * Ll, Ll), 0.0,
+         ov(X2_, 2LL * Ll, 1, 2LL * bl * Ll, Ll));
+    // W_n[(h,a)][l] = sum_s sum_h' H[h][s][h'] X2[h'][a][s][l]
+    for (int s = 0; s < 2; ++s)
+      gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1),
+           mv(X2_ + (size_t)s * Ll, 2LL * bl * Ll, 1, 2LL * Ll), s == 0 ? 0.0 : 1.0,
+           ov(Wn, (long long)bl * Ll, 1, Ll));
+  }
+}
+
+void Engine::zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha) {
+  const int bl = t.f->b[n], br = t.f->b[n + 1];
+  const int wl = t.w(n), wr = t.w(n + 1);
+  const double* A = t.f->core(n);
+  // P[(rho,w)][(s',a')] = sum_a C[(rho,w)][a] A[a][(s',a')]
+  gemm(r * wl, 2 * br, bl, 1, 1, 1.0, mv(C, bl, 1), mv(A, 2LL * br, 1), 0.0, ov(P_, 2LL * br, 1));
+  if (!t.diag(n)) {
+    // T[(rho,s)][(w',a')] = sum_{(w,s')} Wt[s][w'][(w,s')] P[rho][(w,s')][a']
+    const double* Wt = t.op->Wt(n);
+    gemm(wr, br, 2 * wl, r, 2, alpha, mv(Wt, 2LL * wl, 1, 0, (long long)wr * 2 * wl),
+         mv(P_, br, 1, 2LL * wl * br, 0), 0.0, ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
+  } else {
+    const double* H = t.H(n);
+    // T[(rho,s)][(h',a')] = sum_h H[h][s][h'] P[(rho,h)][(s,a')]
+    gemm(wr, br, wl, r, 2, alpha, mv(H, 1, 2LL * wr, 0, wr), mv(P_, 2LL * br, 1, (long long)wl * 2 * br, br), 0.0,
+         ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
+  }
+}
+
+Term Engine::term_dense(int slot, const DevOp* op, const DevMps* f, double scale) const {
+  Term t;
+  t.f = f;
+  t.kind = 0;
+  t.op = op;
+  t.kphi = kphi_;
+  t.slot = slot;
+  t.scale = scale;
+  return t;
+}
+
+Term Engine::term_mix(const DevMps* f, const double* hf, double scale) const {
+  Term t;
+  t.f = f;
+  t.kind = 1;
+  t.op = &had_;
+  t.hfirst = hf;
+  t.kphi = kphi_;
+  t.slot = 2;
+  t.scale = scale;
+  return t;
+}
+
+void Engine::run_stage(Term* terms, int nt, DevMps& out) {
+  if (exact_) {
+    run_stage_exact(terms, nt, out);
+    return;
+  }
+  const int N = N_;
+  ++stage_counter_;
+  {
+    TimeScope ts(timer_, TM_OTHER, st_);
+    for (int n = 1; n < N; ++n) {
+      const double sigma = 1.0 / std::sqrt(2.0 * (double)ell_[n + 1]);
+      fill_gaussian(st_, omega_.core(n), omega_.core_elems(n), sigma, p_.seed,
+                    stage_counter_ * (unsigned long long)kMaxSites + (unsigned long long)n);
+    }
+  }
+  // 1. right-to-left sketch: W_n = (right part of the term) x (right part of the random MPS)
+  for (int i = 0; i < nt; ++i) {
+    const Term& t = terms[i];
+    double* W = Wslot_[t.slot];
+    fill_value(st_, W + Woff_[t.slot][N], 1, 1.0);
+    for (int n = N - 1; n >= 1; --n)
+      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], omega_.core(n), ell_[n], ell_[n + 1]);
+  }
+  // 2. left-to-right orthogonalisation of the sketched site tensors
+  for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
+  int r = 1;
+  for (int n = 0; n < N; ++n) {
+    for (int i = 0; i < nt; ++i)
+      zip_site(terms[i], n, r, C_[terms[i].slot], T_[terms[i].slot], n == 0 ? terms[i].scale : 1.0);
+    if (n == N - 1) {  // all terms close with bond 1: the last core is their sum
+      for (int i = 0; i < nt; ++i) {
+        const Term& t = terms[i];
+        gemm(2 * r, 1, (int)t.B(N), 1, 1, 1.0, mv(T_[t.slot], t.B(N), 1), mv(Wslot_[t.slot] + Woff_[t.slot][N], 1, 1),
+             i == 0 ? 0.0 : 1.0, ov(mid_.core(n), 1, 1));
+      }
+      break;
+    }
+    const int rn = rz_[n + 1];
+    if (rn == 2 * r) {  // bond still below the sketch size: keep everything
+      {
+        TimeScope ts(timer_, TM_OTHER, st_);
+        fill_identity_left(st_, mid_.core(n), r);
+      }
+      for (int i = 0; i < nt; ++i) std::swap(C_[terms[i].slot], T_[terms[i].slot]);
+    } else {
+      const int L = ell_[n + 1];
+      for (int i = 0; i < nt; ++i) {
+        const Term& t = terms[i];
+        gemm(2 * r, L, (int)t.B(n + 1), 1, 1, 1.0, mv(T_[t.slot], t.B(n + 1), 1),
+             mv(Wslot_[t.slot] + Woff_[t.slot][n + 1], L, 1), i == 0 ? 0.0 : 1.0, ov(Y_, L, 1));
+      }
+      {
+        TimeScope ts(timer_, TM_QR, st_);
+        qr_thin(st_, 2 * r, rn, Y_, mid_.core(n), qrwork_, prec_bits_, status_);
+      }
+      for (int i = 0; i < nt; ++i) {
+        const Term& t = terms[i];
+        gemm(rn, (int)t.B(n + 1), 2 * r, 1, 1, 1.0, mv(mid_.core(n), 1, rn), mv(T_[t.slot], t.B(n + 1), 1), 0.0,
+             ov(C_[t.slot], t.B(n + 1), 1));
+      }
+    }
+    r = rn;
+  }
+  // 3. right-to-left SVD truncation to chi (FP64 Gram + eigensolve per bond)
+  const double floor_rel = 1e-24;
+  int cur = 0;
+  fill_value(st_, Mb_[0], 1, 1.0);
+  for (int n = N - 1; n >= 1; --n) {
+    const int rl = rz_[n], rr = rz_[n + 1], Dn = D_[n], Dn1 = D_[n + 1];
+    const int mi = (cur + 1) % 3;
+    double* M = Mb_[mi];
+    gemm(2 * rl, Dn1, rr, 1, 1, 1.0, mv(mid_.core(n), rr, 1), mv(Mb_[cur], Dn1, 1), 0.0, ov(M, Dn1, 1));
+    if (Dn == 2 * Dn1) {  // structural bond: nothing to truncate, identity core
+      TimeScope ts(timer_, TM_OTHER, st_);
+      fill_identity_right(st_, out.core(n), Dn1);
+      cur = mi;
+    } else {
+      gemm(rl, rl, 2 * Dn1, 1, 1, 1.0, mv(M, 2LL * Dn1, 1), mv(M, 1, 2LL * Dn1), 0.0, ov(G_, rl, 1));
+      const int ku = std::min(rl, Dn);
+      {
+        TimeScope ts(timer_, TM_EIG, st_);
+        eig_sym(st_, rl, ku, G_, U_, lam_, eigwork_, 64, status_);
+      }
+      const int li = (cur + 2) % 3;
+      {
+        TimeScope ts(timer_, TM_OTHER, st_);
+        sweep_scales(st_, rl, Dn, ku, U_, lam_, p_.svd_rel_tol, floor_rel, Us_, Mb_[li], disc_, ranks_ + n);
+      }
+      gemm(Dn, 2 * Dn1, rl, 1, 1, 1.0, mv(Us_, 1, Dn), mv(M, 2LL * Dn1, 1), 0.0, ov(out.core(n), 2LL * Dn1, 1));
+      cur = li;
+    }
+  }
+  gemm(2, D_[1], rz_[1], 1, 1, 1.0, mv(mid_.core(0), rz_[1], 1), mv(Mb_[cur], D_[1], 1), 0.0,
+       ov(out.core(0), D_[1], 1));
+}
+
+void Engine::run_stage_exact(Term* terms, int nt, DevMps& out) {
+  const int N = N_, nc = nc_;
+  {
+    TimeScope ts(timer_, TM_OTHER, st_);
+    for (int n = nc + 1; n < N; ++n) fill_identity_right(st_, out.core(n), ell_[n + 1]);
+  }
+  for (int i = 0; i < nt; ++i) {
+    const Term& t = terms[i];
+    double* W = Wslot_[t.slot];
+    fill_value(st_, W + Woff_[t.slot][N], 1, 1.0);
+    for (int n = N - 1; n > nc; --n)
+      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], out.core(n), ell_[n], ell_[n + 1]);
+  }
+  for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
+  int r = 1;
+  for (int n = 0; n <= nc; ++n) {
+    for (int i = 0; i < nt; ++i)
+      zip_site(terms[i], n, r, C_[terms[i].slot], T_[terms[i].slot], n == 0 ? terms[i].scale : 1.0);
+    if (n == nc) {
+      const int L = ell_[nc + 1];
+      for (int i = 0; i < nt; ++i) {
+        const Term& t = terms[i];
+        gemm(2 * r, L, (int)t.B(n + 1), 1, 1, 1.0, mv(T_[t.slot], t.B(n + 1), 1),
+             mv(Wslot_[t.slot] + Woff_[t.slot][n + 1], L, 1), i == 0 ? 0.0 : 1.0, ov(out.core(n), L, 1));
+      }
+      break;
+    }
+    {
+      TimeScope ts(timer_, TM_OTHER, st_);
+      fill_identity_left(st_, out.core(n), r);
+    }
+    for (int i = 0; i < nt; ++i) std::swap(C_[terms[i].slot], T_[terms[i].slot]);
+    r *= 2;
+  }
+}
+
+void Engine::step(int nsteps) {
+  for (int k = 0; k < nsteps; ++k) {
+    QTT_CUDA(cudaMemsetAsync(disc_, 0, sizeof(double), st_));
+    if (p_.rk_variant == 0) {
+      // Heun: f* = f + dt L(f);  f_{n+1} = (f + f* + dt L(f*)) / 2
+      cond_means(f_, v_[0]);
+      make_hfirst(f_, v_[0], hf_[0]);
+      Term a[2] = {term_dense(1, &op_lin_, &f_, 1.0), term_mix(&f_, hf_[0], 1.0)};
+      run_stage(a, 2, fs_);
+      cond_means(fs_, v_[1]);
+      make_hfirst(fs_, v_[1], hf_[1]);
+      Term b[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &fs_, 0.5), term_mix(&fs_, hf_[1], 0.5)};
+      run_stage(b, 3, g_);
+    } else {
+      // midpoint: f_h = f + dt/2 L(f);  f_{n+1} = f + dt L(f_h)
+      cond_means(f_, v_[0]);
+      make_hfirst(f_, v_[0], hf_[0]);
+      Term a[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &f_, 0.5), term_mix(&f_, hf_[0], 0.5)};
+      run_stage(a, 3, fs_);
+      cond_means(fs_, v_[1]);
+      make_hfirst(fs_, v_[1], hf_[1]);
+      Term b[4] = {term_dense(0, &ident_, &f_, 1.0), term_dense(1, &op_lin_, &fs_, 1.0),
+                   term_dense(3, &ident_, &fs_, -1.0), term_mix(&fs_, hf_[1], 1.0)};
+      run_stage(b, 4, g_);
+    }
+    std::swap(f_, g_);
+    time_ += p_.dt;
+    ++steps_;
+  }
+  QTT_CUDA(cudaGetLastError());
+  if (timer_->on) {
+    QTT_CUDA(cudaStreamSynchronize(st_));
+    timer_->flush();
+  }
+}
+
+int Engine::check_status(std::string& msg) {
+  check_finite(st_, f_.data, f_.total, status_ + 1);
+  int h[2] = {0, 0};
+  double dis = 0;
+  QTT_CUDA(cudaMemcpyAsync(h, status_, sizeof(h), cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaMemcpyAsync(&dis, disc_, sizeof(double), cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+  QTT_CUDA(cudaGetLastError());
+  discarded_last_ = dis;
+  if (h[1]) {
+    msg = "non-finite value in the state after step " + std::to_string(steps_);
+    return 6;  // QTT_ENAN
+  }
+  if (h[0] & 2) {
+    msg = "eigen-decomposition hit its QL sweep cap";
+    QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), st_));
+    return 4;  // QTT_ENOCONV
+  }
+  if (h[0]) {
+    msg = "QR / eigensolver reported an invalid factorisation";
+    QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), st_));
+    return 4;
+  }
+  return 0;
+}
+
+void Engine::xgram(const DevMps& f, double* E) {
+  // E[b][b'] = sum over the x indices of F(x)[b] F(x)[b'] at the phi/x cut
+  fill_value(st_, obsA_, 1, 1.0);
+  double* cur = obsA_;
+  double* nxt = obsB_;
+  for (int n = N_ - 1; n >= kphi_; --n) {
+    const int bl = f.b[n], br = f.b[n + 1];
+    gemm(2 * bl, br, br, 1, 1, 1.0, mv(f.core(n), br, 1), mv(cur, br, 1), 0.0, ov(obsX_, br, 1));
+    gemm(bl, bl, 2 * br, 1, 1, 1.0, mv(obsX_, 2LL * br, 1), mv(f.core(n), 1, 2LL * br), 0.0, ov(nxt, bl, 1));
+    std::swap(cur, nxt);
+  }
+  QTT_CUDA(cudaMemcpyAsync(E, cur, sizeof(double) * f.b[kphi_] * f.b[kphi_], cudaMemcpyDeviceToDevice, st_));
+}
+
+void Engine::scalars(double out[12]) {
+  const int b = D_[kphi_];
+  double* V = envout_;              // 6 x b weight environments
+  double* u = V + 6 * (size_t)b;    // b
+  double* E = u + b;                // b x b
+  double* res = E + (size_t)b * b;  // 6 + b + 1
+  const Chain fc = f_.chain();
+  for (int w = 0; w < 6; ++w) left_weight_env(st_, fc, wphi_[w].chain(), kphi_, max_bond_, V + (size_t)w * b, b, envw_);
+  right_ones_env(st_, fc, kphi_, max_bond_, u, envw_);
+  xgram(f_, E);
+  gemm(6, 1, b, 1, 1, 1.0, mv(V, b, 1), mv(u, 1, 1), 0.0, ov(res, 1, 1));                 // <w> sums
+  gemm(1, b, b, 1, 1, 1.0, mv(V + b, b, 1), mv(E, b, 1), 0.0, ov(res + 6, b, 1));           // v1^T E
+  gemm(1, 1, b, 1, 1, 1.0, mv(res + 6, b, 1), mv(V + 2 * (size_t)b, 1, 1), 0.0, ov(res + 6 + b, 1, 1));
+  double h[6];
+  double m12 = 0;
+  QTT_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaMemcpyAsync(&m12, res + 6 + b, sizeof(double), cudaMemcpyDeviceToHost, st_));
+  std::string msg;
+  check_status(msg);
+  const double Mx = std::ldexp(1.0, p_.bits[2] + p_.bits[3] + p_.bits[4]);
+  for (double& x : h) x /= Mx;
+  m12 /= Mx;
+  out[0] = time_;
+  out[1] = h[0];
+  out[2] = h[1];
+  out[3] = h[2];
+  out[4] = h[3];
+  out[5] = h[4];
+  out[6] = h[5];
+  out[7] = m12 - h[1] * h[2];  // R12
+  out[8] = h[5] - m12;         // Y12
+  out[9] = h[0] - h[1] - h[2];  // mean of <1 - phi1 - phi2>
+  out[10] = discarded_last_;
+  out[11] = (double)steps_;
+}
+
+void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out) {
+  // rows = multi-index of the processed sites, columns = open bond; out gets head_rows * 2^(N - n0) values
+  size_t rows = head_rows;
+  for (int n = n0; n < N_; ++n) rows *= 2;
+  double* a = nullptr;
+  double* b = nullptr;
+  QTT_CUDA(cudaMalloc(&a, sizeof(double) * (rows * 1 + 16) * 2));
+  QTT_CUDA(cudaMalloc(&b, sizeof(double) * (rows * 1 + 16) * 2));
+  // buffer bound: rows_so_far * bond <= head_rows * 2^(N-n0) when bonds follow the structural profile
+  size_t R = head_rows;
+  int bond = f.b[n0];
+  QTT_CUDA(cudaMemcpyAsync(a, head, sizeof(double) * R * bond, cudaMemcpyDeviceToDevice, st_));
+  for (int n = n0; n < N_; ++n) {
+    const int br = f.b[n + 1];
+    gemm((int)R, 2 * br, bond, 1, 1, 1.0, mv(a, bond, 1), mv(f.core(n), 2LL * br, 1), 0.0, ov(b, 2LL * br, 1));
+    std::swap(a, b);
+    R *= 2;
+    bond = br;
+  }
+  QTT_CUDA(cudaMemcpyAsync(out, a, sizeof(double) * R, cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+  cudaFree(a);
+  cudaFree(b);
+}
+
+void Engine::dense(double* out) {
+  fill_value(st_, obsA_, 1, 1.0);
+  chain_dense(f_, 0, obsA_, 1, out);
+}
+
+void Engine::means(double* out) {
+  const int b = D_[kphi_];
+  const size_t Mx = (size_t)1 << (p_.bits[2] + p_.bits[3] + p_.bits[4]);
+  const Chain fc = f_.chain();
+  for (int w = 0; w < 3; ++w) {
+    left_weight_env(st_, fc, wphi_[w].chain(), kphi_, max_bond_, envout_, b, envw_);
+    chain_dense(f_, kphi_, envout_, 1, out + w * Mx);
+  }
+}
+
+void Engine::points(const std::vector<unsigned char>& bits, int npts, double* out) {
+  unsigned char* db = nullptr;
+  double *dout = nullptr, *work = nullptr;
+  QTT_CUDA(cudaMalloc(&db, bits.size() + 1));
+  QTT_CUDA(cudaMalloc(&dout, sizeof(double) * npts));
+  QTT_CUDA(cudaMalloc(&work, sizeof(double) * (size_t)npts * 2 * max_bond_));
+  QTT_CUDA(cudaMemcpyAsync(db, bits.data(), bits.size(), cudaMemcpyHostToDevice, st_));
+  eval_points(st_, f_.chain(), npts, db, max_bond_, dout, work);
+  QTT_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * npts, cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+  cudaFree(db);
+  cudaFree(dout);
+  cudaFree(work);
+}
+
+double Engine::overlap(const Engine& o) {
+  // <this|o> by left environments: E_{n+1} = sum_s A_s^T E_n B_s
+  if (o.N_ != N_) throw std::runtime_error("EINVAL: states have different numbers of sites");
+  for (int d = 0; d < 5; ++d)
+    if (o.p_.bits[d] != p_.bits[d]) throw std::runtime_error("EINVAL: states live on different grids");
+  QTT_CUDA(cudaStreamSynchronize(o.st_));
+  const DevMps& A = f_;
+  const DevMps& B = o.f_;
+  size_t need = 1;
+  for (int n = 0; n < N_; ++n) {
+    const size_t ma = (size_t)std::max(A.b[n], A.b[n + 1]), mb = (size_t)std::max(B.b[n], B.b[n + 1]);
+    need = std::max(need, ma * 2 * mb);
+  }
+  double *e0 = nullptr, *e1 = nullptr, *x = nullptr;
+  QTT_CUDA(cudaMalloc(&e0, need * sizeof(double)));
+  QTT_CUDA(cudaMalloc(&e1, need * sizeof(double)));
+  QTT_CUDA(cudaMalloc(&x, need * sizeof(double)));
+  fill_value(st_, e0, 1, 1.0);
+  for (int n = 0; n < N_; ++n) {
+    const int ba = A.b[n], bb = B.b[n], ba2 = A.b[n + 1], bb2 = B.b[n + 1];
+    gemm(ba, 2 * bb2, bb, 1, 1, 1.0, mv(e0, bb, 1), mv(B.core(n), 2LL * bb2, 1), 0.0, ov(x, 2LL * bb2, 1));
+    gemm(ba2, bb2, 2 * ba, 1, 1, 1.0, mv(A.core(n), 1, ba2), mv(x, bb2, 1), 0.0, ov(e1, bb2, 1));
+    std::swap(e0, e1);
+  }
+  double r = 0;
+  QTT_CUDA(cudaMemcpyAsync(&r, e0, sizeof(double), cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+  cudaFree(e0);
+  cudaFree(e1);
+  cudaFree(x);
+  return r;
+}
+
+std::vector<double> Engine::download_state() const {
+  std::vector<double> h(f_.total);
+  QTT_CUDA(cudaMemcpyAsync(h.data(), f_.data, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+  return h;
+}
+
+void Engine::upload_state(const std::vector<double>& cores) {
+  if (cores.size() != f_.total) throw std::runtime_error("EINVAL: checkpoint size does not match the bond profile");
+  QTT_CUDA(cudaMemcpyAsync(f_.data, cores.data(), cores.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
+}
+
+std::vector<double> Engine::timings() const {
+  std::vector<double> t;
+  for (int c = 0; c < 4; ++c) {
+    t.push_back(timer_->launches[c]);
+    t.push_back(timer_->ms[c]);
+  }
+  return t;
+}
+
+void Engine::set_time(double t, long long s) {
+  time_ = t;
+  steps_ = s;
+}
+
+}  // namespace qtt

@@ -1,0 +1,134 @@
+// Device engine: storage of the PDF and operators on the GPU and the RK2
+// stage algorithm (see engine.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "model.hpp"
+
+namespace qtt {
+
+// MPS with a static bond profile b[0..N], cores [b[n]][2][b[n+1]] in one allocation.
+struct DevMps {
+  int N = 0;
+  std::vector<int> b;
+  std::vector<size_t> off;
+  size_t total = 0;
+  double* data = nullptr;
+  double* core(int n) const { return data + off[n]; }
+  size_t core_elems(int n) const { return (size_t)b[n] * 2 * b[n + 1]; }
+  Chain chain() const;
+};
+
+// Dense MPO on the device in the two layouts the contractions read:
+// Wt[s][w'][w*2+s'] and Wss[s*2+s'][w][w'] (both = W[w][s*2+s'][w']).
+struct DevOp {
+  int N = 0;
+  std::vector<int> w;
+  std::vector<size_t> off_t, off_ss;
+  double* data = nullptr;
+  const double* Wt(int n) const { return data + off_t[n]; }
+  const double* Wss(int n) const { return data + off_ss[n]; }
+};
+
+// One summand c * Op * f of a stage.  kind 0: dense MPO over all sites;
+// kind 1: mixing Hadamard term -- dense composition-space MPO on the phi
+// sites, then the diagonal operator diag(<Phi_a>(x)) whose cores are f's own
+// x cores (the first one mixed with the conditional-mean vectors).
+struct Term {
+  const DevMps* f = nullptr;
+  int kind = 0;
+  const DevOp* op = nullptr;
+  const double* hfirst = nullptr;
+  int kphi = 0;
+  int slot = 0;  // scratch slot: 0 / 3 identity, 1 linear, 2 mixing
+  double scale = 1.0;
+  int w(int n) const { return kind == 0 ? op->w[n] : (n <= kphi ? op->w[n] : f->b[n]); }
+  bool diag(int n) const { return kind == 1 && n >= kphi; }
+  const double* H(int n) const { return n == kphi ? hfirst : f->core(n); }
+  long long B(int n) const { return (long long)w(n) * f->b[n]; }
+};
+
+struct KernelTimer;
+
+class Engine {
+ public:
+  explicit Engine(const Params& p, cudaStream_t stream);
+  ~Engine();
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
+
+  void init();                 // uploads the model; throws std::runtime_error
+  void step(int nsteps);       // RK2 steps
+  int check_status(std::string& msg);  // syncs; returns a qtt_status value
+  // observables (host outputs)
+  void scalars(double out[12]);
+  std::vector<int> bonds() const { return f_.b; }
+  void dense(double* out);                     // 2^N values
+  void means(double* out);                     // 3 * 2^Kx values
+  void points(const std::vector<unsigned char>& bits, int npts, double* out);
+  double overlap(const Engine& other);         // <this|other>
+  double norm2() { return overlap(*this); }
+  std::vector<double> download_state() const;
+  void upload_state(const std::vector<double>& cores);
+  std::vector<double> timings() const;
+
+  const Params& params() const { return p_; }
+  int N() const { return N_; }
+  double time() const { return time_; }
+  long long steps() const { return steps_; }
+  double discarded_last() const { return discarded_last_; }
+  cudaStream_t stream() const { return st_; }
+  void set_time(double t, long long s);
+
+ private:
+  void* dalloc(size_t bytes);
+  void alloc_mps(DevMps& m, const std::vector<int>& bonds);
+  void upload_op(DevOp& op, const TT& t);
+  void upload_tt_mps(DevMps& m, const TT& t, const std::vector<int>& bonds);
+  void gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C);
+  void cond_means(const DevMps& f, double* v);
+  void make_hfirst(const DevMps& f, double* v, double* hf);
+  void sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr);
+  void zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha);
+  void run_stage(Term* terms, int nterms, DevMps& out);
+  void run_stage_exact(Term* terms, int nterms, DevMps& out);
+  void xgram(const DevMps& f, double* E);
+  Term term_dense(int slot, const DevOp* op, const DevMps* f, double scale) const;
+  Term term_mix(const DevMps* f, const double* hf, double scale) const;
+  void chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out);
+
+  Params p_;
+  Model model_;
+  cudaStream_t st_ = nullptr;
+  int N_ = 0, kphi_ = 0, nc_ = 0;
+  int prec_bits_ = 64;
+  bool exact_ = false;
+  std::vector<void*> allocs_;
+  std::vector<int> D_, ell_, rz_;
+  DevMps f_, fs_, g_, mid_, omega_, wphi_[6];
+  DevOp op_lin_, had_, ident_;
+  // scratch
+  double *Wslot_[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<size_t> Woff_[4];
+  double *C_[4] = {nullptr, nullptr, nullptr, nullptr}, *T_[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *P_ = nullptr, *X1_ = nullptr, *X2_ = nullptr, *Y_ = nullptr;
+  double *Mb_[3] = {nullptr, nullptr, nullptr}, *G_ = nullptr, *U_ = nullptr, *lam_ = nullptr, *Us_ = nullptr;
+  double *v_[2] = {nullptr, nullptr}, *hf_[2] = {nullptr, nullptr};
+  double *envw_ = nullptr, *envout_ = nullptr, *ws_ = nullptr, *qrwork_ = nullptr, *eigwork_ = nullptr;
+  double *disc_ = nullptr, *obsA_ = nullptr, *obsB_ = nullptr, *obsX_ = nullptr;
+  int *status_ = nullptr, *ranks_ = nullptr;
+  size_t ws_elems_ = 0;
+  int max_bond_ = 1;
+  unsigned long long stage_counter_ = 0;
+  double time_ = 0.0;
+  long long steps_ = 0;
+  double discarded_last_ = 0.0;
+  KernelTimer* timer_ = nullptr;
+};
+
+}  // namespace qtt

@@ -1,0 +1,49 @@
+// Host-side tensor-train toolkit used once at initialisation: encoding of
+// 1-D vectors as quantics tensor trains (TT-SVD), Kronecker products and sums
+// of trains, operator (MPO) algebra and rounding.  All FP64; sizes are small
+// (bonds of the analytic fields and operators are O(10)).
+//
+// Paper: "Matrix product state algorithm" -- vectors are MPSs and matrices
+// are MPOs; "Computational complexity" -- initial states are prepared once
+// at O(chi^3 d log M) cost.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace qtt {
+
+// A train of N cores; core n has shape [r[n]][d][r[n+1]] (row-major).
+// d = 2 for vectors (MPS).  d = 4 for operators (MPO) with the physical index
+// i = s_out * 2 + s_in.
+struct TT {
+  int d = 2;
+  std::vector<int> r;                   // N + 1 bond dimensions
+  std::vector<std::vector<double>> c;   // N cores
+  int N() const { return (int)c.size(); }
+  double& at(int n, int a, int i, int b) { return c[n][((size_t)a * d + i) * r[n + 1] + b]; }
+  double at(int n, int a, int i, int b) const { return c[n][((size_t)a * d + i) * r[n + 1] + b]; }
+};
+
+// Dense helpers (row-major).
+void svd_jacobi(int m, int n, const double* A, std::vector<double>& U, std::vector<double>& S,
+                std::vector<double>& Vt);  // thin SVD, k = min(m, n), S descending
+void qr_householder(int m, int n, const double* A, std::vector<double>& Q,
+                    std::vector<double>& R);  // thin QR, Q m x k, R k x n, k = min(m, n)
+
+TT tt_from_vector(const std::vector<double>& v, int K, double rel_tol);  // MSB-first TT-SVD
+TT tt_constant(int K, double value);
+TT tt_kron(const TT& a, const TT& b);
+TT tt_add(const TT& a, const TT& b);
+TT tt_stack_right(const TT& a, const TT& b);  // direct sum with an open right bond ra + rb
+void tt_scale(TT& a, double s);
+TT tt_round(const TT& a, double rel_tol, int max_rank);  // drop sigma < rel_tol * sigma_1 per bond
+TT tt_hadamard(const TT& a, const TT& b);
+TT mpo_identity(int K);
+TT mpo_diag(const TT& v);
+TT mpo_mul(const TT& A, const TT& B);  // operator product A * B
+std::vector<double> tt_dense(const TT& a);  // all d^N entries, site 0 most significant
+double tt_norm(const TT& a);
+
+}  // namespace qtt

@@ -1,0 +1,86 @@
+// Device kernels of the QTT Fokker-Planck path (launch wrappers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace qtt {
+
+constexpr int kMaxSites = 64;
+
+// Operand view for the strided batched GEMM: element (i, j) of batch
+// (bo, bi) lives at p[bo * so + bi * si + i * rs + j * cs].
+struct MatView {
+  const double* p = nullptr;
+  long long rs = 0, cs = 0, so = 0, si = 0;
+};
+struct OutView {
+  double* p = nullptr;
+  long long rs = 0, cs = 0, so = 0, si = 0;
+};
+
+// A chain of MPS cores passed by value to kernels: core n is
+// [bond[n]][2][bond[n+1]] row-major.
+struct Chain {
+  const double* core[kMaxSites];
+  int bond[kMaxSites + 1];
+  int n;
+};
+
+// C[b] = alpha * A[b] * B[b] + beta * C[b] for b in [0, outer * inner).
+// M x K times K x N.  A split of K accumulates partial products in `ws`
+// (reduced in a fixed order, so results are deterministic); ws must hold
+// split * outer * inner * M * N doubles or the product runs unsplit.
+void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double alpha, MatView A,
+              MatView B, double beta, OutView C, double* ws, size_t ws_elems);
+int gemm_split_k(int M, int N, int K, int batch);
+
+// Thin Householder QR of an m x n row-major matrix (m >= n): Q (m x n,
+// row-major) overwrites Qout.  Computed in float (prec_bits 32) or double;
+// work must hold 2 * m * n + n elements of that type.  *status != 0 on failure.
+void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void* work, int prec_bits,
+             int* status);
+
+// Symmetric eigen-decomposition of an n x n row-major matrix G (n <= 1024).
+// Eigenvalues descending in lam[0..n); eigenvectors of the leading k in the
+// columns of U (n x k, row-major).  Computed in float or double; work must
+// hold 3 * n * n + 3 * n elements of that type.  *status |= 2 when the QL
+// iteration hits its cap.
+void eig_sym(cudaStream_t st, int n, int k, const double* G, double* U, double* lam, void* work, int prec_bits,
+             int* status);
+
+// One bond of the SVD truncation sweep.  With G = M M^T = U diag(lam) U^T
+// (U: r x ku, ld ku) keep kk = min(D, ku, #{lam_i > thr}) directions,
+// thr = max(tol^2, floor_rel) * lam_0.  Writes Us[:, i] = U[:, i]/sqrt(lam_i)
+// and L[:, i] = U[:, i] sqrt(lam_i) for i < kk, zeros for kk <= i < D
+// (both r x D row-major); adds sum_{i >= kk} lam_i to *discarded; stores kk.
+void sweep_scales(cudaStream_t st, int r, int D, int ku, const double* U, const double* lam, double tol,
+                  double floor_rel, double* Us, double* L, double* discarded, int* rank);
+
+// core[a][s][b] = (b == 2a + s): an r x 2 x 2r left identity core.
+void fill_identity_left(cudaStream_t st, double* core, int r);
+// core[a][s][b] = (a == s * c + b): a 2c x 2 x c right identity core.
+void fill_identity_right(cudaStream_t st, double* core, int c);
+void fill_value(cudaStream_t st, double* p, size_t n, double v);
+// Gaussian N(0, sigma^2) entries from a counter-based generator (splitmix64
+// hashing of (seed, stream, index), Box-Muller).
+void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned long long seed,
+                   unsigned long long stream_id);
+
+// out[q * ldo + b] = contraction of the sites [0, nsites) of the weight
+// chain w (bond <= 4) with the MPS chain f, left to right; result indexed by
+// the weight's last bond q and f's bond b at position nsites.  One block;
+// work holds 16 * max_bond doubles.
+void left_weight_env(cudaStream_t st, const Chain& f, const Chain& w, int nsites, int max_bond, double* out,
+                     int ldo, double* work);
+// u[b] = sum over the indices of sites [n0, N) of f(..)[b]: right environment
+// with the all-ones vector.  One block; work holds 2 * max_bond doubles.
+void right_ones_env(cudaStream_t st, const Chain& f, int n0, int max_bond, double* out, double* work);
+// Evaluates f at npts multi-indices given as bits[p * N + n] (one warp per
+// point); work holds npts * 2 * max_bond doubles.
+void eval_points(cudaStream_t st, const Chain& f, int npts, const unsigned char* bits, int max_bond, double* out,
+                 double* work);
+// flag[0] = 1 if any of the n entries is NaN or infinite.
+void check_finite(cudaStream_t st, const double* p, size_t n, int* flag);
+
+}  // namespace qtt

@@ -1,0 +1,225 @@
+// Small kernels: identity cores, constant / Gaussian fills, the truncation
+// scaling of the SVD sweep, weight environments (conditional means and
+// moments), point evaluation, finite checks.
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace qtt {
+
+namespace {
+
+__global__ void identity_left_kernel(double* core, int r) {
+  const long long total = (long long)r * 2 * (2 * r);
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long b = x % (2 * r), as = x / (2 * r);
+    const long long s = as % 2, a = as / 2;
+    core[x] = (b == 2 * a + s) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void identity_right_kernel(double* core, int c) {
+  const long long total = (long long)(2 * c) * 2 * c;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long b = x % c, as = x / c;
+    const long long s = as % 2, a = as / 2;
+    core[x] = (a == s * c + b) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void fill_kernel(double* p, size_t n, double v) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x)
+    p[x] = v;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(double* p, size_t n, double sigma, unsigned long long seed,
+                                unsigned long long stream_id) {
+  const unsigned long long base = mix64(seed ^ mix64(stream_id + 0x632BE59BD9B4E019ull));
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long h1 = mix64(base + 2 * (unsigned long long)x);
+    const unsigned long long h2 = mix64(base + 2 * (unsigned long long)x + 1);
+    const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
+    p[x] = sigma * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  }
+}
+
+__global__ void sweep_scales_kernel(int r, int D, int ku, const double* U, const double* lam, double tol,
+                                    double floor_rel, double* Us, double* L, double* discarded, int* rank) {
+  __shared__ int s_kk;
+  if (threadIdx.x == 0) {
+    const double l0 = lam[0] > 0.0 ? lam[0] : 0.0;
+    const double rel = tol * tol > floor_rel ? tol * tol : floor_rel;
+    const double thr = rel * l0;
+    int lim = D < ku ? D : ku;
+    lim = lim < r ? lim : r;
+    int kk = 0;
+    while (kk < lim && lam[kk] > thr && lam[kk] > 0.0) ++kk;
+    double dis = 0.0;
+    for (int i = kk; i < r; ++i) dis += lam[i] > 0.0 ? lam[i] : 0.0;
+    *discarded += dis;
+    *rank = kk;
+    s_kk = kk;
+  }
+  __syncthreads();
+  const int kk = s_kk;
+  for (int x = threadIdx.x; x < r * D; x += blockDim.x) {
+    const int i = x / D, c = x - i * D;
+    if (c < kk) {
+      const double sl = sqrt(lam[c]);
+      const double u = U[(size_t)i * ku + c];
+      Us[x] = u / sl;
+      L[x] = u * sl;
+    } else {
+      Us[x] = 0.0;
+      L[x] = 0.0;
+    }
+  }
+}
+
+__global__ void left_weight_env_kernel(Chain f, Chain w, int nsites, int max_bond, double* out, int ldo,
+                                       double* work) {
+  double* E = work;                    // [4][max_bond]
+  double* X = E + 4 * max_bond;        // [4][2][max_bond]
+  double* E2 = X + 8 * max_bond;       // [4][max_bond]
+  if (threadIdx.x == 0) E[0] = 1.0;
+  __syncthreads();
+  for (int n = 0; n < nsites; ++n) {
+    const int bl = f.bond[n], br = f.bond[n + 1], ql = w.bond[n], qr = w.bond[n + 1];
+    const double* A = f.core[n];
+    const double* W = w.core[n];
+    for (int x = threadIdx.x; x < ql * 2 * br; x += blockDim.x) {
+      const int q = x / (2 * br), sb = x - q * 2 * br;
+      double acc = 0.0;
+      for (int b = 0; b < bl; ++b) acc += E[q * max_bond + b] * A[(size_t)b * 2 * br + sb];
+      X[q * 2 * max_bond + sb] = acc;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < qr * br; x += blockDim.x) {
+      const int q2 = x / br, b2 = x - q2 * br;
+      double acc = 0.0;
+      for (int q = 0; q < ql; ++q)
+        for (int s = 0; s < 2; ++s) acc += W[(q * 2 + s) * qr + q2] * X[q * 2 * max_bond + s * br + b2];
+      E2[q2 * max_bond + b2] = acc;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < qr * br; x += blockDim.x) {
+      const int q2 = x / br, b2 = x - q2 * br;
+      E[q2 * max_bond + b2] = E2[q2 * max_bond + b2];
+    }
+    __syncthreads();
+  }
+  const int qn = w.bond[nsites], bn = f.bond[nsites];
+  for (int x = threadIdx.x; x < qn * bn; x += blockDim.x) {
+    const int q = x / bn, b = x - q * bn;
+    out[(size_t)q * ldo + b] = E[q * max_bond + b];
+  }
+}
+
+__global__ void right_ones_env_kernel(Chain f, int n0, int max_bond, double* out, double* work) {
+  double* R = work;
+  double* R2 = work + max_bond;
+  if (threadIdx.x == 0) R[0] = 1.0;
+  __syncthreads();
+  for (int n = f.n - 1; n >= n0; --n) {
+    const int bl = f.bond[n], br = f.bond[n + 1];
+    const double* A = f.core[n];
+    for (int b = threadIdx.x; b < bl; b += blockDim.x) {
+      double acc = 0.0;
+      for (int s = 0; s < 2; ++s)
+        for (int c = 0; c < br; ++c) acc += A[((size_t)b * 2 + s) * br + c] * R[c];
+      R2[b] = acc;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < bl; b += blockDim.x) R[b] = R2[b];
+    __syncthreads();
+  }
+  for (int b = threadIdx.x; b < f.bond[n0]; b += blockDim.x) out[b] = R[b];
+}
+
+__global__ void eval_points_kernel(Chain f, int npts, const unsigned char* bits, int max_bond, double* out,
+                                   double* work) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= npts) return;
+  double* v = work + (size_t)warp * 2 * max_bond;
+  double* v2 = v + max_bond;
+  if (lane == 0) v[0] = 1.0;
+  __syncwarp();
+  for (int n = 0; n < f.n; ++n) {
+    const int bl = f.bond[n], br = f.bond[n + 1];
+    const int s = bits[(size_t)warp * f.n + n] ? 1 : 0;
+    const double* A = f.core[n];
+    for (int c = lane; c < br; c += 32) {
+      double acc = 0.0;
+      for (int b = 0; b < bl; ++b) acc += v[b] * A[((size_t)b * 2 + s) * br + c];
+      v2[c] = acc;
+    }
+    __syncwarp();
+    for (int c = lane; c < br; c += 32) v[c] = v2[c];
+    __syncwarp();
+  }
+  if (lane == 0) out[warp] = v[0];
+}
+
+__global__ void finite_kernel(const double* p, size_t n, int* flag) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(p[x])) {
+      atomicOr(flag, 1);
+      return;
+    }
+}
+
+int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 2048) b = 2048;
+  return (int)b;
+}
+
+}  // namespace
+
+void fill_identity_left(cudaStream_t st, double* core, int r) {
+  identity_left_kernel<<<grid_for((size_t)r * 4 * r), 256, 0, st>>>(core, r);
+}
+void fill_identity_right(cudaStream_t st, double* core, int c) {
+  identity_right_kernel<<<grid_for((size_t)c * 4 * c), 256, 0, st>>>(core, c);
+}
+void fill_value(cudaStream_t st, double* p, size_t n, double v) {
+  if (n) fill_kernel<<<grid_for(n), 256, 0, st>>>(p, n, v);
+}
+void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned long long seed,
+                   unsigned long long stream_id) {
+  if (n) gaussian_kernel<<<grid_for(n), 256, 0, st>>>(p, n, sigma, seed, stream_id);
+}
+void sweep_scales(cudaStream_t st, int r, int D, int ku, const double* U, const double* lam, double tol,
+                  double floor_rel, double* Us, double* L, double* discarded, int* rank) {
+  sweep_scales_kernel<<<1, 256, 0, st>>>(r, D, ku, U, lam, tol, floor_rel, Us, L, discarded, rank);
+}
+void left_weight_env(cudaStream_t st, const Chain& f, const Chain& w, int nsites, int max_bond, double* out,
+                     int ldo, double* work) {
+  left_weight_env_kernel<<<1, 256, 0, st>>>(f, w, nsites, max_bond, out, ldo, work);
+}
+void right_ones_env(cudaStream_t st, const Chain& f, int n0, int max_bond, double* out, double* work) {
+  right_ones_env_kernel<<<1, 256, 0, st>>>(f, n0, max_bond, out, work);
+}
+void eval_points(cudaStream_t st, const Chain& f, int npts, const unsigned char* bits, int max_bond, double* out,
+                 double* work) {
+  if (npts <= 0) return;
+  const int warps_per_block = 8;
+  eval_points_kernel<<<(npts + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+      f, npts, bits, max_bond, out, work);
+}
+void check_finite(cudaStream_t st, const double* p, size_t n, int* flag) {
+  if (n) finite_kernel<<<grid_for(n), 256, 0, st>>>(p, n, flag);
+}
+
+}  // namespace qtt

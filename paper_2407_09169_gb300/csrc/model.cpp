@@ -1,0 +1,322 @@
+// Problem set-up (see model.hpp).
+//
+// Paper references:
+//   Eq. FP0 / FP2     -- the operator: transport -u.grad f, diffusion gamma lap f,
+//                        composition drift d/dphi_a [Omega (phi_a - <Phi_a>) f]
+//                        and reaction -d/dphi_a (S_a f), S_a = -Da phi1 phi2,
+//                        plus the artificial dissipation D_phi d2f/dphi_a^2.
+//   Eq. compBCs       -- zero-sum ghost rules for composition derivatives.
+//   "Finite-difference discretisation" -- CFD2 stencils, periodic x.
+//   "Matrix product state encoding"    -- site order phi1, phi2, x1, x2, x3,
+//                        each dimension coarse-to-fine (most significant bit first).
+#include "model.hpp"
+
+#include <cmath>
+#include <sstream>
+#include <stdexcept>
+
+namespace qtt {
+
+static const double kPi = 3.14159265358979323846;
+static const double kTol = 1e-14;  // numerical-rank threshold of the exact encodings
+
+std::string validate(const Params& p) {
+  std::ostringstream e;
+  for (int d = 0; d < 5; ++d)
+    if (p.bits[d] < 1 || p.bits[d] > 12) e << "bits[" << d << "]=" << p.bits[d] << " outside 1..12; ";
+  if (p.chi_max < 1) e << "chi_max must be >= 1; ";
+  if (p.chi_max > 4096) e << "chi_max > 4096 unsupported; ";
+  if (!(p.svd_rel_tol >= 0.0) || p.svd_rel_tol >= 1.0) e << "svd_rel_tol must be in [0, 1); ";
+  if (p.precision < 0 || p.precision > 3) e << "unknown precision " << p.precision << "; ";
+  if (!(p.dt > 0.0) || !std::isfinite(p.dt)) e << "dt must be positive; ";
+  if (!(p.ic_sigma > 0.0)) e << "ic_sigma must be positive; ";
+  if (!(p.ic_blend_width > 0.0)) e << "ic_blend_width must be positive; ";
+  if (p.oversample < 0 || p.oversample > 256) e << "oversample outside 0..256; ";
+  if (p.rk_variant != 0 && p.rk_variant != 1) e << "rk_variant must be 0 or 1; ";
+  for (const Mode& m : p.umodes) {
+    if (m.comp < 0 || m.comp > 2) e << "velocity mode component outside 0..2; ";
+    else if (m.k[m.comp] != 0) e << "velocity mode must have k[comp] = 0 (divergence-free); ";
+  }
+  const double vals[] = {p.omega, p.da, p.gamma, p.d_phi, p.shear_amp};
+  for (double v : vals)
+    if (!std::isfinite(v)) e << "non-finite coefficient; ";
+  if (p.exact) {
+    const int N = p.N();
+    if (p.svd_rel_tol != 0.0) e << "exact mode requires svd_rel_tol = 0; ";
+    if (N > 26) e << "exact mode supports N <= 26; ";
+    else if ((long long)p.chi_max < (1LL << (N / 2))) e << "exact mode requires chi_max >= 2^(N/2); ";
+  }
+  return e.str();
+}
+
+// ---------------------------------------------------------------- operators
+TT op_shift(int K, int dir, bool periodic) {
+  // Core W[c_out][s_out*2 + s_in][c_in]; the carry (dir = +1) or borrow
+  // (dir = -1) enters at the least significant (rightmost) site with value 1
+  // and leaves at the most significant site, where it is summed (periodic
+  // wrap) or required to vanish (no row beyond the lattice).
+  std::vector<double> W(2 * 4 * 2, 0.0);
+  auto at = [&](int co, int so, int si, int ci) -> double& { return W[(co * 4 + so * 2 + si) * 2 + ci]; };
+  for (int s = 0; s < 2; ++s) at(0, s, s, 0) = 1.0;  // no carry: copy the bit
+  if (dir > 0) {  // s_in = s_out + 1
+    at(0, 0, 1, 1) = 1.0;
+    at(1, 1, 0, 1) = 1.0;
+  } else {        // s_in = s_out - 1
+    at(1, 0, 1, 1) = 1.0;
+    at(0, 1, 0, 1) = 1.0;
+  }
+  const double lv[2] = {1.0, periodic ? 1.0 : 0.0};
+  TT t;
+  t.d = 4;
+  t.r.assign(K + 1, 2);
+  t.r[0] = t.r[K] = 1;
+  t.c.resize(K);
+  for (int n = 0; n < K; ++n) {
+    const int L = t.r[n], R = t.r[n + 1];
+    t.c[n].assign((size_t)L * 4 * R, 0.0);
+    for (int co = 0; co < 2; ++co)
+      for (int i = 0; i < 4; ++i)
+        for (int ci = 0; ci < 2; ++ci) {
+          const double w = W[(co * 4 + i) * 2 + ci];
+          if (w == 0.0) continue;
+          double lw = (n == 0) ? lv[co] : 1.0;
+          double rw = (n == K - 1) ? (ci == 1 ? 1.0 : 0.0) : 1.0;
+          const int l = (n == 0) ? 0 : co, r = (n == K - 1) ? 0 : ci;
+          t.c[n][((size_t)l * 4 + i) * R + r] += w * lw * rw;
+        }
+  }
+  return t;
+}
+
+static TT op_projector(int K, int bit) {
+  TT t = mpo_identity(K);
+  for (int n = 0; n < K; ++n) t.c[n] = bit ? std::vector<double>{0, 0, 0, 1} : std::vector<double>{1, 0, 0, 0};
+  return t;
+}
+
+static TT scaled(TT t, double s) {
+  tt_scale(t, s);
+  return t;
+}
+
+TT op_d1_periodic(int K, double h) {
+  TT t = tt_add(scaled(op_shift(K, +1, true), 1.0 / (2 * h)), scaled(op_shift(K, -1, true), -1.0 / (2 * h)));
+  return tt_round(t, kTol, 0);
+}
+
+TT op_d2_periodic(int K, double h) {
+  TT t = tt_add(op_shift(K, +1, true), op_shift(K, -1, true));
+  t = tt_add(t, scaled(mpo_identity(K), -2.0));
+  tt_scale(t, 1.0 / (h * h));
+  return tt_round(t, kTol, 0);
+}
+
+TT op_d1_zero_sum(int K, double h) {
+  // (g_{i+1} - g_{i-1}) / 2h with g_{-1} = -g_0 and g_M = -g_{M-1}:
+  // the non-periodic shifts plus (P_0 - P_{M-1}) / 2h on the end rows.
+  TT t = tt_add(op_shift(K, +1, false), scaled(op_shift(K, -1, false), -1.0));
+  t = tt_add(t, op_projector(K, 0));
+  t = tt_add(t, scaled(op_projector(K, 1), -1.0));
+  tt_scale(t, 1.0 / (2 * h));
+  return tt_round(t, kTol, 0);
+}
+
+TT op_d2_zero_sum(int K, double h) {
+  // (f_{i+1} - 2 f_i + f_{i-1}) / h^2 with f_{-1} = f_0 and f_M = f_{M-1}.
+  TT t = tt_add(op_shift(K, +1, false), op_shift(K, -1, false));
+  t = tt_add(t, scaled(mpo_identity(K), -2.0));
+  t = tt_add(t, op_projector(K, 0));
+  t = tt_add(t, op_projector(K, 1));
+  tt_scale(t, 1.0 / (h * h));
+  return tt_round(t, kTol, 0);
+}
+
+TT embed_op(const Params& p, const TT& op, int dim) {
+  TT t;
+  for (int d = 0; d < 5; ++d) {
+    TT piece = (d == dim) ? op : mpo_identity(p.bits[d]);
+    t = (d == 0) ? piece : tt_kron(t, piece);
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------- fields
+static std::vector<double> grid_phi(int K) {
+  const size_t M = (size_t)1 << K;
+  std::vector<double> v(M);
+  for (size_t i = 0; i < M; ++i) v[i] = (i + 0.5) / (double)M;
+  return v;
+}
+
+static std::vector<double> grid_x(int K) {
+  const size_t M = (size_t)1 << K;
+  std::vector<double> v(M);
+  for (size_t i = 0; i < M; ++i) v[i] = 2.0 * kPi * (double)i / (double)M;
+  return v;
+}
+
+template <typename F>
+static TT encode(int K, const std::vector<double>& grid, F fn) {
+  std::vector<double> v(grid.size());
+  for (size_t i = 0; i < grid.size(); ++i) v[i] = fn(grid[i]);
+  return tt_from_vector(v, K, kTol);
+}
+
+static TT kron3(const TT& a, const TT& b, const TT& c) { return tt_kron(tt_kron(a, b), c); }
+
+// sum over the 4 separable terms of sin/cos(k1 x1 + k2 x2 + k3 x3 + theta)
+static TT fourier_tt(const Params& p, const int k[3], double theta, bool use_sin) {
+  const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
+  TT c1 = encode(Kx[0], grid_x(Kx[0]), [&](double x) { return std::cos(k[0] * x + theta); });
+  TT s1 = encode(Kx[0], grid_x(Kx[0]), [&](double x) { return std::sin(k[0] * x + theta); });
+  TT c2 = encode(Kx[1], grid_x(Kx[1]), [&](double x) { return std::cos(k[1] * x); });
+  TT s2 = encode(Kx[1], grid_x(Kx[1]), [&](double x) { return std::sin(k[1] * x); });
+  TT c3 = encode(Kx[2], grid_x(Kx[2]), [&](double x) { return std::cos(k[2] * x); });
+  TT s3 = encode(Kx[2], grid_x(Kx[2]), [&](double x) { return std::sin(k[2] * x); });
+  TT t;
+  if (use_sin) {
+    // sin(a+b+c) = s c c + c s c + c c s - s s s
+    t = kron3(s1, c2, c3);
+    t = tt_add(t, kron3(c1, s2, c3));
+    t = tt_add(t, kron3(c1, c2, s3));
+    t = tt_add(t, scaled(kron3(s1, s2, s3), -1.0));
+  } else {
+    // cos(a+b+c) = c c c - c s s - s c s - s s c
+    t = kron3(c1, c2, c3);
+    t = tt_add(t, scaled(kron3(c1, s2, s3), -1.0));
+    t = tt_add(t, scaled(kron3(s1, c2, s3), -1.0));
+    t = tt_add(t, scaled(kron3(s1, s2, c3), -1.0));
+  }
+  return tt_round(t, kTol, 0);
+}
+
+TT velocity_tt(const Params& p, int comp) {
+  const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
+  TT u = kron3(tt_constant(Kx[0], 0.0), tt_constant(Kx[1], 1.0), tt_constant(Kx[2], 1.0));
+  if (comp == 0 && p.shear_amp != 0.0) {
+    TT sh = kron3(tt_constant(Kx[0], 1.0),
+                  encode(Kx[1], grid_x(Kx[1]), [&](double x) { return std::tanh(x - kPi); }),
+                  tt_constant(Kx[2], 1.0));
+    tt_scale(sh, p.shear_amp);
+    u = tt_add(u, sh);
+  }
+  for (const Mode& m : p.umodes) {
+    if (m.comp != comp || m.amp == 0.0) continue;
+    u = tt_add(u, scaled(fourier_tt(p, m.k, m.phase, true), m.amp));
+  }
+  return tt_round(u, kTol, 0);
+}
+
+static TT ones_x(const Params& p) {
+  return kron3(tt_constant(p.bits[2], 1.0), tt_constant(p.bits[3], 1.0), tt_constant(p.bits[4], 1.0));
+}
+
+static TT phi_weight(const Params& p, int e1, int e2) {
+  // h1 h2 phi1^e1 phi2^e2 over the phi sites
+  const double h1 = 1.0 / (double)(1 << p.bits[0]), h2 = 1.0 / (double)(1 << p.bits[1]);
+  TT a = encode(p.bits[0], grid_phi(p.bits[0]), [&](double v) { return std::pow(v, e1); });
+  TT b = encode(p.bits[1], grid_phi(p.bits[1]), [&](double v) { return std::pow(v, e2); });
+  TT t = tt_kron(a, b);
+  tt_scale(t, h1 * h2);
+  return t;
+}
+
+static TT gaussian_phi(const Params& p, const double c[2]) {
+  // normalised separable Gaussian: h1 h2 sum g = 1 on the cell-centred grid
+  TT out;
+  for (int a = 0; a < 2; ++a) {
+    const int K = p.bits[a];
+    const std::vector<double> g = grid_phi(K);
+    std::vector<double> v(g.size());
+    double s = 0;
+    for (size_t i = 0; i < g.size(); ++i) {
+      v[i] = std::exp(-(g[i] - c[a]) * (g[i] - c[a]) / (2.0 * p.ic_sigma * p.ic_sigma));
+      s += v[i];
+    }
+    const double h = 1.0 / (double)g.size();
+    for (double& x : v) x /= (s * h);
+    TT t = tt_from_vector(v, K, kTol);
+    out = (a == 0) ? t : tt_kron(out, t);
+  }
+  return out;
+}
+
+static TT initial_pdf(const Params& p) {
+  const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
+  auto w = [&](double x) { return 0.5 * (1.0 + std::tanh((x - kPi) / p.ic_blend_width)); };
+  TT whi = kron3(tt_constant(Kx[0], 1.0), encode(Kx[1], grid_x(Kx[1]), w), tt_constant(Kx[2], 1.0));
+  TT wlo = kron3(tt_constant(Kx[0], 1.0), encode(Kx[1], grid_x(Kx[1]), [&](double x) { return 1.0 - w(x); }),
+                 tt_constant(Kx[2], 1.0));
+  TT f = tt_add(tt_kron(gaussian_phi(p, p.ic_c_hi), whi), tt_kron(gaussian_phi(p, p.ic_c_lo), wlo));
+  f = tt_round(f, kTol, 0);
+  bool any = false;
+  for (const Mode& m : p.icmodes) any = any || (m.amp != 0.0);
+  if (any) {
+    TT mod = ones_x(p);
+    for (const Mode& m : p.icmodes)
+      if (m.amp != 0.0) mod = tt_add(mod, scaled(fourier_tt(p, m.k, m.phase, false), m.amp));
+    mod = tt_round(mod, kTol, 0);
+    TT phi1 = tt_kron(tt_constant(p.bits[0], 1.0), tt_constant(p.bits[1], 1.0));
+    f = tt_round(tt_hadamard(f, tt_kron(phi1, mod)), kTol, 0);
+  }
+  return f;
+}
+
+TT linear_operator(const Params& p, const TT* u3) {
+  const int Kphi = p.bits[0] + p.bits[1];
+  TT idphi = mpo_identity(Kphi);
+  TT W;
+  bool have = false;
+  auto acc = [&](const TT& t) {
+    W = have ? tt_round(tt_add(W, t), kTol, 0) : t;
+    have = true;
+  };
+  // transport and diffusion in x (periodic CFD2)
+  for (int i = 0; i < 3; ++i) {
+    const int K = p.bits[2 + i];
+    const double h = 2.0 * kPi / (double)(1 << K);
+    TT du = tt_kron(idphi, mpo_diag(u3[i]));
+    TT adv = mpo_mul(du, embed_op(p, op_d1_periodic(K, h), 2 + i));
+    tt_scale(adv, -1.0);
+    acc(tt_round(adv, kTol, 0));
+    if (p.gamma != 0.0) acc(scaled(embed_op(p, op_d2_periodic(K, h), 2 + i), p.gamma));
+  }
+  // composition drift (linear part) + reaction + artificial dissipation
+  for (int a = 0; a < 2; ++a) {
+    const int K = p.bits[a];
+    const double h = 1.0 / (double)(1 << K);
+    TT c = scaled(phi_weight(p, a == 0 ? 1 : 0, a == 1 ? 1 : 0), p.omega);
+    c = tt_add(c, scaled(phi_weight(p, 1, 1), p.da));
+    const double h12 = (1.0 / (double)(1 << p.bits[0])) * (1.0 / (double)(1 << p.bits[1]));
+    tt_scale(c, 1.0 / h12);  // phi_weight carries h1 h2
+    c = tt_round(c, kTol, 0);
+    TT dc = mpo_diag(tt_kron(c, ones_x(p)));
+    TT drift = mpo_mul(embed_op(p, op_d1_zero_sum(K, h), a), dc);
+    acc(tt_round(drift, kTol, 0));
+    if (p.d_phi != 0.0) acc(scaled(embed_op(p, op_d2_zero_sum(K, h), a), p.d_phi));
+  }
+  return W;
+}
+
+Model build_model(const Params& p) {
+  Model m;
+  m.N = p.N();
+  m.off[0] = 0;
+  for (int d = 0; d < 5; ++d) m.off[d + 1] = m.off[d] + p.bits[d];
+  for (int i = 0; i < 3; ++i) m.u[i] = velocity_tt(p, i);
+  m.f0 = initial_pdf(p);
+  TT W = linear_operator(p, m.u);
+  tt_scale(W, p.dt);
+  m.op_lin = tt_round(tt_add(embed_op(p, mpo_identity(p.bits[0]), 0), W), kTol, 0);
+  // phi part of the mixing drift -Omega d/dphi_a (<Phi_a> f): D1phi_a on
+  // phi_a's sites, the open bond a = 0, 1 carries the choice of species.
+  TT d1a = tt_kron(op_d1_zero_sum(p.bits[0], 1.0 / (double)(1 << p.bits[0])), mpo_identity(p.bits[1]));
+  TT d1b = tt_kron(mpo_identity(p.bits[0]), op_d1_zero_sum(p.bits[1], 1.0 / (double)(1 << p.bits[1])));
+  m.had_phi = tt_stack_right(d1a, d1b);
+  tt_scale(m.had_phi, -p.dt * p.omega);
+  const int ex[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {0, 2}, {1, 1}};
+  for (int w = 0; w < 6; ++w) m.wphi[w] = phi_weight(p, ex[w][0], ex[w][1]);
+  return m;
+}
+
+}  // namespace qtt

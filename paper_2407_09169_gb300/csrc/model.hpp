@@ -1,0 +1,58 @@
+// Problem set-up for the Fokker-Planck PDF: grids, initial PDF, velocity and
+// the operators of Eq. FP2 as trains (host, FP64, once per context).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "host_tt.hpp"
+
+namespace qtt {
+
+struct Mode {
+  int comp = 0;
+  int k[3] = {0, 0, 0};
+  double phase = 0, amp = 0;
+};
+
+struct Params {
+  int bits[5] = {0, 0, 0, 0, 0};
+  int chi_max = 0;
+  double svd_rel_tol = 0;
+  int precision = 0;
+  int oversample = 8;
+  int exact = 0;
+  unsigned long long seed = 0;
+  double omega = 0, da = 0, gamma = 0, d_phi = 0, dt = 0, shear_amp = 0;
+  std::vector<Mode> umodes, icmodes;
+  double ic_sigma = 0.05, ic_blend_width = 0.2;
+  double ic_c_hi[2] = {1, 0}, ic_c_lo[2] = {0, 1};
+  int rk_variant = 0;
+  int N() const { return bits[0] + bits[1] + bits[2] + bits[3] + bits[4]; }
+  int Kphi() const { return bits[0] + bits[1]; }
+};
+
+// Validates the parameters; returns an empty string or the reason.
+std::string validate(const Params& p);
+
+struct Model {
+  int N = 0, off[6] = {0, 0, 0, 0, 0, 0};
+  TT f0;        // initial PDF, rounded (right-canonical)
+  TT op_lin;    // I + dt * W_lin over all N sites (d = 4)
+  TT had_phi;   // -dt * Omega * [D1phi1 (+) D1phi2] over the phi sites, open right bond 2
+  TT wphi[6];   // h1 h2 * {1, phi1, phi2, phi1^2, phi2^2, phi1 phi2} over the phi sites
+  TT u[3];      // velocity components over the x sites (for checks)
+};
+
+// Single-dimension building blocks (exposed for the host debug entry points).
+TT op_shift(int K, int dir, bool periodic);   // (S f)_i = f_{i + dir}, dir = +1 / -1
+TT op_d1_periodic(int K, double h);
+TT op_d2_periodic(int K, double h);
+TT op_d1_zero_sum(int K, double h);           // ghosts g_{-1} = -g_0, g_M = -g_{M-1}
+TT op_d2_zero_sum(int K, double h);           // ghosts f_{-1} = f_0, f_M = f_{M-1}
+TT embed_op(const Params& p, const TT& op, int dim);  // identity on the other dimensions
+TT velocity_tt(const Params& p, int comp);    // over the 3 x dimensions
+TT linear_operator(const Params& p, const TT* u3);    // W_lin of Eq. FP2 (no identity, no dt)
+Model build_model(const Params& p);
+
+}  // namespace qtt

@@ -1,0 +1,141 @@
+"""GPU path (through the C ABI) against the CPU finite-difference oracle."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+pkg = pytest.importorskip("paper_2407_09169_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib(gpu_available):
+    from paper_2407_09169_gb300 import build
+    build.build()
+    return pkg.load_library()
+
+
+def exact_params(K, **kw):
+    p = workload.make_params("small", **kw)
+    p["bits"] = [K] * 5 if isinstance(K, int) else list(K)
+    N = sum(p["bits"])
+    p["chi_max"] = 2 ** (N // 2)
+    p["svd_rel_tol"] = 0.0
+    p["exact"] = 1
+    ub = abs(p["shear_amp"]) + sum(abs(m["amp"]) for m in p["umodes"])
+    p["dt"] = workload.cfl_dt(p["bits"], p["omega"], p["da"], p["gamma"], p["d_phi"], ub)
+    return p
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ------------------------------------------------------------ exact parity
+@pytest.mark.parametrize("K,steps,rk", [(2, 6, 0), (2, 4, 1), ([2, 2, 3, 2, 3], 3, 0), (3, 3, 0)])
+def test_exact_mode_matches_oracle(K, steps, rk):
+    p = exact_params(K, rk_variant=rk)
+    with pkg.qtt_init(p) as ctx:
+        g = oracle.make_grid(p["bits"])
+        f0 = ctx.observe(pkg.OBS_DENSE)
+        assert rel_l2(f0, oracle.initial_pdf(p, g).ravel()) < 1e-12
+        ctx.step(steps)
+        got = ctx.observe(pkg.OBS_DENSE)
+    ref = oracle.solve(p, steps).ravel()
+    err = rel_l2(got, ref)
+    assert err <= 1e-10, err
+
+
+def test_exact_mode_observables_match_oracle():
+    p = exact_params(2, da=1.3)
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(3)
+        s = ctx.scalars()
+        means = ctx.observe(pkg.OBS_MEANS)
+    g = oracle.make_grid(p["bits"])
+    o = oracle.observables(oracle.solve(p, 3), g)
+    for k in ("norm_avg", "mean1_avg", "mean2_avg", "phi11_avg", "phi22_avg", "phi12_avg", "R12", "Y12", "product_J"):
+        assert abs(s[k] - o[k]) <= 1e-11 * max(1.0, abs(o[k])), (k, s[k], o[k])
+    Mx = g.M[2] * g.M[3] * g.M[4]
+    assert np.abs(means[:Mx] - o["norm"].ravel()).max() < 1e-11
+    assert np.abs(means[Mx:2 * Mx] - o["mean1"].ravel()).max() < 1e-11
+    assert np.abs(means[2 * Mx:] - o["mean2"].ravel()).max() < 1e-11
+    assert s["steps"] == 3 and math.isclose(s["time"], 3 * p["dt"])
+
+
+# -------------------------------------------------------- truncating machinery
+def test_truncating_path_without_cap_matches_oracle():
+    """Randomized rounding + SVD sweep with chi >= every structural rank: only
+    round-off (Gram-based truncation at ~sqrt(eps)) separates it from the oracle."""
+    p = exact_params(2)
+    p["exact"] = 0
+    p["chi_max"] = 64
+    p["svd_rel_tol"] = 0.0
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(4)
+        got = ctx.observe(pkg.OBS_DENSE)
+        b = ctx.observe(pkg.OBS_BONDS)
+    ref = oracle.solve(p, 4).ravel()
+    assert rel_l2(got, ref) < 1e-7
+    N = sum(p["bits"])
+    assert list(b.astype(int)) == [min(2 ** n, 2 ** (N - n)) for n in range(N + 1)]
+
+
+def test_small_workload_vs_oracle():
+    """2^4 points per dimension, chi = 32, Heun steps: truncated MPS against the
+    full-grid oracle (reported error, conservation of probability)."""
+    p = workload.make_params("small")
+    nsteps = 10
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(nsteps)
+        got = ctx.observe(pkg.OBS_DENSE)
+        s = ctx.scalars()
+    ref = oracle.solve(p, nsteps).ravel()
+    err = rel_l2(got, ref)
+    print(f"small workload, chi=32, {nsteps} steps: rel-L2 vs oracle = {err:.3e}, norm-1 = {s['norm_avg'] - 1:.2e}")
+    assert err < 5e-2
+    assert abs(s["norm_avg"] - 1.0) < 1e-3
+
+
+def test_points_match_dense():
+    p = exact_params(2)
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(1)
+        dense = ctx.observe(pkg.OBS_DENSE).reshape([4] * 5)
+        rng = np.random.default_rng(0)
+        idx = rng.integers(0, 4, size=(17, 5))
+        vals = ctx.points(idx)
+    assert np.abs(vals - dense[tuple(idx.T)]).max() < 1e-14 * np.abs(dense).max()
+
+
+def test_checkpoint_roundtrip_and_compare():
+    p = workload.make_params("small")
+    with pkg.qtt_init(p) as a, pkg.qtt_init(p) as b:
+        a.step(2)
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "state.qtt")
+            a.save(path)
+            b.load(path)
+            assert b.scalars()["steps"] == 2
+            assert a.compare(b) < 1e-12
+            with open(path, "r+b") as fh:  # corrupt one byte: checksum must catch it
+                fh.seek(100)
+                c = fh.read(1)
+                fh.seek(100)
+                fh.write(bytes([c[0] ^ 0xFF]))
+            with pytest.raises(pkg.QttError):
+                b.load(path)
+        a.step(1)
+        assert a.compare(b) > 1e-6
+
+
+def test_nvpp_observable():
+    p = workload.make_params("large")
+    with pkg.qtt_init(p) as ctx:
+        nv = ctx.observe(pkg.OBS_NVPP)[0]
+    assert nv == oracle.nvpp(40, 128)
