@@ -95,7 +95,11 @@ typedef enum {
                             (as doubles 0/1, MSB first per dimension), cap = n * N;
                             the first n entries are overwritten with the values */
   QTT_OBS_NVPP = 5,      /* 1 value: number of variables parameterising f (Eq. MPSdofs) */
-  QTT_OBS_TIMINGS = 6    /* per kernel class: launches, total ms (profiling builds) */
+  QTT_OBS_TIMINGS = 6    /* 13 values: for the kernel classes GEMM, QR, eigensolver, other:
+                            launches, total ms, algorithmic flops, recorded with CUDA events
+                            only when the environment variable QTT_KERNEL_TIMING=1 was set
+                            at qtt_init (zeros otherwise); then the number of kernels the
+                            library has launched since it was loaded (always counted) */
 } qtt_observable;
 
 /* Build the initial PDF, velocity and operators (paper: "Flow case

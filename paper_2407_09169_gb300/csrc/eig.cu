@@ -265,6 +265,7 @@ void eig_sym(cudaStream_t st, int n, int k, const double* G, double* U, double* 
     cudaMemsetAsync(status, 0xff, sizeof(int), st);
     return;
   }
+  count_launches(1);
   if (prec_bits == 32)
     eig_sym_kernel<float><<<1, EIG_THREADS, 0, st>>>(n, k, G, U, lam, (float*)work, status);
   else

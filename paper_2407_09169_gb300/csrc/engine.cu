@@ -51,10 +51,12 @@ struct KernelTimer {
   struct Rec {
     int cls;
     cudaEvent_t a, b;
+    double flops;
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
-  double ms[8] = {0}, launches[8] = {0};
+  double ms[8] = {0}, launches[8] = {0}, flops[8] = {0};
+  double pending_flops = 0;
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -71,6 +73,7 @@ struct KernelTimer {
       if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
         ms[r.cls] += t;
         launches[r.cls] += 1;
+        flops[r.cls] += r.flops;
       }
       pool.push_back(r.a);
       pool.push_back(r.b);
@@ -92,12 +95,12 @@ struct TimeScope {
   int cls;
   cudaStream_t st;
   cudaEvent_t b = nullptr;
-  TimeScope(KernelTimer* tm, int c, cudaStream_t s) : t(tm), cls(c), st(s) {
+  TimeScope(KernelTimer* tm, int c, cudaStream_t s, double flops = 0.0) : t(tm), cls(c), st(s) {
     if (t && t->on) {
       cudaEvent_t a = t->get();
       b = t->get();
       cudaEventRecord(a, st);
-      t->recs.push_back({cls, a, b});
+      t->recs.push_back({cls, a, b, flops});
     }
   }
   ~TimeScope() {
@@ -201,7 +204,7 @@ void Engine::upload_op(DevOp& op, const TT& t) {
 
 void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
                   OutView C) {
-  TimeScope ts(timer_, TM_GEMM, st_);
+  TimeScope ts(timer_, TM_GEMM, st_, 2.0 * M * (double)N * K * outer * inner);
   gemm_f64(st_, M, N, K, outer, inner, alpha, A, B, beta, C, ws_, ws_elems_);
 }
 
@@ -783,7 +786,9 @@ std::vector<double> Engine::timings() const {
   for (int c = 0; c < 4; ++c) {
     t.push_back(timer_->launches[c]);
     t.push_back(timer_->ms[c]);
+    t.push_back(timer_->flops[c]);
   }
+  t.push_back((double)launch_count());
   return t;
 }
 

@@ -142,6 +142,7 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
     const long long total = (long long)M * N * batch;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
+    count_launches(1);
     scale_out_kernel<<<blocks, 256, 0, st>>>(M, N, inner, batch, beta, C);
     return;
   }
@@ -151,6 +152,7 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
   kchunk = ((kchunk + BK - 1) / BK) * BK;
   splitk = (K + kchunk - 1) / kchunk;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splitk);
+  count_launches(splitk == 1 ? 1 : 2);
   if (splitk == 1) {
     gemm_f64_kernel<<<grid, NT, 0, st>>>(M, N, K, inner, 1, kchunk, alpha, A, B, beta, C, nullptr);
   } else {

@@ -8,6 +8,10 @@ namespace qtt {
 
 constexpr int kMaxSites = 64;
 
+// Number of kernels launched by this library since it was loaded.
+unsigned long long launch_count();
+void count_launches(int n);
+
 // Operand view for the strided batched GEMM: element (i, j) of batch
 // (bo, bi) lives at p[bo * so + bi * si + i * rs + j * cs].
 struct MatView {

@@ -7,6 +7,10 @@
 
 namespace qtt {
 
+static unsigned long long g_launches = 0;
+unsigned long long launch_count() { return g_launches; }
+void count_launches(int n) { g_launches += (unsigned long long)n; }
+
 namespace {
 
 __global__ void identity_left_kernel(double* core, int r) {
@@ -188,37 +192,46 @@ int grid_for(size_t n) {
 }  // namespace
 
 void fill_identity_left(cudaStream_t st, double* core, int r) {
+  count_launches(1);
   identity_left_kernel<<<grid_for((size_t)r * 4 * r), 256, 0, st>>>(core, r);
 }
 void fill_identity_right(cudaStream_t st, double* core, int c) {
+  count_launches(1);
   identity_right_kernel<<<grid_for((size_t)c * 4 * c), 256, 0, st>>>(core, c);
 }
 void fill_value(cudaStream_t st, double* p, size_t n, double v) {
+  if (n) count_launches(1);
   if (n) fill_kernel<<<grid_for(n), 256, 0, st>>>(p, n, v);
 }
 void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned long long seed,
                    unsigned long long stream_id) {
+  if (n) count_launches(1);
   if (n) gaussian_kernel<<<grid_for(n), 256, 0, st>>>(p, n, sigma, seed, stream_id);
 }
 void sweep_scales(cudaStream_t st, int r, int D, int ku, const double* U, const double* lam, double tol,
                   double floor_rel, double* Us, double* L, double* discarded, int* rank) {
+  count_launches(1);
   sweep_scales_kernel<<<1, 256, 0, st>>>(r, D, ku, U, lam, tol, floor_rel, Us, L, discarded, rank);
 }
 void left_weight_env(cudaStream_t st, const Chain& f, const Chain& w, int nsites, int max_bond, double* out,
                      int ldo, double* work) {
+  count_launches(1);
   left_weight_env_kernel<<<1, 256, 0, st>>>(f, w, nsites, max_bond, out, ldo, work);
 }
 void right_ones_env(cudaStream_t st, const Chain& f, int n0, int max_bond, double* out, double* work) {
+  count_launches(1);
   right_ones_env_kernel<<<1, 256, 0, st>>>(f, n0, max_bond, out, work);
 }
 void eval_points(cudaStream_t st, const Chain& f, int npts, const unsigned char* bits, int max_bond, double* out,
                  double* work) {
   if (npts <= 0) return;
   const int warps_per_block = 8;
+  count_launches(1);
   eval_points_kernel<<<(npts + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
       f, npts, bits, max_bond, out, work);
 }
 void check_finite(cudaStream_t st, const double* p, size_t n, int* flag) {
+  if (n) count_launches(1);
   if (n) finite_kernel<<<grid_for(n), 256, 0, st>>>(p, n, flag);
 }
 

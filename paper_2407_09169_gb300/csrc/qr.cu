@@ -115,6 +115,7 @@ void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void*
     cudaMemsetAsync(status, 0xff, sizeof(int), st);
     return;
   }
+  count_launches(1);
   if (prec_bits == 32)
     qr_thin_kernel<float><<<1, QR_THREADS, 0, st>>>(m, n, A, Qout, (float*)work, status);
   else
