@@ -214,7 +214,7 @@ def run_mine(args, rank, world, local_rank):
     ctx = q.qtt_init(p, stream=stream.cuda_stream)
     for _ in range(args.warmup):
         ctx.step(1)
-    launches0 = ctx.observe(q.OBS_TIMINGS)[12]
+    launches0 = ctx.observe(q.OBS_TIMINGS)[15]
     barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
@@ -228,7 +228,7 @@ def run_mine(args, rank, world, local_rank):
     clocks = sampler.stop()
     barrier()
     ms = e0.elapsed_time(e1)
-    launches = ctx.observe(q.OBS_TIMINGS)[12] - launches0
+    launches = ctx.observe(q.OBS_TIMINGS)[15] - launches0
     ms_max = max_over_ranks(ms)
     value = args.steps * world / (ms_max / 1e3)
     scal = ctx.scalars()
@@ -249,7 +249,7 @@ def run_mine(args, rank, world, local_rank):
         cp.step(nprof)
         t1 = cp.observe(q.OBS_TIMINGS)
         cp.close()
-        names = ["gemm_f64", "qr_thin", "eig_sym", "other"]
+        names = ["gemm_f64", "qr_thin", "eig_sym", "other", "gemm_tc"]
         classes = {}
         for c, nm in enumerate(names):
             launches_c = t1[3 * c] - t0[3 * c]

@@ -95,7 +95,8 @@ typedef enum {
                             (as doubles 0/1, MSB first per dimension), cap = n * N;
                             the first n entries are overwritten with the values */
   QTT_OBS_NVPP = 5,      /* 1 value: number of variables parameterising f (Eq. MPSdofs) */
-  QTT_OBS_TIMINGS = 6    /* 13 values: for the kernel classes GEMM, QR, eigensolver, other:
+  QTT_OBS_TIMINGS = 6    /* 16 values: for the kernel classes FP64 GEMM, QR, eigensolver,
+                            other, tensor-core GEMM (incl. operand packing):
                             launches, total ms, algorithmic flops, recorded with CUDA events
                             only when the environment variable QTT_KERNEL_TIMING=1 was set
                             at qtt_init (zeros otherwise); then the number of kernels the
@@ -158,6 +159,17 @@ const char* qtt_version(void);
  * Returns QTT_EINVAL for an unknown `which`, invalid params or cap too small.
  * ------------------------------------------------------------------- */
 qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, int64_t cap, int64_t* written);
+
+/* Device self-checks of the kernel families on seeded random operands
+ * (needs a GPU; no context).  The paper has no counterpart: these check the
+ * implementation, not the method.  Values written (then one error-flag word):
+ *   0  tensor-core GEMM: for 7 shapes x 4 modes (BF16X3, TF32, TF32X3, BF16)
+ *      max |C_tc - C_fp64| / max |C_fp64| (-1 when a shape is not supported)
+ *   1  Householder QR: for 4 shapes x (FP64, FP32) the orthogonality
+ *      max |Q^T Q - I| and the projection residual ||Y - Q Q^T Y|| / ||Y||
+ *   2  eigensolver: for 5 sizes x (FP64, FP32) max |G U - U diag(lam)| / max |G|,
+ *      max |U^T U - I| and 1 if the eigenvalues are not descending */
+qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written);
 
 #ifdef __cplusplus
 }

@@ -88,7 +88,9 @@ def load_library(path: str | None = None):
     lib.qtt_version.argtypes = []
     lib.qtt_version.restype = C.c_char_p
     lib.qtt_host_dense.argtypes = [P(QttParams), C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
-    for fn in ("qtt_init", "qtt_step", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense"):
+    lib.qtt_selftest.argtypes = [C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
+    for fn in ("qtt_init", "qtt_step", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense",
+               "qtt_selftest"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -174,7 +176,7 @@ class Context:
         if out is None:
             if cap is None:
                 cap = {OBS_SCALARS: 12, OBS_BONDS: self.N + 1, OBS_DENSE: 2 ** self.N, OBS_MEANS: 3 * 2 ** Kx,
-                       OBS_NVPP: 1, OBS_TIMINGS: 13}[what]
+                       OBS_NVPP: 1, OBS_TIMINGS: 16}[what]
             out = np.zeros(cap, dtype=np.float64)
         written = C.c_int64(0)
         _check(load_library().qtt_observe(self._handle(), int(what), out.ctypes.data_as(C.POINTER(C.c_double)),
@@ -265,4 +267,13 @@ def qtt_host_dense(params: dict, which: int, cap: int) -> np.ndarray:
     _check(lib.qtt_host_dense(C.byref(cp), int(which), out.ctypes.data_as(C.POINTER(C.c_double)), cap,
                               C.byref(written)), None)
     del keep
+    return out[: written.value]
+
+
+def qtt_selftest(which: int, cap: int = 4096) -> np.ndarray:
+    """Device self-checks of the kernel families (see include/qtt_fp.h)."""
+    lib = load_library()
+    out = np.zeros(cap, dtype=np.float64)
+    written = C.c_int64(0)
+    _check(lib.qtt_selftest(int(which), out.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(written)), None)
     return out[: written.value]

@@ -18,6 +18,10 @@
 #include "host_tt.hpp"
 #include "model.hpp"
 
+namespace qtt {
+std::vector<double> run_selftest(int which);
+}
+
 struct qtt_ctx {
   std::unique_ptr<qtt::Engine> eng;
   std::string err;
@@ -484,6 +488,22 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
       return put(std::vector<double>(m.f0.r.begin(), m.f0.r.end()), out, cap, written);
     }
     return QTT_EINVAL;
+  } catch (const std::exception& ex) {
+    g_init_err = ex.what();
+    return classify(g_init_err);
+  }
+}
+
+qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written) {
+  if (written) *written = 0;
+  try {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      g_init_err = "CUDA: no usable CUDA device";
+      return QTT_ECUDA;
+    }
+    return put(qtt::run_selftest(which), out, cap, written);
   } catch (const std::exception& ex) {
     g_init_err = ex.what();
     return classify(g_init_err);

@@ -28,6 +28,7 @@
 // chain, step 2 keeps identity cores (no QR) up to the centre and writes the
 // centre core as T W, so the whole stage is a chain of exact contractions.
 #include "engine.hpp"
+#include "gemm_tc.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -88,7 +89,7 @@ struct KernelTimer {
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
-enum { TM_GEMM = 0, TM_QR = 1, TM_EIG = 2, TM_OTHER = 3 };
+enum { TM_GEMM = 0, TM_QR = 1, TM_EIG = 2, TM_OTHER = 3, TM_TC = 4 };
 
 struct TimeScope {
   KernelTimer* t;
@@ -124,12 +125,15 @@ Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
   kphi_ = p.Kphi();
   exact_ = p.exact != 0;
   prec_bits_ = (p.precision == 0) ? 64 : 32;
+  // contraction arithmetic: FP32 -> 3-pass TF32, TF32 -> 1-pass TF32, BF16X3 -> 3-pass BF16
+  tc_mode_ = p.precision == 1 ? TC_TF32X3 : p.precision == 2 ? TC_TF32 : p.precision == 3 ? TC_BF16X3 : -1;
   timer_ = new KernelTimer();
   if (const char* e = std::getenv("QTT_KERNEL_TIMING")) timer_->on = (e[0] == '1');
 }
 
 Engine::~Engine() {
   for (void* a : allocs_) cudaFree(a);
+  if (pack_ws_) cudaFree(pack_ws_);
   delete timer_;
 }
 
@@ -202,10 +206,36 @@ void Engine::upload_op(DevOp& op, const TT& t) {
   QTT_CUDA(cudaMemcpy(op.data, h.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
 }
 
-void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
-                  OutView C) {
+void Engine::gemm64(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
+                    OutView C) {
   TimeScope ts(timer_, TM_GEMM, st_, 2.0 * M * (double)N * K * outer * inner);
   gemm_f64(st_, M, N, K, outer, inner, alpha, A, B, beta, C, ws_, ws_elems_);
+}
+
+void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
+                  OutView C) {
+  if (tc_mode_ < 0) {
+    gemm64(M, N, K, outer, inner, alpha, A, B, beta, C);
+    return;
+  }
+  const size_t need = tc_workspace_bytes(M, N, K, (long long)outer * inner, tc_mode_);
+  if (need > pack_bytes_) {  // grows during the first step only (static shapes)
+    QTT_CUDA(cudaStreamSynchronize(st_));
+    if (pack_ws_) QTT_CUDA(cudaFree(pack_ws_));
+    pack_ws_ = nullptr;
+    const size_t bytes = need + need / 4;
+    if (cudaMalloc(&pack_ws_, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      pack_ws_ = nullptr;
+      pack_bytes_ = 0;
+      throw std::runtime_error("ENOMEM: tensor-core packing workspace");
+    }
+    pack_bytes_ = bytes;
+  }
+  TimeScope ts(timer_, TM_TC, st_, 2.0 * M * (double)N * K * outer * inner);
+  if (!gemm_tc(st_, tc_mode_, M, N, K, outer, inner, alpha, A, B, beta, C, pack_ws_, pack_bytes_, ws_, ws_elems_,
+               status_ + 2))
+    throw std::runtime_error("EINVAL: tensor-core GEMM shape outside the supported grid");
 }
 
 static MatView mv(const double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
@@ -231,7 +261,6 @@ void Engine::init() {
   std::string why = validate(p_);
   if (!why.empty()) throw std::runtime_error("EINVAL: " + why);
   if (N_ > kMaxSites) throw std::runtime_error("EINVAL: too many sites");
-  if (p_.precision != 0) throw std::runtime_error("EINVAL: reduced-precision contraction forms are not built yet");
   model_ = build_model(p_);
   const int N = N_;
   // static bond profiles
@@ -360,7 +389,7 @@ void Engine::cond_means(const DevMps& f, double* v) {
 void Engine::make_hfirst(const DevMps& f, double* v, double* hf) {
   // first x core of diag(<Phi_a>(x)): hf[a][s][b'] = sum_b v[a][b] A_kphi[b][s][b']
   const int bl = D_[kphi_], br = D_[kphi_ + 1];
-  gemm(2, 2 * br, bl, 1, 1, 1.0, mv(v, bl, 1), mv(f.core(kphi_), 2 * br, 1), 0.0, ov(hf, 2 * br, 1));
+  gemm64(2, 2 * br, bl, 1, 1, 1.0, mv(v, bl, 1), mv(f.core(kphi_), 2 * br, 1), 0.0, ov(hf, 2 * br, 1));
 }
 
 void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr) {
@@ -513,7 +542,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out) {
       fill_identity_right(st_, out.core(n), Dn1);
       cur = mi;
     } else {
-      gemm(rl, rl, 2 * Dn1, 1, 1, 1.0, mv(M, 2LL * Dn1, 1), mv(M, 1, 2LL * Dn1), 0.0, ov(G_, rl, 1));
+      gemm64(rl, rl, 2 * Dn1, 1, 1, 1.0, mv(M, 2LL * Dn1, 1), mv(M, 1, 2LL * Dn1), 0.0, ov(G_, rl, 1));
       const int ku = std::min(rl, Dn);
       {
         TimeScope ts(timer_, TM_EIG, st_);
@@ -606,13 +635,18 @@ void Engine::step(int nsteps) {
 
 int Engine::check_status(std::string& msg) {
   check_finite(st_, f_.data, f_.total, status_ + 1);
-  int h[2] = {0, 0};
+  int h[3] = {0, 0, 0};
   double dis = 0;
   QTT_CUDA(cudaMemcpyAsync(h, status_, sizeof(h), cudaMemcpyDeviceToHost, st_));
   QTT_CUDA(cudaMemcpyAsync(&dis, disc_, sizeof(double), cudaMemcpyDeviceToHost, st_));
   QTT_CUDA(cudaStreamSynchronize(st_));
   QTT_CUDA(cudaGetLastError());
   discarded_last_ = dis;
+  if (h[2]) {
+    msg = "a tensor-core GEMM gave up waiting on a pipeline barrier (code " + std::to_string(h[2]) + ")";
+    QTT_CUDA(cudaMemsetAsync(status_ + 2, 0, sizeof(int), st_));
+    return 5;  // QTT_ETIMEOUT
+  }
   if (h[1]) {
     msg = "non-finite value in the state after step " + std::to_string(steps_);
     return 6;  // QTT_ENAN
@@ -637,8 +671,8 @@ void Engine::xgram(const DevMps& f, double* E) {
   double* nxt = obsB_;
   for (int n = N_ - 1; n >= kphi_; --n) {
     const int bl = f.b[n], br = f.b[n + 1];
-    gemm(2 * bl, br, br, 1, 1, 1.0, mv(f.core(n), br, 1), mv(cur, br, 1), 0.0, ov(obsX_, br, 1));
-    gemm(bl, bl, 2 * br, 1, 1, 1.0, mv(obsX_, 2LL * br, 1), mv(f.core(n), 1, 2LL * br), 0.0, ov(nxt, bl, 1));
+    gemm64(2 * bl, br, br, 1, 1, 1.0, mv(f.core(n), br, 1), mv(cur, br, 1), 0.0, ov(obsX_, br, 1));
+    gemm64(bl, bl, 2 * br, 1, 1, 1.0, mv(obsX_, 2LL * br, 1), mv(f.core(n), 1, 2LL * br), 0.0, ov(nxt, bl, 1));
     std::swap(cur, nxt);
   }
   QTT_CUDA(cudaMemcpyAsync(E, cur, sizeof(double) * f.b[kphi_] * f.b[kphi_], cudaMemcpyDeviceToDevice, st_));
@@ -654,9 +688,9 @@ void Engine::scalars(double out[12]) {
   for (int w = 0; w < 6; ++w) left_weight_env(st_, fc, wphi_[w].chain(), kphi_, max_bond_, V + (size_t)w * b, b, envw_);
   right_ones_env(st_, fc, kphi_, max_bond_, u, envw_);
   xgram(f_, E);
-  gemm(6, 1, b, 1, 1, 1.0, mv(V, b, 1), mv(u, 1, 1), 0.0, ov(res, 1, 1));                 // <w> sums
-  gemm(1, b, b, 1, 1, 1.0, mv(V + b, b, 1), mv(E, b, 1), 0.0, ov(res + 6, b, 1));           // v1^T E
-  gemm(1, 1, b, 1, 1, 1.0, mv(res + 6, b, 1), mv(V + 2 * (size_t)b, 1, 1), 0.0, ov(res + 6 + b, 1, 1));
+  gemm64(6, 1, b, 1, 1, 1.0, mv(V, b, 1), mv(u, 1, 1), 0.0, ov(res, 1, 1));                 // <w> sums
+  gemm64(1, b, b, 1, 1, 1.0, mv(V + b, b, 1), mv(E, b, 1), 0.0, ov(res + 6, b, 1));           // v1^T E
+  gemm64(1, 1, b, 1, 1, 1.0, mv(res + 6, b, 1), mv(V + 2 * (size_t)b, 1, 1), 0.0, ov(res + 6 + b, 1, 1));
   double h[6];
   double m12 = 0;
   QTT_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st_));
@@ -694,7 +728,7 @@ void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_r
   QTT_CUDA(cudaMemcpyAsync(a, head, sizeof(double) * R * bond, cudaMemcpyDeviceToDevice, st_));
   for (int n = n0; n < N_; ++n) {
     const int br = f.b[n + 1];
-    gemm((int)R, 2 * br, bond, 1, 1, 1.0, mv(a, bond, 1), mv(f.core(n), 2LL * br, 1), 0.0, ov(b, 2LL * br, 1));
+    gemm64((int)R, 2 * br, bond, 1, 1, 1.0, mv(a, bond, 1), mv(f.core(n), 2LL * br, 1), 0.0, ov(b, 2LL * br, 1));
     std::swap(a, b);
     R *= 2;
     bond = br;
@@ -755,8 +789,8 @@ double Engine::overlap(const Engine& o) {
   fill_value(st_, e0, 1, 1.0);
   for (int n = 0; n < N_; ++n) {
     const int ba = A.b[n], bb = B.b[n], ba2 = A.b[n + 1], bb2 = B.b[n + 1];
-    gemm(ba, 2 * bb2, bb, 1, 1, 1.0, mv(e0, bb, 1), mv(B.core(n), 2LL * bb2, 1), 0.0, ov(x, 2LL * bb2, 1));
-    gemm(ba2, bb2, 2 * ba, 1, 1, 1.0, mv(A.core(n), 1, ba2), mv(x, bb2, 1), 0.0, ov(e1, bb2, 1));
+    gemm64(ba, 2 * bb2, bb, 1, 1, 1.0, mv(e0, bb, 1), mv(B.core(n), 2LL * bb2, 1), 0.0, ov(x, 2LL * bb2, 1));
+    gemm64(ba2, bb2, 2 * ba, 1, 1, 1.0, mv(A.core(n), 1, ba2), mv(x, bb2, 1), 0.0, ov(e1, bb2, 1));
     std::swap(e0, e1);
   }
   double r = 0;
@@ -783,7 +817,7 @@ void Engine::upload_state(const std::vector<double>& cores) {
 
 std::vector<double> Engine::timings() const {
   std::vector<double> t;
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < 5; ++c) {
     t.push_back(timer_->launches[c]);
     t.push_back(timer_->ms[c]);
     t.push_back(timer_->flops[c]);

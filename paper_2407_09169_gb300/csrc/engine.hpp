@@ -90,7 +90,10 @@ class Engine {
   void alloc_mps(DevMps& m, const std::vector<int>& bonds);
   void upload_op(DevOp& op, const TT& t);
   void upload_tt_mps(DevMps& m, const TT& t, const std::vector<int>& bonds);
+  // Contraction in the context's precision form (tensor cores for the reduced forms).
   void gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C);
+  // FP64 product (Gram matrices, norms, masses, observables).
+  void gemm64(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C);
   void cond_means(const DevMps& f, double* v);
   void make_hfirst(const DevMps& f, double* v, double* hf);
   void sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr);
@@ -123,6 +126,9 @@ class Engine {
   double *disc_ = nullptr, *obsA_ = nullptr, *obsB_ = nullptr, *obsX_ = nullptr;
   int *status_ = nullptr, *ranks_ = nullptr;
   size_t ws_elems_ = 0;
+  void* pack_ws_ = nullptr;
+  size_t pack_bytes_ = 0;
+  int tc_mode_ = -1;
   int max_bond_ = 1;
   unsigned long long stage_counter_ = 0;
   double time_ = 0.0;

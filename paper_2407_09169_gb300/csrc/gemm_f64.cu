@@ -125,6 +125,14 @@ __global__ void scale_out_kernel(int M, int N, int inner, int batch, double beta
 }
 }  // namespace
 
+void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int batch, double alpha, const double* ws,
+                   double beta, OutView C) {
+  const long long total = (long long)M * N * batch;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, inner, splitk, batch, alpha, ws, beta, C);
+}
+
 int gemm_split_k(int M, int N, int K, int batch) {
   const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
   if (tiles >= 152 || K < 4 * BK) return 1;

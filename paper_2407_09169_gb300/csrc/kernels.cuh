@@ -38,6 +38,9 @@ struct Chain {
 void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double alpha, MatView A,
               MatView B, double beta, OutView C, double* ws, size_t ws_elems);
 int gemm_split_k(int M, int N, int K, int batch);
+// C = alpha * sum_k ws[b][k] + beta * C: the fixed-order reduction of split-K partial tiles.
+void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int batch, double alpha, const double* ws,
+                   double beta, OutView C);
 
 // Thin Householder QR of an m x n row-major matrix (m >= n): Q (m x n,
 // row-major) overwrites Qout.  Computed in float (prec_bits 32) or double;

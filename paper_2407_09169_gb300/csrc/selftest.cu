@@ -1,0 +1,191 @@
+// Device self-checks behind qtt_selftest: each kernel family against an
+// independent computation on seeded random operands.
+#include <cmath>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "gemm_tc.cuh"
+#include "kernels.cuh"
+
+namespace qtt {
+
+namespace {
+struct DBuf {
+  double* p = nullptr;
+  explicit DBuf(size_t n) {
+    if (cudaMalloc(&p, (n + 16) * sizeof(double)) != cudaSuccess) throw std::runtime_error("ENOMEM: selftest");
+  }
+  ~DBuf() { cudaFree(p); }
+};
+
+std::vector<double> down(const double* d, size_t n) {
+  std::vector<double> h(n);
+  if (cudaMemcpy(h.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    throw std::runtime_error("CUDA error: selftest copy");
+  return h;
+}
+}  // namespace
+
+// which = 0: tensor-core GEMM modes against the FP64 GEMM.  For every case
+// and mode (BF16X3, TF32, TF32X3, BF16) one value: max |C_tc - C_64| / max |C_64|.
+// which = 1: QR (FP64 and FP32): ||Q^T Q - I||_max and ||Q Q^T Y - Y|| / ||Y|| per case.
+// which = 2: eigensolver (FP64 and FP32): ||G U - U diag(lam)|| / ||G|| and ||U^T U - I||_max.
+std::vector<double> run_selftest(int which) {
+  cudaStream_t st = nullptr;
+  std::vector<double> out;
+  int* err = nullptr;
+  if (cudaMalloc(&err, 16) != cudaSuccess) throw std::runtime_error("ENOMEM: selftest");
+  cudaMemset(err, 0, 16);
+  if (which == 0) {
+    struct Case {
+      int M, N, K, outer, inner;
+      bool ta, tb;
+      double beta;
+    };
+    const Case cases[] = {
+        {128, 128, 64, 1, 1, false, false, 0.0},  {300, 136, 200, 1, 1, false, false, 0.0},
+        {130, 70, 100, 3, 2, true, false, 0.0},  {272, 136, 5000, 1, 1, false, true, 0.0},
+        {256, 256, 128, 2, 1, false, false, 0.5}, {136, 160, 272, 1, 1, true, true, 1.0},
+        {17, 300, 40, 4, 1, false, false, 0.0}};
+    const size_t ws_elems = (size_t)32 << 20;
+    DBuf ws(ws_elems);
+    size_t pack_bytes = (size_t)256 << 20;
+    void* pack = nullptr;
+    if (cudaMalloc(&pack, pack_bytes) != cudaSuccess) throw std::runtime_error("ENOMEM: selftest pack");
+    unsigned long long seed = 12345;
+    for (const Case& c : cases) {
+      const long long batch = (long long)c.outer * c.inner;
+      const size_t asz = (size_t)c.M * c.K * batch, bsz = (size_t)c.K * c.N * batch, csz = (size_t)c.M * c.N * batch;
+      DBuf A(asz), B(bsz), C0(csz), C1(csz);
+      fill_gaussian(st, A.p, asz, 1.0, seed++, 1);
+      fill_gaussian(st, B.p, bsz, 1.0, seed++, 2);
+      MatView av, bv;
+      av.p = A.p;
+      av.rs = c.ta ? 1 : c.K;
+      av.cs = c.ta ? c.M : 1;
+      av.si = (long long)c.M * c.K;
+      av.so = av.si * c.inner;
+      bv.p = B.p;
+      bv.rs = c.tb ? 1 : c.N;
+      bv.cs = c.tb ? c.K : 1;
+      bv.si = (long long)c.K * c.N;
+      bv.so = bv.si * c.inner;
+      for (int mode = 0; mode < 4; ++mode) {
+        fill_gaussian(st, C0.p, csz, 1.0, 777, 3);
+        fill_gaussian(st, C1.p, csz, 1.0, 777, 3);
+        OutView c0, c1;
+        c0.p = C0.p;
+        c0.rs = c.N;
+        c0.cs = 1;
+        c0.si = (long long)c.M * c.N;
+        c0.so = c0.si * c.inner;
+        c1 = c0;
+        c1.p = C1.p;
+        gemm_f64(st, c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, c0, ws.p, ws_elems);
+        const int tc_mode[4] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16};
+        if (!gemm_tc(st, tc_mode[mode], c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, c1, pack, pack_bytes,
+                     ws.p, ws_elems, err)) {
+          out.push_back(-1.0);
+          continue;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest gemm");
+        std::vector<double> h0 = down(C0.p, csz), h1 = down(C1.p, csz);
+        double mx = 0, md = 0;
+        for (size_t i = 0; i < csz; ++i) {
+          mx = std::fmax(mx, std::fabs(h0[i]));
+          md = std::fmax(md, std::fabs(h0[i] - h1[i]));
+        }
+        out.push_back(md / (mx > 0 ? mx : 1.0));
+      }
+    }
+    cudaFree(pack);
+  } else if (which == 1) {
+    const int shapes[][2] = {{272, 136}, {64, 33}, {256, 256}, {40, 1}};
+    for (auto& sh : shapes) {
+      const int m = sh[0], n = sh[1];
+      DBuf Y((size_t)m * n), Q((size_t)m * n), W((size_t)2 * m * n + n + 64);
+      fill_gaussian(st, Y.p, (size_t)m * n, 1.0, 99 + m, 5);
+      for (int prec : {64, 32}) {
+        qr_thin(st, m, n, Y.p, Q.p, W.p, prec, err);
+        if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest qr");
+        std::vector<double> y = down(Y.p, (size_t)m * n), q = down(Q.p, (size_t)m * n);
+        double orth = 0;
+        for (int a = 0; a < n; ++a)
+          for (int b2 = 0; b2 < n; ++b2) {
+            double s = 0;
+            for (int i = 0; i < m; ++i) s += q[(size_t)i * n + a] * q[(size_t)i * n + b2];
+            orth = std::fmax(orth, std::fabs(s - (a == b2 ? 1.0 : 0.0)));
+          }
+        // projection residual ||Y - Q Q^T Y||_F / ||Y||_F
+        double num = 0, den = 0;
+        for (int c = 0; c < n; ++c) {
+          std::vector<double> coef(n, 0.0);
+          for (int a = 0; a < n; ++a)
+            for (int i = 0; i < m; ++i) coef[a] += q[(size_t)i * n + a] * y[(size_t)i * n + c];
+          for (int i = 0; i < m; ++i) {
+            double r = y[(size_t)i * n + c];
+            for (int a = 0; a < n; ++a) r -= q[(size_t)i * n + a] * coef[a];
+            num += r * r;
+            den += y[(size_t)i * n + c] * y[(size_t)i * n + c];
+          }
+        }
+        out.push_back(orth);
+        out.push_back(std::sqrt(num / den));
+      }
+    }
+  } else if (which == 2) {
+    const int sizes[] = {136, 64, 7, 1, 200};
+    for (int n : sizes) {
+      // G = X X^T with a graded spectrum (columns scaled by 10^(-6 i / n))
+      std::vector<double> x((size_t)n * n);
+      DBuf X((size_t)n * n), G((size_t)n * n), U((size_t)n * n), L(n), W((size_t)3 * n * n + 3 * n + 64);
+      fill_gaussian(st, X.p, (size_t)n * n, 1.0, 4242 + n, 6);
+      if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest eig");
+      x = down(X.p, (size_t)n * n);
+      std::vector<double> g((size_t)n * n, 0.0);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          double s = 0;
+          for (int k = 0; k < n; ++k) s += x[(size_t)i * n + k] * x[(size_t)j * n + k] * std::pow(10.0, -6.0 * k / n);
+          g[(size_t)i * n + j] = s;
+        }
+      if (cudaMemcpy(G.p, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        throw std::runtime_error("CUDA error: selftest eig upload");
+      for (int prec : {64, 32}) {
+        eig_sym(st, n, n, G.p, U.p, L.p, W.p, prec, err);
+        if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest eig");
+        std::vector<double> u = down(U.p, (size_t)n * n), lam = down(L.p, n);
+        double gn = 0, res = 0, orth = 0, order = 0;
+        for (double v : g) gn = std::fmax(gn, std::fabs(v));
+        for (int c = 0; c < n; ++c) {
+          if (c > 0 && lam[c] > lam[c - 1]) order = 1;
+          for (int i = 0; i < n; ++i) {
+            double s = 0;
+            for (int k = 0; k < n; ++k) s += g[(size_t)i * n + k] * u[(size_t)k * n + c];
+            res = std::fmax(res, std::fabs(s - lam[c] * u[(size_t)i * n + c]));
+          }
+          for (int c2 = 0; c2 < n; ++c2) {
+            double s = 0;
+            for (int k = 0; k < n; ++k) s += u[(size_t)k * n + c] * u[(size_t)k * n + c2];
+            orth = std::fmax(orth, std::fabs(s - (c == c2 ? 1.0 : 0.0)));
+          }
+        }
+        out.push_back(res / gn);
+        out.push_back(orth);
+        out.push_back(order);
+      }
+    }
+  } else {
+    cudaFree(err);
+    throw std::runtime_error("EINVAL: unknown selftest");
+  }
+  int herr[4] = {0, 0, 0, 0};
+  cudaMemcpy(herr, err, 16, cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  if (cudaGetLastError() != cudaSuccess) throw std::runtime_error("CUDA error: selftest launch");
+  out.push_back((double)herr[0]);
+  return out;
+}
+
+}  // namespace qtt

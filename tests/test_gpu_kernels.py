@@ -1,0 +1,47 @@
+"""Kernel families on the GPU, through qtt_selftest (C ABI): tensor-core GEMM
+modes against the FP64 GEMM, Householder QR, and the eigensolver, each on
+seeded random operands including ragged, batched, transposed and split-K shapes."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+pkg = pytest.importorskip("paper_2407_09169_gb300")
+
+MODES = ["bf16x3", "tf32", "tf32x3", "bf16"]
+# per-mode bound on max|C_tc - C_fp64| / max|C_fp64|: 3 * 2^-17 for the split
+# forms (dropped lo*lo term and the hi/lo representation), 2^-10 / 2^-7 for the
+# single-pass forms, with room for FP32 accumulation
+TOL = {"bf16x3": 6e-5, "tf32": 4e-3, "tf32x3": 5e-6, "bf16": 3e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib(gpu_available):
+    from paper_2407_09169_gb300 import build
+    build.build()
+    return pkg.load_library()
+
+
+def test_tensor_core_gemm_modes():
+    v = pkg.qtt_selftest(0)
+    assert v[-1] == 0, "a bounded wait gave up"
+    errs = np.array(v[:-1]).reshape(-1, 4)
+    print("\n".join(" ".join(f"{m}={e:.2e}" for m, e in zip(MODES, row)) for row in errs))
+    for row in errs:
+        for m, e in zip(MODES, row):
+            assert 0 <= e <= TOL[m], (m, e)
+
+
+def test_householder_qr():
+    v = np.array(pkg.qtt_selftest(1)[:-1]).reshape(-1, 2, 2)  # shape, precision, (orth, resid)
+    for case in v:
+        (o64, r64), (o32, r32) = case
+        assert o64 < 1e-13 and r64 < 1e-13
+        assert o32 < 2e-5 and r32 < 2e-5
+
+
+def test_eigensolver():
+    v = np.array(pkg.qtt_selftest(2)[:-1]).reshape(-1, 2, 3)  # size, precision, (res, orth, order)
+    for case in v:
+        (r64, o64, ord64), (r32, o32, ord32) = case
+        assert r64 < 1e-12 and o64 < 1e-12 and ord64 == 0
+        assert r32 < 5e-5 and o32 < 5e-5 and ord32 == 0
