@@ -168,7 +168,10 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
  *   1  Householder QR: for 4 shapes x (FP64, FP32) the orthogonality
  *      max |Q^T Q - I| and the projection residual ||Y - Q Q^T Y|| / ||Y||
  *   2  eigensolver: for 5 sizes x (FP64, FP32) max |G U - U diag(lam)| / max |G|,
- *      max |U^T U - I| and 1 if the eigenvalues are not descending */
+ *      max |U^T U - I| and 1 if the eigenvalues are not descending
+ *   3  accumulation bias of the tensor-core GEMM: positive operands, K = 32,
+ *      256, 2048, modes (TF32X3, BF16X3), accumulation (one FP32 accumulator,
+ *      FP64 sum of per-k-block accumulators): mean signed and max relative error */
 qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written);
 
 #ifdef __cplusplus

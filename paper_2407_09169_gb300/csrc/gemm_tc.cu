@@ -429,7 +429,8 @@ size_t tc_workspace_bytes(int M, int N, int K, long long batch, int mode) {
 }
 
 bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B,
-             double beta, OutView C, void* pack_ws, size_t pack_bytes, double* ws, size_t ws_elems, int* err) {
+             double beta, OutView C, void* pack_ws, size_t pack_bytes, double* ws, size_t ws_elems, int* err,
+             int max_kb_per_split) {
   if (M <= 0 || N <= 0 || K <= 0 || outer <= 0 || inner <= 0) return false;
   load_encode();
   const long long batch = (long long)outer * inner;
@@ -487,6 +488,9 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     if (ws == nullptr || (size_t)splitk * batch * (size_t)M * N > ws_elems) splitk = 1;
   }
   int kbps = (kblocks + splitk - 1) / splitk;
+  if (max_kb_per_split > 0 && kbps > max_kb_per_split && ws != nullptr &&
+      (size_t)((kblocks + max_kb_per_split - 1) / max_kb_per_split) * batch * (size_t)M * N <= ws_elems)
+    kbps = max_kb_per_split;
   splitk = (kblocks + kbps - 1) / kbps;
   if ((long long)splitk * batch > 65535) {
     splitk = 1;

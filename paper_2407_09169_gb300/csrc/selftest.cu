@@ -176,6 +176,52 @@ std::vector<double> run_selftest(int which) {
         out.push_back(order);
       }
     }
+  } else if (which == 3) {
+    // accumulation bias: positive operands, signed mean of (C_tc - C_64) / C_64
+    const size_t ws_elems = (size_t)64 << 20;
+    DBuf ws(ws_elems);
+    size_t pack_bytes = (size_t)128 << 20;
+    void* pack = nullptr;
+    if (cudaMalloc(&pack, pack_bytes) != cudaSuccess) throw std::runtime_error("ENOMEM: selftest pack");
+    const int Ks[3] = {32, 256, 2048};
+    for (int K : Ks) {
+      const int M = 256, N = 128;
+      DBuf A((size_t)M * K), B((size_t)K * N), C0((size_t)M * N), C1((size_t)M * N);
+      fill_gaussian(st, A.p, (size_t)M * K, 1.0, 31 + K, 7);
+      fill_gaussian(st, B.p, (size_t)K * N, 1.0, 37 + K, 8);
+      std::vector<double> ha = down(A.p, (size_t)M * K), hb = down(B.p, (size_t)K * N);
+      for (double& v : ha) v = std::fabs(v);
+      for (double& v : hb) v = std::fabs(v);
+      cudaMemcpy(A.p, ha.data(), ha.size() * 8, cudaMemcpyHostToDevice);
+      cudaMemcpy(B.p, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice);
+      MatView av, bv;
+      av.p = A.p; av.rs = K; av.cs = 1;
+      bv.p = B.p; bv.rs = N; bv.cs = 1;
+      OutView c0, c1;
+      c0.p = C0.p; c0.rs = N; c0.cs = 1;
+      c1 = c0; c1.p = C1.p;
+      gemm_f64(st, M, N, K, 1, 1, 1.0, av, bv, 0.0, c0, ws.p, ws_elems);
+      const int modes[2] = {TC_TF32X3, TC_BF16X3};
+      for (int mode : modes)
+        for (int chunk : {0, 1}) {
+          if (!gemm_tc(st, mode, M, N, K, 1, 1, 1.0, av, bv, 0.0, c1, pack, pack_bytes, ws.p, ws_elems, err, chunk)) {
+            out.push_back(-1.0);
+            out.push_back(-1.0);
+            continue;
+          }
+          cudaStreamSynchronize(st);
+          std::vector<double> h0 = down(C0.p, (size_t)M * N), h1 = down(C1.p, (size_t)M * N);
+          double mean = 0, mx = 0;
+          for (size_t i = 0; i < h0.size(); ++i) {
+            const double r = (h1[i] - h0[i]) / h0[i];
+            mean += r;
+            mx = std::fmax(mx, std::fabs(r));
+          }
+          out.push_back(mean / (double)h0.size());
+          out.push_back(mx);
+        }
+    }
+    cudaFree(pack);
   } else {
     cudaFree(err);
     throw std::runtime_error("EINVAL: unknown selftest");
