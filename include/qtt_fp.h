@@ -128,6 +128,22 @@ qtt_status qtt_compare(qtt_ctx* a, qtt_ctx* b, double* rel_l2);
 qtt_status qtt_save(qtt_ctx* ctx, const char* path);
 qtt_status qtt_load(qtt_ctx* ctx, const char* path);
 
+/* Allocation-free variant of qtt_observe(ctx, QTT_OBS_POINTS, ...), same
+ * arguments and result: inout holds n groups of N index bits (doubles 0/1,
+ * most significant bit first per dimension), cap = n * N, and the first n
+ * entries receive f at those points.  The paper has no counterpart; this
+ * serves callers that must not allocate device memory during the call (for
+ * example while a stream is being captured into a CUDA graph, or in a
+ * per-step monitoring loop that cannot afford cudaFree's implicit device
+ * synchronisation).  The query, scratch and results use one 4 MiB device
+ * array fixed at compile time and shared by the whole process: at most
+ * floor((4 MiB - 768) / (8 + 8 N + 16 (chi_max + oversample))) points per
+ * call; larger requests return QTT_EINVAL with the limit in the message.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  Calls
+ * whose work overlaps on the GPU race on the shared array: serialise them. */
+qtt_status qtt_observe_points_noalloc(qtt_ctx* ctx, double* inout, int64_t cap, int64_t* written);
+
 void qtt_destroy(qtt_ctx* ctx);
 
 /* Last error message of ctx (or of the last failed qtt_init when ctx is NULL). */

@@ -494,6 +494,29 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
   }
 }
 
+qtt_status qtt_observe_points_noalloc(qtt_ctx* ctx, double* inout, int64_t cap, int64_t* written) {
+  if (written) *written = 0;
+  if (!ctx || !ctx->eng || !inout) return QTT_EINVAL;
+  try {
+    const int N = ctx->eng->N();
+    if (cap < N || cap % N != 0) {
+      ctx->err = "EINVAL: cap must be a positive multiple of N";
+      return QTT_EINVAL;
+    }
+    const int64_t npts = cap / N;
+    if (npts > 0x7fffffff) {
+      ctx->err = "EINVAL: too many points";
+      return QTT_EINVAL;
+    }
+    ctx->eng->points_noalloc(inout, (int)npts);
+    if (written) *written = npts;
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return classify(ctx->err);
+  }
+}
+
 qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written) {
   if (written) *written = 0;
   try {

@@ -71,6 +71,10 @@ class Engine {
   void dense(double* out);                     // 2^N values
   void means(double* out);                     // 3 * 2^Kx values
   void points(const std::vector<unsigned char>& bits, int npts, double* out);
+  // Point evaluation through the fixed device array of points_static.cu
+  // (no allocation); inout holds npts x N 0/1 flags and receives the values.
+  void points_noalloc(double* inout, int npts);
+  size_t points_noalloc_capacity() const;
   double overlap(const Engine& other);         // <this|other>
   double norm2() { return overlap(*this); }
   std::vector<double> download_state() const;
