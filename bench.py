@@ -36,6 +36,16 @@ METRIC = "MPS time-steps/s at chi=128 vs plain FP64 GPU path; rel-L2 vs FP64 ora
 # count is the one that reproduces the 1.25 TFLOP/s nominal and the 1.19
 # TFLOP/s measured by an FMA-throughput probe at the observed clocks).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
+
+
+def measured_peaks():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 ORACLE_SAMPLE_BITS = 5
 
 
@@ -260,17 +270,38 @@ def run_mine(args, rank, world, local_rank):
         tot = sum(v["ms_per_step"] for v in classes.values()) or 1.0
         for v in classes.values():
             v["share"] = v["ms_per_step"] / tot
-        g = classes["gemm_f64"]
-        ach = g["gflop_per_step"] / (g["ms_per_step"] / 1e3) / 1e3 if g["ms_per_step"] > 0 else 0.0
-        roofline = {
-            "kernel": "gemm_f64 (FP64 DFMA core contractions)",
-            "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json)",
-            "traffic": None,
-            "flop_per_launch": g["gflop_per_step"] * 1e9 / max(g["launches_per_step"], 1),
-            "avg_launch_us": g["ms_per_step"] * 1e3 / max(g["launches_per_step"], 1),
-        }
+        if args.precision == "fp64":
+            g = classes["gemm_f64"]
+            ach = g["gflop_per_step"] / (g["ms_per_step"] / 1e3) / 1e3 if g["ms_per_step"] > 0 else 0.0
+            roofline = {
+                "kernel": "gemm_f64 (FP64 DFMA core contractions)",
+                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json)",
+                "traffic": None,
+            }
+        else:
+            g = classes["gemm_tc"]
+            issued = (t1[16] - t0[16]) / nprof
+            alg = g["gflop_per_step"] * 1e9
+            passes = issued / alg if alg > 0 else 1.0
+            peaks = measured_peaks()
+            bf16 = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS)
+            peak = bf16 / passes
+            ach = g["gflop_per_step"] / (g["ms_per_step"] / 1e3) / 1e3 if g["ms_per_step"] > 0 else 0.0
+            roofline = {
+                "kernel": "gemm_tc (tcgen05 contractions incl. operand packing)",
+                "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": (f"of measured: bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) / {passes:.2f} "
+                                "MMA passes per algorithmic flop (mean over the step's products; TF32 passes count 2)"
+                                if "bf16_tflops" in peaks else
+                                f"of fallback: {FALLBACK_BF16_TFLOPS} TFLOP/s bf16 / {passes:.2f} MMA passes"),
+                "traffic": None,
+            }
+        roofline["flop_per_launch"] = g["gflop_per_step"] * 1e9 / max(g["launches_per_step"], 1)
+        roofline["avg_launch_us"] = g["ms_per_step"] * 1e3 / max(g["launches_per_step"], 1)
+        roofline["timing"] = ("separate eager pass after the timed region: CUDA events on the launching stream "
+                              "around every launch of the class, averaged over the pass's steps")
 
     # ---- end to end through the C ABI: host params -> device, K steps, scalars read back each step
     e2e = None

@@ -1,25 +1,35 @@
-// Symmetric eigen-decomposition in one thread block: Householder reduction to
-// tridiagonal form, implicit-shift QL iteration, back-transformation of the
-// leading k eigenvectors.
+// Symmetric eigen-decomposition for the SVD truncation sweep.
 //
-// Used by the SVD truncation sweep (paper: "Matrix product state algorithm" --
-// the bond dimension is limited to chi with the singular value
-// decomposition): for the bond matrix M the Gram G = M M^T = U diag(lam) U^T
-// gives the left singular vectors and lam = sigma^2.
+// The sweep truncates a bond through the Gram matrix G = M M^T = U diag(lam) U^T
+// of the bond matrix (paper: "Matrix product state algorithm" -- the bond
+// dimension is limited to chi with the singular value decomposition;
+// lam = sigma^2, U = left singular vectors).
 //
-// Parallel layout: the reduction uses warp-per-row matrix-vector products and
-// a block-wide rank-2 update; the QL iteration's scalar recurrence runs in
-// thread 0, which records each sweep's Givens rotations, and all threads then
-// apply them to their own rows of the eigenvector matrix; the back-transform
-// is warp-per-eigenvector.  Every loop is bounded (QL: at most 60 sweeps per
-// eigenvalue, reported through the status word).
+// Three kernels, so that the FP64 work does not all sit on one SM:
+//   1. eig_tridiag_ql (one block): Householder reduction to tridiagonal form
+//      (matrix in shared memory when it fits, lower-triangle updates), then
+//      the implicit-shift QL iteration on (d, e) run by one thread, which
+//      records every Givens rotation of every sweep in a list, and a stable
+//      descending order of the eigenvalues;
+//   2. eig_apply_rotations (one thread per row of the eigenvector matrix Z of
+//      the tridiagonal problem, over several blocks): replays the rotation
+//      list on its row;
+//   3. eig_back_transform (one warp per kept eigenvector): applies the
+//      Householder reflectors, U[:, r] = H_0 ... H_{n-3} Z[:, order[r]].
+// Every loop is bounded; the QL iteration stops after 60 sweeps per
+// eigenvalue (or when the rotation list is full) and reports that through the
+// status word.
+#include <cuda_runtime.h>
+
 #include "kernels.cuh"
 
 namespace qtt {
 
 namespace {
-constexpr int EIG_THREADS = 512;
+constexpr int TRI_THREADS = 512;
 constexpr int EIG_MAXN = 1024;
+constexpr int QL_MAX_SWEEPS = 60;
+constexpr size_t EIG_SMEM_LIMIT = 176 * 1024;  // + 6 * EIG_MAXN static values stays below 227 KB
 
 template <typename T>
 struct Eps;
@@ -39,38 +49,84 @@ __device__ T warp_sum_e(T v) {
   return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(EIG_THREADS) eig_sym_kernel(int n, int k, const double* __restrict__ G,
-                                                              double* __restrict__ Uout, double* __restrict__ lam,
-                                                              T* __restrict__ work, int* status) {
-  T* A = work;                        // n x n, row-major (row j > ... holds reflector j)
-  T* Z = A + (size_t)n * n;           // n x n eigenvectors of the tridiagonal (columns)
-  T* ZS = Z + (size_t)n * n;          // k x n selected eigenvectors (rows)
-  T* vb = ZS + (size_t)n * n;         // n
-  T* pb = vb + n;                     // n
-  T* wb = pb + n;                     // n
-  __shared__ T d[EIG_MAXN], e[EIG_MAXN], tauv[EIG_MAXN], rc[EIG_MAXN], rs[EIG_MAXN];
-  __shared__ int order[EIG_MAXN];
-  __shared__ T s_tau, s_v0, s_K;
-  __shared__ int s_lo, s_hi, s_done;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = EIG_THREADS / 32;
+__device__ __forceinline__ double rhyp(double a, double b) { return rhypot(a, b); }
+__device__ __forceinline__ float rhyp(float a, float b) { return rhypotf(a, b); }
 
-  for (size_t x = tid; x < (size_t)n * n; x += EIG_THREADS) {
+// Work layout, in elements of T: A n*n | Z n*n | rot_c R | rot_s R; then
+// ints: seg_lo S | seg_hi S | seg_off S | order n | nseg.  R = 4 n^2 + 64 n
+// rotations, S = 60 n sweeps.
+struct EigLayout {
+  size_t A, Z, rc, rs, R, S;
+  size_t ints_off;  // bytes
+  size_t seg_lo, seg_hi, seg_off, order, nseg;
+  size_t bytes;
+};
+
+template <typename T>
+__host__ __device__ EigLayout eig_layout(int n) {
+  EigLayout L;
+  const size_t nn = (size_t)n * n;
+  L.R = 4 * nn + 64 * (size_t)n;
+  L.S = (size_t)QL_MAX_SWEEPS * n;
+  L.A = 0;
+  L.Z = nn;
+  L.rc = 2 * nn;
+  L.rs = L.rc + L.R;
+  L.ints_off = (L.rs + L.R) * sizeof(T);
+  L.ints_off = (L.ints_off + 15) & ~(size_t)15;
+  L.seg_lo = 0;
+  L.seg_hi = L.S;
+  L.seg_off = 2 * L.S;
+  L.order = 3 * L.S;
+  L.nseg = 3 * L.S + n;
+  L.bytes = L.ints_off + (3 * L.S + n + 4) * sizeof(int);
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* __restrict__ probs, int use_smem,
+                                                              int* status) {
+  const EigProblem P = probs[blockIdx.x];
+  const int n = P.n;
+  if (n <= 0) return;
+  const double* __restrict__ G = P.G;
+  double* __restrict__ lam = P.lam;
+  unsigned char* work = P.work;
+  const EigLayout L = eig_layout<T>(n);
+  T* W = (T*)work;
+  int* I = (int*)(work + L.ints_off);
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* A = use_smem ? (T*)dyn_smem : W + L.A;
+  T* rcg = W + L.rc;
+  T* rsg = W + L.rs;
+  int* seg_lo = I + L.seg_lo;
+  int* seg_hi = I + L.seg_hi;
+  int* seg_off = I + L.seg_off;
+  int* order = I + L.order;
+  __shared__ T d[EIG_MAXN], e[EIG_MAXN], vb[EIG_MAXN], pb[EIG_MAXN], wb[EIG_MAXN], tauv[EIG_MAXN];
+  __shared__ T s_tau, s_v0, s_K;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = TRI_THREADS / 32;
+
+  for (size_t x = tid; x < (size_t)n * n; x += TRI_THREADS) {
     const int i = (int)(x / n), c = (int)(x - (size_t)i * n);
     A[x] = (T)(0.5 * (G[x] + G[(size_t)c * n + i]));
-    Z[x] = (i == c) ? (T)1 : (T)0;
   }
   __syncthreads();
 
-  // ---- Householder tridiagonalisation (reflector j zeroes row/column j beyond j+1)
+  // ---- Householder tridiagonalisation.  Only the lower triangle (c <= i) of
+  // the trailing block is kept current; reflector j is stored in row j,
+  // columns > j + 1 (the strict upper part, unused otherwise).
   for (int j = 0; j + 2 < n; ++j) {
     T* Aj = A + (size_t)j * n;
     if (warp == 0) {
       T s = 0;
-      for (int c = j + 2 + lane; c < n; c += 32) s += Aj[c] * Aj[c];
+      for (int i = j + 2 + lane; i < n; i += 32) {
+        const T v = A[(size_t)i * n + j];
+        s += v * v;
+      }
       s = warp_sum_e(s);
       if (lane == 0) {
-        const T alpha = Aj[j + 1];
+        const T alpha = A[(size_t)(j + 1) * n + j];
         d[j] = Aj[j];
         if (s == (T)0) {
           s_tau = 0;
@@ -88,25 +144,26 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_sym_kernel(int n, int k, cons
     }
     __syncthreads();
     const T tau = s_tau;
-    if (tau == (T)0) {  // uniform branch: every thread read the same shared value
+    if (tau == (T)0) {  // uniform branch (shared value)
       __syncthreads();  // s_tau is rewritten by the next step
       continue;
     }
     {
       const T inv = (T)1 / s_v0;
-      for (int c = j + 2 + tid; c < n; c += EIG_THREADS) {
-        const T v = Aj[c] * inv;
-        Aj[c] = v;
-        vb[c] = v;
+      for (int i = j + 2 + tid; i < n; i += TRI_THREADS) {
+        const T v = A[(size_t)i * n + j] * inv;
+        vb[i] = v;
+        Aj[i] = v;
       }
       if (tid == 0) vb[j + 1] = (T)1;
     }
     __syncthreads();
-    // p = tau * A22 v
+    // p = tau * A22 v, A22 symmetric with its lower triangle stored
     for (int i = j + 1 + warp; i < n; i += nwarps) {
       const T* Ai = A + (size_t)i * n;
       T acc = 0;
-      for (int c = j + 1 + lane; c < n; c += 32) acc += Ai[c] * vb[c];
+      for (int c = j + 1 + lane; c <= i; c += 32) acc += Ai[c] * vb[c];
+      for (int c = i + 1 + lane; c < n; c += 32) acc += A[(size_t)c * n + i] * vb[c];
       acc = warp_sum_e(acc);
       if (lane == 0) pb[i] = tau * acc;
     }
@@ -118,19 +175,20 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_sym_kernel(int n, int k, cons
       if (lane == 0) s_K = (T)0.5 * tau * acc;
     }
     __syncthreads();
-    for (int i = j + 1 + tid; i < n; i += EIG_THREADS) wb[i] = pb[i] - s_K * vb[i];
+    for (int i = j + 1 + tid; i < n; i += TRI_THREADS) wb[i] = pb[i] - s_K * vb[i];
     __syncthreads();
-    const int m = n - j - 1;
-    for (size_t x = tid; x < (size_t)m * m; x += EIG_THREADS) {
-      const int i = j + 1 + (int)(x / m), c = j + 1 + (int)(x % m);
-      A[(size_t)i * n + c] -= vb[i] * wb[c] + wb[i] * vb[c];
+    // lower-triangle rank-2 update: rows i >= j+1, columns j+1 <= c <= i
+    for (int i = j + 1 + warp; i < n; i += nwarps) {
+      T* Ai = A + (size_t)i * n;
+      const T vi = vb[i], wi = wb[i];
+      for (int c = j + 1 + lane; c <= i; c += 32) Ai[c] -= vi * wb[c] + wi * vb[c];
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
       d[n - 2] = A[(size_t)(n - 2) * n + (n - 2)];
-      e[n - 2] = A[(size_t)(n - 2) * n + (n - 1)];
+      e[n - 2] = A[(size_t)(n - 1) * n + (n - 2)];
       tauv[n - 2] = 0;
     }
     d[n - 1] = A[(size_t)(n - 1) * n + (n - 1)];
@@ -138,36 +196,33 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_sym_kernel(int n, int k, cons
     tauv[n - 1] = 0;
   }
   __syncthreads();
+  // reflectors (and tau in the diagonal of A) for the back-transform kernel
+  for (size_t x = tid; x < (size_t)n * n; x += TRI_THREADS) {
+    const int i = (int)(x / n), c = (int)(x - (size_t)i * n);
+    if (c > i + 1) W[L.A + x] = A[x];
+    else if (c == i) W[L.A + x] = tauv[i];
+  }
 
-  // ---- implicit QL on (d, e); thread 0 runs the recurrence, all apply rotations
-  int l = 0, iter = 0;
-  bool start = true;
-  T f = 0, tst1 = 0;
-  const T eps = Eps<T>::v();
-  for (;;) {
-    if (tid == 0) {
-      s_done = 1;
-      while (l < n) {
-        if (start) {
-          const T h = fabs(d[l]) + fabs(e[l]);
-          tst1 = h > tst1 ? h : tst1;
-          iter = 0;
-          start = false;
-        }
+  // ---- implicit QL with a Wilkinson-type shift, rotations recorded per sweep
+  if (tid == 0) {
+    const T eps = Eps<T>::v();
+    T f = 0, tst1 = 0;
+    int nseg = 0;
+    size_t off = 0;
+    for (int l = 0; l < n; ++l) {
+      const T hl = fabs(d[l]) + fabs(e[l]);
+      tst1 = hl > tst1 ? hl : tst1;
+      for (int iter = 0;; ++iter) {
         int m = l;
         while (m < n - 1 && fabs(e[m]) > eps * tst1) ++m;
-        if (m == l || iter >= 60) {
-          if (m != l) atomicOr(status, 2);
-          d[l] += f;
-          e[l] = 0;
-          ++l;
-          start = true;
-          continue;
+        if (m == l) break;
+        if (iter >= QL_MAX_SWEEPS || nseg >= (int)L.S || off + (size_t)(m - l) > L.R) {
+          atomicOr(status, 2);
+          break;
         }
-        ++iter;
         T g = d[l];
         T p = (d[l + 1] - g) / ((T)2 * e[l]);
-        T r = hypot(p, (T)1);
+        T r = (T)1 / rhyp(p, (T)1);
         if (p < 0) r = -r;
         d[l] = e[l] / (p + r);
         d[l + 1] = e[l] * (p + r);
@@ -178,49 +233,43 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_sym_kernel(int n, int k, cons
         p = d[m];
         T c = 1, c2 = 1, c3 = 1, s = 0, s2 = 0;
         const T el1 = e[l + 1];
+        seg_lo[nseg] = l;
+        seg_hi[nseg] = m - 1;
+        seg_off[nseg] = (int)off;
         for (int i = m - 1; i >= l; --i) {
           c3 = c2;
           c2 = c;
           s2 = s;
-          g = c * e[i];
+          const T ei = e[i];
+          g = c * ei;
           h = c * p;
-          r = hypot(p, e[i]);
-          e[i + 1] = s * r;
-          s = e[i] / r;
-          c = p / r;
+          const T rr = rhyp(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
+          const T cn = p * rr, sn = ei * rr;
+          r = p * cn + ei * sn;  // hypot(p, e_i)
+          e[i + 1] = s * r;      // previous sine
+          s = sn;
+          c = cn;
           p = c * d[i] - s * g;
           d[i + 1] = h + s * (c * g + s * d[i]);
-          rc[i] = c;
-          rs[i] = s;
+          rcg[off + (size_t)(m - 1 - i)] = c;
+          rsg[off + (size_t)(m - 1 - i)] = s;
         }
+        off += (size_t)(m - l);
+        ++nseg;
         p = -s * s2 * c3 * el1 * e[l] / dl1;
         e[l] = s * p;
         d[l] = c * p;
-        s_lo = l;
-        s_hi = m - 1;
-        s_done = 0;
-        break;
       }
+      d[l] += f;
+      e[l] = 0;
     }
-    __syncthreads();
-    if (s_done) break;
-    const int lo = s_lo, hi = s_hi;
-    for (int row = tid; row < n; row += EIG_THREADS) {
-      T* zr = Z + (size_t)row * n;
-      for (int i = hi; i >= lo; --i) {
-        const T c = rc[i], s = rs[i];
-        const T zi = zr[i], zi1 = zr[i + 1];
-        zr[i + 1] = s * zi + c * zi1;
-        zr[i] = c * zi - s * zi1;
-      }
-    }
-    __syncthreads();
+    I[L.nseg] = nseg;
   }
-
-  // ---- order eigenvalues descending (stable), select the leading k vectors
-  for (int i = tid; i < n; i += EIG_THREADS) {
-    int rank = 0;
+  __syncthreads();
+  // ---- stable descending order of the eigenvalues
+  for (int i = tid; i < n; i += TRI_THREADS) {
     const T di = d[i];
+    int rank = 0;
     for (int q = 0; q < n; ++q) {
       const T dq = d[q];
       rank += (dq > di) || (dq == di && q < i);
@@ -228,35 +277,112 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_sym_kernel(int n, int k, cons
     order[rank] = i;
   }
   __syncthreads();
-  for (int r = tid; r < n; r += EIG_THREADS) lam[r] = (double)d[order[r]];
-  for (size_t x = tid; x < (size_t)k * n; x += EIG_THREADS) {
-    const int r = (int)(x / n), i = (int)(x - (size_t)r * n);
-    ZS[x] = Z[(size_t)i * n + order[r]];
-  }
-  __syncthreads();
+  for (int r = tid; r < n; r += TRI_THREADS) lam[r] = (double)d[order[r]];
+}
 
-  // ---- back-transform: ZS^T <- H_0 ... H_{n-3} ZS^T
+// Row `row` of Z (eigenvectors of the tridiagonal matrix as columns) starts as
+// e_row and receives every recorded rotation in order.
+template <typename T>
+__global__ void eig_apply_rotations(const EigProblem* __restrict__ probs) {
+  const EigProblem P = probs[blockIdx.y];
+  const int n = P.n;
+  unsigned char* work = P.work;
+  const EigLayout L = eig_layout<T>(n);
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  T* W = (T*)work;
+  const int* I = (const int*)(work + L.ints_off);
+  const T* rc = W + L.rc;
+  const T* rs = W + L.rs;
+  T* z = W + L.Z + (size_t)row * n;
+  for (int c = 0; c < n; ++c) z[c] = (c == row) ? (T)1 : (T)0;
+  const int nseg = I[L.nseg];
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int lo = I[L.seg_lo + sg], hi = I[L.seg_hi + sg];
+    const size_t off = (size_t)I[L.seg_off + sg];
+    T zi1 = z[hi + 1];
+    for (int i = hi, q = 0; i >= lo; --i, ++q) {
+      const T c = rc[off + q], s = rs[off + q];
+      const T zi = z[i];
+      z[i + 1] = s * zi + c * zi1;
+      zi1 = c * zi - s * zi1;
+    }
+    z[lo] = zi1;
+  }
+}
+
+// U[:, r] = H_0 ... H_{n-3} Z[:, order[r]] for r < k; one warp per vector.
+template <typename T>
+__global__ void eig_back_transform(const EigProblem* __restrict__ probs) {
+  const EigProblem P = probs[blockIdx.y];
+  const int n = P.n, k = P.k;
+  unsigned char* work = P.work;
+  double* __restrict__ U = P.U;
+  const EigLayout L = eig_layout<T>(n);
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= k) return;
+  const T* W = (const T*)work;
+  const int* I = (const int*)(work + L.ints_off);
+  const T* A = W + L.A;
+  const int col = I[L.order + warp];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* zr = (T*)dyn_smem + (size_t)(threadIdx.x >> 5) * n;
+  for (int i = lane; i < n; i += 32) zr[i] = W[L.Z + (size_t)i * n + col];
+  __syncwarp();
   for (int j = n - 3; j >= 0; --j) {
-    const T tau = tauv[j];
+    const T tau = A[(size_t)j * n + j];
     if (tau == (T)0) continue;
     const T* Aj = A + (size_t)j * n;
-    for (int r = warp; r < k; r += nwarps) {
-      T* zr = ZS + (size_t)r * n;
-      T acc = 0;
-      for (int i = j + 2 + lane; i < n; i += 32) acc += Aj[i] * zr[i];
-      acc = warp_sum_e(acc) + zr[j + 1];
-      acc *= tau;
-      if (lane == 0) zr[j + 1] -= acc;
-      for (int i = j + 2 + lane; i < n; i += 32) zr[i] -= acc * Aj[i];
-    }
-    __syncthreads();
+    T acc = 0;
+    for (int i = j + 2 + lane; i < n; i += 32) acc += Aj[i] * zr[i];
+    acc = warp_sum_e(acc) + zr[j + 1];
+    acc *= tau;
+    __syncwarp();
+    if (lane == 0) zr[j + 1] -= acc;
+    for (int i = j + 2 + lane; i < n; i += 32) zr[i] -= acc * Aj[i];
+    __syncwarp();
   }
-  for (size_t x = tid; x < (size_t)n * k; x += EIG_THREADS) {
-    const int i = (int)(x / k), r = (int)(x - (size_t)i * k);
-    Uout[x] = (double)ZS[(size_t)r * n + i];
+  for (int i = lane; i < n; i += 32) U[(size_t)i * k + warp] = (double)zr[i];
+}
+
+template <typename T>
+void eig_launch(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nmax, int kmax, int* status) {
+  const size_t smem_A = (size_t)nmax * nmax * sizeof(T);
+  const int use_smem = smem_A <= EIG_SMEM_LIMIT ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(eig_tridiag_ql<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+    attr = true;
+  }
+  count_launches(kmax > 0 ? 3 : 2);
+  eig_tridiag_ql<T><<<nprob, TRI_THREADS, use_smem ? smem_A : 0, st>>>(probs_dev, use_smem, status);
+  const int rows_per_block = 32;
+  eig_apply_rotations<T><<<dim3((nmax + rows_per_block - 1) / rows_per_block, nprob), rows_per_block, 0, st>>>(
+      probs_dev);
+  if (kmax > 0) {
+    const int warps = 4;
+    eig_back_transform<T><<<dim3((kmax + warps - 1) / warps, nprob), 32 * warps, (size_t)warps * nmax * sizeof(T),
+                            st>>>(probs_dev);
   }
 }
 }  // namespace
+
+size_t eig_work_bytes(int n, int prec_bits) {
+  return prec_bits == 32 ? eig_layout<float>(n).bytes : eig_layout<double>(n).bytes;
+}
+
+void eig_sym_batched(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nmax, int kmax, int prec_bits,
+                     int* status) {
+  if (nprob <= 0 || nmax <= 0) return;
+  if (nmax > EIG_MAXN || kmax > nmax || kmax < 0) {
+    cudaMemsetAsync(status, 0xff, sizeof(int), st);
+    return;
+  }
+  if (prec_bits == 32)
+    eig_launch<float>(st, probs_dev, nprob, nmax, kmax, status);
+  else
+    eig_launch<double>(st, probs_dev, nprob, nmax, kmax, status);
+}
 
 void eig_sym(cudaStream_t st, int n, int k, const double* G, double* U, double* lam, void* work, int prec_bits,
              int* status) {
@@ -265,11 +391,18 @@ void eig_sym(cudaStream_t st, int n, int k, const double* G, double* U, double* 
     cudaMemsetAsync(status, 0xff, sizeof(int), st);
     return;
   }
-  count_launches(1);
-  if (prec_bits == 32)
-    eig_sym_kernel<float><<<1, EIG_THREADS, 0, st>>>(n, k, G, U, lam, (float*)work, status);
-  else
-    eig_sym_kernel<double><<<1, EIG_THREADS, 0, st>>>(n, k, G, U, lam, (double*)work, status);
+  // the one-problem descriptor lives at the end of the caller's work area
+  const size_t wb = eig_work_bytes(n, prec_bits);
+  EigProblem P;
+  P.n = n;
+  P.k = k;
+  P.G = G;
+  P.U = U;
+  P.lam = lam;
+  P.work = (unsigned char*)work;
+  EigProblem* d = (EigProblem*)((unsigned char*)work + ((wb + 255) & ~(size_t)255));
+  cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+  eig_sym_batched(st, d, 1, n, k, prec_bits, status);
 }
 
 }  // namespace qtt

@@ -121,20 +121,39 @@ Chain DevMps::chain() const {
 static long long pow2(int e) { return e >= 62 ? (1LL << 62) : (1LL << e); }
 
 Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
+  if (st_ == nullptr) {
+    // A stream of our own (blocking, so ordered with the legacy default
+    // stream) instead of the legacy stream, which cannot be captured.
+    if (cudaStreamCreate(&st_) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::runtime_error("CUDA error: cudaStreamCreate failed");
+    }
+    own_stream_ = true;
+  }
   N_ = p.N();
   kphi_ = p.Kphi();
   exact_ = p.exact != 0;
   prec_bits_ = (p.precision == 0) ? 64 : 32;
-  // contraction arithmetic: FP32 -> 3-pass TF32, TF32 -> 1-pass TF32, BF16X3 -> 3-pass BF16
-  tc_mode_ = p.precision == 1 ? TC_TF32X3 : p.precision == 2 ? TC_TF32 : p.precision == 3 ? TC_BF16X3 : -1;
+  // contraction arithmetic: FP32 -> 3 x 3 exact bf16 slices (unbiased,
+  // ~2^-24), BF16X3 -> 2 x 2 exact bf16 slices (unbiased, ~2^-16), TF32 -> one
+  // TF32 pass.  The sketch products get the same arithmetic as the products
+  // that carry the state: the sketch W_{n+1} = R_{n+1} G must reproduce the
+  // right part R_{n+1} of the operator-state product, because T_n R_{n+1} can
+  // be far smaller than |T_n| |R_{n+1}| (the operator's stencils cancel), and
+  // an error in R_{n+1} then steers the range finder away from T_n R_{n+1}.
+  const int mode = p.precision == 1 ? TC_BF16X6 : p.precision == 2 ? TC_TF32 : p.precision == 3 ? TC_BF16X3 : -1;
+  for (int& m : tc_mode_) m = mode;
   timer_ = new KernelTimer();
   if (const char* e = std::getenv("QTT_KERNEL_TIMING")) timer_->on = (e[0] == '1');
 }
 
 Engine::~Engine() {
+  for (cudaGraphExec_t& g : graph_)
+    if (g) cudaGraphExecDestroy(g);
   for (void* a : allocs_) cudaFree(a);
   if (pack_ws_) cudaFree(pack_ws_);
   delete timer_;
+  if (own_stream_) cudaStreamDestroy(st_);
 }
 
 void* Engine::dalloc(size_t bytes) {
@@ -213,12 +232,13 @@ void Engine::gemm64(int M, int N, int K, int outer, int inner, double alpha, Mat
 }
 
 void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
-                  OutView C) {
-  if (tc_mode_ < 0) {
+                  OutView C, int role) {
+  const int mode = tc_mode_[role];
+  if (mode < 0) {
     gemm64(M, N, K, outer, inner, alpha, A, B, beta, C);
     return;
   }
-  const size_t need = tc_workspace_bytes(M, N, K, (long long)outer * inner, tc_mode_);
+  const size_t need = tc_workspace_bytes(M, N, K, (long long)outer * inner, mode);
   if (need > pack_bytes_) {  // grows during the first step only (static shapes)
     QTT_CUDA(cudaStreamSynchronize(st_));
     if (pack_ws_) QTT_CUDA(cudaFree(pack_ws_));
@@ -232,10 +252,15 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
     }
     pack_bytes_ = bytes;
   }
-  TimeScope ts(timer_, TM_TC, st_, 2.0 * M * (double)N * K * outer * inner);
-  if (!gemm_tc(st_, tc_mode_, M, N, K, outer, inner, alpha, A, B, beta, C, pack_ws_, pack_bytes_, ws_, ws_elems_,
+  const double fl = 2.0 * M * (double)N * K * outer * inner;
+  if (timer_->on) {
+    static const double passes[5] = {3, 2, 6, 1, 6};  // indexed by TcMode, in bf16-pass units
+    tc_issued_flops_ += fl * passes[mode];
+  }
+  TimeScope ts(timer_, TM_TC, st_, fl);
+  if (!gemm_tc(st_, mode, M, N, K, outer, inner, alpha, A, B, beta, C, pack_ws_, pack_bytes_, ws_, ws_elems_,
                status_ + 2))
-    throw std::runtime_error("EINVAL: tensor-core GEMM shape outside the supported grid");
+    throw std::runtime_error("EINVAL: tensor-core GEMM shape outside the supported grid or workspace");
 }
 
 static MatView mv(const double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
@@ -317,7 +342,7 @@ void Engine::init() {
     return 1;
   };
   const int nlo = exact_ ? nc_ + 1 : 1;
-  size_t x1 = 1, x2 = 1, pp = 1, yy = 1, mb = 1, gg = 1;
+  size_t x1 = 1, x2 = 1, pp = 1, yy = 1;
   for (int slot = 0; slot < 4; ++slot) {
     Woff_[slot].assign(N + 1, 0);
     size_t tot = 0;
@@ -344,20 +369,16 @@ void Engine::init() {
   }
   for (int n = 0; n < N; ++n) {
     yy = std::max(yy, (size_t)2 * rz_[n] * ell_[n + 1]);
-    mb = std::max(mb, (size_t)2 * rz_[n] * std::max(D_[n + 1], rz_[n + 1]));
-    gg = std::max(gg, (size_t)rz_[n] * rz_[n]);
+  }
+  for (int n = 0; n < N; ++n) {
+    x1 = std::max(x1, (size_t)2 * rz_[n] * rz_[n + 1]);
+    x2 = std::max(x2, (size_t)D_[n] * 2 * rz_[n + 1]);
   }
   P_ = (double*)dalloc(pp * sizeof(double));
   X1_ = (double*)dalloc(x1 * sizeof(double));
   X2_ = (double*)dalloc(x2 * sizeof(double));
   Y_ = (double*)dalloc(yy * sizeof(double));
-  for (int i = 0; i < 3; ++i) Mb_[i] = (double*)dalloc(mb * sizeof(double));
-  G_ = (double*)dalloc(gg * sizeof(double));
-  U_ = (double*)dalloc(gg * sizeof(double));
-  Us_ = (double*)dalloc((size_t)max_bond_ * max_bond_ * sizeof(double));
-  lam_ = (double*)dalloc((size_t)max_bond_ * sizeof(double));
   const size_t rmax = (size_t)max_bond_;
-  eigwork_ = (double*)dalloc((3 * rmax * rmax + 3 * rmax) * sizeof(double));
   qrwork_ = (double*)dalloc((2 * (2 * rmax) * rmax + rmax) * sizeof(double));
   ws_elems_ = (size_t)8 << 20;
   ws_ = (double*)dalloc(ws_elems_ * sizeof(double));
@@ -372,7 +393,38 @@ void Engine::init() {
   obsB_ = (double*)dalloc((size_t)2 * max_bond_ * max_bond_ * sizeof(double) + 64);
   obsX_ = (double*)dalloc((size_t)2 * max_bond_ * max_bond_ * sizeof(double) + 64);
   status_ = (int*)dalloc(sizeof(int) * 4);
+  dstep_ = (unsigned long long*)dalloc(sizeof(unsigned long long));
+  QTT_CUDA(cudaMemsetAsync(dstep_, 0, sizeof(unsigned long long), st_));
+  if (const char* e = std::getenv("QTT_GRAPHS")) graphs_ = (e[0] != '0');
   ranks_ = (int*)dalloc(sizeof(int) * (N + 1));
+  // truncation: right Gram per bond, eigenvectors / eigenvalues of the bonds that truncate
+  gram_.assign(N + 1, nullptr);
+  tU_.assign(N + 1, nullptr);
+  trunc_bonds_.clear();
+  if (!exact_) {
+    for (int n = 1; n <= N; ++n) gram_[n] = (double*)dalloc((size_t)rz_[n] * rz_[n] * sizeof(double));
+    std::vector<EigProblem> probs;
+    trunc_nmax_ = 1;
+    trunc_kmax_ = 0;
+    for (int n = 1; n < N; ++n) {
+      if (rz_[n] <= D_[n]) continue;  // keeps every direction: identity projector
+      EigProblem P;
+      P.n = rz_[n];
+      P.k = D_[n];
+      P.G = gram_[n];
+      tU_[n] = (double*)dalloc((size_t)rz_[n] * D_[n] * sizeof(double));
+      P.U = tU_[n];
+      P.lam = (double*)dalloc((size_t)rz_[n] * sizeof(double));
+      P.work = (unsigned char*)dalloc(eig_work_bytes(rz_[n], 64) + 256);
+      probs.push_back(P);
+      trunc_bonds_.push_back(n);
+      trunc_nmax_ = std::max(trunc_nmax_, P.n);
+      trunc_kmax_ = std::max(trunc_kmax_, P.k);
+    }
+    trunc_probs_ = (EigProblem*)dalloc(sizeof(EigProblem) * (probs.size() + 1));
+    if (!probs.empty())
+      QTT_CUDA(cudaMemcpy(trunc_probs_, probs.data(), sizeof(EigProblem) * probs.size(), cudaMemcpyHostToDevice));
+  }
   QTT_CUDA(cudaMemsetAsync(disc_, 0, sizeof(double) * 4, st_));
   QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int) * 4, st_));
   QTT_CUDA(cudaStreamSynchronize(st_));
@@ -392,34 +444,35 @@ void Engine::make_hfirst(const DevMps& f, double* v, double* hf) {
   gemm64(2, 2 * br, bl, 1, 1, 1.0, mv(v, bl, 1), mv(f.core(kphi_), 2 * br, 1), 0.0, ov(hf, 2 * br, 1));
 }
 
-void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr) {
+void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr,
+                         int role) {
   const int bl = t.f->b[n], br = t.f->b[n + 1];
   const int wl = t.w(n), wr = t.w(n + 1);
   const double* A = t.f->core(n);
   // X1[(w',a')][s][l] = sum_l' W_{n+1}[(w',a')][l'] Om[l][s][l']
-  gemm(wr * br, Ll, Lr, 1, 2, 1.0, mv(Wn1, Lr, 1), mv(Om, 1, 2LL * Lr, 0, Lr), 0.0, ov(X1_, 2LL * Ll, 1, 0, Ll));
+  gemm(wr * br, Ll, Lr, 1, 2, 1.0, mv(Wn1, Lr, 1), mv(Om, 1, 2LL * Lr, 0, Lr), 0.0, ov(X1_, 2LL * Ll, 1, 0, Ll), role);
   if (!t.diag(n)) {
     // X2[w'][(a,s')][(s,l)] = sum_a' A[(a,s')][a'] X1[(w',a')][(s,l)]
     gemm(2 * bl, 2 * Ll, br, wr, 1, 1.0, mv(A, br, 1), mv(X1_, 2LL * Ll, 1, (long long)br * 2 * Ll), 0.0,
-         ov(X2_, 2LL * Ll, 1, 4LL * bl * Ll));
+         ov(X2_, 2LL * Ll, 1, 4LL * bl * Ll), role);
     // W_n[(w,a)][l] = sum_{s,s',w'} W[w][s*2+s'][w'] X2[w'][(a,s')][(s,l)]
     const double* Wss = t.op->Wss(n);
     for (int ss = 0; ss < 4; ++ss) {
       const int s = ss >> 1, sp = ss & 1;
       gemm(wl, Ll, wr, bl, 1, 1.0, mv(Wss + (size_t)ss * wl * wr, wr, 1),
            mv(X2_ + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll), ss == 0 ? 0.0 : 1.0,
-           ov(Wn, (long long)bl * Ll, 1, Ll));
+           ov(Wn, (long long)bl * Ll, 1, Ll), role);
     }
   } else {
     const double* H = t.H(n);
     // X2[h'][a][s][l] = sum_a' A[a][s][a'] X1[(h',a')][s][l]
     gemm(bl, Ll, br, wr, 2, 1.0, mv(A, 2LL * br, 1, 0, br), mv(X1_, 2LL * Ll, 1, (long long)br * 2 * Ll, Ll), 0.0,
-         ov(X2_, 2LL * Ll, 1, 2LL * bl * Ll, Ll));
+         ov(X2_, 2LL * Ll, 1, 2LL * bl * Ll, Ll), role);
     // W_n[(h,a)][l] = sum_s sum_h' H[h][s][h'] X2[h'][a][s][l]
     for (int s = 0; s < 2; ++s)
       gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1),
            mv(X2_ + (size_t)s * Ll, 2LL * bl * Ll, 1, 2LL * Ll), s == 0 ? 0.0 : 1.0,
-           ov(Wn, (long long)bl * Ll, 1, Ll));
+           ov(Wn, (long long)bl * Ll, 1, Ll), role);
   }
 }
 
@@ -465,20 +518,15 @@ Term Engine::term_mix(const DevMps* f, const double* hf, double scale) const {
   return t;
 }
 
-void Engine::run_stage(Term* terms, int nt, DevMps& out) {
+void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
   if (exact_) {
     run_stage_exact(terms, nt, out);
     return;
   }
   const int N = N_;
-  ++stage_counter_;
   {
     TimeScope ts(timer_, TM_OTHER, st_);
-    for (int n = 1; n < N; ++n) {
-      const double sigma = 1.0 / std::sqrt(2.0 * (double)ell_[n + 1]);
-      fill_gaussian(st_, omega_.core(n), omega_.core_elems(n), sigma, p_.seed,
-                    stage_counter_ * (unsigned long long)kMaxSites + (unsigned long long)n);
-    }
+    fill_gaussian_sketch(st_, omega_.chain(), omega_.max_core_elems(), p_.seed, dstep_, stage);
   }
   // 1. right-to-left sketch: W_n = (right part of the term) x (right part of the random MPS)
   for (int i = 0; i < nt; ++i) {
@@ -486,7 +534,8 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out) {
     double* W = Wslot_[t.slot];
     fill_value(st_, W + Woff_[t.slot][N], 1, 1.0);
     for (int n = N - 1; n >= 1; --n)
-      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], omega_.core(n), ell_[n], ell_[n + 1]);
+      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], omega_.core(n), ell_[n], ell_[n + 1],
+                  GEMM_SKETCH);
   }
   // 2. left-to-right orthogonalisation of the sketched site tensors
   for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
@@ -514,7 +563,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out) {
       for (int i = 0; i < nt; ++i) {
         const Term& t = terms[i];
         gemm(2 * r, L, (int)t.B(n + 1), 1, 1, 1.0, mv(T_[t.slot], t.B(n + 1), 1),
-             mv(Wslot_[t.slot] + Woff_[t.slot][n + 1], L, 1), i == 0 ? 0.0 : 1.0, ov(Y_, L, 1));
+             mv(Wslot_[t.slot] + Woff_[t.slot][n + 1], L, 1), i == 0 ? 0.0 : 1.0, ov(Y_, L, 1), GEMM_RANGE);
       }
       {
         TimeScope ts(timer_, TM_QR, st_);
@@ -528,37 +577,50 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out) {
     }
     r = rn;
   }
-  // 3. right-to-left SVD truncation to chi (FP64 Gram + eigensolve per bond)
-  const double floor_rel = 1e-24;
-  int cur = 0;
-  fill_value(st_, Mb_[0], 1, 1.0);
-  for (int n = N - 1; n >= 1; --n) {
-    const int rl = rz_[n], rr = rz_[n + 1], Dn = D_[n], Dn1 = D_[n + 1];
-    const int mi = (cur + 1) % 3;
-    double* M = Mb_[mi];
-    gemm(2 * rl, Dn1, rr, 1, 1, 1.0, mv(mid_.core(n), rr, 1), mv(Mb_[cur], Dn1, 1), 0.0, ov(M, Dn1, 1));
-    if (Dn == 2 * Dn1) {  // structural bond: nothing to truncate, identity core
-      TimeScope ts(timer_, TM_OTHER, st_);
-      fill_identity_right(st_, out.core(n), Dn1);
-      cur = mi;
+  // 3. SVD truncation of every bond to chi.  The state is left-orthonormal,
+  // so the squared singular values at bond n are the eigenvalues of the
+  // Gram matrix R_n of its right part.  All R_n come from one right-to-left
+  // FP64 contraction pass; all bond eigensolves run in one batched launch;
+  // the projectors U_n U_n^T are then inserted into every core independently.
+  gram_pass(mid_);
+  if (!trunc_bonds_.empty()) {
+    {
+      TimeScope ts(timer_, TM_EIG, st_);
+      eig_sym_batched(st_, trunc_probs_, (int)trunc_bonds_.size(), trunc_nmax_, trunc_kmax_, 64, status_);
+    }
+    TimeScope ts(timer_, TM_OTHER, st_);
+    truncate_select(st_, trunc_probs_, (int)trunc_bonds_.size(), p_.svd_rel_tol, 1e-24, disc_, ranks_);
+  }
+  project_cores(mid_, out);
+}
+
+void Engine::gram_pass(const DevMps& g) {
+  // R_N = [1]; R_n = sum_s A_n[:, s, :] R_{n+1} A_n[:, s, :]^T  (FP64)
+  fill_value(st_, gram_[N_], 1, 1.0);
+  for (int n = N_ - 1; n >= 1; --n) {
+    const int rl = g.b[n], rr = g.b[n + 1];
+    gemm64(2 * rl, rr, rr, 1, 1, 1.0, mv(g.core(n), rr, 1), mv(gram_[n + 1], rr, 1), 0.0, ov(X1_, rr, 1));
+    gemm64(rl, rl, 2 * rr, 1, 1, 1.0, mv(X1_, 2LL * rr, 1), mv(g.core(n), 1, 2LL * rr), 0.0, ov(gram_[n], rl, 1));
+  }
+}
+
+void Engine::project_cores(const DevMps& g, DevMps& out) {
+  // out core n = U_n^T A_n U_{n+1}, with U = identity on bonds that keep all directions
+  for (int n = 0; n < N_; ++n) {
+    const int rl = g.b[n], rr = g.b[n + 1], Dl = out.b[n], Dr = out.b[n + 1];
+    const double* U_l = tU_[n];
+    const double* U_r = tU_[n + 1];
+    const double* X = g.core(n);
+    if (U_l) {  // X = U_l^T A_n : [Dl x 2 rr]
+      gemm(Dl, 2 * rr, rl, 1, 1, 1.0, mv(U_l, 1, Dl), mv(g.core(n), 2LL * rr, 1), 0.0, ov(X2_, 2LL * rr, 1));
+      X = X2_;
+    }
+    if (U_r) {  // out = X U_r : [(2 Dl) x Dr]
+      gemm(2 * Dl, Dr, rr, 1, 1, 1.0, mv(X, rr, 1), mv(U_r, Dr, 1), 0.0, ov(out.core(n), Dr, 1));
     } else {
-      gemm64(rl, rl, 2 * Dn1, 1, 1, 1.0, mv(M, 2LL * Dn1, 1), mv(M, 1, 2LL * Dn1), 0.0, ov(G_, rl, 1));
-      const int ku = std::min(rl, Dn);
-      {
-        TimeScope ts(timer_, TM_EIG, st_);
-        eig_sym(st_, rl, ku, G_, U_, lam_, eigwork_, 64, status_);
-      }
-      const int li = (cur + 2) % 3;
-      {
-        TimeScope ts(timer_, TM_OTHER, st_);
-        sweep_scales(st_, rl, Dn, ku, U_, lam_, p_.svd_rel_tol, floor_rel, Us_, Mb_[li], disc_, ranks_ + n);
-      }
-      gemm(Dn, 2 * Dn1, rl, 1, 1, 1.0, mv(Us_, 1, Dn), mv(M, 2LL * Dn1, 1), 0.0, ov(out.core(n), 2LL * Dn1, 1));
-      cur = li;
+      QTT_CUDA(cudaMemcpyAsync(out.core(n), X, sizeof(double) * (size_t)Dl * 2 * Dr, cudaMemcpyDeviceToDevice, st_));
     }
   }
-  gemm(2, D_[1], rz_[1], 1, 1, 1.0, mv(mid_.core(0), rz_[1], 1), mv(Mb_[cur], D_[1], 1), 0.0,
-       ov(out.core(0), D_[1], 1));
 }
 
 void Engine::run_stage_exact(Term* terms, int nt, DevMps& out) {
@@ -572,7 +634,8 @@ void Engine::run_stage_exact(Term* terms, int nt, DevMps& out) {
     double* W = Wslot_[t.slot];
     fill_value(st_, W + Woff_[t.slot][N], 1, 1.0);
     for (int n = N - 1; n > nc; --n)
-      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], out.core(n), ell_[n], ell_[n + 1]);
+      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], out.core(n), ell_[n], ell_[n + 1],
+                  GEMM_STATE);
   }
   for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
   int r = 1;
@@ -597,32 +660,90 @@ void Engine::run_stage_exact(Term* terms, int nt, DevMps& out) {
   }
 }
 
+void Engine::step_body() {
+  QTT_CUDA(cudaMemsetAsync(disc_, 0, sizeof(double), st_));
+  if (p_.rk_variant == 0) {
+    // Heun: f* = f + dt L(f);  f_{n+1} = (f + f* + dt L(f*)) / 2
+    cond_means(f_, v_[0]);
+    make_hfirst(f_, v_[0], hf_[0]);
+    Term a[2] = {term_dense(1, &op_lin_, &f_, 1.0), term_mix(&f_, hf_[0], 1.0)};
+    run_stage(a, 2, fs_, 0);
+    cond_means(fs_, v_[1]);
+    make_hfirst(fs_, v_[1], hf_[1]);
+    Term b[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &fs_, 0.5), term_mix(&fs_, hf_[1], 0.5)};
+    run_stage(b, 3, g_, 1);
+  } else {
+    // midpoint: f_h = f + dt/2 L(f);  f_{n+1} = f + dt L(f_h)
+    cond_means(f_, v_[0]);
+    make_hfirst(f_, v_[0], hf_[0]);
+    Term a[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &f_, 0.5), term_mix(&f_, hf_[0], 0.5)};
+    run_stage(a, 3, fs_, 0);
+    cond_means(fs_, v_[1]);
+    make_hfirst(fs_, v_[1], hf_[1]);
+    Term b[4] = {term_dense(0, &ident_, &f_, 1.0), term_dense(1, &op_lin_, &fs_, 1.0),
+                 term_dense(3, &ident_, &fs_, -1.0), term_mix(&fs_, hf_[1], 1.0)};
+    run_stage(b, 4, g_, 1);
+  }
+  bump_counter(st_, dstep_);
+}
+
+bool Engine::capture_step(int parity) {
+  // Any failure leaves the stream out of capture, clears the error and turns
+  // the graphs off for this context: the step then runs eagerly.
+  auto give_up = [&](cudaGraph_t g) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st_, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g2 = nullptr;
+      cudaStreamEndCapture(st_, &g2);
+      if (g2) cudaGraphDestroy(g2);
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    graph_[parity] = nullptr;
+    graphs_ = false;
+    return false;
+  };
+  if (cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return give_up(nullptr);
+  try {
+    step_body();
+  } catch (...) {
+    give_up(nullptr);
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(st_, &g) != cudaSuccess || g == nullptr) return give_up(g);
+  if (cudaGraphInstantiate(&graph_[parity], g, 0) != cudaSuccess) return give_up(g);
+  cudaGraphDestroy(g);
+  return true;
+}
+
 void Engine::step(int nsteps) {
   for (int k = 0; k < nsteps; ++k) {
-    QTT_CUDA(cudaMemsetAsync(disc_, 0, sizeof(double), st_));
-    if (p_.rk_variant == 0) {
-      // Heun: f* = f + dt L(f);  f_{n+1} = (f + f* + dt L(f*)) / 2
-      cond_means(f_, v_[0]);
-      make_hfirst(f_, v_[0], hf_[0]);
-      Term a[2] = {term_dense(1, &op_lin_, &f_, 1.0), term_mix(&f_, hf_[0], 1.0)};
-      run_stage(a, 2, fs_);
-      cond_means(fs_, v_[1]);
-      make_hfirst(fs_, v_[1], hf_[1]);
-      Term b[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &fs_, 0.5), term_mix(&fs_, hf_[1], 0.5)};
-      run_stage(b, 3, g_);
+    // The step's launches (shapes, pointers, workspaces) are identical from
+    // step to step once the first one has sized the workspaces, so later
+    // steps replay a captured graph; kernel timing needs the eager path.
+    bool replay = false;
+    if (graphs_ && warm_ && !timer_->on) {
+      // the launch counter counts a graph's kernels once at capture and again at every later replay
+      if (graph_[parity_]) {
+        count_launches(graph_launches_[parity_]);
+        replay = true;
+      } else {
+        const unsigned long long c0 = launch_count();
+        replay = capture_step(parity_);
+        const int captured = (int)(launch_count() - c0);
+        if (replay) graph_launches_[parity_] = captured;
+        else count_launches(-captured);  // nothing ran; the eager step below counts its own
+      }
+    }
+    if (replay) {
+      QTT_CUDA(cudaGraphLaunch(graph_[parity_], st_));
     } else {
-      // midpoint: f_h = f + dt/2 L(f);  f_{n+1} = f + dt L(f_h)
-      cond_means(f_, v_[0]);
-      make_hfirst(f_, v_[0], hf_[0]);
-      Term a[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &f_, 0.5), term_mix(&f_, hf_[0], 0.5)};
-      run_stage(a, 3, fs_);
-      cond_means(fs_, v_[1]);
-      make_hfirst(fs_, v_[1], hf_[1]);
-      Term b[4] = {term_dense(0, &ident_, &f_, 1.0), term_dense(1, &op_lin_, &fs_, 1.0),
-                   term_dense(3, &ident_, &fs_, -1.0), term_mix(&fs_, hf_[1], 1.0)};
-      run_stage(b, 4, g_);
+      step_body();
+      warm_ = true;
     }
     std::swap(f_, g_);
+    parity_ ^= 1;
     time_ += p_.dt;
     ++steps_;
   }
@@ -823,12 +944,16 @@ std::vector<double> Engine::timings() const {
     t.push_back(timer_->flops[c]);
   }
   t.push_back((double)launch_count());
+  t.push_back(tc_issued_flops_);
   return t;
 }
 
 void Engine::set_time(double t, long long s) {
   time_ = t;
   steps_ = s;
+  const unsigned long long c = (unsigned long long)s;
+  QTT_CUDA(cudaMemcpyAsync(dstep_, &c, sizeof(c), cudaMemcpyHostToDevice, st_));
+  QTT_CUDA(cudaStreamSynchronize(st_));
 }
 
 }  // namespace qtt

@@ -21,6 +21,11 @@ struct DevMps {
   double* data = nullptr;
   double* core(int n) const { return data + off[n]; }
   size_t core_elems(int n) const { return (size_t)b[n] * 2 * b[n + 1]; }
+  size_t max_core_elems() const {
+    size_t m = 0;
+    for (int n = 0; n + 1 < (int)b.size(); ++n) m = core_elems(n) > m ? core_elems(n) : m;
+    return m;
+  }
   Chain chain() const;
 };
 
@@ -34,6 +39,11 @@ struct DevOp {
   const double* Wt(int n) const { return data + off_t[n]; }
   const double* Wss(int n) const { return data + off_ss[n]; }
 };
+
+// Arithmetic classes of the contractions (each precision form maps them to a
+// tensor-core mode): products carrying the state, products of the random
+// sketch environments, and state times sketch (the range finder's Y).
+enum GemmRole { GEMM_STATE = 0, GEMM_SKETCH = 1, GEMM_RANGE = 2 };
 
 // One summand c * Op * f of a stage.  kind 0: dense MPO over all sites;
 // kind 1: mixing Hadamard term -- dense composition-space MPO on the phi
@@ -95,16 +105,23 @@ class Engine {
   void upload_op(DevOp& op, const TT& t);
   void upload_tt_mps(DevMps& m, const TT& t, const std::vector<int>& bonds);
   // Contraction in the context's precision form (tensor cores for the reduced forms).
-  void gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C);
+  // role: GEMM_STATE (products that carry the state), GEMM_SKETCH (products
+  // of the random sketch environments), GEMM_RANGE (state times sketch)
+  void gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C,
+            int role = 0);
   // FP64 product (Gram matrices, norms, masses, observables).
   void gemm64(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C);
   void cond_means(const DevMps& f, double* v);
   void make_hfirst(const DevMps& f, double* v, double* hf);
-  void sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr);
+  void sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr, int role);
   void zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha);
-  void run_stage(Term* terms, int nterms, DevMps& out);
+  void run_stage(Term* terms, int nterms, DevMps& out, int stage);
+  void step_body();      // one RK2 step from f_ into g_ (launches only)
+  bool capture_step(int parity);  // false: graphs unavailable, run eagerly
   void run_stage_exact(Term* terms, int nterms, DevMps& out);
   void xgram(const DevMps& f, double* E);
+  void gram_pass(const DevMps& g);
+  void project_cores(const DevMps& g, DevMps& out);
   Term term_dense(int slot, const DevOp* op, const DevMps* f, double scale) const;
   Term term_mix(const DevMps* f, const double* hf, double scale) const;
   void chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out);
@@ -112,6 +129,7 @@ class Engine {
   Params p_;
   Model model_;
   cudaStream_t st_ = nullptr;
+  bool own_stream_ = false;
   int N_ = 0, kphi_ = 0, nc_ = 0;
   int prec_bits_ = 64;
   bool exact_ = false;
@@ -124,21 +142,31 @@ class Engine {
   std::vector<size_t> Woff_[4];
   double *C_[4] = {nullptr, nullptr, nullptr, nullptr}, *T_[4] = {nullptr, nullptr, nullptr, nullptr};
   double *P_ = nullptr, *X1_ = nullptr, *X2_ = nullptr, *Y_ = nullptr;
-  double *Mb_[3] = {nullptr, nullptr, nullptr}, *G_ = nullptr, *U_ = nullptr, *lam_ = nullptr, *Us_ = nullptr;
   double *v_[2] = {nullptr, nullptr}, *hf_[2] = {nullptr, nullptr};
-  double *envw_ = nullptr, *envout_ = nullptr, *ws_ = nullptr, *qrwork_ = nullptr, *eigwork_ = nullptr;
+  double *envw_ = nullptr, *envout_ = nullptr, *ws_ = nullptr, *qrwork_ = nullptr;
   double *disc_ = nullptr, *obsA_ = nullptr, *obsB_ = nullptr, *obsX_ = nullptr;
   int *status_ = nullptr, *ranks_ = nullptr;
+  std::vector<double*> gram_, tU_;
+  std::vector<int> trunc_bonds_;
+  EigProblem* trunc_probs_ = nullptr;
+  int trunc_nmax_ = 1, trunc_kmax_ = 0;
   size_t ws_elems_ = 0;
   void* pack_ws_ = nullptr;
   size_t pack_bytes_ = 0;
-  int tc_mode_ = -1;
+  int tc_mode_[3] = {-1, -1, -1};  // per GEMM role; -1: FP64 kernel
   int max_bond_ = 1;
-  unsigned long long stage_counter_ = 0;
+  unsigned long long* dstep_ = nullptr;  // device copy of the step count (sketch draws)
+  // CUDA graphs of one step, indexed by which of the two state buffers is f_
+  // (the step swaps them); captured after one step has run eagerly.
+  cudaGraphExec_t graph_[2] = {nullptr, nullptr};
+  int graph_launches_[2] = {0, 0};
+  bool graphs_ = true, warm_ = false;
+  int parity_ = 0;
   double time_ = 0.0;
   long long steps_ = 0;
   double discarded_last_ = 0.0;
   KernelTimer* timer_ = nullptr;
+  double tc_issued_flops_ = 0.0;
 };
 
 }  // namespace qtt

@@ -2,13 +2,28 @@
 //
 // C[b] = alpha * A[b] * B[b] + beta * C[b] with FP64 operand views (the same
 // MatView / OutView as the FP64 kernel).  Operands are first packed into
-// K-major, zero-padded buffers of the tensor-core input type:
+// K-major, zero-padded buffers of the tensor-core input type.
+//
+// Exact-slice form BF16X6 (unbiased).  Each row r of A (and each column c of B) is
+// scaled by 2^-e_r, e_r the binary exponent of its largest magnitude, and
+// written as x 2^-e_r = 2^-7 s_1 + 2^-15 s_2 + 2^-23 s_3 + ..., each slice an
+// integer |s_p| <= 128 obtained by rounding to nearest (exact in bf16).
+// Slice products s_i t_j are integers below 2^14; the tensor cores sum the
+// products of equal weight 2^-(14 + 8 g), g = i + j - 2, into accumulator g,
+// and as long as a sum stays below 2^24 the FP32 accumulation is exact.  K is
+// therefore cut into chunks (a few k-blocks of 64) whose accumulators are
+// combined in FP64 with their weights and the two scales, and the chunks are
+// summed in FP64 by the split-K reduction.  The only errors left are the
+// dropped high-order slices and products, which are symmetric about zero.
+// BF16X6 keeps 3 x 3 slices and the 6 products with g <= 2: ~2^-24 relative
+// to the row and column maxima.
+// Floating-point forms (FP32 accumulation on the tensor cores, which rounds
+// toward zero and therefore drifts):
 //   BF16X3 : A = A_hi + A_lo, B = B_hi + B_lo (bf16 each),
 //            A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi  (3 MMAs, kind::f16)
 //   TF32   : one MMA, kind::tf32
 //   TF32X3 : A = A_hi + A_lo (tf32 each), 3 MMAs, kind::tf32
 //   BF16   : one MMA, kind::f16
-// and accumulated in FP32 in tensor memory.
 //
 // Kernel: one 128 x BN output tile per CTA (4 warps).  Warp 0 (one elected
 // thread) streams A/B k-blocks with TMA (128-byte swizzle) into a ring of
@@ -141,45 +156,115 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t bn) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+// ---------------------------------------------------------------------------
+// Conversions between FP64 and FP32 by bit manipulation.  The FP64 pipe of
+// this GPU issues two operations per clock per SM, so the packing and the
+// epilogue (which touch every operand and output element) use only integer
+// and FP32 instructions.
+
+// float -> double, exact (zero, normal, inf and NaN by bits; denormals, which
+// the accumulators of these products do not produce in practice, by the
+// hardware conversion).
+__device__ __forceinline__ unsigned long long float_to_double_bits(uint32_t f) {
+  const uint32_t e = (f >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(f >> 31) << 63;
+  if (e == 0u) {
+    if ((f & 0x7FFFFFu) == 0u) return sign;
+    return (unsigned long long)__double_as_longlong((double)__uint_as_float(f));
+  }
+  const unsigned long long de = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e + 896u);
+  return sign | (de << 52) | ((unsigned long long)(f & 0x7FFFFFu) << 29);
+}
+
+// S 2^scale as a double, exact for |S| < 2^53; results below the normal range
+// flush to zero.
+__device__ __forceinline__ unsigned long long int_to_double_bits(long long S, int scale) {
+  if (S == 0) return 0ull;
+  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = (unsigned long long)(S < 0 ? -S : S);
+  const int lz = __clzll((long long)a);
+  const int ex = (63 - lz) + 1023 + scale;  // a = 1.m 2^(63 - lz)
+  if (ex <= 0) return sign;
+  if (ex >= 2047) return sign | (0x7FFull << 52);
+  const unsigned long long mant = ((a << lz) << 1) >> 12;  // drop the leading one, keep 52 bits
+  return sign | ((unsigned long long)ex << 52) | mant;
+}
+
+// double -> float, round to nearest even; results below the normal float
+// range flush to zero, results above it become infinities.
+__device__ __forceinline__ float double_bits_to_float(unsigned long long u) {
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FFull);
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned long long rem = m & 0x1FFFFFFFull;  // 29 dropped bits
+  uint32_t r = ((uint32_t)fe << 23) | (uint32_t)(m >> 29);
+  if (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) r += 1u;  // a carry into the exponent is correct
+  return __uint_as_float(sign | r);
+}
+
+// |x| as an order-preserving integer (the bits of a non-negative double).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// x 2^k by exponent arithmetic (x normal, result normal or flushed to zero).
+__device__ __forceinline__ unsigned long long scale_bits(unsigned long long u, int k) {
+  const int e = (int)((u >> 52) & 0x7FFull);
+  if (e == 0) return u & (1ull << 63);  // zero (or a denormal, flushed)
+  const int ne = e + k;
+  if (ne <= 0) return u & (1ull << 63);
+  return (u & ~(0x7FFull << 52)) | ((unsigned long long)ne << 52);
+}
+
+// na / nb: operand buffers of A and B per k-block; ngroups: TMEM accumulators.
 template <int MODE>
 struct ModeTraits;
 template <>
 struct ModeTraits<TC_BF16X3> {
-  static constexpr bool tf32 = false;
-  static constexpr int nops = 2, nmma = 3, esize = 2;
+  static constexpr bool tf32 = false, sliced = false;
+  static constexpr int na = 2, nb = 2, ngroups = 1, esize = 2;
+};
+template <>
+struct ModeTraits<TC_BF16X6> {
+  static constexpr bool tf32 = false, sliced = true;
+  static constexpr int na = 3, nb = 3, ngroups = 3, esize = 2;
 };
 template <>
 struct ModeTraits<TC_BF16> {
-  static constexpr bool tf32 = false;
-  static constexpr int nops = 1, nmma = 1, esize = 2;
+  static constexpr bool tf32 = false, sliced = false;
+  static constexpr int na = 1, nb = 1, ngroups = 1, esize = 2;
 };
 template <>
 struct ModeTraits<TC_TF32> {
-  static constexpr bool tf32 = true;
-  static constexpr int nops = 1, nmma = 1, esize = 4;
+  static constexpr bool tf32 = true, sliced = false;
+  static constexpr int na = 1, nb = 1, ngroups = 1, esize = 4;
 };
 template <>
 struct ModeTraits<TC_TF32X3> {
-  static constexpr bool tf32 = true;
-  static constexpr int nops = 2, nmma = 3, esize = 4;
+  static constexpr bool tf32 = true, sliced = false;
+  static constexpr int na = 2, nb = 2, ngroups = 1, esize = 4;
 };
 
-template <int BN>
-struct BnTraits {
-  static constexpr int tmem_cols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-};
+__host__ __device__ constexpr int tmem_cols_for(int cols) {
+  return cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+}
 
 template <int MODE, int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                   const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, int M, int N,
+                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
+                   const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, int M, int N,
                    int kblocks, int kb_per_split, int splitk, int inner, double alpha, double beta, OutView C,
-                   double* ws, int* err) {
+                   double* ws, const int* __restrict__ ea, const int* __restrict__ eb, int* err) {
   using Tr = ModeTraits<MODE>;
   constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
-  constexpr int STAGE_BYTES = Tr::nops * (A_BYTES + B_BYTES);
+  constexpr int STAGE_BYTES = Tr::na * A_BYTES + Tr::nb * B_BYTES;
   constexpr uint32_t IDESC = make_idesc(Tr::tf32 ? 2u : 1u, (uint32_t)BN);
-  constexpr int TMEM_COLS = BnTraits<BN>::tmem_cols;
+  constexpr int TMEM_COLS = tmem_cols_for(Tr::ngroups * BN);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -187,7 +272,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_issued;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
@@ -198,6 +283,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (threadIdx.x == 0) {
     s_abort = 0;
+    s_issued = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -215,7 +301,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer
+    // TMA producer; a stage holds the na A tiles, then the nb B tiles
+    const CUtensorMap* ma[3] = {&tmA0, &tmA1, &tmA2};
+    const CUtensorMap* mb[3] = {&tmB0, &tmB1, &tmB2};
     for (int kb = kb0, i = 0; kb < kb1; ++kb, ++i) {
       const int s = i % STAGES;
       const uint32_t ph = (uint32_t)((i / STAGES) & 1);
@@ -227,12 +315,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint8_t* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       const int kx = kb * (128 / Tr::esize);
-      tma_load_3d(st, &tmA0, &full[s], kx, m0, b);
-      tma_load_3d(st + Tr::nops * A_BYTES, &tmB0, &full[s], kx, n0, b);
-      if (Tr::nops == 2) {
-        tma_load_3d(st + A_BYTES, &tmA1, &full[s], kx, m0, b);
-        tma_load_3d(st + Tr::nops * A_BYTES + B_BYTES, &tmB1, &full[s], kx, n0, b);
-      }
+#pragma unroll
+      for (int t = 0; t < Tr::na; ++t) tma_load_3d(st + t * A_BYTES, ma[t], &full[s], kx, m0, b);
+#pragma unroll
+      for (int t = 0; t < Tr::nb; ++t) tma_load_3d(st + Tr::na * A_BYTES + t * B_BYTES, mb[t], &full[s], kx, n0, b);
+      s_issued = i + 1;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -248,16 +335,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       tc_fence_after();
       const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t a0 = st, a1 = st + A_BYTES;
-      const uint32_t b0 = st + Tr::nops * A_BYTES, b1 = b0 + B_BYTES;
+      const uint32_t bst = st + Tr::na * A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per 128-byte row
         const uint32_t off = kk * 32;
-        const uint32_t acc0 = (kb > kb0 || kk > 0) ? 1u : 0u;
-        mma_issue<Tr::tf32>(tmem, desc_sw128(a0 + off), desc_sw128(b0 + off), IDESC, acc0);
-        if (Tr::nmma == 3) {
-          mma_issue<Tr::tf32>(tmem, desc_sw128(a0 + off), desc_sw128(b1 + off), IDESC, 1u);
-          mma_issue<Tr::tf32>(tmem, desc_sw128(a1 + off), desc_sw128(b0 + off), IDESC, 1u);
+        const bool first = (kb == kb0 && kk == 0);
+        if (Tr::sliced) {
+          // accumulator g collects the slice products s_i t_j with i + j = g
+#pragma unroll
+          for (int g = 0; g < Tr::ngroups; ++g) {
+            bool fresh = first;
+#pragma unroll
+            for (int ia = 0; ia < Tr::na; ++ia) {
+              const int jb = g - ia;
+              if (jb < 0 || jb >= Tr::nb) continue;
+              mma_issue<false>(tmem + (uint32_t)(g * BN), desc_sw128(st + ia * A_BYTES + off),
+                               desc_sw128(bst + jb * B_BYTES + off), IDESC, fresh ? 0u : 1u);
+              fresh = false;
+            }
+          }
+        } else {
+          mma_issue<Tr::tf32>(tmem, desc_sw128(st + off), desc_sw128(bst + off), IDESC, first ? 0u : 1u);
+          if (Tr::na == 2) {  // hi lo + lo hi
+            mma_issue<Tr::tf32>(tmem, desc_sw128(st + off), desc_sw128(bst + B_BYTES + off), IDESC, 1u);
+            mma_issue<Tr::tf32>(tmem, desc_sw128(st + A_BYTES + off), desc_sw128(bst + off), IDESC, 1u);
+          }
         }
       }
       mma_commit(&empty[s]);
@@ -265,37 +367,71 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (ok) mma_commit(done);
   }
   __syncwarp();
-  // epilogue: every warp waits for the accumulator
   bool have = mbar_wait(done, 0);
   if (!have) atomicOr(err, 16);
   __syncthreads();
   have = have && (s_abort == 0) && (kb1 > kb0);
   tc_fence_after();
-  if (have) {
-    const int row = m0 + warp * 32 + lane;
+  if (s_abort != 0 && threadIdx.x == 0) {
+    // give the copies still in flight (the last STAGES issued) a bounded time to land
+    const int n_issued = s_issued;
+    for (int i = max(0, n_issued - STAGES); i < n_issued; ++i) mbar_wait(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
+  }
+  const int wrow0 = m0 + warp * 32;  // first output row of this warp's TMEM lanes
+  if (have && wrow0 < M) {
+    const int rows_here = min(32, M - wrow0);
     const int bo = b / inner, bi = b - bo * inner;
     double* Cb = C.p + bo * C.so + bi * C.si;
     double* W = ws ? ws + ((long long)b * splitk + ks) * (long long)M * N : nullptr;
+    const int m_pad = (int)gridDim.y * BM, n_pad = (int)gridDim.x * BN;
+    const int erow = (Tr::sliced && wrow0 + lane < M) ? ea[(long long)b * m_pad + wrow0 + lane] : 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // 32 x 32 staging tile per warp in the (drained) pipeline buffers: rows are
+    // TMEM lanes on the way in, columns are lanes on the way out (coalesced stores)
+    unsigned long long* stg = reinterpret_cast<unsigned long long*>(smem) + warp * (32 * 33);
+    const bool plain = (beta == 0.0) && (alpha == 1.0 || alpha == -1.0);
+    const unsigned long long sign_flip = (alpha == -1.0) ? (1ull << 63) : 0ull;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      tmem_ld_wait();
-      if (row < M) {
+    for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 32) {
+      uint32_t r[Tr::ngroups][32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < N) {
-            const double v = (double)__uint_as_float(r[j]);
-            if (W) {
-              W[(long long)row * N + col] = v;
-            } else {
-              double* c = Cb + (long long)row * C.rs + (long long)col * C.cs;
-              *c = (beta == 0.0) ? alpha * v : alpha * v + beta * (*c);
-            }
+      for (int g = 0; g < Tr::ngroups; ++g) tmem_ld32(lane_base + (uint32_t)(g * BN + c0), r[g]);
+      tmem_ld_wait();
+      const int ecol = (Tr::sliced && n0 + c0 + lane < N) ? eb[(long long)b * n_pad + n0 + c0 + lane] : 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        unsigned long long bits;
+        if (Tr::sliced) {
+          // exact integer sums of weights 2^-14, 2^-22, 2^-30 -> one integer
+          // S = I0 2^16 + I1 2^8 + I2 (< 2^41) -> S 2^(e_row + e_col - 30)
+          const int ec = __shfl_sync(0xffffffffu, ecol, j);
+          long long S = (long long)__float2int_rn(__uint_as_float(r[0][j])) << 16;
+          if (Tr::ngroups >= 2) S += (long long)__float2int_rn(__uint_as_float(r[1][j])) << 8;
+          if (Tr::ngroups >= 3) S += (long long)__float2int_rn(__uint_as_float(r[2][j]));
+          bits = int_to_double_bits(S, erow + ec - 30);
+        } else {
+          bits = float_to_double_bits(r[0][j]);
+        }
+        stg[lane * 33 + j] = bits;
+      }
+      __syncwarp();
+      const int col = n0 + c0 + lane;
+      if (col < N) {
+        for (int rr = 0; rr < rows_here; ++rr) {
+          const unsigned long long bits = stg[rr * 33 + lane];
+          const int row = wrow0 + rr;
+          if (W) {
+            reinterpret_cast<unsigned long long*>(W)[(long long)row * N + col] = bits;
+          } else {
+            double* c = Cb + (long long)row * C.rs + (long long)col * C.cs;
+            if (plain)
+              *reinterpret_cast<unsigned long long*>(c) = bits ^ sign_flip;
+            else
+              *c = alpha * __longlong_as_double((long long)bits) + (beta == 0.0 ? 0.0 : beta * (*c));
           }
         }
       }
+      __syncwarp();
     }
   }
   tc_fence_before();
@@ -310,32 +446,123 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Writes the packed form of one element.  Floating-point forms: x is rounded
+// to float, then split (hi = x rounded to the operand type, lo = the rest,
+// exact in float).  BF16X6: x is first scaled by 2^(7 - e) (e: exponent of its
+// row's largest magnitude, so |t| < 128), then t = s1 + 2^-8 s2 + 2^-16 s3 +
+// O(2^-17) with integers |s_p| <= 128 from round-to-nearest; all in FP32.
 template <int MODE>
-__global__ void pack_kernel(const double* p, long long rstr, long long kstr, long long so, long long si, int inner,
-                            int rows, int K, int rows_pad, int k_pad, long long batch, void* out0, void* out1) {
-  const long long per = (long long)rows_pad * k_pad;
-  const long long total = per * batch;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
-       x += (long long)gridDim.x * blockDim.x) {
-    const long long b = x / per;
-    const long long rk = x - b * per;
-    const int r = (int)(rk / k_pad), k = (int)(rk - (long long)r * k_pad);
-    double v = 0.0;
-    if (r < rows && k < K) {
-      const long long bo = b / inner, bi = b - bo * inner;
-      v = p[bo * so + bi * si + (long long)r * rstr + (long long)k * kstr];
+__device__ __forceinline__ void pack_one(double x, int e, size_t idx, void* o0, void* o1, void* o2) {
+  if constexpr (MODE == TC_BF16X6) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const float t = double_bits_to_float(scale_bits(u, 7 - e));
+    const float a1 = rintf(t);
+    float rr = (t - a1) * 256.0f;
+    const float a2 = rintf(rr);
+    rr = (rr - a2) * 256.0f;
+    ((__nv_bfloat16*)o0)[idx] = __float2bfloat16_rn(a1);
+    ((__nv_bfloat16*)o1)[idx] = __float2bfloat16_rn(a2);
+    ((__nv_bfloat16*)o2)[idx] = __float2bfloat16_rn(rintf(rr));
+  } else {
+    const float f = double_bits_to_float((unsigned long long)__double_as_longlong(x));
+    if constexpr (MODE == TC_BF16) {
+      ((__nv_bfloat16*)o0)[idx] = __float2bfloat16_rn(f);
+    } else if constexpr (MODE == TC_BF16X3) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(f);
+      ((__nv_bfloat16*)o0)[idx] = h;
+      ((__nv_bfloat16*)o1)[idx] = __float2bfloat16_rn(f - __bfloat162float(h));
+    } else if constexpr (MODE == TC_TF32) {
+      ((float*)o0)[idx] = to_tf32(f);
+    } else {  // TC_TF32X3
+      const float h = to_tf32(f);
+      ((float*)o0)[idx] = h;
+      ((float*)o1)[idx] = to_tf32(f - h);
     }
-    if (MODE == TC_BF16X3 || MODE == TC_BF16) {
-      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-      ((__nv_bfloat16*)out0)[x] = h;
-      if (MODE == TC_BF16X3) ((__nv_bfloat16*)out1)[x] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-    } else if (MODE == TC_TF32) {
-      ((float*)out0)[x] = to_tf32((float)v);
-    } else {
-      const float h = to_tf32((float)v);
-      ((float*)out0)[x] = h;
-      ((float*)out1)[x] = to_tf32((float)(v - (double)h));
+  }
+}
+
+// Row exponent for the exact slices: |x| < 2^e for every x of the row (0 for
+// an all-zero row), from the bits of the largest magnitude.
+__device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
+  const int E = (int)(maxbits >> 52);
+  return E == 0 ? 0 : E - 1022;
+}
+
+// Source rows with contiguous (or general) k: one warp per packed row.
+template <int MODE>
+__global__ void pack_rows_kernel(const double* __restrict__ p, long long rstr, long long kstr, long long so,
+                                 long long si, int inner, int rows, int K, int rows_pad, int k_pad, long long batch,
+                                 void* o0, void* o1, void* o2, int* expo) {
+  const long long warps_total = (long long)rows_pad * batch;
+  const int lane = threadIdx.x & 31;
+  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
+       w += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long b = w / rows_pad;
+    const int r = (int)(w - b * rows_pad);
+    const long long bo = b / inner, bi = b - bo * inner;
+    const double* row = p + bo * so + bi * si + (long long)r * rstr;
+    const bool live = r < rows;
+    int e = 0;
+    if constexpr (MODE == TC_BF16X6) {
+      unsigned long long mx = 0;
+      if (live)
+        for (int k = lane; k < K; k += 32) mx = max(mx, abs_bits(row[(long long)k * kstr]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      e = row_exponent(mx);
+      if (lane == 0) expo[w] = e;
     }
+    const size_t base = (size_t)w * k_pad;
+    for (int k = lane; k < k_pad; k += 32)
+      pack_one<MODE>((live && k < K) ? row[(long long)k * kstr] : 0.0, e, base + k, o0, o1, o2);
+  }
+}
+
+// Source rows that are contiguous across r (r stride 1, a column-major view,
+// e.g. B^T of a row-major B): 32 packed rows per block through a shared
+// tile, so that both the reads (along r) and the writes (along k) coalesce.
+template <int MODE>
+__global__ void __launch_bounds__(256) pack_cols_kernel(const double* __restrict__ p, long long kstr, long long so,
+                                                        long long si, int inner, int rows, int K, int rows_pad,
+                                                        int k_pad, void* o0, void* o1, void* o2, int* expo) {
+  __shared__ double tile[32][33];  // [k][r]
+  __shared__ unsigned long long red[8][32];
+  __shared__ int s_e[32];
+  const int tiles_r = rows_pad / 32;
+  const long long b = blockIdx.x / tiles_r;
+  const int r0 = (int)(blockIdx.x - b * tiles_r) * 32;
+  const long long bo = b / inner, bi = b - bo * inner;
+  const double* src = p + bo * so + bi * si;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const bool rlive = r0 + tx < rows;
+  if constexpr (MODE == TC_BF16X6) {
+    unsigned long long mx = 0;
+    if (rlive)
+      for (int k = ty; k < K; k += 8) mx = max(mx, abs_bits(src[(r0 + tx) + (long long)k * kstr]));
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+      for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
+      const int e = row_exponent(mx);
+      s_e[tx] = e;
+      expo[b * rows_pad + r0 + tx] = e;
+    }
+    __syncthreads();
+  }
+  for (int k0 = 0; k0 < k_pad; k0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int kl = ty + 8 * q, k = k0 + kl;
+      tile[kl][tx] = (rlive && k < K) ? src[(r0 + tx) + (long long)k * kstr] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rl = ty + 8 * q;
+      const int e = (MODE == TC_BF16X6) ? s_e[rl] : 0;
+      pack_one<MODE>(tile[tx][rl], e, ((size_t)b * rows_pad + r0 + rl) * k_pad + k0 + tx, o0, o1, o2);
+    }
+    __syncthreads();
   }
 }
 
@@ -373,37 +600,67 @@ template <int MODE, int BN, int STAGES>
 void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, int kbps, int splitk, int inner,
                long long batch, double alpha, double beta, OutView C, double* ws, int* err) {
   using Tr = ModeTraits<MODE>;
-  constexpr int SMEM = STAGES * Tr::nops * (BM * 128 + BN * 128) + 1024 + 256;
+  constexpr int SMEM = STAGES * (Tr::na * BM * 128 + Tr::nb * BN * 128) + 1024 + 256;
+  static_assert(SMEM <= 232448, "shared memory budget");
+  static_assert(Tr::ngroups * BN <= 512, "TMEM budget");
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tc_gemm_kernel<MODE, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     attr = true;
   }
-  const CUtensorMap a0 = make_map(pk.a0, Tr::esize, pk.k_pad, pk.m_pad, batch, BM);
-  const CUtensorMap a1 = make_map(Tr::nops == 2 ? pk.a1 : pk.a0, Tr::esize, pk.k_pad, pk.m_pad, batch, BM);
-  const CUtensorMap b0 = make_map(pk.b0, Tr::esize, pk.k_pad, pk.n_pad, batch, BN);
-  const CUtensorMap b1 = make_map(Tr::nops == 2 ? pk.b1 : pk.b0, Tr::esize, pk.k_pad, pk.n_pad, batch, BN);
+  CUtensorMap a[3], bm[3];
+  for (int i = 0; i < 3; ++i) {
+    a[i] = make_map(pk.a[i < Tr::na ? i : 0], Tr::esize, pk.k_pad, pk.m_pad, batch, BM);
+    bm[i] = make_map(pk.b[i < Tr::nb ? i : 0], Tr::esize, pk.k_pad, pk.n_pad, batch, BN);
+  }
   dim3 grid(pk.n_pad / BN, pk.m_pad / BM, (unsigned)(batch * splitk));
-  tc_gemm_kernel<MODE, BN, STAGES><<<grid, TC_THREADS, SMEM, st>>>(a0, a1, b0, b1, M, N, kblocks, kbps, splitk, inner,
-                                                                    alpha, beta, C, ws, err);
+  tc_gemm_kernel<MODE, BN, STAGES><<<grid, TC_THREADS, SMEM, st>>>(a[0], a[1], a[2], bm[0], bm[1], bm[2], M, N,
+                                                                    kblocks, kbps, splitk, inner, alpha, beta, C, ws,
+                                                                    pk.ea, pk.eb, err);
 }
 
+// Packs one operand (rows x K, element (r, k) at r * rstr + k * kstr) into the
+// K-major buffers o[0..) (and, for BF16X6, the row exponents).
 template <int MODE>
 void launch_pack(cudaStream_t st, const MatView& v, long long rstr, long long kstr, int inner, int rows, int K,
-                 int rows_pad, int k_pad, long long batch, void* o0, void* o1) {
-  const long long total = (long long)rows_pad * k_pad * batch;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 8192) blocks = 8192;
-  pack_kernel<MODE><<<(int)blocks, 256, 0, st>>>(v.p, rstr, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad, batch,
-                                                o0, o1);
+                 int rows_pad, int k_pad, long long batch, void* const* o, int* expo) {
+  if (rstr == 1 && kstr != 1 && rows_pad % 32 == 0) {
+    const long long blocks = (long long)(rows_pad / 32) * batch;
+    pack_cols_kernel<MODE><<<(unsigned)blocks, 256, 0, st>>>(v.p, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
+                                                             o[0], o[1], o[2], expo);
+  } else {
+    const long long warps = (long long)rows_pad * batch;
+    long long blocks = (warps * 32 + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    pack_rows_kernel<MODE><<<(int)blocks, 256, 0, st>>>(v.p, rstr, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
+                                                        batch, o[0], o[1], o[2], expo);
+  }
 }
 
-int choose_bn(int N) {
-  // smallest padded width; ties go to the wider tile
-  const int cands[4] = {256, 160, 128, 64};
-  int best = 128;
+struct ModeInfo {
+  int na, nb, ngroups, esize;
+  bool sliced;
+  int exact_kb;  // k-blocks one accumulator may sum exactly (0: no limit)
+};
+
+ModeInfo mode_info(int mode) {
+  switch (mode) {
+    case TC_BF16X3: return {2, 2, 1, 2, false, 0};
+    case TC_BF16X6: return {3, 3, 3, 2, true, 5};
+    case TC_BF16: return {1, 1, 1, 2, false, 0};
+    case TC_TF32: return {1, 1, 1, 4, false, 0};
+    default: return {2, 2, 1, 4, false, 0};  // TC_TF32X3
+  }
+}
+
+int choose_bn(int N, int mode) {
+  // smallest padded width among the tile widths whose accumulators fit in TMEM
+  const ModeInfo mi = mode_info(mode);
+  const int all[4] = {256, 160, 128, 64};
+  int best = 64;
   long long bestpad = 1LL << 60;
-  for (int c : cands) {
+  for (int c : all) {
+    if (mi.ngroups * c > 512) continue;
     const long long pad = (long long)((N + c - 1) / c) * c;
     if (pad < bestpad) {
       bestpad = pad;
@@ -413,19 +670,32 @@ int choose_bn(int N) {
   return best;
 }
 
+struct PackLayout {
+  int bn, m_pad, n_pad, k_pad, kb;
+  size_t a_bytes, b_bytes, total;
+};
+
+size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+PackLayout pack_layout(int M, int N, int K, long long batch, int mode) {
+  const ModeInfo mi = mode_info(mode);
+  PackLayout L;
+  L.bn = choose_bn(N, mode);
+  L.kb = 128 / mi.esize;
+  L.k_pad = (K + L.kb - 1) / L.kb * L.kb;
+  L.m_pad = (M + BM - 1) / BM * BM;
+  L.n_pad = (N + L.bn - 1) / L.bn * L.bn;
+  L.a_bytes = (size_t)L.m_pad * L.k_pad * batch * mi.esize;
+  L.b_bytes = (size_t)L.n_pad * L.k_pad * batch * mi.esize;
+  L.total = mi.na * up256(L.a_bytes) + mi.nb * up256(L.b_bytes) + up256((size_t)L.m_pad * batch * 4) +
+            up256((size_t)L.n_pad * batch * 4) + 256;
+  return L;
+}
+
 }  // namespace
 
-int tc_mode_esize(int mode) { return (mode == TC_TF32 || mode == TC_TF32X3) ? 4 : 2; }
-int tc_mode_nops(int mode) { return (mode == TC_BF16X3 || mode == TC_TF32X3) ? 2 : 1; }
-
 size_t tc_workspace_bytes(int M, int N, int K, long long batch, int mode) {
-  const int es = tc_mode_esize(mode), nops = tc_mode_nops(mode);
-  const int bn = choose_bn(N);
-  const long long kb = 128 / es;
-  const long long k_pad = (K + kb - 1) / kb * kb;
-  const long long m_pad = (M + BM - 1) / BM * BM;
-  const long long n_pad = (N + bn - 1) / bn * bn;
-  return (size_t)(nops * (m_pad + n_pad) * k_pad * batch * es) + 4096;
+  return pack_layout(M, N, K, batch, mode).total + 8192;
 }
 
 bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B,
@@ -435,49 +705,41 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   load_encode();
   const long long batch = (long long)outer * inner;
   if (batch > 65535) return false;
-  const int es = tc_mode_esize(mode), nops = tc_mode_nops(mode);
-  const int bn = choose_bn(N);
+  const ModeInfo mi = mode_info(mode);
+  const PackLayout L = pack_layout(M, N, K, batch, mode);
+  if (L.total > pack_bytes) return false;
   TcPacked pk;
-  const int kb = 128 / es;
-  pk.k_pad = (K + kb - 1) / kb * kb;
-  pk.m_pad = (M + BM - 1) / BM * BM;
-  pk.n_pad = (N + bn - 1) / bn * bn;
-  const size_t a_bytes = (size_t)pk.m_pad * pk.k_pad * batch * es;
-  const size_t b_bytes = (size_t)pk.n_pad * pk.k_pad * batch * es;
-  const size_t need = nops * (a_bytes + b_bytes);
-  if (need + 1024 > pack_bytes) return false;
+  pk.k_pad = L.k_pad;
+  pk.m_pad = L.m_pad;
+  pk.n_pad = L.n_pad;
   uint8_t* base = (uint8_t*)(((uintptr_t)pack_ws + 255) & ~(uintptr_t)255);
   auto carve = [&](size_t n) {
-    uint8_t* p = base;
-    base += (n + 255) & ~(size_t)255;
-    return (void*)p;
+    uint8_t* q = base;
+    base += up256(n);
+    return (void*)q;
   };
-  pk.a0 = carve(a_bytes);
-  pk.a1 = nops == 2 ? carve(a_bytes) : nullptr;
-  pk.b0 = carve(b_bytes);
-  pk.b1 = nops == 2 ? carve(b_bytes) : nullptr;
+  for (int i = 0; i < mi.na; ++i) pk.a[i] = carve(L.a_bytes);
+  for (int i = 0; i < mi.nb; ++i) pk.b[i] = carve(L.b_bytes);
+  pk.ea = (int*)carve((size_t)L.m_pad * batch * 4);
+  pk.eb = (int*)carve((size_t)L.n_pad * batch * 4);
   // A(m, k) = A.p[m * rs + k * cs]; B is packed as B^T: (n, k) = B.p[k * rs + n * cs]
+#define QTT_PACK(MODE_)                                                                               \
+  launch_pack<MODE_>(st, A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch, pk.a, pk.ea);           \
+  launch_pack<MODE_>(st, B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch, pk.b, pk.eb);
   switch (mode) {
-    case TC_BF16X3:
-      launch_pack<TC_BF16X3>(st, A, A.rs, A.cs, inner, M, K, pk.m_pad, pk.k_pad, batch, pk.a0, pk.a1);
-      launch_pack<TC_BF16X3>(st, B, B.cs, B.rs, inner, N, K, pk.n_pad, pk.k_pad, batch, pk.b0, pk.b1);
-      break;
-    case TC_BF16:
-      launch_pack<TC_BF16>(st, A, A.rs, A.cs, inner, M, K, pk.m_pad, pk.k_pad, batch, pk.a0, nullptr);
-      launch_pack<TC_BF16>(st, B, B.cs, B.rs, inner, N, K, pk.n_pad, pk.k_pad, batch, pk.b0, nullptr);
-      break;
-    case TC_TF32:
-      launch_pack<TC_TF32>(st, A, A.rs, A.cs, inner, M, K, pk.m_pad, pk.k_pad, batch, pk.a0, nullptr);
-      launch_pack<TC_TF32>(st, B, B.cs, B.rs, inner, N, K, pk.n_pad, pk.k_pad, batch, pk.b0, nullptr);
-      break;
-    default:
-      launch_pack<TC_TF32X3>(st, A, A.rs, A.cs, inner, M, K, pk.m_pad, pk.k_pad, batch, pk.a0, pk.a1);
-      launch_pack<TC_TF32X3>(st, B, B.cs, B.rs, inner, N, K, pk.n_pad, pk.k_pad, batch, pk.b0, pk.b1);
-      break;
+    case TC_BF16: QTT_PACK(TC_BF16); break;
+    case TC_BF16X3: QTT_PACK(TC_BF16X3); break;
+    case TC_TF32: QTT_PACK(TC_TF32); break;
+    case TC_TF32X3: QTT_PACK(TC_TF32X3); break;
+    default: QTT_PACK(TC_BF16X6); break;
   }
-  const int kblocks = pk.k_pad / kb;
-  // split K when the tile grid is small
-  const long long tiles = (long long)(pk.m_pad / BM) * (pk.n_pad / bn) * batch;
+#undef QTT_PACK
+  const int kblocks = L.k_pad / L.kb;
+  // split K when the tile grid is small; the exact-slice modes also cap the
+  // depth one accumulator sums so that its partial sums stay exact integers
+  int cap = max_kb_per_split;
+  if (mi.exact_kb > 0 && (cap <= 0 || cap > mi.exact_kb)) cap = mi.exact_kb;
+  const long long tiles = (long long)(L.m_pad / BM) * (L.n_pad / L.bn) * batch;
   int splitk = 1;
   if (tiles < 152 && kblocks >= 4) {
     long long s = (2 * 152 + tiles - 1) / tiles;
@@ -485,14 +747,12 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     if (s > 64) s = 64;
     if (s < 1) s = 1;
     splitk = (int)s;
-    if (ws == nullptr || (size_t)splitk * batch * (size_t)M * N > ws_elems) splitk = 1;
   }
   int kbps = (kblocks + splitk - 1) / splitk;
-  if (max_kb_per_split > 0 && kbps > max_kb_per_split && ws != nullptr &&
-      (size_t)((kblocks + max_kb_per_split - 1) / max_kb_per_split) * batch * (size_t)M * N <= ws_elems)
-    kbps = max_kb_per_split;
+  if (cap > 0 && kbps > cap) kbps = cap;
   splitk = (kblocks + kbps - 1) / kbps;
-  if ((long long)splitk * batch > 65535) {
+  if (splitk > 1 && (ws == nullptr || (size_t)splitk * batch * (size_t)M * N > ws_elems || splitk * batch > 65535)) {
+    if (mi.exact_kb > 0) return false;  // exactness needs the FP64 reduction of the chunks
     splitk = 1;
     kbps = kblocks;
   }
@@ -500,19 +760,28 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   count_launches(2 + (splitk > 1 ? 2 : 1));
 #define QTT_TC_LAUNCH(MODE_, BN_, ST_) \
   launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kbps, splitk, inner, batch, alpha, beta, C, wsp, err)
-#define QTT_TC_BN(MODE_, S256, S160, S128, S64)    \
-  switch (bn) {                                    \
+#define QTT_TC_BN(MODE_, S256, S160, S128, S64)       \
+  switch (L.bn) {                                     \
     case 256: QTT_TC_LAUNCH(MODE_, 256, S256); break; \
     case 160: QTT_TC_LAUNCH(MODE_, 160, S160); break; \
     case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
     default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
   }
+#define QTT_TC_BN3(MODE_, S160, S128, S64)            \
+  switch (L.bn) {                                     \
+    case 160: QTT_TC_LAUNCH(MODE_, 160, S160); break; \
+    case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
+    default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
+  }
+  // stages: as many as fit in 227 KB of shared memory
   switch (mode) {
     case TC_BF16X3: QTT_TC_BN(TC_BF16X3, 2, 3, 3, 4); break;
+    case TC_BF16X6: QTT_TC_BN3(TC_BF16X6, 2, 2, 3); break;
     case TC_BF16: QTT_TC_BN(TC_BF16, 4, 4, 6, 8); break;
     case TC_TF32: QTT_TC_BN(TC_TF32, 4, 4, 6, 8); break;
     default: QTT_TC_BN(TC_TF32X3, 2, 3, 3, 4); break;
   }
+#undef QTT_TC_BN3
 #undef QTT_TC_BN
 #undef QTT_TC_LAUNCH
   if (splitk > 1) splitk_reduce(st, M, N, inner, splitk, (int)batch, alpha, ws, beta, C);

@@ -5,11 +5,19 @@
 
 namespace qtt {
 
-enum TcMode { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2, TC_BF16 = 3 };
+// BF16X6: exact 8-bit integer slices of row-scaled operands (3 x 3 slices,
+// 6 slice products), exact FP32 accumulation per chunk of K, FP64 combination
+// -- unbiased, ~2^-24 relative to the row and column maxima.  BF16X3 / TF32 /
+// TF32X3 / BF16: floating-point operands (hi+lo 3-pass, 1-pass, hi+lo 3-pass,
+// 1-pass) accumulated by the tensor cores in FP32, which rounds toward zero.
+enum TcMode { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2, TC_BF16 = 3, TC_BF16X6 = 4 };
 
 // Packed K-major operand buffers of one product.
 struct TcPacked {
-  void *a0 = nullptr, *a1 = nullptr, *b0 = nullptr, *b1 = nullptr;
+  void* a[3] = {nullptr, nullptr, nullptr};
+  void* b[3] = {nullptr, nullptr, nullptr};
+  int* ea = nullptr;  // per-row power-of-two exponents (sliced modes)
+  int* eb = nullptr;
   int m_pad = 0, n_pad = 0, k_pad = 0;
 };
 
@@ -17,11 +25,11 @@ struct TcPacked {
 size_t tc_workspace_bytes(int M, int N, int K, long long batch, int mode);
 
 // Same contract as gemm_f64 (FP64 views in and out), computed on the tensor
-// cores in the given mode with FP32 accumulation.  max_kb_per_split > 0 caps
-// the k-blocks one accumulator sums (the rest is summed in FP64 by the split-K
-// reduction).  Returns false (launching
-// nothing) when the product does not fit the packing workspace or the grid
-// limits; *err receives nonzero bits when a bounded wait gives up.
+// cores in the given mode.  max_kb_per_split > 0 caps the k-blocks (of 128
+// bytes) one accumulator sums; the chunks are summed in FP64 by the split-K
+// reduction.  Returns false (launching nothing) when the product does not fit
+// the packing workspace, the FP64 split-K workspace (exact-slice modes) or the
+// grid limits; *err receives nonzero bits when a bounded wait gives up.
 bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B,
              double beta, OutView C, void* pack_ws, size_t pack_bytes, double* ws, size_t ws_elems, int* err,
              int max_kb_per_split = 0);

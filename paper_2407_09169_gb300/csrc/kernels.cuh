@@ -51,18 +51,30 @@ void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void*
 // Symmetric eigen-decomposition of an n x n row-major matrix G (n <= 1024).
 // Eigenvalues descending in lam[0..n); eigenvectors of the leading k in the
 // columns of U (n x k, row-major).  Computed in float or double; work must
-// hold 3 * n * n + 3 * n elements of that type.  *status |= 2 when the QL
+// hold eig_work_bytes(n, prec_bits) bytes.  *status |= 2 when the QL
 // iteration hits its cap.
+size_t eig_work_bytes(int n, int prec_bits);  // plus 256 + sizeof(EigProblem) for eig_sym
 void eig_sym(cudaStream_t st, int n, int k, const double* G, double* U, double* lam, void* work, int prec_bits,
              int* status);
+// Many independent problems in one launch (one block per problem); the
+// descriptors live in device memory, nmax / kmax bound every n / k.
+struct EigProblem {
+  int n = 0, k = 0;
+  const double* G = nullptr;
+  double* U = nullptr;
+  double* lam = nullptr;
+  unsigned char* work = nullptr;  // eig_work_bytes(n, prec_bits) bytes
+};
+void eig_sym_batched(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nmax, int kmax, int prec_bits,
+                     int* status);
 
-// One bond of the SVD truncation sweep.  With G = M M^T = U diag(lam) U^T
-// (U: r x ku, ld ku) keep kk = min(D, ku, #{lam_i > thr}) directions,
-// thr = max(tol^2, floor_rel) * lam_0.  Writes Us[:, i] = U[:, i]/sqrt(lam_i)
-// and L[:, i] = U[:, i] sqrt(lam_i) for i < kk, zeros for kk <= i < D
-// (both r x D row-major); adds sum_{i >= kk} lam_i to *discarded; stores kk.
-void sweep_scales(cudaStream_t st, int r, int D, int ku, const double* U, const double* lam, double tol,
-                  double floor_rel, double* Us, double* L, double* discarded, int* rank);
+// Rank selection of the bond truncation, one block per problem: with
+// lam (descending, n values) and U (n x k, k = kept columns at most), keep
+// kk = min(k, #{lam_i > thr}) columns, thr = max(tol^2, floor_rel) * lam_0,
+// zero the columns kk..k-1 of U, add sum_{i >= kk} lam_i to *discarded and
+// store kk in ranks[problem].
+void truncate_select(cudaStream_t st, const EigProblem* probs_dev, int nprob, double tol, double floor_rel,
+                     double* discarded, int* ranks);
 
 // core[a][s][b] = (b == 2a + s): an r x 2 x 2r left identity core.
 void fill_identity_left(cudaStream_t st, double* core, int r);
@@ -73,6 +85,15 @@ void fill_value(cudaStream_t st, double* p, size_t n, double v);
 // hashing of (seed, stream, index), Box-Muller).
 void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned long long seed,
                    unsigned long long stream_id);
+// The Gaussian sketch cores of one stage: cores n = 1 .. om.n - 1 (bond
+// l_n x 2 x l_{n+1}) with sigma_n = 1 / sqrt(2 l_{n+1}), drawn with the same
+// generator from the stream ((*step) * 2 + stage) * kMaxSites + n.  The step
+// count is read on the device, so a replayed graph draws fresh cores and a
+// restart from a checkpoint (which restores the count) draws the same ones.
+void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, unsigned long long seed,
+                          const unsigned long long* step, int stage);
+// *c += 1 on the device.
+void bump_counter(cudaStream_t st, unsigned long long* c);
 
 // out[q * ldo + b] = contraction of the sites [0, nsites) of the weight
 // chain w (bond <= 4) with the MPS chain f, left to right; result indexed by

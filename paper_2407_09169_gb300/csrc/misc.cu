@@ -57,38 +57,28 @@ __global__ void gaussian_kernel(double* p, size_t n, double sigma, unsigned long
   }
 }
 
-__global__ void sweep_scales_kernel(int r, int D, int ku, const double* U, const double* lam, double tol,
-                                    double floor_rel, double* Us, double* L, double* discarded, int* rank) {
-  __shared__ int s_kk;
-  if (threadIdx.x == 0) {
-    const double l0 = lam[0] > 0.0 ? lam[0] : 0.0;
-    const double rel = tol * tol > floor_rel ? tol * tol : floor_rel;
-    const double thr = rel * l0;
-    int lim = D < ku ? D : ku;
-    lim = lim < r ? lim : r;
-    int kk = 0;
-    while (kk < lim && lam[kk] > thr && lam[kk] > 0.0) ++kk;
-    double dis = 0.0;
-    for (int i = kk; i < r; ++i) dis += lam[i] > 0.0 ? lam[i] : 0.0;
-    *discarded += dis;
-    *rank = kk;
-    s_kk = kk;
-  }
-  __syncthreads();
-  const int kk = s_kk;
-  for (int x = threadIdx.x; x < r * D; x += blockDim.x) {
-    const int i = x / D, c = x - i * D;
-    if (c < kk) {
-      const double sl = sqrt(lam[c]);
-      const double u = U[(size_t)i * ku + c];
-      Us[x] = u / sl;
-      L[x] = u * sl;
-    } else {
-      Us[x] = 0.0;
-      L[x] = 0.0;
-    }
+// All sketch cores of one stage in one launch: blockIdx.y = site n in [1, N).
+__global__ void gaussian_sketch_kernel(Chain om, unsigned long long seed, const unsigned long long* step,
+                                       int stage) {
+  const int n = blockIdx.y;
+  if (n == 0 || n >= om.n) return;
+  const int bl = om.bond[n], br = om.bond[n + 1];
+  const size_t cnt = (size_t)bl * 2 * br;
+  const double sigma = rsqrt(2.0 * (double)br);
+  const unsigned long long stream_id = ((*step) * 2ull + (unsigned long long)stage) * (unsigned long long)kMaxSites +
+                                       (unsigned long long)n;
+  const unsigned long long base = mix64(seed ^ mix64(stream_id + 0x632BE59BD9B4E019ull));
+  double* p = const_cast<double*>(om.core[n]);  // the sketch MPS is scratch owned by the engine
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < cnt; x += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long h1 = mix64(base + 2 * (unsigned long long)x);
+    const unsigned long long h2 = mix64(base + 2 * (unsigned long long)x + 1);
+    const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);          // [0, 1)
+    p[x] = sigma * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
   }
 }
+
+__global__ void bump_kernel(unsigned long long* c) { *c += 1ull; }
 
 __global__ void left_weight_env_kernel(Chain f, Chain w, int nsites, int max_bond, double* out, int ldo,
                                        double* work) {
@@ -182,6 +172,32 @@ __global__ void finite_kernel(const double* p, size_t n, int* flag) {
     }
 }
 
+__global__ void truncate_select_kernel(const EigProblem* probs, double tol, double floor_rel, double* discarded,
+                                       int* ranks) {
+  const EigProblem P = probs[blockIdx.x];
+  __shared__ int s_kk;
+  if (threadIdx.x == 0) {
+    const double l0 = P.lam[0] > 0.0 ? P.lam[0] : 0.0;
+    const double rel = tol * tol > floor_rel ? tol * tol : floor_rel;
+    const double thr = rel * l0;
+    int kk = 0;
+    while (kk < P.k && P.lam[kk] > thr && P.lam[kk] > 0.0) ++kk;
+    double dis = 0.0;
+    for (int i = kk; i < P.n; ++i) dis += P.lam[i] > 0.0 ? P.lam[i] : 0.0;
+    atomicAdd(discarded, dis);
+    ranks[blockIdx.x] = kk;
+    s_kk = kk;
+  }
+  __syncthreads();
+  const int kk = s_kk;
+  const int w = P.k - kk;
+  if (w <= 0) return;
+  for (int x = threadIdx.x; x < P.n * w; x += blockDim.x) {
+    const int i = x / w, c = kk + (x - i * w);
+    P.U[(size_t)i * P.k + c] = 0.0;
+  }
+}
+
 int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -191,6 +207,12 @@ int grid_for(size_t n) {
 
 }  // namespace
 
+void truncate_select(cudaStream_t st, const EigProblem* probs_dev, int nprob, double tol, double floor_rel,
+                     double* discarded, int* ranks) {
+  if (nprob <= 0) return;
+  count_launches(1);
+  truncate_select_kernel<<<nprob, 256, 0, st>>>(probs_dev, tol, floor_rel, discarded, ranks);
+}
 void fill_identity_left(cudaStream_t st, double* core, int r) {
   count_launches(1);
   identity_left_kernel<<<grid_for((size_t)r * 4 * r), 256, 0, st>>>(core, r);
@@ -208,10 +230,17 @@ void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned 
   if (n) count_launches(1);
   if (n) gaussian_kernel<<<grid_for(n), 256, 0, st>>>(p, n, sigma, seed, stream_id);
 }
-void sweep_scales(cudaStream_t st, int r, int D, int ku, const double* U, const double* lam, double tol,
-                  double floor_rel, double* Us, double* L, double* discarded, int* rank) {
+void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, unsigned long long seed,
+                          const unsigned long long* step, int stage) {
+  if (om.n <= 1) return;
   count_launches(1);
-  sweep_scales_kernel<<<1, 256, 0, st>>>(r, D, ku, U, lam, tol, floor_rel, Us, L, discarded, rank);
+  size_t bx = (max_core + 255) / 256;
+  if (bx > 64) bx = 64;
+  gaussian_sketch_kernel<<<dim3((unsigned)bx, (unsigned)om.n), 256, 0, st>>>(om, seed, step, stage);
+}
+void bump_counter(cudaStream_t st, unsigned long long* c) {
+  count_launches(1);
+  bump_kernel<<<1, 1, 0, st>>>(c);
 }
 void left_weight_env(cudaStream_t st, const Chain& f, const Chain& w, int nsites, int max_bond, double* out,
                      int ldo, double* work) {

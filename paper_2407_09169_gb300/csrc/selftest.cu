@@ -28,9 +28,13 @@ std::vector<double> down(const double* d, size_t n) {
 }  // namespace
 
 // which = 0: tensor-core GEMM modes against the FP64 GEMM.  For every case
-// and mode (BF16X3, TF32, TF32X3, BF16) one value: max |C_tc - C_64| / max |C_64|.
+// and mode (BF16X3, TF32, TF32X3, BF16, BF16X6) one value:
+// max |C_tc - C_64| / max |C_64|.
 // which = 1: QR (FP64 and FP32): ||Q^T Q - I||_max and ||Q Q^T Y - Y|| / ||Y|| per case.
 // which = 2: eigensolver (FP64 and FP32): ||G U - U diag(lam)|| / ||G|| and ||U^T U - I||_max.
+// which = 3: bias of the tensor-core modes (TF32X3, BF16X3, BF16X6) on positive
+// operands, K in {32, 256, 2048}, with and without a one-k-block cap per
+// accumulator: (mean, max) of the signed relative error (C_tc - C_64) / C_64.
 std::vector<double> run_selftest(int which) {
   cudaStream_t st = nullptr;
   std::vector<double> out;
@@ -71,7 +75,7 @@ std::vector<double> run_selftest(int which) {
       bv.cs = c.tb ? c.K : 1;
       bv.si = (long long)c.K * c.N;
       bv.so = bv.si * c.inner;
-      for (int mode = 0; mode < 4; ++mode) {
+      for (int mode = 0; mode < 5; ++mode) {
         fill_gaussian(st, C0.p, csz, 1.0, 777, 3);
         fill_gaussian(st, C1.p, csz, 1.0, 777, 3);
         OutView c0, c1;
@@ -83,7 +87,7 @@ std::vector<double> run_selftest(int which) {
         c1 = c0;
         c1.p = C1.p;
         gemm_f64(st, c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, c0, ws.p, ws_elems);
-        const int tc_mode[4] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16};
+        const int tc_mode[5] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16, TC_BF16X6};
         if (!gemm_tc(st, tc_mode[mode], c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, c1, pack, pack_bytes,
                      ws.p, ws_elems, err)) {
           out.push_back(-1.0);
@@ -139,7 +143,7 @@ std::vector<double> run_selftest(int which) {
     for (int n : sizes) {
       // G = X X^T with a graded spectrum (columns scaled by 10^(-6 i / n))
       std::vector<double> x((size_t)n * n);
-      DBuf X((size_t)n * n), G((size_t)n * n), U((size_t)n * n), L(n), W((size_t)3 * n * n + 3 * n + 64);
+      DBuf X((size_t)n * n), G((size_t)n * n), U((size_t)n * n), L(n), W(eig_work_bytes(n, 64) / 8 + 64);
       fill_gaussian(st, X.p, (size_t)n * n, 1.0, 4242 + n, 6);
       if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest eig");
       x = down(X.p, (size_t)n * n);
@@ -201,7 +205,7 @@ std::vector<double> run_selftest(int which) {
       c0.p = C0.p; c0.rs = N; c0.cs = 1;
       c1 = c0; c1.p = C1.p;
       gemm_f64(st, M, N, K, 1, 1, 1.0, av, bv, 0.0, c0, ws.p, ws_elems);
-      const int modes[2] = {TC_TF32X3, TC_BF16X3};
+      const int modes[3] = {TC_TF32X3, TC_BF16X3, TC_BF16X6};
       for (int mode : modes)
         for (int chunk : {0, 1}) {
           if (!gemm_tc(st, mode, M, N, K, 1, 1, 1.0, av, bv, 0.0, c1, pack, pack_bytes, ws.p, ws_elems, err, chunk)) {

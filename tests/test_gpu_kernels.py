@@ -7,11 +7,14 @@ import pytest
 pytestmark = pytest.mark.gpu
 pkg = pytest.importorskip("paper_2407_09169_gb300")
 
-MODES = ["bf16x3", "tf32", "tf32x3", "bf16"]
-# per-mode bound on max|C_tc - C_fp64| / max|C_fp64|: 3 * 2^-17 for the split
-# forms (dropped lo*lo term and the hi/lo representation), 2^-10 / 2^-7 for the
-# single-pass forms, with room for FP32 accumulation
-TOL = {"bf16x3": 6e-5, "tf32": 4e-3, "tf32x3": 5e-6, "bf16": 3e-2}
+MODES = ["bf16x3", "tf32", "tf32x3", "bf16", "bf16x6"]
+# per-mode bound on max|C_tc - C_fp64| / max|C_fp64|.  Exact-slice forms: each
+# operand element is kept to 2^-16 (2 slices) / 2^-24 (3 slices) of its row's
+# (column's) largest power of two, and the dropped slice products are of the
+# same order; with rows of Gaussian entries (max ~4 sigma) the error of C is a
+# few units of 2^-16 / 2^-24 times 16 relative to max|C|.  TF32X3: 2^-21 plus
+# FP32 accumulation; single-pass forms 2^-10 / 2^-7.
+TOL = {"bf16x3": 4e-4, "tf32": 4e-3, "tf32x3": 5e-6, "bf16": 3e-2, "bf16x6": 3e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -24,7 +27,7 @@ def lib(gpu_available):
 def test_tensor_core_gemm_modes():
     v = pkg.qtt_selftest(0)
     assert v[-1] == 0, "a bounded wait gave up"
-    errs = np.array(v[:-1]).reshape(-1, 4)
+    errs = np.array(v[:-1]).reshape(-1, len(MODES))
     print("\n".join(" ".join(f"{m}={e:.2e}" for m, e in zip(MODES, row)) for row in errs))
     for row in errs:
         for m, e in zip(MODES, row):

@@ -17,10 +17,13 @@ def lib(gpu_available):
     return pkg.load_library()
 
 
-# Bounds of the current tensor-core forms after 10 steps of the 2^4-point workload
-# (chi 32).  The floor ~2e-4 comes from the tensor cores' FP32 accumulation,
-# which rounds toward zero (see test_accumulation_bias_is_measured).
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 5e-4), ("fp32", 5e-4), ("tf32", 3e-2)])
+# Bounds of the reduced-precision forms after 10 steps of the 2^4-point
+# workload (chi 32), relative L2 distance to the FP64 path at equal chi.  The
+# measured levels are 2.3e-4 (bf16x3: biased FP32 accumulation), 7.6e-5
+# (fp32: exact-slice products, whose resolution is relative to each row's
+# largest element, plus the FP32 QR, which alone gives 1.1e-5) and 1.5e-2
+# (tf32); the bounds leave a factor ~2.
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 5e-4), ("fp32", 2e-4), ("tf32", 3e-2)])
 def test_precision_form_vs_fp64_small(prec, tol):
     p64 = workload.make_params("small")
     pr = workload.make_params("small", precision=prec)
@@ -37,14 +40,19 @@ def test_precision_form_vs_fp64_small(prec, tol):
     print(f"{prec}: rel-L2 vs fp64 {rel:.2e}, vs oracle {vs_oracle:.2e}, "
           f"norm err {sb['norm_avg'] - 1:.1e}, d<Phi1> {sb['mean1_avg'] - sa['mean1_avg']:.1e}")
     assert rel < tol
-    assert abs(sb["norm_avg"] - 1.0) < 2e-2
+    assert abs(sb["norm_avg"] - 1.0) < {"tf32": 5e-2, "bf16x3": 1e-3, "fp32": 2e-5}[prec]
 
 
-def test_accumulation_bias_is_measured():
-    """Positive operands: the tensor-core product is systematically smaller than
-    the FP64 one (mean signed relative error < 0), at the 1e-7..1e-6 level."""
-    v = np.array(pkg.qtt_selftest(3)[:-1]).reshape(3, 2, 2, 2)
-    means = v[..., 0]
-    print("mean signed relative errors:", means.ravel())
-    assert np.all(np.abs(v[..., 1]) < 1e-5)
-    assert np.all(means < 0) and np.all(means > -5e-6)
+def test_accumulation_bias():
+    """Positive operands, K in {32, 256, 2048}, with and without a one-k-block
+    cap per accumulator.  The floating-point forms (TF32X3, BF16X3) are
+    systematically low: the tensor cores' FP32 accumulation rounds toward
+    zero.  The exact-slice form BF16X6 is unbiased: its mean signed error is a
+    small fraction of its largest error."""
+    v = np.array(pkg.qtt_selftest(3)[:-1]).reshape(3, 3, 2, 2)  # K, mode, cap, (mean, max)
+    means, maxes = v[..., 0], v[..., 1]
+    for name, k in (("tf32x3", 0), ("bf16x3", 1), ("bf16x6", 2)):
+        print(name, "mean", means[:, k].ravel(), "max", maxes[:, k].ravel())
+    for k, bound in ((0, 1e-5), (1, 3e-5)):
+        assert np.all(maxes[:, k] < bound) and np.all(means[:, k] < 0) and np.all(means[:, k] > -5e-6)
+    assert np.all(maxes[:, 2] < 2e-6) and np.all(np.abs(means[:, 2]) < 0.05 * maxes[:, 2])
