@@ -37,6 +37,7 @@ METRIC = "MPS time-steps/s at chi=128 vs plain FP64 GPU path; rel-L2 vs FP64 ora
 # TFLOP/s measured by an FMA-throughput probe at the observed clocks).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
+TIMING_LAUNCHES, TIMING_TC_ISSUED = 18, 19  # positions in OBS_TIMINGS after the 6 classes x 3
 
 
 def measured_peaks():
@@ -56,7 +57,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--workload", default="large", choices=list(workload.WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=list(workload.PRECISIONS))
+    ap.add_argument("--precision", default="bf16x3", choices=list(workload.PRECISIONS),
+                    help="contraction arithmetic of the timed form (the FP64 path is timed beside it)")
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path beside the form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -224,7 +227,7 @@ def run_mine(args, rank, world, local_rank):
     ctx = q.qtt_init(p, stream=stream.cuda_stream)
     for _ in range(args.warmup):
         ctx.step(1)
-    launches0 = ctx.observe(q.OBS_TIMINGS)[15]
+    launches0 = ctx.observe(q.OBS_TIMINGS)[TIMING_LAUNCHES]
     barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
@@ -238,7 +241,7 @@ def run_mine(args, rank, world, local_rank):
     clocks = sampler.stop()
     barrier()
     ms = e0.elapsed_time(e1)
-    launches = ctx.observe(q.OBS_TIMINGS)[15] - launches0
+    launches = ctx.observe(q.OBS_TIMINGS)[TIMING_LAUNCHES] - launches0
     ms_max = max_over_ranks(ms)
     value = args.steps * world / (ms_max / 1e3)
     scal = ctx.scalars()
@@ -259,7 +262,7 @@ def run_mine(args, rank, world, local_rank):
         cp.step(nprof)
         t1 = cp.observe(q.OBS_TIMINGS)
         cp.close()
-        names = ["gemm_f64", "qr_thin", "eig_sym", "other", "gemm_tc"]
+        names = ["gemm_f64", "qr_thin", "eig_sym", "other", "gemm_tc", "gemm_small"]
         classes = {}
         for c, nm in enumerate(names):
             launches_c = t1[3 * c] - t0[3 * c]
@@ -282,7 +285,7 @@ def run_mine(args, rank, world, local_rank):
             }
         else:
             g = classes["gemm_tc"]
-            issued = (t1[16] - t0[16]) / nprof
+            issued = (t1[TIMING_TC_ISSUED] - t0[TIMING_TC_ISSUED]) / nprof
             alg = g["gflop_per_step"] * 1e9
             passes = issued / alg if alg > 0 else 1.0
             peaks = measured_peaks()
@@ -302,6 +305,35 @@ def run_mine(args, rank, world, local_rank):
         roofline["avg_launch_us"] = g["ms_per_step"] * 1e3 / max(g["launches_per_step"], 1)
         roofline["timing"] = ("separate eager pass after the timed region: CUDA events on the launching stream "
                               "around every launch of the class, averaged over the pass's steps")
+
+    # ---- the plain FP64 GPU path at equal chi: steps/s, and the form's distance to it
+    fp64_path = None
+    if args.precision != "fp64" and not args.no_fp64_path:
+        p64 = workload.make_params(args.workload, seed=rank, precision="fp64")
+        c64 = q.qtt_init(p64, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            c64.step(1)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c64.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        # advance a copy of the form to the same step count and compare at equal chi
+        cf = q.qtt_init(p, stream=stream.cuda_stream)
+        cf.step(args.warmup + args.steps)
+        rel = cf.compare(c64)
+        s64, sf = c64.scalars(), cf.scalars()
+        cf.close()
+        c64.close()
+        v64 = args.steps * world / (ms64 / 1e3)
+        fp64_path = {
+            "value": v64, "unit": "steps/s", "ms_per_step": ms64 / args.steps, "speedup": value / v64,
+            "rel_l2_vs_fp64_after_steps": rel, "steps_compared": args.warmup + args.steps,
+            "d_norm_avg": sf["norm_avg"] - s64["norm_avg"], "d_mean1_avg": sf["mean1_avg"] - s64["mean1_avg"],
+            "d_phi11_avg": sf["phi11_avg"] - s64["phi11_avg"],
+        }
 
     # ---- end to end through the C ABI: host params -> device, K steps, scalars read back each step
     e2e = None
@@ -356,7 +388,7 @@ def run_mine(args, rank, world, local_rank):
             "clocks": clocks, "gpu_launches": int(launches),
             "state": {"norm_avg": scal["norm_avg"], "mean1_avg": scal["mean1_avg"], "nvpp": nvpp,
                       "discarded_weight_last_step": scal["discarded_weight"]},
-            "parity": parity,
+            "parity": parity, "fp64_path": fp64_path,
         }
         print(json.dumps(line), flush=True)
 

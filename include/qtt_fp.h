@@ -95,15 +95,16 @@ typedef enum {
                             (as doubles 0/1, MSB first per dimension), cap = n * N;
                             the first n entries are overwritten with the values */
   QTT_OBS_NVPP = 5,      /* 1 value: number of variables parameterising f (Eq. MPSdofs) */
-  QTT_OBS_TIMINGS = 6    /* 17 values: for the kernel classes FP64 GEMM, QR, eigensolver,
-                            other, tensor-core GEMM (incl. operand packing):
-                            launches, total ms, algorithmic flops, recorded with CUDA events
-                            only when the environment variable QTT_KERNEL_TIMING=1 was set
-                            at qtt_init (zeros otherwise); then the number of kernels the
-                            library has launched since it was loaded (always counted);
-                            then the tensor-core flops as issued: algorithmic flops times
-                            the MMA passes of each product's mode, TF32 passes counted
-                            twice (half the bf16 rate), recorded like the classes */
+  QTT_OBS_TIMINGS = 6    /* 20 values: for the kernel classes FP64 GEMM, QR, eigensolver,
+                            other, tensor-core GEMM (incl. operand packing), CUDA-core GEMM
+                            of the operator-bond contractions: launches, total ms,
+                            algorithmic flops, recorded with CUDA events only when the
+                            environment variable QTT_KERNEL_TIMING=1 was set at qtt_init
+                            (zeros otherwise); then the number of kernels the library has
+                            launched since it was loaded (always counted); then the
+                            tensor-core flops as issued: algorithmic flops times the MMA
+                            passes of each product's mode, TF32 passes counted twice (half
+                            the bf16 rate), recorded like the classes */
 } qtt_observable;
 
 /* Build the initial PDF, velocity and operators (paper: "Flow case

@@ -176,7 +176,7 @@ class Context:
         if out is None:
             if cap is None:
                 cap = {OBS_SCALARS: 12, OBS_BONDS: self.N + 1, OBS_DENSE: 2 ** self.N, OBS_MEANS: 3 * 2 ** Kx,
-                       OBS_NVPP: 1, OBS_TIMINGS: 17}[what]
+                       OBS_NVPP: 1, OBS_TIMINGS: 20}[what]
             out = np.zeros(cap, dtype=np.float64)
         written = C.c_int64(0)
         _check(load_library().qtt_observe(self._handle(), int(what), out.ctypes.data_as(C.POINTER(C.c_double)),

@@ -89,7 +89,7 @@ struct KernelTimer {
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
-enum { TM_GEMM = 0, TM_QR = 1, TM_EIG = 2, TM_OTHER = 3, TM_TC = 4 };
+enum { TM_GEMM = 0, TM_QR = 1, TM_EIG = 2, TM_OTHER = 3, TM_TC = 4, TM_SMALL = 5 };
 
 struct TimeScope {
   KernelTimer* t;
@@ -142,6 +142,10 @@ Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
   // be far smaller than |T_n| |R_{n+1}| (the operator's stencils cancel), and
   // an error in R_{n+1} then steers the range finder away from T_n R_{n+1}.
   const int mode = p.precision == 1 ? TC_BF16X6 : p.precision == 2 ? TC_TF32 : p.precision == 3 ? TC_BF16X3 : -1;
+  // The FP32 form re-orthonormalises the float QR's Q in FP64 (one
+  // Newton-Schulz step): the float Q alone leaves ~1e-5 relative error
+  // after ten steps of the 2^4-point workload.
+  qr_refine_ = (p.precision == 1);
   for (int& m : tc_mode_) m = mode;
   timer_ = new KernelTimer();
   if (const char* e = std::getenv("QTT_KERNEL_TIMING")) timer_->on = (e[0] == '1');
@@ -234,6 +238,12 @@ void Engine::gemm64(int M, int N, int K, int outer, int inner, double alpha, Mat
 void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
                   OutView C, int role) {
   const int mode = tc_mode_[role];
+  if (small_gemm_fits(M, N, K, outer, inner)) {
+    // operator-bond contractions: memory-bound, on the CUDA cores
+    TimeScope ts(timer_, TM_SMALL, st_, 2.0 * M * (double)N * K * outer * inner);
+    small_gemm(st_, mode >= 0, M, N, K, outer, inner, alpha, A, B, beta, C);
+    return;
+  }
   if (mode < 0) {
     gemm64(M, N, K, outer, inner, alpha, A, B, beta, C);
     return;
@@ -380,6 +390,7 @@ void Engine::init() {
   Y_ = (double*)dalloc(yy * sizeof(double));
   const size_t rmax = (size_t)max_bond_;
   qrwork_ = (double*)dalloc((2 * (2 * rmax) * rmax + rmax) * sizeof(double));
+  gq_ = (double*)dalloc(rmax * rmax * sizeof(double));
   ws_elems_ = (size_t)8 << 20;
   ws_ = (double*)dalloc(ws_elems_ * sizeof(double));
   for (int i = 0; i < 2; ++i) {
@@ -567,7 +578,17 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
       }
       {
         TimeScope ts(timer_, TM_QR, st_);
-        qr_thin(st_, 2 * r, rn, Y_, mid_.core(n), qrwork_, prec_bits_, status_);
+        qr_thin(st_, 2 * r, rn, Y_, qr_refine_ ? X1_ : mid_.core(n), qrwork_, prec_bits_, status_);
+      }
+      if (qr_refine_) {
+        // one Newton-Schulz step in FP64, Q <- Q (3 I - Q^T Q) / 2: the span of
+        // the float Q, orthonormal to double round-off
+        {
+          TimeScope ts(timer_, TM_OTHER, st_);
+          fill_eye(st_, gq_, rn);
+        }
+        gemm64(rn, rn, 2 * r, 1, 1, -0.5, mv(X1_, 1, rn), mv(X1_, rn, 1), 1.5, ov(gq_, rn, 1));
+        gemm64(2 * r, rn, rn, 1, 1, 1.0, mv(X1_, rn, 1), mv(gq_, rn, 1), 0.0, ov(mid_.core(n), rn, 1));
       }
       for (int i = 0; i < nt; ++i) {
         const Term& t = terms[i];
@@ -938,7 +959,7 @@ void Engine::upload_state(const std::vector<double>& cores) {
 
 std::vector<double> Engine::timings() const {
   std::vector<double> t;
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < 6; ++c) {
     t.push_back(timer_->launches[c]);
     t.push_back(timer_->ms[c]);
     t.push_back(timer_->flops[c]);

@@ -132,6 +132,7 @@ class Engine {
   bool own_stream_ = false;
   int N_ = 0, kphi_ = 0, nc_ = 0;
   int prec_bits_ = 64;
+  bool qr_refine_ = false;
   bool exact_ = false;
   std::vector<void*> allocs_;
   std::vector<int> D_, ell_, rz_;
@@ -143,7 +144,7 @@ class Engine {
   double *C_[4] = {nullptr, nullptr, nullptr, nullptr}, *T_[4] = {nullptr, nullptr, nullptr, nullptr};
   double *P_ = nullptr, *X1_ = nullptr, *X2_ = nullptr, *Y_ = nullptr;
   double *v_[2] = {nullptr, nullptr}, *hf_[2] = {nullptr, nullptr};
-  double *envw_ = nullptr, *envout_ = nullptr, *ws_ = nullptr, *qrwork_ = nullptr;
+  double *envw_ = nullptr, *envout_ = nullptr, *ws_ = nullptr, *qrwork_ = nullptr, *gq_ = nullptr;
   double *disc_ = nullptr, *obsA_ = nullptr, *obsB_ = nullptr, *obsX_ = nullptr;
   int *status_ = nullptr, *ranks_ = nullptr;
   std::vector<double*> gram_, tU_;

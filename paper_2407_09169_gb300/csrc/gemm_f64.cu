@@ -135,9 +135,11 @@ void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int bat
 
 int gemm_split_k(int M, int N, int K, int batch) {
   const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
-  if (tiles >= 152 || K < 4 * BK) return 1;
+  if (tiles >= 152 || K < 2 * BK) return 1;
+  // FP64 issues at two operations per clock per SM: spread small products
+  // over about two waves of SMs, down to one k-tile per split
   long long s = (304 + tiles - 1) / tiles;
-  s = s < (K / (2 * BK)) ? s : (K / (2 * BK));
+  s = s < (K / BK) ? s : (K / BK);
   if (s > 64) s = 64;
   return s < 1 ? 1 : (int)s;
 }

@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -217,6 +218,7 @@ __device__ __forceinline__ unsigned long long scale_bits(unsigned long long u, i
   if (e == 0) return u & (1ull << 63);  // zero (or a denormal, flushed)
   const int ne = e + k;
   if (ne <= 0) return u & (1ull << 63);
+  if (ne >= 2047) return (u & (1ull << 63)) | (0x7FFull << 52);
   return (u & ~(0x7FFull << 52)) | ((unsigned long long)ne << 52);
 }
 
@@ -448,14 +450,15 @@ __device__ __forceinline__ float to_tf32(float x) {
 
 // Writes the packed form of one element.  Floating-point forms: x is rounded
 // to float, then split (hi = x rounded to the operand type, lo = the rest,
-// exact in float).  BF16X6: x is first scaled by 2^(7 - e) (e: exponent of its
-// row's largest magnitude, so |t| < 128), then t = s1 + 2^-8 s2 + 2^-16 s3 +
-// O(2^-17) with integers |s_p| <= 128 from round-to-nearest; all in FP32.
+// exact in float).  BF16X6: x is first scaled by 2^(ks + 7 - e) (ks: the
+// K-index balancing shift; e: exponent of the row's largest balanced
+// magnitude, so |t| < 128), then t = s1 + 2^-8 s2 + 2^-16 s3 + O(2^-17) with
+// integers |s_p| <= 128 from round-to-nearest; all in FP32.
 template <int MODE>
-__device__ __forceinline__ void pack_one(double x, int e, size_t idx, void* o0, void* o1, void* o2) {
+__device__ __forceinline__ void pack_one(double x, int e, int ks, size_t idx, void* o0, void* o1, void* o2) {
   if constexpr (MODE == TC_BF16X6) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const float t = double_bits_to_float(scale_bits(u, 7 - e));
+    const float t = double_bits_to_float(scale_bits(u, 7 - e + ks));
     const float a1 = rintf(t);
     float rr = (t - a1) * 256.0f;
     const float a2 = rintf(rr);
@@ -488,45 +491,110 @@ __device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
   return E == 0 ? 0 : E - 1022;
 }
 
-// Source rows with contiguous (or general) k: one warp per packed row.
-template <int MODE>
-__global__ void pack_rows_kernel(const double* __restrict__ p, long long rstr, long long kstr, long long so,
-                                 long long si, int inner, int rows, int K, int rows_pad, int k_pad, long long batch,
-                                 void* o0, void* o1, void* o2, int* expo) {
-  const long long warps_total = (long long)rows_pad * batch;
+// The exact slices need, per packed row, the largest balanced magnitude over
+// all of K.  It is reduced in a pass of its own (partial maxima of k segments
+// combined with atomicMax on the order-preserving bits into a zeroed buffer),
+// so that the packing itself can split K across blocks without re-reading.
+
+// Rows with contiguous (or general) k: one warp per (packed row, k segment).
+__global__ void opmax_rows_kernel(const double* __restrict__ p, long long rstr, long long kstr, long long so,
+                                  long long si, int inner, int rows, int K, int rows_pad, int k_pad, long long batch,
+                                  int kseg, const int* __restrict__ kshift, int ksign, unsigned long long* maxbits) {
+  const int nseg = (k_pad + kseg - 1) / kseg;
+  const long long warps_total = (long long)rows_pad * batch * nseg;
   const int lane = threadIdx.x & 31;
   for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
        w += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const long long b = w / rows_pad;
-    const int r = (int)(w - b * rows_pad);
+    const long long rowid = w / nseg;
+    const int seg = (int)(w - rowid * nseg);
+    const long long b = rowid / rows_pad;
+    const int r = (int)(rowid - b * rows_pad);
+    if (r >= rows) continue;  // warp-uniform
     const long long bo = b / inner, bi = b - bo * inner;
     const double* row = p + bo * so + bi * si + (long long)r * rstr;
+    const int* ksh = kshift + b * k_pad;
+    unsigned long long mx = 0;
+    const int k1 = min(K, (seg + 1) * kseg);
+    for (int k = seg * kseg + lane; k < k1; k += 32) mx = max(mx, scale_bits(abs_bits(row[(long long)k * kstr]), ksign * ksh[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx != 0ull) atomicMax(maxbits + rowid, mx);
+  }
+}
+
+// Rows contiguous across r: 32 rows x one k segment per block.
+__global__ void __launch_bounds__(256) opmax_cols_kernel(const double* __restrict__ p, long long kstr, long long so,
+                                                         long long si, int inner, int rows, int K, int rows_pad,
+                                                         int k_pad, int kseg, const int* __restrict__ kshift,
+                                                         int ksign, unsigned long long* maxbits) {
+  __shared__ unsigned long long red[8][32];
+  const int tiles_r = rows_pad / 32;
+  const long long b = blockIdx.x / tiles_r;
+  const int r0 = (int)(blockIdx.x - b * tiles_r) * 32;
+  const long long bo = b / inner, bi = b - bo * inner;
+  const double* src = p + bo * so + bi * si;
+  const int* ksh = kshift + b * k_pad;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  unsigned long long mx = 0;
+  if (r0 + tx < rows) {
+    const int k1 = min(K, ((int)blockIdx.y + 1) * kseg);
+    for (int k = blockIdx.y * kseg + ty; k < k1; k += 8)
+      mx = max(mx, scale_bits(abs_bits(src[(r0 + tx) + (long long)k * kstr]), ksign * ksh[k]));
+  }
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
+    if (mx != 0ull) atomicMax(maxbits + b * rows_pad + r0 + tx, mx);
+  }
+}
+
+// Source rows with contiguous (or general) k: one warp per (packed row, k
+// segment of kseg elements).
+template <int MODE>
+__global__ void pack_rows_kernel(const double* __restrict__ p, long long rstr, long long kstr, long long so,
+                                 long long si, int inner, int rows, int K, int rows_pad, int k_pad, long long batch,
+                                 int kseg, const int* __restrict__ kshift, int ksign,
+                                 const unsigned long long* __restrict__ maxbits, void* o0, void* o1, void* o2,
+                                 int* expo) {
+  const int nseg = (k_pad + kseg - 1) / kseg;
+  const long long warps_total = (long long)rows_pad * batch * nseg;
+  const int lane = threadIdx.x & 31;
+  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
+       w += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long rowid = w / nseg;
+    const int seg = (int)(w - rowid * nseg);
+    const long long b = rowid / rows_pad;
+    const int r = (int)(rowid - b * rows_pad);
+    const long long bo = b / inner, bi = b - bo * inner;
+    const double* row = p + bo * so + bi * si + (long long)r * rstr;
+    const int* ksh = kshift ? kshift + b * k_pad : nullptr;
     const bool live = r < rows;
     int e = 0;
     if constexpr (MODE == TC_BF16X6) {
-      unsigned long long mx = 0;
-      if (live)
-        for (int k = lane; k < K; k += 32) mx = max(mx, abs_bits(row[(long long)k * kstr]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      e = row_exponent(mx);
-      if (lane == 0) expo[w] = e;
+      e = row_exponent(maxbits[rowid]);
+      if (lane == 0 && seg == 0) expo[rowid] = e;
     }
-    const size_t base = (size_t)w * k_pad;
-    for (int k = lane; k < k_pad; k += 32)
-      pack_one<MODE>((live && k < K) ? row[(long long)k * kstr] : 0.0, e, base + k, o0, o1, o2);
+    const size_t base = (size_t)rowid * k_pad;
+    const int k1 = min(k_pad, (seg + 1) * kseg);
+    for (int k = seg * kseg + lane; k < k1; k += 32)
+      pack_one<MODE>((live && k < K) ? row[(long long)k * kstr] : 0.0, e, (ksh && k < K) ? ksign * ksh[k] : 0,
+                     base + k, o0, o1, o2);
   }
 }
 
 // Source rows that are contiguous across r (r stride 1, a column-major view,
-// e.g. B^T of a row-major B): 32 packed rows per block through a shared
-// tile, so that both the reads (along r) and the writes (along k) coalesce.
+// e.g. B^T of a row-major B): 32 packed rows x one k segment (kseg, a
+// multiple of 32) per block through a shared tile, so that both the reads
+// (along r) and the writes (along k) coalesce.  grid = (row tiles * batch,
+// segments).
 template <int MODE>
 __global__ void __launch_bounds__(256) pack_cols_kernel(const double* __restrict__ p, long long kstr, long long so,
                                                         long long si, int inner, int rows, int K, int rows_pad,
-                                                        int k_pad, void* o0, void* o1, void* o2, int* expo) {
+                                                        int k_pad, int kseg, const int* __restrict__ kshift,
+                                                        int ksign, const unsigned long long* __restrict__ maxbits,
+                                                        void* o0, void* o1, void* o2, int* expo) {
   __shared__ double tile[32][33];  // [k][r]
-  __shared__ unsigned long long red[8][32];
   __shared__ int s_e[32];
   const int tiles_r = rows_pad / 32;
   const long long b = blockIdx.x / tiles_r;
@@ -535,21 +603,17 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const double* __restrict
   const double* src = p + bo * so + bi * si;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const bool rlive = r0 + tx < rows;
+  const int* ksh = kshift ? kshift + b * k_pad : nullptr;
   if constexpr (MODE == TC_BF16X6) {
-    unsigned long long mx = 0;
-    if (rlive)
-      for (int k = ty; k < K; k += 8) mx = max(mx, abs_bits(src[(r0 + tx) + (long long)k * kstr]));
-    red[ty][tx] = mx;
-    __syncthreads();
     if (ty == 0) {
-      for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
-      const int e = row_exponent(mx);
+      const int e = row_exponent(maxbits[b * rows_pad + r0 + tx]);
       s_e[tx] = e;
-      expo[b * rows_pad + r0 + tx] = e;
+      if (blockIdx.y == 0) expo[b * rows_pad + r0 + tx] = e;
     }
     __syncthreads();
   }
-  for (int k0 = 0; k0 < k_pad; k0 += 32) {
+  const int kend = min(k_pad, ((int)blockIdx.y + 1) * kseg);
+  for (int k0 = blockIdx.y * kseg; k0 < kend; k0 += 32) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int kl = ty + 8 * q, k = k0 + kl;
@@ -560,9 +624,64 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const double* __restrict
     for (int q = 0; q < 4; ++q) {
       const int rl = ty + 8 * q;
       const int e = (MODE == TC_BF16X6) ? s_e[rl] : 0;
-      pack_one<MODE>(tile[tx][rl], e, ((size_t)b * rows_pad + r0 + rl) * k_pad + k0 + tx, o0, o1, o2);
+      const int k = k0 + tx;
+      pack_one<MODE>(tile[tx][rl], e, (ksh && k < K) ? ksign * ksh[k] : 0,
+                     ((size_t)b * rows_pad + r0 + rl) * k_pad + k, o0, o1, o2);
     }
     __syncthreads();
+  }
+}
+
+// K-index balancing for the exact slices: kshift[b][k] = exponent of
+// max_n |B(k, n)| (|B(k, n)| < 2^kshift).  Packing then uses B(k, n) 2^-kshift
+// and A(r, k) 2^+kshift, which leaves A B unchanged (powers of two, exact) and
+// makes every row of B' of magnitude < 1, so that A''s row exponent follows
+// the largest product term a_rk b_kn rather than the largest a_rk.  (In the
+// products of this method B is often a right environment whose rows carry
+// the bond's singular values.)  B(k, n) at k * rs + n * cs; a warp per k when
+// n is contiguous, 32 k per block otherwise.
+__global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long long cs, long long so, long long si,
+                                int inner, int K, int N, int k_pad, long long batch, int* kshift) {
+  const int lane = threadIdx.x & 31;
+  if (cs == 1) {
+    const long long warps_total = (long long)k_pad * batch;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+      const long long b = w / k_pad;
+      const int k = (int)(w - b * k_pad);
+      const long long bo = b / inner, bi = b - bo * inner;
+      unsigned long long mx = 0;
+      if (k < K) {
+        const double* row = p + bo * so + bi * si + (long long)k * rs;
+        for (int n = lane; n < N; n += 32) mx = max(mx, abs_bits(row[n]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) kshift[w] = row_exponent(mx);
+    }
+  } else {
+    // 32 k x 8 n-groups per block (reads coalesce along k when rs == 1)
+    __shared__ unsigned long long red[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int ktiles = (k_pad + 31) / 32;
+    const long long tiles = (long long)ktiles * batch;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const long long b = t / ktiles;
+      const int k = (int)(t - b * ktiles) * 32 + tx;
+      const long long bo = b / inner, bi = b - bo * inner;
+      unsigned long long mx = 0;
+      if (k < K) {
+        const double* row = p + bo * so + bi * si + (long long)k * rs;
+        for (int n = ty; n < N; n += 8) mx = max(mx, abs_bits(row[(long long)n * cs]));
+      }
+      red[ty][tx] = mx;
+      __syncthreads();
+      if (ty == 0) {
+        for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
+        if (k < k_pad) kshift[b * k_pad + k] = row_exponent(mx);
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -623,17 +742,32 @@ void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, i
 // K-major buffers o[0..) (and, for BF16X6, the row exponents).
 template <int MODE>
 void launch_pack(cudaStream_t st, const MatView& v, long long rstr, long long kstr, int inner, int rows, int K,
-                 int rows_pad, int k_pad, long long batch, void* const* o, int* expo) {
-  if (rstr == 1 && kstr != 1 && rows_pad % 32 == 0) {
-    const long long blocks = (long long)(rows_pad / 32) * batch;
-    pack_cols_kernel<MODE><<<(unsigned)blocks, 256, 0, st>>>(v.p, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
-                                                             o[0], o[1], o[2], expo);
+                 int rows_pad, int k_pad, long long batch, void* const* o, int* expo, const int* kshift,
+                 int ksign, unsigned long long* maxbits) {
+  // k segments so that about two waves of 152 SMs' worth of blocks exist
+  constexpr long long kTarget = 2 * 152 * 8;  // warps (rows kernel) / 8 = blocks
+  const bool cols = (rstr == 1 && kstr != 1 && rows_pad % 32 == 0);
+  const int chunks = (k_pad + 31) / 32;
+  long long units = cols ? (long long)(rows_pad / 32) * batch : (long long)rows_pad * batch;
+  const long long want = cols ? 2 * 152 : kTarget;
+  int nseg = (int)std::min<long long>(chunks, std::max<long long>(1, (want + units - 1) / units));
+  const int kseg = 32 * ((chunks + nseg - 1) / nseg);
+  nseg = (k_pad + kseg - 1) / kseg;
+  if (cols) {
+    const dim3 grid((unsigned)units, (unsigned)nseg);
+    if constexpr (MODE == TC_BF16X6)
+      opmax_cols_kernel<<<grid, 256, 0, st>>>(v.p, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad, kseg, kshift,
+                                              ksign, maxbits);
+    pack_cols_kernel<MODE><<<grid, 256, 0, st>>>(v.p, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad, kseg, kshift,
+                                                 ksign, maxbits, o[0], o[1], o[2], expo);
   } else {
-    const long long warps = (long long)rows_pad * batch;
-    long long blocks = (warps * 32 + 255) / 256;
+    long long blocks = (units * nseg * 32 + 255) / 256;
     if (blocks > 8192) blocks = 8192;
+    if constexpr (MODE == TC_BF16X6)
+      opmax_rows_kernel<<<(int)blocks, 256, 0, st>>>(v.p, rstr, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
+                                                     batch, kseg, kshift, ksign, maxbits);
     pack_rows_kernel<MODE><<<(int)blocks, 256, 0, st>>>(v.p, rstr, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
-                                                        batch, o[0], o[1], o[2], expo);
+                                                        batch, kseg, kshift, ksign, maxbits, o[0], o[1], o[2], expo);
   }
 }
 
@@ -688,7 +822,8 @@ PackLayout pack_layout(int M, int N, int K, long long batch, int mode) {
   L.a_bytes = (size_t)L.m_pad * L.k_pad * batch * mi.esize;
   L.b_bytes = (size_t)L.n_pad * L.k_pad * batch * mi.esize;
   L.total = mi.na * up256(L.a_bytes) + mi.nb * up256(L.b_bytes) + up256((size_t)L.m_pad * batch * 4) +
-            up256((size_t)L.n_pad * batch * 4) + 256;
+            up256((size_t)L.n_pad * batch * 4) + up256((size_t)L.k_pad * batch * 4) +
+            up256((size_t)(L.m_pad + L.n_pad) * batch * 8) + 256;
   return L;
 }
 
@@ -722,10 +857,23 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   for (int i = 0; i < mi.nb; ++i) pk.b[i] = carve(L.b_bytes);
   pk.ea = (int*)carve((size_t)L.m_pad * batch * 4);
   pk.eb = (int*)carve((size_t)L.n_pad * batch * 4);
+  int* kshift = nullptr;
+  unsigned long long* maxa = nullptr;
+  unsigned long long* maxb = nullptr;
+  if (mi.sliced) {
+    kshift = (int*)carve((size_t)L.k_pad * batch * 4);
+    maxa = (unsigned long long*)carve((size_t)(L.m_pad + L.n_pad) * batch * 8);
+    maxb = maxa + (size_t)L.m_pad * batch;
+    cudaMemsetAsync(maxa, 0, (size_t)(L.m_pad + L.n_pad) * batch * 8, st);
+    const long long items = B.cs == 1 ? 32LL * L.k_pad * batch : 256LL * ((L.k_pad + 31) / 32) * batch;
+    long long blocks = (items + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    kbalance_kernel<<<(int)blocks, 256, 0, st>>>(B.p, B.rs, B.cs, B.so, B.si, inner, K, N, L.k_pad, batch, kshift);
+  }
   // A(m, k) = A.p[m * rs + k * cs]; B is packed as B^T: (n, k) = B.p[k * rs + n * cs]
 #define QTT_PACK(MODE_)                                                                               \
-  launch_pack<MODE_>(st, A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch, pk.a, pk.ea);           \
-  launch_pack<MODE_>(st, B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch, pk.b, pk.eb);
+  launch_pack<MODE_>(st, A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch, pk.a, pk.ea, kshift, 1, maxa);  \
+  launch_pack<MODE_>(st, B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch, pk.b, pk.eb, kshift, -1, maxb);
   switch (mode) {
     case TC_BF16: QTT_PACK(TC_BF16); break;
     case TC_BF16X3: QTT_PACK(TC_BF16X3); break;
@@ -757,7 +905,7 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     kbps = kblocks;
   }
   double* wsp = splitk > 1 ? ws : nullptr;
-  count_launches(2 + (splitk > 1 ? 2 : 1));
+  count_launches(2 + (mi.sliced ? 3 : 0) + (splitk > 1 ? 2 : 1));
 #define QTT_TC_LAUNCH(MODE_, BN_, ST_) \
   launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kbps, splitk, inner, batch, alpha, beta, C, wsp, err)
 #define QTT_TC_BN(MODE_, S256, S160, S128, S64)       \

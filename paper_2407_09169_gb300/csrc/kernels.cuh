@@ -42,6 +42,12 @@ int gemm_split_k(int M, int N, int K, int batch);
 void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int batch, double alpha, const double* ws,
                    double beta, OutView C);
 
+// Batched GEMM with a small M (<= 32) and K (<= 64) on the CUDA cores, same
+// views as gemm_f64; fp32 selects float arithmetic (round to nearest).
+bool small_gemm_fits(int M, int N, int K, int outer, int inner);
+void small_gemm(cudaStream_t st, bool fp32, int M, int N, int K, int outer, int inner, double alpha, MatView A,
+                MatView B, double beta, OutView C);
+
 // Thin Householder QR of an m x n row-major matrix (m >= n): Q (m x n,
 // row-major) overwrites Qout.  Computed in float (prec_bits 32) or double;
 // work must hold 2 * m * n + n elements of that type.  *status != 0 on failure.
@@ -92,6 +98,8 @@ void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned 
 // restart from a checkpoint (which restores the count) draws the same ones.
 void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, unsigned long long seed,
                           const unsigned long long* step, int stage);
+// p = the n x n identity (row-major).
+void fill_eye(cudaStream_t st, double* p, int n);
 // *c += 1 on the device.
 void bump_counter(cudaStream_t st, unsigned long long* c);
 

@@ -80,6 +80,12 @@ __global__ void gaussian_sketch_kernel(Chain om, unsigned long long seed, const 
 
 __global__ void bump_kernel(unsigned long long* c) { *c += 1ull; }
 
+__global__ void eye_kernel(double* p, int n) {
+  const size_t total = (size_t)n * n;
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x)
+    p[x] = (x / n == x % n) ? 1.0 : 0.0;
+}
+
 __global__ void left_weight_env_kernel(Chain f, Chain w, int nsites, int max_bond, double* out, int ldo,
                                        double* work) {
   double* E = work;                    // [4][max_bond]
@@ -237,6 +243,11 @@ void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, uns
   size_t bx = (max_core + 255) / 256;
   if (bx > 64) bx = 64;
   gaussian_sketch_kernel<<<dim3((unsigned)bx, (unsigned)om.n), 256, 0, st>>>(om, seed, step, stage);
+}
+void fill_eye(cudaStream_t st, double* p, int n) {
+  if (n <= 0) return;
+  count_launches(1);
+  eye_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>(p, n);
 }
 void bump_counter(cudaStream_t st, unsigned long long* c) {
   count_launches(1);

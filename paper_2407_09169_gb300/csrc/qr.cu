@@ -24,8 +24,9 @@
 namespace qtt {
 
 namespace {
-constexpr int QR_THREADS = 1024;
-constexpr int QR_WARPS = QR_THREADS / 32;
+// threads per block: 1024 in float, 512 in double (register budget)
+template <typename T>
+__host__ __device__ constexpr int qr_threads() { return sizeof(T) == 4 ? 1024 : 512; }
 constexpr size_t kQrSmemLimit = 200 * 1024;
 
 template <typename T>
@@ -59,16 +60,60 @@ __device__ void make_reflector(T* wc, int c, int m, T* tau, int lane, int* statu
   }
 }
 
+// Applies H = I - t v v^T (v[j] = 1 implicit, rows > j stored in v) to the
+// columns c0, c0 + (warps per block), ... (up to four, c < n) of the
+// column-major X, rows >= j.  One warp; the four dot products and their
+// shuffle reductions are interleaved so that their latencies overlap.
+template <typename T>
+__device__ __forceinline__ void reflect4(const T* v, T t, int j, int m, T* X, int c0, int n, int lane) {
+  constexpr int QR_WARPS = qr_threads<T>() / 32;
+  T* xc[4];
+  T dot[4], xj[4];
+  bool on[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = c0 + q * QR_WARPS;
+    on[q] = c < n;
+    xc[q] = X + (size_t)(on[q] ? c : c0) * m;
+    xj[q] = on[q] ? xc[q][j] : (T)0;
+    dot[q] = 0;
+  }
+  for (int i = j + 1 + lane; i < m; i += 32) {
+    const T vi = v[i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (on[q]) dot[q] += vi * xc[q][i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dot[q] = (dot[q] + xj[q]) * t;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (on[q]) xc[q][j] = xj[q] - dot[q];
+  }
+  for (int i = j + 1 + lane; i < m; i += 32) {
+    const T vi = v[i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (on[q]) xc[q][i] -= dot[q] * vi;
+  }
+}
+
 // Work (global, type T): [m n] reflectors, [m n] Q when it does not fit in
 // shared memory.  Shared: [m n] matrix (when it fits), then tau.
 template <typename T>
-__global__ void __launch_bounds__(QR_THREADS) qr_thin_kernel(int m, int n, const double* __restrict__ A,
+__global__ void __launch_bounds__(qr_threads<T>()) qr_thin_kernel(int m, int n, const double* __restrict__ A,
                                                              double* __restrict__ Qout, T* __restrict__ Wg,
                                                              int use_smem, int* status) {
   extern __shared__ __align__(16) unsigned char qr_smem[];
   const size_t mn = (size_t)m * n;
   T* tau = (T*)(qr_smem + (use_smem ? align16(mn * sizeof(T)) : 0));
   T* W = use_smem ? (T*)qr_smem : Wg;
+  constexpr int QR_THREADS = qr_threads<T>(), QR_WARPS = QR_THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (size_t e = tid; e < mn; e += QR_THREADS) {
@@ -80,21 +125,12 @@ __global__ void __launch_bounds__(QR_THREADS) qr_thin_kernel(int m, int n, const
   __syncthreads();
 
   for (int j = 0; j < n; ++j) {
-    const T* vj = W + (size_t)j * m;
     const T tj = tau[j];
-    for (int c = j + 1 + warp; c < n; c += QR_WARPS) {
-      T* wc = W + (size_t)c * m;
-      if (tj != (T)0) {
-        const T wcj = wc[j];
-        T dot = 0;
-        for (int i = j + 1 + lane; i < m; i += 32) dot += vj[i] * wc[i];
-        dot = (warp_sum(dot) + wcj) * tj;
-        if (lane == 0) wc[j] = wcj - dot;
-        for (int i = j + 1 + lane; i < m; i += 32) wc[i] -= dot * vj[i];
-      }
-      if (c == j + 1) {
+    for (int c0 = j + 1 + warp; c0 < n; c0 += 4 * QR_WARPS) {
+      if (tj != (T)0) reflect4(W + (size_t)j * m, tj, j, m, W, c0, n, lane);
+      if (c0 == j + 1) {  // look-ahead: this warp holds column j + 1
         __syncwarp();
-        make_reflector(wc, c, m, tau, lane, status);  // look-ahead
+        make_reflector(W + (size_t)c0 * m, c0, m, tau, lane, status);
       }
     }
     __syncthreads();
@@ -114,22 +150,209 @@ __global__ void __launch_bounds__(QR_THREADS) qr_thin_kernel(int m, int n, const
   for (int j = n - 1; j >= 0; --j) {
     const T tj = tau[j];
     if (tj == (T)0) continue;  // uniform across the block
-    const T* vj = U + (size_t)j * m;
-    for (int c = j + warp; c < n; c += QR_WARPS) {
-      T* qc = Q + (size_t)c * m;
-      const T qcj = qc[j];
-      T dot = 0;
-      for (int i = j + 1 + lane; i < m; i += 32) dot += vj[i] * qc[i];
-      dot = (warp_sum(dot) + qcj) * tj;
-      if (lane == 0) qc[j] = qcj - dot;
-      for (int i = j + 1 + lane; i < m; i += 32) qc[i] -= dot * vj[i];
-    }
+    for (int c0 = j + warp; c0 < n; c0 += 4 * QR_WARPS) reflect4(U + (size_t)j * m, tj, j, m, Q, c0, n, lane);
     __syncthreads();
   }
   for (size_t e = tid; e < mn; e += QR_THREADS) {
     const int i = (int)(e / n), c = (int)(e - (size_t)i * n);
     Qout[e] = (double)Q[(size_t)c * m + i];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Float QR with the matrix in registers (m <= 32 RPL, n <= 16 CPW, 512
+// threads).  Thread (warp w, lane l) owns rows l + 32 k (k < RPL) of columns
+// w + 16 q (q < CPW): a reflector step is then RPL FMAs per owned column for
+// the dot product, a warp reduction, and RPL FMAs for the update, with no
+// shared-memory traffic except the reflector itself (the instruction count of
+// the shared-memory kernel above bounds it at this size).  The reflectors are
+// kept in shared memory for the accumulation of Q, which uses the same
+// register layout.
+constexpr int QRR_WARPS = 16;
+constexpr int QRR_THREADS = QRR_WARPS * 32;
+
+template <int RPL, int CPW>
+__device__ __forceinline__ void qrr_column(const float (&X)[RPL][CPW], int q, float (&col)[RPL]) {
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    float v = 0.f;
+#pragma unroll
+    for (int qq = 0; qq < CPW; ++qq)
+      if (qq == q) v = X[k][qq];
+    col[k] = v;
+  }
+}
+
+// Reflector of column c held by this warp (values col[k] at rows lane + 32 k):
+// writes v (v_c = 1, zeros above c) to V[c][.] and tau[c].
+template <int RPL>
+__device__ __forceinline__ void qrr_reflector(const float (&col)[RPL], int c, int lane, int ldv, float* V, float* tau,
+                                              int* status) {
+  float s = 0.f, a = 0.f;
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int i = lane + 32 * k;
+    if (i > c) s += col[k] * col[k];
+    if (i == c) a = col[k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    a += __shfl_xor_sync(0xffffffffu, a, o);  // one lane holds x_c, the others 0
+  }
+  float t = 0.f, v0 = 1.f;
+  if (s != 0.f) {
+    const float mu = sqrtf(a * a + s);
+    const float beta = a <= 0.f ? mu : -mu;
+    t = (beta - a) / beta;
+    v0 = a - beta;
+  }
+  float* v = V + (size_t)c * ldv;
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int i = lane + 32 * k;
+    v[i] = i < c ? 0.f : (i == c ? 1.f : (t != 0.f ? col[k] / v0 : 0.f));
+  }
+  if (lane == 0) {
+    tau[c] = t;
+    if (!isfinite(t)) atomicOr(status, 1);
+  }
+}
+
+template <int RPL, int CPW>
+__global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const double* __restrict__ A,
+                                                             double* __restrict__ Qout, int* status) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  constexpr int LDV = 32 * RPL;
+  float* V = (float*)qr_smem;      // [n][LDV] reflectors; first the input, later the output staging
+  float* tau = V + (size_t)n * LDV;  // [n]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // input, column-major in shared memory, then into registers
+  for (int e = tid; e < m * n; e += QRR_THREADS) {
+    const int i = e / n, c = e - i * n;
+    V[(size_t)c * LDV + i] = (float)A[e];
+  }
+  __syncthreads();
+  float X[RPL][CPW];
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + QRR_WARPS * q;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = lane + 32 * k;
+      X[k][q] = (c < n && i < m) ? V[(size_t)c * LDV + i] : 0.f;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float col[RPL];
+    qrr_column<RPL, CPW>(X, 0, col);
+    qrr_reflector<RPL>(col, 0, lane, LDV, V, tau, status);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const float t = tau[j];
+    if (t != 0.f) {
+      float v[RPL];
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) v[k] = V[(size_t)j * LDV + lane + 32 * k];
+      float dot[CPW];
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        dot[q] = 0.f;
+        const int c = warp + QRR_WARPS * q;
+        if (c > j && c < n) {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) dot[q] += v[k] * X[k][q];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const int c = warp + QRR_WARPS * q;
+        if (c > j && c < n) {
+          const float f = t * dot[q];
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
+        }
+      }
+    }
+    const int cn = j + 1;  // look-ahead: the warp owning column j + 1 forms its reflector
+    if (cn < n && (cn % QRR_WARPS) == warp) {
+      float col[RPL];
+      qrr_column<RPL, CPW>(X, cn / QRR_WARPS, col);
+      qrr_reflector<RPL>(col, cn, lane, LDV, V, tau, status);
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{n-1} [I; 0], accumulated backwards in the same registers
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + QRR_WARPS * q;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) X[k][q] = (lane + 32 * k == c) ? 1.f : 0.f;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const float t = tau[j];
+    if (t == 0.f) continue;  // uniform across the block
+    float v[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) v[k] = V[(size_t)j * LDV + lane + 32 * k];
+    float dot[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      dot[q] = 0.f;
+      const int c = warp + QRR_WARPS * q;
+      if (c >= j && c < n) {
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) dot[q] += v[k] * X[k][q];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) {
+      const int c = warp + QRR_WARPS * q;
+      if (c >= j && c < n) {
+        const float f = t * dot[q];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
+      }
+    }
+  }
+  // stage Q row-major through shared memory (the reflectors are no longer
+  // read) and write it out coalesced
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + QRR_WARPS * q;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = lane + 32 * k;
+      if (c < n && i < m) V[(size_t)i * n + c] = X[k][q];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < m * n; e += QRR_THREADS) Qout[e] = (double)V[e];
+}
+
+template <int RPL, int CPW>
+bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, int* status) {
+  if (m > 32 * RPL || n > QRR_WARPS * CPW) return false;
+  const size_t smem = ((size_t)n * 32 * RPL + (size_t)n) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(qr_reg_kernel<RPL, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + QRR_WARPS * CPW) * sizeof(float)));
+    attr = true;
+  }
+  qr_reg_kernel<RPL, CPW><<<1, QRR_THREADS, smem, st>>>(m, n, A, Qout, status);
+  return true;
 }
 
 template <typename T>
@@ -143,7 +366,7 @@ void launch_qr(cudaStream_t st, int m, int n, const double* A, double* Qout, voi
   const size_t wbytes = (size_t)m * n * sizeof(T);
   const int use_smem = wbytes <= kQrSmemLimit ? 1 : 0;
   const size_t smem = (use_smem ? align16(wbytes) : 0) + (size_t)n * sizeof(T);
-  qr_thin_kernel<T><<<1, QR_THREADS, smem, st>>>(m, n, A, Qout, (T*)work, use_smem, status);
+  qr_thin_kernel<T><<<1, qr_threads<T>(), smem, st>>>(m, n, A, Qout, (T*)work, use_smem, status);
 }
 }  // namespace
 
@@ -154,8 +377,12 @@ void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void*
     return;
   }
   count_launches(1);
-  if (prec_bits == 32)
+  if (prec_bits == 32) {
+    if (try_qr_reg<3, 3>(st, m, n, A, Qout, status) || try_qr_reg<5, 5>(st, m, n, A, Qout, status) ||
+        try_qr_reg<9, 9>(st, m, n, A, Qout, status))
+      return;
     launch_qr<float>(st, m, n, A, Qout, work, status);
+  }
   else
     launch_qr<double>(st, m, n, A, Qout, work, status);
 }
