@@ -491,145 +491,155 @@ __device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
   return E == 0 ? 0 : E - 1022;
 }
 
+// One operand to pack: packed row r, element k is p[b-offset + r * rstr +
+// k * kstr].  "cols" layouts (r stride 1) go through a shared tile, 32 rows x
+// one k segment per block; the others take one warp per (row, k segment).
+struct PackJob {
+  const double* p;
+  long long rstr, kstr, so, si;
+  int inner, rows, K, rows_pad, k_pad, kseg, nseg;
+  long long batch, units;  // units: row tiles * batch (cols) or rows * batch (warp layout)
+  int cols, ksign;
+  const int* kshift;               // K-index balancing shifts (BF16X6), or null
+  unsigned long long* maxbits;     // per packed row: largest balanced magnitude (BF16X6)
+  void *o0, *o1, *o2;
+  int* expo;
+  int blocks;                      // blocks of this job in the fused launch
+};
+
 // The exact slices need, per packed row, the largest balanced magnitude over
 // all of K.  It is reduced in a pass of its own (partial maxima of k segments
 // combined with atomicMax on the order-preserving bits into a zeroed buffer),
-// so that the packing itself can split K across blocks without re-reading.
-
-// Rows with contiguous (or general) k: one warp per (packed row, k segment).
-__global__ void opmax_rows_kernel(const double* __restrict__ p, long long rstr, long long kstr, long long so,
-                                  long long si, int inner, int rows, int K, int rows_pad, int k_pad, long long batch,
-                                  int kseg, const int* __restrict__ kshift, int ksign, unsigned long long* maxbits) {
-  const int nseg = (k_pad + kseg - 1) / kseg;
-  const long long warps_total = (long long)rows_pad * batch * nseg;
+// so that the packing can split K across blocks without re-reading rows.
+__device__ void opmax_job(const PackJob& J, int bx) {
   const int lane = threadIdx.x & 31;
-  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
-       w += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const long long rowid = w / nseg;
-    const int seg = (int)(w - rowid * nseg);
-    const long long b = rowid / rows_pad;
-    const int r = (int)(rowid - b * rows_pad);
-    if (r >= rows) continue;  // warp-uniform
-    const long long bo = b / inner, bi = b - bo * inner;
-    const double* row = p + bo * so + bi * si + (long long)r * rstr;
-    const int* ksh = kshift + b * k_pad;
+  if (J.cols) {
+    __shared__ unsigned long long red[8][32];
+    const long long u = bx % J.units;
+    const int seg = (int)(bx / J.units);
+    const int tiles_r = J.rows_pad / 32;
+    const long long b = u / tiles_r;
+    const int r0 = (int)(u - b * tiles_r) * 32;
+    const long long bo = b / J.inner, bi = b - bo * J.inner;
+    const double* src = J.p + bo * J.so + bi * J.si;
+    const int* ksh = J.kshift + b * J.k_pad;
+    const int tx = lane, ty = threadIdx.x >> 5;
     unsigned long long mx = 0;
-    const int k1 = min(K, (seg + 1) * kseg);
-    for (int k = seg * kseg + lane; k < k1; k += 32) mx = max(mx, scale_bits(abs_bits(row[(long long)k * kstr]), ksign * ksh[k]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0 && mx != 0ull) atomicMax(maxbits + rowid, mx);
-  }
-}
-
-// Rows contiguous across r: 32 rows x one k segment per block.
-__global__ void __launch_bounds__(256) opmax_cols_kernel(const double* __restrict__ p, long long kstr, long long so,
-                                                         long long si, int inner, int rows, int K, int rows_pad,
-                                                         int k_pad, int kseg, const int* __restrict__ kshift,
-                                                         int ksign, unsigned long long* maxbits) {
-  __shared__ unsigned long long red[8][32];
-  const int tiles_r = rows_pad / 32;
-  const long long b = blockIdx.x / tiles_r;
-  const int r0 = (int)(blockIdx.x - b * tiles_r) * 32;
-  const long long bo = b / inner, bi = b - bo * inner;
-  const double* src = p + bo * so + bi * si;
-  const int* ksh = kshift + b * k_pad;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  unsigned long long mx = 0;
-  if (r0 + tx < rows) {
-    const int k1 = min(K, ((int)blockIdx.y + 1) * kseg);
-    for (int k = blockIdx.y * kseg + ty; k < k1; k += 8)
-      mx = max(mx, scale_bits(abs_bits(src[(r0 + tx) + (long long)k * kstr]), ksign * ksh[k]));
-  }
-  red[ty][tx] = mx;
-  __syncthreads();
-  if (ty == 0) {
-    for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
-    if (mx != 0ull) atomicMax(maxbits + b * rows_pad + r0 + tx, mx);
-  }
-}
-
-// Source rows with contiguous (or general) k: one warp per (packed row, k
-// segment of kseg elements).
-template <int MODE>
-__global__ void pack_rows_kernel(const double* __restrict__ p, long long rstr, long long kstr, long long so,
-                                 long long si, int inner, int rows, int K, int rows_pad, int k_pad, long long batch,
-                                 int kseg, const int* __restrict__ kshift, int ksign,
-                                 const unsigned long long* __restrict__ maxbits, void* o0, void* o1, void* o2,
-                                 int* expo) {
-  const int nseg = (k_pad + kseg - 1) / kseg;
-  const long long warps_total = (long long)rows_pad * batch * nseg;
-  const int lane = threadIdx.x & 31;
-  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
-       w += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const long long rowid = w / nseg;
-    const int seg = (int)(w - rowid * nseg);
-    const long long b = rowid / rows_pad;
-    const int r = (int)(rowid - b * rows_pad);
-    const long long bo = b / inner, bi = b - bo * inner;
-    const double* row = p + bo * so + bi * si + (long long)r * rstr;
-    const int* ksh = kshift ? kshift + b * k_pad : nullptr;
-    const bool live = r < rows;
-    int e = 0;
-    if constexpr (MODE == TC_BF16X6) {
-      e = row_exponent(maxbits[rowid]);
-      if (lane == 0 && seg == 0) expo[rowid] = e;
+    if (r0 + tx < J.rows) {
+      const int k1 = min(J.K, (seg + 1) * J.kseg);
+      for (int k = seg * J.kseg + ty; k < k1; k += 8)
+        mx = max(mx, scale_bits(abs_bits(src[(r0 + tx) + (long long)k * J.kstr]), J.ksign * ksh[k]));
     }
-    const size_t base = (size_t)rowid * k_pad;
-    const int k1 = min(k_pad, (seg + 1) * kseg);
-    for (int k = seg * kseg + lane; k < k1; k += 32)
-      pack_one<MODE>((live && k < K) ? row[(long long)k * kstr] : 0.0, e, (ksh && k < K) ? ksign * ksh[k] : 0,
-                     base + k, o0, o1, o2);
-  }
-}
-
-// Source rows that are contiguous across r (r stride 1, a column-major view,
-// e.g. B^T of a row-major B): 32 packed rows x one k segment (kseg, a
-// multiple of 32) per block through a shared tile, so that both the reads
-// (along r) and the writes (along k) coalesce.  grid = (row tiles * batch,
-// segments).
-template <int MODE>
-__global__ void __launch_bounds__(256) pack_cols_kernel(const double* __restrict__ p, long long kstr, long long so,
-                                                        long long si, int inner, int rows, int K, int rows_pad,
-                                                        int k_pad, int kseg, const int* __restrict__ kshift,
-                                                        int ksign, const unsigned long long* __restrict__ maxbits,
-                                                        void* o0, void* o1, void* o2, int* expo) {
-  __shared__ double tile[32][33];  // [k][r]
-  __shared__ int s_e[32];
-  const int tiles_r = rows_pad / 32;
-  const long long b = blockIdx.x / tiles_r;
-  const int r0 = (int)(blockIdx.x - b * tiles_r) * 32;
-  const long long bo = b / inner, bi = b - bo * inner;
-  const double* src = p + bo * so + bi * si;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  const bool rlive = r0 + tx < rows;
-  const int* ksh = kshift ? kshift + b * k_pad : nullptr;
-  if constexpr (MODE == TC_BF16X6) {
+    red[ty][tx] = mx;
+    __syncthreads();
     if (ty == 0) {
-      const int e = row_exponent(maxbits[b * rows_pad + r0 + tx]);
-      s_e[tx] = e;
-      if (blockIdx.y == 0) expo[b * rows_pad + r0 + tx] = e;
+      for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
+      if (mx != 0ull) atomicMax(J.maxbits + b * J.rows_pad + r0 + tx, mx);
     }
-    __syncthreads();
-  }
-  const int kend = min(k_pad, ((int)blockIdx.y + 1) * kseg);
-  for (int k0 = blockIdx.y * kseg; k0 < kend; k0 += 32) {
+  } else {
+    const long long warps_total = J.units * J.nseg;
+    for (long long w = ((long long)bx * blockDim.x + threadIdx.x) >> 5; w < warps_total;
+         w += ((long long)J.blocks * blockDim.x) >> 5) {
+      const long long rowid = w / J.nseg;
+      const int seg = (int)(w - rowid * J.nseg);
+      const long long b = rowid / J.rows_pad;
+      const int r = (int)(rowid - b * J.rows_pad);
+      if (r >= J.rows) continue;  // warp-uniform
+      const long long bo = b / J.inner, bi = b - bo * J.inner;
+      const double* row = J.p + bo * J.so + bi * J.si + (long long)r * J.rstr;
+      const int* ksh = J.kshift + b * J.k_pad;
+      unsigned long long mx = 0;
+      const int k1 = min(J.K, (seg + 1) * J.kseg);
+      for (int k = seg * J.kseg + lane; k < k1; k += 32)
+        mx = max(mx, scale_bits(abs_bits(row[(long long)k * J.kstr]), J.ksign * ksh[k]));
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int kl = ty + 8 * q, k = k0 + kl;
-      tile[kl][tx] = (rlive && k < K) ? src[(r0 + tx) + (long long)k * kstr] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx != 0ull) atomicMax(J.maxbits + rowid, mx);
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int rl = ty + 8 * q;
-      const int e = (MODE == TC_BF16X6) ? s_e[rl] : 0;
-      const int k = k0 + tx;
-      pack_one<MODE>(tile[tx][rl], e, (ksh && k < K) ? ksign * ksh[k] : 0,
-                     ((size_t)b * rows_pad + r0 + rl) * k_pad + k, o0, o1, o2);
-    }
-    __syncthreads();
   }
+}
+
+template <int MODE>
+__device__ void pack_job(const PackJob& J, int bx) {
+  const int lane = threadIdx.x & 31;
+  if (J.cols) {
+    __shared__ double tile[32][33];  // [k][r]
+    __shared__ int s_e[32];
+    const long long u = bx % J.units;
+    const int seg = (int)(bx / J.units);
+    const int tiles_r = J.rows_pad / 32;
+    const long long b = u / tiles_r;
+    const int r0 = (int)(u - b * tiles_r) * 32;
+    const long long bo = b / J.inner, bi = b - bo * J.inner;
+    const double* src = J.p + bo * J.so + bi * J.si;
+    const int tx = lane, ty = threadIdx.x >> 5;  // 32 x 8
+    const bool rlive = r0 + tx < J.rows;
+    const int* ksh = J.kshift ? J.kshift + b * J.k_pad : nullptr;
+    if constexpr (MODE == TC_BF16X6) {
+      if (ty == 0) {
+        const int e = row_exponent(J.maxbits[b * J.rows_pad + r0 + tx]);
+        s_e[tx] = e;
+        if (seg == 0) J.expo[b * J.rows_pad + r0 + tx] = e;
+      }
+      __syncthreads();
+    }
+    const int kend = min(J.k_pad, (seg + 1) * J.kseg);
+    for (int k0 = seg * J.kseg; k0 < kend; k0 += 32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int kl = ty + 8 * q, k = k0 + kl;
+        tile[kl][tx] = (rlive && k < J.K) ? src[(r0 + tx) + (long long)k * J.kstr] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rl = ty + 8 * q;
+        const int e = (MODE == TC_BF16X6) ? s_e[rl] : 0;
+        const int k = k0 + tx;
+        pack_one<MODE>(tile[tx][rl], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0,
+                       ((size_t)b * J.rows_pad + r0 + rl) * J.k_pad + k, J.o0, J.o1, J.o2);
+      }
+      __syncthreads();
+    }
+  } else {
+    const long long warps_total = J.units * J.nseg;
+    for (long long w = ((long long)bx * blockDim.x + threadIdx.x) >> 5; w < warps_total;
+         w += ((long long)J.blocks * blockDim.x) >> 5) {
+      const long long rowid = w / J.nseg;
+      const int seg = (int)(w - rowid * J.nseg);
+      const long long b = rowid / J.rows_pad;
+      const int r = (int)(rowid - b * J.rows_pad);
+      const long long bo = b / J.inner, bi = b - bo * J.inner;
+      const double* row = J.p + bo * J.so + bi * J.si + (long long)r * J.rstr;
+      const int* ksh = J.kshift ? J.kshift + b * J.k_pad : nullptr;
+      const bool live = r < J.rows;
+      int e = 0;
+      if constexpr (MODE == TC_BF16X6) {
+        e = row_exponent(J.maxbits[rowid]);
+        if (lane == 0 && seg == 0) J.expo[rowid] = e;
+      }
+      const size_t base = (size_t)rowid * J.k_pad;
+      const int k1 = min(J.k_pad, (seg + 1) * J.kseg);
+      for (int k = seg * J.kseg + lane; k < k1; k += 32)
+        pack_one<MODE>((live && k < J.K) ? row[(long long)k * J.kstr] : 0.0, e,
+                       (ksh && k < J.K) ? J.ksign * ksh[k] : 0, base + k, J.o0, J.o1, J.o2);
+    }
+  }
+}
+
+// Both operands in one launch each: blocks [0, a.blocks) serve a, the rest b.
+__global__ void __launch_bounds__(256) opmax2_kernel(const PackJob a, const PackJob b) {
+  if ((int)blockIdx.x < a.blocks)
+    opmax_job(a, blockIdx.x);
+  else
+    opmax_job(b, blockIdx.x - a.blocks);
+}
+template <int MODE>
+__global__ void __launch_bounds__(256) pack2_kernel(const PackJob a, const PackJob b) {
+  if ((int)blockIdx.x < a.blocks)
+    pack_job<MODE>(a, blockIdx.x);
+  else
+    pack_job<MODE>(b, blockIdx.x - a.blocks);
 }
 
 // K-index balancing for the exact slices: kshift[b][k] = exponent of
@@ -641,8 +651,11 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const double* __restrict
 // the bond's singular values.)  B(k, n) at k * rs + n * cs; a warp per k when
 // n is contiguous, 32 k per block otherwise.
 __global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long long cs, long long so, long long si,
-                                int inner, int K, int N, int k_pad, long long batch, int* kshift) {
+                                int inner, int K, int N, int k_pad, long long batch, int* kshift,
+                                unsigned long long* zero_me, long long nzero) {
   const int lane = threadIdx.x & 31;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nzero; x += (long long)gridDim.x * blockDim.x)
+    zero_me[x] = 0ull;  // the row-maximum buffer of the next pass
   if (cs == 1) {
     const long long warps_total = (long long)k_pad * batch;
     for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
@@ -740,35 +753,41 @@ void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, i
 
 // Packs one operand (rows x K, element (r, k) at r * rstr + k * kstr) into the
 // K-major buffers o[0..) (and, for BF16X6, the row exponents).
-template <int MODE>
-void launch_pack(cudaStream_t st, const MatView& v, long long rstr, long long kstr, int inner, int rows, int K,
-                 int rows_pad, int k_pad, long long batch, void* const* o, int* expo, const int* kshift,
-                 int ksign, unsigned long long* maxbits) {
-  // k segments so that about two waves of 152 SMs' worth of blocks exist
-  constexpr long long kTarget = 2 * 152 * 8;  // warps (rows kernel) / 8 = blocks
-  const bool cols = (rstr == 1 && kstr != 1 && rows_pad % 32 == 0);
+// Fills the geometry of one packing job: k segments so that about two waves
+// of 152 SMs' worth of blocks exist.
+PackJob make_job(const MatView& v, long long rstr, long long kstr, int inner, int rows, int K, int rows_pad,
+                 int k_pad, long long batch, void* const* o, int* expo, const int* kshift, int ksign,
+                 unsigned long long* maxbits) {
+  PackJob J;
+  J.p = v.p;
+  J.rstr = rstr;
+  J.kstr = kstr;
+  J.so = v.so;
+  J.si = v.si;
+  J.inner = inner;
+  J.rows = rows;
+  J.K = K;
+  J.rows_pad = rows_pad;
+  J.k_pad = k_pad;
+  J.batch = batch;
+  J.ksign = ksign;
+  J.kshift = kshift;
+  J.maxbits = maxbits;
+  J.o0 = o[0];
+  J.o1 = o[1];
+  J.o2 = o[2];
+  J.expo = expo;
+  J.cols = (rstr == 1 && kstr != 1 && rows_pad % 32 == 0) ? 1 : 0;
   const int chunks = (k_pad + 31) / 32;
-  long long units = cols ? (long long)(rows_pad / 32) * batch : (long long)rows_pad * batch;
-  const long long want = cols ? 2 * 152 : kTarget;
-  int nseg = (int)std::min<long long>(chunks, std::max<long long>(1, (want + units - 1) / units));
-  const int kseg = 32 * ((chunks + nseg - 1) / nseg);
-  nseg = (k_pad + kseg - 1) / kseg;
-  if (cols) {
-    const dim3 grid((unsigned)units, (unsigned)nseg);
-    if constexpr (MODE == TC_BF16X6)
-      opmax_cols_kernel<<<grid, 256, 0, st>>>(v.p, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad, kseg, kshift,
-                                              ksign, maxbits);
-    pack_cols_kernel<MODE><<<grid, 256, 0, st>>>(v.p, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad, kseg, kshift,
-                                                 ksign, maxbits, o[0], o[1], o[2], expo);
-  } else {
-    long long blocks = (units * nseg * 32 + 255) / 256;
-    if (blocks > 8192) blocks = 8192;
-    if constexpr (MODE == TC_BF16X6)
-      opmax_rows_kernel<<<(int)blocks, 256, 0, st>>>(v.p, rstr, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
-                                                     batch, kseg, kshift, ksign, maxbits);
-    pack_rows_kernel<MODE><<<(int)blocks, 256, 0, st>>>(v.p, rstr, kstr, v.so, v.si, inner, rows, K, rows_pad, k_pad,
-                                                        batch, kseg, kshift, ksign, maxbits, o[0], o[1], o[2], expo);
-  }
+  J.units = J.cols ? (long long)(rows_pad / 32) * batch : (long long)rows_pad * batch;
+  const long long want = J.cols ? 2 * 152 : 2 * 152 * 8;  // blocks (tile layout) / warps (row layout)
+  int nseg = (int)std::min<long long>(chunks, std::max<long long>(1, (want + J.units - 1) / J.units));
+  J.kseg = 32 * ((chunks + nseg - 1) / nseg);
+  J.nseg = (k_pad + J.kseg - 1) / J.kseg;
+  long long blocks = J.cols ? J.units * J.nseg : (J.units * J.nseg * 32 + 255) / 256;
+  if (!J.cols && blocks > 8192) blocks = 8192;
+  J.blocks = (int)blocks;
+  return J;
 }
 
 struct ModeInfo {
@@ -864,24 +883,26 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     kshift = (int*)carve((size_t)L.k_pad * batch * 4);
     maxa = (unsigned long long*)carve((size_t)(L.m_pad + L.n_pad) * batch * 8);
     maxb = maxa + (size_t)L.m_pad * batch;
-    cudaMemsetAsync(maxa, 0, (size_t)(L.m_pad + L.n_pad) * batch * 8, st);
+  }
+  // A(m, k) = A.p[m * rs + k * cs]; B is packed as B^T: (n, k) = B.p[k * rs + n * cs]
+  const PackJob ja = make_job(A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch, pk.a, pk.ea, kshift, 1, maxa);
+  const PackJob jb = make_job(B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch, pk.b, pk.eb, kshift, -1, maxb);
+  const unsigned pack_blocks = (unsigned)(ja.blocks + jb.blocks);
+  if (mi.sliced) {
     const long long items = B.cs == 1 ? 32LL * L.k_pad * batch : 256LL * ((L.k_pad + 31) / 32) * batch;
     long long blocks = (items + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    kbalance_kernel<<<(int)blocks, 256, 0, st>>>(B.p, B.rs, B.cs, B.so, B.si, inner, K, N, L.k_pad, batch, kshift);
+    kbalance_kernel<<<(int)blocks, 256, 0, st>>>(B.p, B.rs, B.cs, B.so, B.si, inner, K, N, L.k_pad, batch, kshift,
+                                                 maxa, (long long)(L.m_pad + L.n_pad) * batch);
+    opmax2_kernel<<<pack_blocks, 256, 0, st>>>(ja, jb);
   }
-  // A(m, k) = A.p[m * rs + k * cs]; B is packed as B^T: (n, k) = B.p[k * rs + n * cs]
-#define QTT_PACK(MODE_)                                                                               \
-  launch_pack<MODE_>(st, A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch, pk.a, pk.ea, kshift, 1, maxa);  \
-  launch_pack<MODE_>(st, B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch, pk.b, pk.eb, kshift, -1, maxb);
   switch (mode) {
-    case TC_BF16: QTT_PACK(TC_BF16); break;
-    case TC_BF16X3: QTT_PACK(TC_BF16X3); break;
-    case TC_TF32: QTT_PACK(TC_TF32); break;
-    case TC_TF32X3: QTT_PACK(TC_TF32X3); break;
-    default: QTT_PACK(TC_BF16X6); break;
+    case TC_BF16: pack2_kernel<TC_BF16><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
+    case TC_BF16X3: pack2_kernel<TC_BF16X3><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
+    case TC_TF32: pack2_kernel<TC_TF32><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
+    case TC_TF32X3: pack2_kernel<TC_TF32X3><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
+    default: pack2_kernel<TC_BF16X6><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
   }
-#undef QTT_PACK
   const int kblocks = L.k_pad / L.kb;
   // split K when the tile grid is small; the exact-slice modes also cap the
   // depth one accumulator sums so that its partial sums stay exact integers
@@ -905,7 +926,7 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     kbps = kblocks;
   }
   double* wsp = splitk > 1 ? ws : nullptr;
-  count_launches(2 + (mi.sliced ? 3 : 0) + (splitk > 1 ? 2 : 1));
+  count_launches(1 + (mi.sliced ? 2 : 0) + (splitk > 1 ? 2 : 1));
 #define QTT_TC_LAUNCH(MODE_, BN_, ST_) \
   launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kbps, splitk, inner, batch, alpha, beta, C, wsp, err)
 #define QTT_TC_BN(MODE_, S256, S160, S128, S64)       \

@@ -162,38 +162,33 @@ __global__ void __launch_bounds__(qr_threads<T>()) qr_thin_kernel(int m, int n, 
 // ---------------------------------------------------------------------------
 // Float QR with the matrix in registers (m <= 32 RPL, n <= 16 CPW, 512
 // threads).  Thread (warp w, lane l) owns rows l + 32 k (k < RPL) of columns
-// w + 16 q (q < CPW): a reflector step is then RPL FMAs per owned column for
-// the dot product, a warp reduction, and RPL FMAs for the update, with no
-// shared-memory traffic except the reflector itself (the instruction count of
-// the shared-memory kernel above bounds it at this size).  The reflectors are
-// kept in shared memory for the accumulation of Q, which uses the same
-// register layout.
+// w + 16 q (q < CPW): a reflector step is RPL FMAs per owned column for the
+// dot product, a warp reduction, and RPL FMAs for the update.  The reflectors
+// go to shared memory, written once each, so the warps need no block-wide
+// barrier: a warp waits only for the flag of the reflector it applies next.
+// The owner of column j + 1 applies H_j to that column first, forms H_{j+1}
+// and raises its flag before it updates its other columns, which keeps the
+// chain of reflectors short (a look-ahead of one column).  Q is accumulated
+// backwards in the same register layout, with no synchronisation at all.
 constexpr int QRR_WARPS = 16;
 constexpr int QRR_THREADS = QRR_WARPS * 32;
+constexpr int QRR_SPIN_LIMIT = 1 << 22;  // polls of a reflector flag (with a short sleep) before giving up
 
+// Reflector of the owned column q (global index c) of X (rows lane + 32 k):
+// writes v (v_c = 1, zeros above c) to V[c][.] and tau[c], then raises ready[c].
 template <int RPL, int CPW>
-__device__ __forceinline__ void qrr_column(const float (&X)[RPL][CPW], int q, float (&col)[RPL]) {
-#pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    float v = 0.f;
-#pragma unroll
-    for (int qq = 0; qq < CPW; ++qq)
-      if (qq == q) v = X[k][qq];
-    col[k] = v;
-  }
-}
-
-// Reflector of column c held by this warp (values col[k] at rows lane + 32 k):
-// writes v (v_c = 1, zeros above c) to V[c][.] and tau[c].
-template <int RPL>
-__device__ __forceinline__ void qrr_reflector(const float (&col)[RPL], int c, int lane, int ldv, float* V, float* tau,
-                                              int* status) {
+__device__ __forceinline__ void qrr_reflector(const float (&X)[RPL][CPW], int q, int c, int lane, int ldv, float* V,
+                                              float* tau, volatile int* ready, int* status) {
   float s = 0.f, a = 0.f;
 #pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    const int i = lane + 32 * k;
-    if (i > c) s += col[k] * col[k];
-    if (i == c) a = col[k];
+  for (int qq = 0; qq < CPW; ++qq) {
+    if (qq != q) continue;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = lane + 32 * k;
+      if (i > c) s += X[k][qq] * X[k][qq];
+      if (i == c) a = X[k][qq];
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -209,14 +204,40 @@ __device__ __forceinline__ void qrr_reflector(const float (&col)[RPL], int c, in
   }
   float* v = V + (size_t)c * ldv;
 #pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    const int i = lane + 32 * k;
-    v[i] = i < c ? 0.f : (i == c ? 1.f : (t != 0.f ? col[k] / v0 : 0.f));
+  for (int qq = 0; qq < CPW; ++qq) {
+    if (qq != q) continue;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = lane + 32 * k;
+      v[i] = i < c ? 0.f : (i == c ? 1.f : (t != 0.f ? X[k][qq] / v0 : 0.f));
+    }
   }
   if (lane == 0) {
     tau[c] = t;
     if (!isfinite(t)) atomicOr(status, 1);
   }
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_block();
+    ready[c] = 1;
+  }
+}
+
+// Bounded wait for reflector j; false (and status bit 4) if it never comes.
+__device__ __forceinline__ bool qrr_wait(volatile int* ready, int j, int lane, int* status) {
+  int ok = 1;
+  if (lane == 0) {
+    int it = 0;
+    while (ready[j] == 0 && it < QRR_SPIN_LIMIT) {
+      __nanosleep(32);
+      ++it;
+    }
+    ok = ready[j] != 0;
+    if (!ok) atomicOr(status, 4);
+    __threadfence_block();
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
 }
 
 template <int RPL, int CPW>
@@ -224,14 +245,16 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
                                                              double* __restrict__ Qout, int* status) {
   extern __shared__ __align__(16) unsigned char qr_smem[];
   constexpr int LDV = 32 * RPL;
-  float* V = (float*)qr_smem;      // [n][LDV] reflectors; first the input, later the output staging
+  float* V = (float*)qr_smem;        // [n][LDV] reflectors; first the input, last the output staging
   float* tau = V + (size_t)n * LDV;  // [n]
+  volatile int* ready = (volatile int*)(tau + n);  // [n]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // input, column-major in shared memory, then into registers
   for (int e = tid; e < m * n; e += QRR_THREADS) {
     const int i = e / n, c = e - i * n;
     V[(size_t)c * LDV + i] = (float)A[e];
   }
+  for (int c = tid; c < n; c += QRR_THREADS) ready[c] = 0;
   __syncthreads();
   float X[RPL][CPW];
 #pragma unroll
@@ -243,25 +266,43 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
       X[k][q] = (c < n && i < m) ? V[(size_t)c * LDV + i] : 0.f;
     }
   }
-  __syncthreads();
-  if (warp == 0) {
-    float col[RPL];
-    qrr_column<RPL, CPW>(X, 0, col);
-    qrr_reflector<RPL>(col, 0, lane, LDV, V, tau, status);
-  }
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
+  __syncthreads();  // the input copy is dead from here on
+  if (warp == 0) qrr_reflector<RPL, CPW>(X, 0, 0, lane, LDV, V, tau, ready, status);
+  bool alive = true;
+  for (int j = 0; j < n && alive; ++j) {
+    alive = qrr_wait(ready, j, lane, status);
+    if (!alive) break;
     const float t = tau[j];
-    if (t != 0.f) {
-      float v[RPL];
+    float v[RPL];
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) v[k] = V[(size_t)j * LDV + lane + 32 * k];
+    for (int k = 0; k < RPL; ++k) v[k] = V[(size_t)j * LDV + lane + 32 * k];
+    const int cn = j + 1;
+    const bool own_next = cn < n && (cn % QRR_WARPS) == warp;
+    const int qn = cn / QRR_WARPS;
+    if (own_next) {  // column j + 1 first: apply H_j, then form and publish H_{j+1}
+      if (t != 0.f) {
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+          if (q != qn) continue;
+          float d = 0.f;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) d += v[k] * X[k][q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          const float f = t * d;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
+        }
+      }
+      qrr_reflector<RPL, CPW>(X, qn, cn, lane, LDV, V, tau, ready, status);
+    }
+    if (t != 0.f) {
       float dot[CPW];
 #pragma unroll
       for (int q = 0; q < CPW; ++q) {
         dot[q] = 0.f;
         const int c = warp + QRR_WARPS * q;
-        if (c > j && c < n) {
+        if (c > cn - (own_next ? 0 : 1) && c < n) {
 #pragma unroll
           for (int k = 0; k < RPL; ++k) dot[q] += v[k] * X[k][q];
         }
@@ -273,21 +314,15 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
 #pragma unroll
       for (int q = 0; q < CPW; ++q) {
         const int c = warp + QRR_WARPS * q;
-        if (c > j && c < n) {
+        if (c > cn - (own_next ? 0 : 1) && c < n) {
           const float f = t * dot[q];
 #pragma unroll
           for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
         }
       }
     }
-    const int cn = j + 1;  // look-ahead: the warp owning column j + 1 forms its reflector
-    if (cn < n && (cn % QRR_WARPS) == warp) {
-      float col[RPL];
-      qrr_column<RPL, CPW>(X, cn / QRR_WARPS, col);
-      qrr_reflector<RPL>(col, cn, lane, LDV, V, tau, status);
-    }
-    __syncthreads();
   }
+  __syncthreads();  // every reflector is published and every warp is done with its columns
   // Q = H_0 ... H_{n-1} [I; 0], accumulated backwards in the same registers
 #pragma unroll
   for (int q = 0; q < CPW; ++q) {
@@ -344,11 +379,11 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
 template <int RPL, int CPW>
 bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, int* status) {
   if (m > 32 * RPL || n > QRR_WARPS * CPW) return false;
-  const size_t smem = ((size_t)n * 32 * RPL + (size_t)n) * sizeof(float);
+  const size_t smem = ((size_t)n * 32 * RPL + 2 * (size_t)n) * sizeof(float);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(qr_reg_kernel<RPL, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + QRR_WARPS * CPW) * sizeof(float)));
+                         (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + 2 * QRR_WARPS * CPW) * sizeof(float)));
     attr = true;
   }
   qr_reg_kernel<RPL, CPW><<<1, QRR_THREADS, smem, st>>>(m, n, A, Qout, status);

@@ -18,12 +18,15 @@ def lib(gpu_available):
 
 
 # Bounds of the reduced-precision forms after 10 steps of the 2^4-point
-# workload (chi 32), relative L2 distance to the FP64 path at equal chi.  The
-# measured levels are 2.3e-4 (bf16x3: biased FP32 accumulation), 7.6e-5
-# (fp32: exact-slice products, whose resolution is relative to each row's
-# largest element, plus the FP32 QR, which alone gives 1.1e-5) and 1.5e-2
-# (tf32); the bounds leave a factor ~2.
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 5e-4), ("fp32", 2e-4), ("tf32", 3e-2)])
+# workload (chi 32), relative L2 distance to the FP64 path at equal chi.
+# Measured: fp32 1.5e-5, bf16x3 5.5e-5, tf32 6.7e-3.  At this chi the
+# comparison has a floor near 1e-5: a float perturbation of a single class of
+# operations (e.g. only the operator-bond products in FP32, all else FP64)
+# already gives 9.6e-6, because the truncation to chi amplifies any change of
+# the near-degenerate singular directions it cuts.  The bounds leave a factor
+# 2 to 4; the mass bounds follow the measured drift (FP64 re-orthonormalised
+# QR in every reduced form).
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-4), ("fp32", 4e-5), ("tf32", 3e-2)])
 def test_precision_form_vs_fp64_small(prec, tol):
     p64 = workload.make_params("small")
     pr = workload.make_params("small", precision=prec)
@@ -40,7 +43,7 @@ def test_precision_form_vs_fp64_small(prec, tol):
     print(f"{prec}: rel-L2 vs fp64 {rel:.2e}, vs oracle {vs_oracle:.2e}, "
           f"norm err {sb['norm_avg'] - 1:.1e}, d<Phi1> {sb['mean1_avg'] - sa['mean1_avg']:.1e}")
     assert rel < tol
-    assert abs(sb["norm_avg"] - 1.0) < {"tf32": 5e-2, "bf16x3": 1e-3, "fp32": 2e-5}[prec]
+    assert abs(sb["norm_avg"] - 1.0) < {"tf32": 2e-2, "bf16x3": 2e-5, "fp32": 2e-5}[prec]
 
 
 def test_accumulation_bias():
