@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--precision", default="bf16x3", choices=list(workload.PRECISIONS),
                     help="contraction arithmetic of the timed form (the FP64 path is timed beside it)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path beside the form")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="instances of the batched configuration stepped together (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -377,6 +380,37 @@ def run_mine(args, rank, world, local_rank):
         except Exception as ex:  # reported, never silently dropped
             parity = {"error": str(ex)}
 
+    # ---- batched independent PDFs (uneven grid and chi), rank 0 at N = 1 only
+    batched = None
+    if rank == 0 and world == 1 and args.batch > 0:
+        bps = workload.make_batch_params(args.batch, seed=0, precision="fp32")
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        t0 = time.perf_counter()
+        ctxs = [q.qtt_init(bp) for bp in bps]
+        t_init = time.perf_counter() - t0
+        free1 = torch.cuda.mem_get_info(dev)[0]
+        q.qtt_step_many(ctxs, 2)  # first step eager, second captures the step graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.qtt_step_many(ctxs, args.batch_steps)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        norms = [c.scalars()["norm_avg"] for c in ctxs]
+        for c in ctxs:
+            c.close()
+        cells = sum(2.0 ** sum(bp["bits"]) for bp in bps)
+        batched = {
+            "instances": args.batch, "steps": args.batch_steps,
+            "instance_steps_per_s": args.batch * args.batch_steps / tb,
+            "ms_per_step_all_instances": tb * 1e3 / args.batch_steps,
+            "precision": "fp32", "config": "Da log-U[0.1,10], Omega U[0.5,2], 2^5..2^7 points per dimension, "
+                                            "chi in {16,32,64,96}, seeds 0..n-1 (workload.make_batch_params)",
+            "timing": "host clock around qtt_step_many with a device synchronize on both sides; "
+                      "2 untimed steps first (eager step, graph capture)",
+            "init_s": t_init, "device_bytes": free0 - free1,
+            "max_abs_norm_err": max(abs(v - 1.0) for v in norms), "sum_cells": cells,
+        }
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -388,7 +422,7 @@ def run_mine(args, rank, world, local_rank):
             "clocks": clocks, "gpu_launches": int(launches),
             "state": {"norm_avg": scal["norm_avg"], "mean1_avg": scal["mean1_avg"], "nvpp": nvpp,
                       "discarded_weight_last_step": scal["discarded_weight"]},
-            "parity": parity, "fp64_path": fp64_path,
+            "parity": parity, "fp64_path": fp64_path, "batched": batched,
         }
         print(json.dumps(line), flush=True)
 

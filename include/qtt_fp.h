@@ -48,7 +48,11 @@ typedef enum {
 /* Arithmetic of the core contractions (MPO x MPS, Hadamard, sketches).
  * FP64: everything in FP64.  The reduced forms keep FP64 for the Gram
  * matrices and eigensolves of the SVD truncation and for all norm / mass
- * accumulation; their QR factorisations run in FP32. */
+ * accumulation; their QR factorisations run in FP32 followed by one FP64
+ * re-orthonormalisation step.  FP32: exact-slice bf16 tensor-core products
+ * (unbiased); TF32 and BF16X3 (hi/lo split): tensor cores with FP32
+ * accumulation.  Contractions with an operator bond <= 32 run on the CUDA
+ * cores (FP32 in the reduced forms). */
 typedef enum { QTT_FP64 = 0, QTT_FP32 = 1, QTT_TF32 = 2, QTT_BF16X3 = 3 } qtt_precision;
 
 typedef struct {
@@ -71,15 +75,22 @@ typedef struct {
   const double* umode_phase;   /* [n_umodes] */
   const double* umode_amp;     /* [n_umodes] */
   double ic_sigma;       /* std of the two composition-space Gaussians */
-  double ic_blend_width; /* w(x2) = (1 + tanh((x2 - pi) / width)) / 2 */
-  double ic_c_hi[2];     /* Gaussian centre used where w -> 1 (x2 > pi) */
+  double ic_blend_width; /* ic_kind 0: w(x2) = (1 + tanh((x2 - pi) / width)) / 2;
+                            ic_kind 1: w(x1) = (tanh((x1 - pi/2) / width) - tanh((x1 - 3pi/2) / width)) / 2 */
+  double ic_c_hi[2];     /* Gaussian centre used where w -> 1 */
   double ic_c_lo[2];     /* Gaussian centre used where w -> 0 */
   int32_t n_icmodes;     /* optional modulation f0 *= 1 + sum b cos(q . x + psi) */
   const int32_t* icmode_k;     /* [3 * n_icmodes] */
   const double* icmode_phase;  /* [n_icmodes] */
   const double* icmode_amp;    /* [n_icmodes] */
   int32_t rk_variant;    /* 0 = Heun (default), 1 = midpoint */
-  void* stream;          /* cudaStream_t or NULL */
+  int32_t flow;          /* 0: shear + seeded modes; 1: the paper's jet through a Taylor-Green
+                            vortex (Eq. velField) on [0, l0)^3, l0 = 2 pi, k = 4 pi / l0, scale u0
+                            (shear_amp unused; seeded modes, if any, are added) */
+  double u0;             /* velocity scale of flow 1 */
+  int32_t ic_kind;       /* 0: blend in x2 (above); 1: the paper's Gaussian step function in x1
+                            (Eq. initPDF) smoothed by tanh edges of width ic_blend_width */
+  void* stream;          /* cudaStream_t or NULL (the context then creates its own stream) */
 } qtt_params;
 
 /* What qtt_observe returns (all FP64, space averages normalised by the
@@ -117,6 +128,19 @@ qtt_status qtt_init(const qtt_params* params, qtt_ctx** out);
  * Hadamard product with the conditional means (mixing drift), compresses it
  * by randomized rounding and truncates it by an SVD sweep to chi_max. */
 qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps);
+
+/* Batched stepping of independent PDFs (no counterpart in the paper, which
+ * steps one PDF): advances each of ctxs[0..n) by nsteps steps, enqueueing the
+ * work of every context before synchronising any of them, so that contexts
+ * on different streams (a context created with stream NULL owns one) run
+ * concurrently on the GPU.  After a context's first step every step is one
+ * CUDA-graph launch, so the host cost is about n launches per step.  The
+ * contexts may differ in grid, chi, coefficients and precision; a context
+ * must not appear twice.  Returns QTT_OK, or the status of the first context
+ * (lowest index) that failed, whose index goes to *failed (-1 when none;
+ * failed may be NULL); the other contexts have still been advanced.
+ * Results are identical to stepping each context alone. */
+qtt_status qtt_step_many(qtt_ctx* const* ctxs, int32_t n, int32_t nsteps, int32_t* failed);
 
 /* Extract observables (see qtt_observable).  `out` has room for `cap`
  * doubles; *written receives the number written.  Returns QTT_EINVAL when

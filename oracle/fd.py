@@ -74,11 +74,21 @@ def make_grid(bits) -> Grid:
 
 
 def velocity_field(params, grid: Grid):
-    """u_i(x) = shear_amp * tanh(x2 - pi) [i = 1] + sum of modes
-    a * sin(k . x + theta) added to component c."""
+    """flow 0: u_1 = shear_amp * tanh(x2 - pi); flow 1: the jet through a
+    Taylor-Green vortex of Eq. velField on [0, l0)^3 with l0 = 2 pi and
+    k = 4 pi / l0.  Then the seeded modes a * sin(k . x + theta) are added to
+    component c."""
     X1, X2, X3 = np.meshgrid(*grid.x, indexing="ij")
     u = [np.zeros(grid.M[2:]), np.zeros(grid.M[2:]), np.zeros(grid.M[2:])]
-    u[0] += params["shear_amp"] * np.tanh(X2 - math.pi)
+    if params.get("flow", 0) == 1:
+        u0, l0 = params.get("u0", 1.0), 2.0 * math.pi
+        k = 4.0 * math.pi / l0
+        jet = np.exp(-((X2 / l0 - 0.5) ** 2 + (X3 / l0 - 0.5) ** 2) / (2.0 * (1.0 / 6.0) ** 2))
+        u[0] += u0 * (np.cos(k * X1) * np.sin(k * X2) * np.sin(k * X3) - jet)
+        u[1] += u0 * np.sin(k * X1) * np.cos(k * X2) * np.sin(k * X3)
+        u[2] += -2.0 * u0 * np.sin(k * X1) * np.sin(k * X2) * np.cos(k * X3)
+    else:
+        u[0] += params["shear_amp"] * np.tanh(X2 - math.pi)
     for m in params["umodes"]:
         k = m["k"]
         u[m["comp"]] += m["amp"] * np.sin(k[0] * X1 + k[1] * X2 + k[2] * X3 + m["phase"])
@@ -92,13 +102,21 @@ def _gaussian2(grid: Grid, centre, sigma):
 
 
 def initial_pdf(params, grid: Grid):
-    """f0 = w(x2) G_hi(phi) + (1 - w(x2)) G_lo(phi), w = (1 + tanh((x2 - pi)/width))/2,
-    G normalised so that h_phi1 h_phi2 sum G = 1; optionally multiplied by
-    (1 + sum_m b_m cos(q_m . x + psi_m))."""
+    """f0 = w G_hi(phi) + (1 - w) G_lo(phi), G normalised so that
+    h_phi1 h_phi2 sum G = 1.  ic_kind 0: w(x2) = (1 + tanh((x2 - pi)/width))/2.
+    ic_kind 1 (Eq. initPDF, smoothed): w(x1) = 1 on l0/4 <= x1 < 3 l0/4
+    (l0 = 2 pi), with tanh edges of the given width.  Optionally multiplied
+    by (1 + sum_m b_m cos(q_m . x + psi_m))."""
     g_hi = _gaussian2(grid, params["ic_c_hi"], params["ic_sigma"])
     g_lo = _gaussian2(grid, params["ic_c_lo"], params["ic_sigma"])
-    w = 0.5 * (1.0 + np.tanh((grid.x[1] - math.pi) / params["ic_blend_width"]))
-    wx = np.broadcast_to(w[None, :, None], grid.M[2:])
+    width = params["ic_blend_width"]
+    if params.get("ic_kind", 0) == 1:
+        x1 = grid.x[0]
+        w = 0.5 * (np.tanh((x1 - 0.5 * math.pi) / width) - np.tanh((x1 - 1.5 * math.pi) / width))
+        wx = np.broadcast_to(w[:, None, None], grid.M[2:])
+    else:
+        w = 0.5 * (1.0 + np.tanh((grid.x[1] - math.pi) / width))
+        wx = np.broadcast_to(w[None, :, None], grid.M[2:])
     f = g_hi[:, :, None, None, None] * wx[None, None] + g_lo[:, :, None, None, None] * (1.0 - wx)[None, None]
     if params.get("icmodes"):
         X1, X2, X3 = np.meshgrid(*grid.x, indexing="ij")

@@ -58,6 +58,9 @@ class QttParams(C.Structure):
         ("icmode_phase", C.POINTER(C.c_double)),
         ("icmode_amp", C.POINTER(C.c_double)),
         ("rk_variant", C.c_int32),
+        ("flow", C.c_int32),
+        ("u0", C.c_double),
+        ("ic_kind", C.c_int32),
         ("stream", C.c_void_p),
     ]
 
@@ -77,6 +80,7 @@ def load_library(path: str | None = None):
     P = C.POINTER
     lib.qtt_init.argtypes = [P(QttParams), P(C.c_void_p)]
     lib.qtt_step.argtypes = [C.c_void_p, C.c_int32]
+    lib.qtt_step_many.argtypes = [P(C.c_void_p), C.c_int32, C.c_int32, P(C.c_int32)]
     lib.qtt_observe.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
     lib.qtt_compare.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double)]
     lib.qtt_save.argtypes = [C.c_void_p, C.c_char_p]
@@ -89,7 +93,7 @@ def load_library(path: str | None = None):
     lib.qtt_version.restype = C.c_char_p
     lib.qtt_host_dense.argtypes = [P(QttParams), C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
     lib.qtt_selftest.argtypes = [C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
-    for fn in ("qtt_init", "qtt_step", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense",
+    for fn in ("qtt_init", "qtt_step", "qtt_step_many", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense",
                "qtt_selftest"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
@@ -132,6 +136,9 @@ def make_c_params(p: dict, stream=None):
     cp.icmode_phase = iph.ctypes.data_as(C.POINTER(C.c_double))
     cp.icmode_amp = iam.ctypes.data_as(C.POINTER(C.c_double))
     cp.rk_variant = int(p.get("rk_variant", 0))
+    cp.flow = int(p.get("flow", 0))
+    cp.u0 = float(p.get("u0", 1.0))
+    cp.ic_kind = int(p.get("ic_kind", 0))
     cp.stream = C.c_void_p(int(stream) if stream else 0)
     return cp, (comp, kk, ph, am, ik, iph, iam)
 
@@ -236,6 +243,17 @@ def qtt_init(params: dict, stream=None) -> Context:
 
 def qtt_step(ctx: Context, nsteps: int = 1):
     ctx.step(nsteps)
+
+
+def qtt_step_many(ctxs, nsteps: int = 1):
+    """Advances every context of the sequence by nsteps, concurrently on the GPU."""
+    ctxs = list(ctxs)
+    arr = (C.c_void_p * max(1, len(ctxs)))(*[c._handle() for c in ctxs])
+    failed = C.c_int32(-1)
+    st = load_library().qtt_step_many(arr, len(ctxs), int(nsteps), C.byref(failed))
+    if st != QTT_OK:
+        i = failed.value
+        _check(st, ctxs[i]._h if 0 <= i < len(ctxs) else None)
 
 
 def qtt_observe(ctx: Context, what: int, cap: int | None = None) -> np.ndarray:

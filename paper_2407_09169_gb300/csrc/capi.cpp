@@ -93,6 +93,9 @@ bool to_params(const qtt_params* in, qtt::Params& p, std::string& err) {
     p.ic_c_lo[i] = in->ic_c_lo[i];
   }
   p.rk_variant = in->rk_variant;
+  p.flow = in->flow;
+  p.u0 = in->u0;
+  p.ic_kind = in->ic_kind;
   std::string why = qtt::validate(p);
   if (!why.empty()) {
     err = "EINVAL: " + why;
@@ -200,6 +203,59 @@ qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps) {
     ctx->err = ex.what();
     return classify(ctx->err);
   }
+}
+
+qtt_status qtt_step_many(qtt_ctx* const* ctxs, int32_t n, int32_t nsteps, int32_t* failed) {
+  if (failed) *failed = -1;
+  if (n < 0 || nsteps < 0 || (n > 0 && !ctxs)) return QTT_EINVAL;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!ctxs[i] || !ctxs[i]->eng) {
+      if (failed) *failed = i;
+      return QTT_EINVAL;
+    }
+    for (int32_t k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) {
+        ctxs[i]->err = "EINVAL: a context appears twice in qtt_step_many";
+        if (failed) *failed = i;
+        return QTT_EINVAL;
+      }
+  }
+  // step-major order: every context's step s is enqueued before any step s+1
+  std::vector<int> bad(n, 0);
+  std::vector<qtt_status> code(n, QTT_OK);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    for (int32_t i = 0; i < n; ++i) {
+      if (bad[i]) continue;
+      try {
+        ctxs[i]->eng->step(1);
+      } catch (const std::exception& ex) {
+        ctxs[i]->err = ex.what();
+        code[i] = classify(ctxs[i]->err);
+        bad[i] = 1;
+      }
+    }
+  }
+  qtt_status first = QTT_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!bad[i]) {
+      try {
+        std::string msg;
+        const int st = ctxs[i]->eng->check_status(msg);
+        if (st != 0) {
+          ctxs[i]->err = msg;
+          code[i] = (qtt_status)st;
+        }
+      } catch (const std::exception& ex) {
+        ctxs[i]->err = ex.what();
+        code[i] = classify(ctxs[i]->err);
+      }
+    }
+    if (code[i] != QTT_OK && first == QTT_OK) {
+      first = code[i];
+      if (failed) *failed = i;
+    }
+  }
+  return first;
 }
 
 qtt_status qtt_observe(qtt_ctx* ctx, int32_t what, double* out, int64_t cap, int64_t* written) {

@@ -31,6 +31,9 @@ std::string validate(const Params& p) {
   if (!(p.dt > 0.0) || !std::isfinite(p.dt)) e << "dt must be positive; ";
   if (!(p.ic_sigma > 0.0)) e << "ic_sigma must be positive; ";
   if (!(p.ic_blend_width > 0.0)) e << "ic_blend_width must be positive; ";
+  if (p.flow != 0 && p.flow != 1) e << "flow must be 0 or 1; ";
+  if (p.ic_kind != 0 && p.ic_kind != 1) e << "ic_kind must be 0 or 1; ";
+  if (!std::isfinite(p.u0)) e << "u0 must be finite; ";
   if (p.oversample < 0 || p.oversample > 256) e << "oversample outside 0..256; ";
   if (p.rk_variant != 0 && p.rk_variant != 1) e << "rk_variant must be 0 or 1; ";
   for (const Mode& m : p.umodes) {
@@ -190,10 +193,36 @@ static TT fourier_tt(const Params& p, const int k[3], double theta, bool use_sin
   return tt_round(t, kTol, 0);
 }
 
+// The paper's flow (Eq. velField) on [0, l0)^3 with l0 = 2 pi: a Taylor-Green
+// vortex of wavenumber k = 4 pi / l0 and, in u1, a Gaussian jet of width l0/6
+// centred at x2 = x3 = l0 / 2.  Every term is a product of one-dimensional
+// functions, so each component is a short sum of Kronecker products.
+static TT paper_velocity_tt(const Params& p, int comp) {
+  const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
+  const double k = 2.0;  // 4 pi / l0
+  auto f1 = [&](int d, bool cosine) {
+    return encode(Kx[d], grid_x(Kx[d]), [=](double x) { return cosine ? std::cos(k * x) : std::sin(k * x); });
+  };
+  // (c1 s2 s3, s1 c2 s3, -2 s1 s2 c3)
+  TT tg = kron3(f1(0, comp == 0), f1(1, comp == 1), f1(2, comp == 2));
+  tt_scale(tg, comp == 2 ? -2.0 * p.u0 : p.u0);
+  if (comp != 0) return tg;
+  auto jet = [&](int d) {
+    return encode(Kx[d], grid_x(Kx[d]), [](double x) {
+      const double z = x / (2.0 * kPi) - 0.5;
+      return std::exp(-z * z / (2.0 / 36.0));
+    });
+  };
+  TT j = kron3(tt_constant(Kx[0], 1.0), jet(1), jet(2));
+  tt_scale(j, -p.u0);
+  return tt_round(tt_add(tg, j), kTol, 0);
+}
+
 TT velocity_tt(const Params& p, int comp) {
   const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
   TT u = kron3(tt_constant(Kx[0], 0.0), tt_constant(Kx[1], 1.0), tt_constant(Kx[2], 1.0));
-  if (comp == 0 && p.shear_amp != 0.0) {
+  if (p.flow == 1) u = paper_velocity_tt(p, comp);
+  if (p.flow == 0 && comp == 0 && p.shear_amp != 0.0) {
     TT sh = kron3(tt_constant(Kx[0], 1.0),
                   encode(Kx[1], grid_x(Kx[1]), [&](double x) { return std::tanh(x - kPi); }),
                   tt_constant(Kx[2], 1.0));
@@ -243,10 +272,21 @@ static TT gaussian_phi(const Params& p, const double c[2]) {
 
 static TT initial_pdf(const Params& p) {
   const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
-  auto w = [&](double x) { return 0.5 * (1.0 + std::tanh((x - kPi) / p.ic_blend_width)); };
-  TT whi = kron3(tt_constant(Kx[0], 1.0), encode(Kx[1], grid_x(Kx[1]), w), tt_constant(Kx[2], 1.0));
-  TT wlo = kron3(tt_constant(Kx[0], 1.0), encode(Kx[1], grid_x(Kx[1]), [&](double x) { return 1.0 - w(x); }),
-                 tt_constant(Kx[2], 1.0));
+  // ic_kind 0: w(x2) = (1 + tanh((x2 - pi) / width)) / 2.  ic_kind 1 (Eq. initPDF):
+  // the band l0/4 <= x1 < 3 l0/4 (l0 = 2 pi) with tanh edges of the given width,
+  // w(x1) = (tanh((x1 - pi/2) / width) - tanh((x1 - 3 pi/2) / width)) / 2.
+  const int d = p.ic_kind == 1 ? 0 : 1;
+  auto w = [&](double x) {
+    if (p.ic_kind == 1)
+      return 0.5 * (std::tanh((x - 0.5 * kPi) / p.ic_blend_width) - std::tanh((x - 1.5 * kPi) / p.ic_blend_width));
+    return 0.5 * (1.0 + std::tanh((x - kPi) / p.ic_blend_width));
+  };
+  auto blend = [&](bool hi) {
+    TT parts[3] = {tt_constant(Kx[0], 1.0), tt_constant(Kx[1], 1.0), tt_constant(Kx[2], 1.0)};
+    parts[d] = encode(Kx[d], grid_x(Kx[d]), [&](double x) { return hi ? w(x) : 1.0 - w(x); });
+    return kron3(parts[0], parts[1], parts[2]);
+  };
+  TT whi = blend(true), wlo = blend(false);
   TT f = tt_add(tt_kron(gaussian_phi(p, p.ic_c_hi), whi), tt_kron(gaussian_phi(p, p.ic_c_lo), wlo));
   f = tt_round(f, kTol, 0);
   bool any = false;

@@ -28,6 +28,9 @@ struct Params {
   double ic_sigma = 0.05, ic_blend_width = 0.2;
   double ic_c_hi[2] = {1, 0}, ic_c_lo[2] = {0, 1};
   int rk_variant = 0;
+  int flow = 0;        // 0: shear + seeded modes; 1: jet through a Taylor-Green vortex (Eq. velField)
+  double u0 = 1.0;     // velocity scale of flow 1
+  int ic_kind = 0;     // 0: tanh blend in x2; 1: Gaussian step function in x1 (Eq. initPDF), smoothed
   int N() const { return bits[0] + bits[1] + bits[2] + bits[3] + bits[4]; }
   int Kphi() const { return bits[0] + bits[1]; }
 };

@@ -139,3 +139,50 @@ def test_nvpp_observable():
     with pkg.qtt_init(p) as ctx:
         nv = ctx.observe(pkg.OBS_NVPP)[0]
     assert nv == oracle.nvpp(40, 128)
+
+
+# ------------------------------------------------------------ the paper's flow case
+def paper_exact_params(bits, **kw):
+    p = workload.make_paper_params(**kw)
+    p["bits"] = list(bits)
+    N = sum(p["bits"])
+    p["chi_max"] = 2 ** (N // 2)
+    p["svd_rel_tol"] = 0.0
+    p["exact"] = 1
+    p["dt"] = workload.cfl_dt(p["bits"], p["omega"], p["da"], p["gamma"], p["d_phi"], workload.velocity_bound(p))
+    return p
+
+
+@pytest.mark.parametrize("bits,da", [([2, 2, 2, 2, 2], 0.0), ([2, 2, 3, 2, 2], 1.2)])
+def test_paper_flow_exact_mode_matches_oracle(bits, da):
+    """Jet through a Taylor-Green vortex (Eq. velField) and the Gaussian step
+    initial PDF (Eq. initPDF), untruncated: the MPS path equals the oracle."""
+    p = paper_exact_params(bits, da=da)
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(4)
+        got = ctx.observe(pkg.OBS_DENSE)
+    err = rel_l2(got, oracle.solve(p, 4).ravel())
+    assert err <= 1e-10, err
+
+
+def test_paper_flow_truncated_vs_oracle():
+    """The paper's case at 2^4 points per dimension, chi = 32, Da = 0, FP64 and
+    FP32 forms: reported error against the oracle, conservation of <1>, and
+    the mean composition against the oracle's moments."""
+    p = workload.make_paper_params(bits=4, chi=32)
+    nsteps = 8
+    ref = oracle.solve(p, nsteps)
+    g = oracle.make_grid(p["bits"])
+    o = oracle.observables(ref, g)
+    for prec in ("fp64", "fp32"):
+        q = dict(p, precision=workload.PRECISIONS[prec], svd_rel_tol=1e-14)
+        with pkg.qtt_init(q) as ctx:
+            ctx.step(nsteps)
+            got = ctx.observe(pkg.OBS_DENSE)
+            s = ctx.scalars()
+        err = rel_l2(got, ref.ravel())
+        print(f"paper case {prec}: rel-L2 vs oracle {err:.3e}, <1>-1 {s['norm_avg'] - 1:.1e}, "
+              f"d<Phi1> {s['mean1_avg'] - o['mean1_avg']:.1e}")
+        assert err < 5e-2
+        assert abs(s["norm_avg"] - 1.0) < 1e-4
+        assert abs(s["mean1_avg"] - o["mean1_avg"]) < 1e-3

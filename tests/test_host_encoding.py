@@ -111,6 +111,45 @@ def test_stage_operator_reproduces_oracle_euler_step(bits, da):
     assert np.linalg.norm(out - ref.ravel()) <= 1e-12 * np.linalg.norm(ref)
 
 
+def _paper(bits, **kw):
+    p = workload.make_paper_params(**kw)
+    p["bits"] = list(bits)
+    return p
+
+
+def test_paper_flow_encodings():
+    """The paper's flow case (Eq. velField velocity, Eq. initPDF initial PDF)
+    against the oracle's dense fields."""
+    p = _paper([3, 3, 4, 3, 3])
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    for i in range(3):
+        got = pkg.qtt_host_dense(p, 1 + i, u[i].size)
+        assert np.abs(got - u[i].ravel()).max() < 1e-12
+    ref = oracle.initial_pdf(p, g).ravel()
+    got = pkg.qtt_host_dense(p, 0, ref.size)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_paper_flow_stage_operator():
+    p = _paper([2, 2, 2, 2, 2], da=0.8, gamma=0.03)
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    rng = np.random.default_rng(11)
+    f = rng.random(g.shape)
+    ref = f + p["dt"] * oracle.rhs(f, g, u, p)
+    n = f.size
+    op = pkg.qtt_host_dense(p, 31, n * n).reshape(n, n)
+    Mphi = g.M[0] * g.M[1]
+    had = pkg.qtt_host_dense(p, 32, 2 * Mphi * Mphi).reshape(2, Mphi, Mphi)
+    m1, m2 = oracle.conditional_means(f, g)
+    fx = f.reshape(Mphi, -1)
+    out = op @ f.ravel()
+    for a, m in enumerate((m1, m2)):
+        out += (had[a] @ (fx * m.ravel()[None, :])).ravel()
+    assert np.linalg.norm(out - ref.ravel()) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_operator_bonds_are_small():
     p = workload.make_params("large")
     b = pkg.qtt_host_dense(p, 40, 64)

@@ -282,3 +282,64 @@ def test_nvpp_brute_force_small():
             entries = sum(p[n] * 2 * p[n + 1] for n in range(N))
             gauge = sum(p[n] ** 2 for n in range(1, N))
             assert oracle.nvpp(N, chi) == entries - gauge
+
+
+# ---- the paper's own flow case (Materials and Methods, Flow case definition)
+def _paper_case(bits, **kw):
+    p = workload.make_paper_params(**kw)
+    p["bits"] = list(bits)
+    return p
+
+
+def test_paper_velocity_values_and_divergence():
+    """Eq. velField on [0, 2 pi)^3 (k = 2): u2 peaks at u0 where
+    sin(2 x1) = cos(2 x2) = sin(2 x3) = 1, u3 reaches -2 u0 where
+    sin(2 x1) = sin(2 x2) = cos(2 x3) = 1, and on the jet axis x2 = x3 = pi the
+    vortex term of u1 vanishes so u1 = -u0; the discrete divergence is zero
+    (the CFD2 symbols of the three cosine/sine factors cancel, 1 + 1 - 2 = 0)."""
+    p = _paper_case([2, 2, 4, 4, 4], u0=1.3)
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    q = g.M[2] // 8  # index of pi / 4
+    assert abs(u[1][q, 0, q] - 1.3) < 1e-12 and abs(np.abs(u[1]).max() - 1.3) < 1e-12
+    assert abs(u[2][q, q, 0] + 2.6) < 1e-12 and abs(np.abs(u[2]).max() - 2.6) < 1e-12
+    c = g.M[2] // 2  # index of pi
+    assert np.abs(u[0][:, c, c] + 1.3).max() < 1e-12
+    div = sum(oracle.d1_periodic(u[i], i, g.h_x[i]) for i in range(3))
+    assert np.abs(div).max() < 1e-12
+
+
+def test_paper_initial_pdf_mass_and_mirror_symmetry():
+    """Eq. initPDF: <1>(x) = 1 everywhere; the two Gaussians are mirror images
+    under phi1 <-> phi2 and the band weight satisfies w(pi) = 1 - w(0), so
+    <Phi_1>(x1 = pi) = <Phi_2>(x1 = 0) and the band centre carries the inner
+    Gaussian (<Phi_1> > 1/2 there)."""
+    p = _paper_case([5, 5, 4, 3, 3])
+    g = oracle.make_grid(p["bits"])
+    o = oracle.observables(oracle.initial_pdf(p, g), g)
+    assert np.abs(o["norm"] - 1.0).max() < 1e-13
+    c = g.M[2] // 2
+    assert np.abs(o["mean1"][c] - o["mean2"][0]).max() < 1e-12
+    assert np.abs(o["mean2"][c] - o["mean1"][0]).max() < 1e-12
+    assert o["mean1"][c].min() > 0.7 and o["mean1"][0].max() < 0.3
+
+
+def test_paper_velocity_moment_equation_da0():
+    """Da = 0 with the paper's velocity (and the step-function blend in x1):
+    <Phi_a>(x, t) of the 5-D scheme equals the RK2-CFD2 solution of Eq. FPMoms.
+    The identity needs the composition-space mass to stay clear of the phi
+    boundaries (the ghost rules add boundary terms to the first moment), so the
+    Gaussians are the interior ones of the other moment pins."""
+    p = _paper_case([5, 5, 3, 3, 3], da=0.0, ic_sigma=0.05, ic_c_hi=[0.62, 0.4], ic_c_lo=[0.38, 0.6])
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    f = oracle.initial_pdf(p, g)
+    m1, m2 = oracle.conditional_means(f, g)
+    for _ in range(6):
+        f = oracle.rk2_step(f, g, u, p)
+        m1 = oracle.moment_step(m1, g, u, p)
+        m2 = oracle.moment_step(m2, g, u, p)
+    f1, f2 = oracle.conditional_means(f, g)
+    assert np.abs(f1 - m1).max() < 1e-12
+    assert np.abs(f2 - m2).max() < 1e-12
+

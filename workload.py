@@ -67,6 +67,30 @@ def cfl_dt(bits, omega, da, gamma, d_phi, u_bound, cfl=0.2):
     return cfl * min(lims)
 
 
+def velocity_bound(p: dict) -> float:
+    """Upper bound of sum_i |u_i| for the stability rule: the shear (flow 0) or
+    the Taylor-Green vortex and jet (flow 1: |u1| <= 2 u0, |u2| <= u0,
+    |u3| <= 2 u0), plus the seeded modes."""
+    base = 5.0 * abs(p.get("u0", 1.0)) if p.get("flow", 0) == 1 else abs(p["shear_amp"])
+    return base + sum(abs(m["amp"]) for m in p["umodes"])
+
+
+def make_paper_params(bits: int = 5, chi: int = 64, seed: int = 0, precision: str = "fp64", **overrides) -> dict:
+    """The paper's own flow case (Materials and Methods, Flow case definition)
+    on [0, 2 pi)^3: jet through a Taylor-Green vortex (Eq. velField, u0 = 1),
+    the Gaussian step-function initial PDF (Eq. initPDF: centres (3/4, 1/4)
+    inside the band 1/4 <= x1/l0 < 3/4 and (1/4, 3/4) outside, width 1/8) with
+    tanh edges of width 0.1, gamma = u0 l0 / Pe with Pe = 10^3, Omega = 1,
+    Da = 0 (the case with a numerically exact moment equation), D_phi = mu
+    Omega with mu = 4e-3.  The subgrid fields gamma_SGS(x) and Omega_mix(x) are
+    constants here (gamma_SGS = 0, Omega_mix = Omega)."""
+    kw = dict(flow=1, u0=1.0, ic_kind=1, ic_sigma=0.125, ic_c_hi=[0.75, 0.25], ic_c_lo=[0.25, 0.75],
+              ic_blend_width=0.1, gamma=2.0 * math.pi / 1.0e3, omega=1.0, da=0.0, d_phi=4e-3, shear_amp=0.0,
+              umodes=[])
+    kw.update(overrides)
+    return make_params({"bits": bits, "chi_max": chi, "steps": 1}, seed=seed, precision=precision, **kw)
+
+
 def make_params(workload: str = "small", seed: int = 0, precision: str = "fp64",
                 **overrides) -> dict:
     """Parameter dictionary for one PDF.  Keys mirror the C struct qtt_params."""
@@ -94,6 +118,30 @@ def make_params(workload: str = "small", seed: int = 0, precision: str = "fp64",
     )
     p.update(copy.deepcopy(overrides))
     if "dt" not in overrides:
-        ub = abs(p["shear_amp"]) + sum(abs(m["amp"]) for m in p["umodes"])
+        ub = velocity_bound(p)
         p["dt"] = cfl_dt(p["bits"], p["omega"], p["da"], p["gamma"], p["d_phi"], ub)
     return p
+
+
+# Batched configuration: independent PDFs of uneven grid and chi.
+BATCH = {"n": 256, "bits": (5, 6, 7), "chi": (16, 32, 64, 96), "da_log10": (-1.0, 1.0), "omega": (0.5, 2.0),
+         "steps": 100, "mu": 4e-3}
+
+
+def make_batch_params(n: int = BATCH["n"], seed: int = 0, precision: str = "fp32") -> list:
+    """n instance parameter dictionaries: Da log-uniform in [0.1, 10], Omega
+    uniform in [0.5, 2], bits per dimension uniform in {5, 6, 7}, chi_max
+    uniform in {16, 32, 64, 96}, drawn from numpy default_rng(seed); instance
+    i takes the velocity modes of seed i; the artificial dissipation is
+    D_phi = mu Omega with mu = 4e-3; dt from the stability rule."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        da = float(10.0 ** rng.uniform(*BATCH["da_log10"]))
+        omega = float(rng.uniform(*BATCH["omega"]))
+        K = int(rng.choice(BATCH["bits"]))
+        chi = int(rng.choice(BATCH["chi"]))
+        w = {"bits": K, "chi_max": chi, "steps": BATCH["steps"]}
+        out.append(make_params(w, seed=i, precision=precision, da=da, omega=omega, d_phi=BATCH["mu"] * omega))
+    return out
+
