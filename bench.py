@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--precision", default="bf16x3", choices=list(workload.PRECISIONS),
                     help="contraction arithmetic of the timed form (the FP64 path is timed beside it)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path beside the form")
+    ap.add_argument("--also", default="fp32,tf32",
+                    help="other reduced forms timed and compared with the FP64 path (comma-separated)")
     ap.add_argument("--batch", type=int, default=64,
                     help="instances of the batched configuration stepped together (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
@@ -329,7 +331,6 @@ def run_mine(args, rank, world, local_rank):
         rel = cf.compare(c64)
         s64, sf = c64.scalars(), cf.scalars()
         cf.close()
-        c64.close()
         v64 = args.steps * world / (ms64 / 1e3)
         fp64_path = {
             "value": v64, "unit": "steps/s", "ms_per_step": ms64 / args.steps, "speedup": value / v64,
@@ -337,6 +338,27 @@ def run_mine(args, rank, world, local_rank):
             "d_norm_avg": sf["norm_avg"] - s64["norm_avg"], "d_mean1_avg": sf["mean1_avg"] - s64["mean1_avg"],
             "d_phi11_avg": sf["phi11_avg"] - s64["phi11_avg"],
         }
+        # the other reduced forms on the same workload: steps/s and distance to the FP64 path
+        others = {}
+        for other in [x for x in args.also.split(",") if x and x != args.precision and x != "fp64"]:
+            po = workload.make_params(args.workload, seed=rank, precision=other)
+            co = q.qtt_init(po, stream=stream.cuda_stream)
+            for _ in range(args.warmup):
+                co.step(1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            co.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mso = max_over_ranks(e0.elapsed_time(e1))
+            so = co.scalars()
+            others[other] = {"value": args.steps * world / (mso / 1e3), "unit": "steps/s",
+                             "speedup": (args.steps * world / (mso / 1e3)) / v64,
+                             "rel_l2_vs_fp64_after_steps": co.compare(c64),
+                             "d_norm_avg": so["norm_avg"] - s64["norm_avg"]}
+            co.close()
+        fp64_path["other_forms"] = others
+        c64.close()
 
     # ---- end to end through the C ABI: host params -> device, K steps, scalars read back each step
     e2e = None
@@ -396,6 +418,12 @@ def run_mine(args, rank, world, local_rank):
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
         norms = [c.scalars()["norm_avg"] for c in ctxs]
+        # the same contexts stepped one after another (each synchronised), for comparison
+        t0 = time.perf_counter()
+        for c in ctxs:
+            c.step(args.batch_steps)
+        torch.cuda.synchronize()
+        tseq = time.perf_counter() - t0
         for c in ctxs:
             c.close()
         cells = sum(2.0 ** sum(bp["bits"]) for bp in bps)
@@ -407,6 +435,7 @@ def run_mine(args, rank, world, local_rank):
                                             "chi in {16,32,64,96}, seeds 0..n-1 (workload.make_batch_params)",
             "timing": "host clock around qtt_step_many with a device synchronize on both sides; "
                       "2 untimed steps first (eager step, graph capture)",
+            "sequential_instance_steps_per_s": args.batch * args.batch_steps / tseq,
             "init_s": t_init, "device_bytes": free0 - free1,
             "max_abs_norm_err": max(abs(v - 1.0) for v in norms), "sum_cells": cells,
         }

@@ -135,19 +135,22 @@ Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
   exact_ = p.exact != 0;
   prec_bits_ = (p.precision == 0) ? 64 : 32;
   // contraction arithmetic: FP32 -> 3 x 3 exact bf16 slices (unbiased,
-  // ~2^-24), BF16X3 -> 2 x 2 exact bf16 slices (unbiased, ~2^-16), TF32 -> one
-  // TF32 pass.  The sketch products get the same arithmetic as the products
-  // that carry the state: the sketch W_{n+1} = R_{n+1} G must reproduce the
-  // right part R_{n+1} of the operator-state product, because T_n R_{n+1} can
-  // be far smaller than |T_n| |R_{n+1}| (the operator's stencils cancel), and
-  // an error in R_{n+1} then steers the range finder away from T_n R_{n+1}.
+  // ~2^-24 of each row's largest term) for the products that carry the state,
+  // hi/lo TF32 (~2^-21 per element) for the sketch products; BF16X3 -> the
+  // hi/lo bf16 split everywhere; TF32 -> one TF32 pass.  The sketch
+  // W_{n+1} = R_{n+1} G must reproduce the right part R_{n+1} of the
+  // operator-state product accurately element by element,
+  // because T_n R_{n+1} can be far smaller than |T_n| |R_{n+1}| (the stencils
+  // cancel) and an error in R_{n+1} steers the range finder away from
+  // T_n R_{n+1}; a bias of the sketch, on the other hand, only rescales it.
   const int mode = p.precision == 1 ? TC_BF16X6 : p.precision == 2 ? TC_TF32 : p.precision == 3 ? TC_BF16X3 : -1;
+  for (int& m : tc_mode_) m = mode;
+  if (p.precision == 1) tc_mode_[GEMM_SKETCH] = tc_mode_[GEMM_RANGE] = TC_TF32X3;
   // The reduced forms re-orthonormalise the float QR's Q in FP64 (one
   // Newton-Schulz step).  The float Q's departure from orthonormality
   // (~1e-6) otherwise shows up as a drift of the mass <1>: -8.7e-5 against
   // -2.1e-6 after ten BF16X3 steps of the 2^4-point workload.
   qr_refine_ = (p.precision != 0);
-  for (int& m : tc_mode_) m = mode;
   timer_ = new KernelTimer();
   if (const char* e = std::getenv("QTT_KERNEL_TIMING")) timer_->on = (e[0] == '1');
 }
@@ -156,7 +159,13 @@ Engine::~Engine() {
   for (cudaGraphExec_t& g : graph_)
     if (g) cudaGraphExecDestroy(g);
   for (void* a : allocs_) cudaFree(a);
-  if (pack_ws_) cudaFree(pack_ws_);
+  for (void* w : pack_ws_)
+    if (w) cudaFree(w);
+  for (int l = 1; l < kLanes; ++l) {
+    if (lane_st_[l]) cudaStreamDestroy(lane_st_[l]);
+    if (ev_join_[l]) cudaEventDestroy(ev_join_[l]);
+  }
+  if (ev_fork_) cudaEventDestroy(ev_fork_);
   delete timer_;
   if (own_stream_) cudaStreamDestroy(st_);
 }
@@ -232,8 +241,8 @@ void Engine::upload_op(DevOp& op, const TT& t) {
 
 void Engine::gemm64(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
                     OutView C) {
-  TimeScope ts(timer_, TM_GEMM, st_, 2.0 * M * (double)N * K * outer * inner);
-  gemm_f64(st_, M, N, K, outer, inner, alpha, A, B, beta, C, ws_, ws_elems_);
+  TimeScope ts(timer_, TM_GEMM, cur(), 2.0 * M * (double)N * K * outer * inner);
+  gemm_f64(cur(), M, N, K, outer, inner, alpha, A, B, beta, C, lane_ws_[lane_], ws_elems_);
 }
 
 void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta,
@@ -241,8 +250,8 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
   const int mode = tc_mode_[role];
   if (small_gemm_fits(M, N, K, outer, inner)) {
     // operator-bond contractions: memory-bound, on the CUDA cores
-    TimeScope ts(timer_, TM_SMALL, st_, 2.0 * M * (double)N * K * outer * inner);
-    small_gemm(st_, mode >= 0, M, N, K, outer, inner, alpha, A, B, beta, C);
+    TimeScope ts(timer_, TM_SMALL, cur(), 2.0 * M * (double)N * K * outer * inner);
+    small_gemm(cur(), mode >= 0, M, N, K, outer, inner, alpha, A, B, beta, C);
     return;
   }
   if (mode < 0) {
@@ -250,26 +259,28 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
     return;
   }
   const size_t need = tc_workspace_bytes(M, N, K, (long long)outer * inner, mode);
-  if (need > pack_bytes_) {  // grows during the first step only (static shapes)
-    QTT_CUDA(cudaStreamSynchronize(st_));
-    if (pack_ws_) QTT_CUDA(cudaFree(pack_ws_));
-    pack_ws_ = nullptr;
+  void*& pw = pack_ws_[lane_];
+  size_t& pb = pack_bytes_[lane_];
+  if (need > pb) {  // grows during the first step only (static shapes)
+    QTT_CUDA(cudaStreamSynchronize(cur()));
+    if (pw) QTT_CUDA(cudaFree(pw));
+    pw = nullptr;
     const size_t bytes = need + need / 4;
-    if (cudaMalloc(&pack_ws_, bytes) != cudaSuccess) {
+    if (cudaMalloc(&pw, bytes) != cudaSuccess) {
       cudaGetLastError();
-      pack_ws_ = nullptr;
-      pack_bytes_ = 0;
+      pw = nullptr;
+      pb = 0;
       throw std::runtime_error("ENOMEM: tensor-core packing workspace");
     }
-    pack_bytes_ = bytes;
+    pb = bytes;
   }
   const double fl = 2.0 * M * (double)N * K * outer * inner;
   if (timer_->on) {
     static const double passes[5] = {3, 2, 6, 1, 6};  // indexed by TcMode, in bf16-pass units
     tc_issued_flops_ += fl * passes[mode];
   }
-  TimeScope ts(timer_, TM_TC, st_, fl);
-  if (!gemm_tc(st_, mode, M, N, K, outer, inner, alpha, A, B, beta, C, pack_ws_, pack_bytes_, ws_, ws_elems_,
+  TimeScope ts(timer_, TM_TC, cur(), fl);
+  if (!gemm_tc(cur(), mode, M, N, K, outer, inner, alpha, A, B, beta, C, pw, pb, lane_ws_[lane_], ws_elems_,
                status_ + 2))
     throw std::runtime_error("EINVAL: tensor-core GEMM shape outside the supported grid or workspace");
 }
@@ -394,6 +405,25 @@ void Engine::init() {
   gq_ = (double*)dalloc(rmax * rmax * sizeof(double));
   ws_elems_ = (size_t)8 << 20;
   ws_ = (double*)dalloc(ws_elems_ * sizeof(double));
+  // lanes for the terms' concurrent work (at most 2 terms in the first stage
+  // and 3 (Heun) or 4 (midpoint) in the second)
+  lane_st_[0] = st_;
+  lane_ws_[0] = ws_;
+  lane_x1_[0] = X1_;
+  lane_x2_[0] = X2_;
+  lane_p_[0] = P_;
+  nlanes_ = 1 + (p_.rk_variant == 0 ? 3 : 4);
+  if (const char* e = std::getenv("QTT_LANES"))
+    if (e[0] == '0') nlanes_ = 1;
+  if (nlanes_ > 1) QTT_CUDA(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+  for (int l = 1; l < nlanes_; ++l) {
+    QTT_CUDA(cudaStreamCreateWithFlags(&lane_st_[l], cudaStreamNonBlocking));
+    QTT_CUDA(cudaEventCreateWithFlags(&ev_join_[l], cudaEventDisableTiming));
+    lane_ws_[l] = (double*)dalloc(ws_elems_ * sizeof(double));
+    lane_x1_[l] = (double*)dalloc(x1 * sizeof(double));
+    lane_x2_[l] = (double*)dalloc(x2 * sizeof(double));
+    lane_p_[l] = (double*)dalloc(pp * sizeof(double));
+  }
   for (int i = 0; i < 2; ++i) {
     v_[i] = (double*)dalloc((size_t)2 * D_[kphi_] * sizeof(double));
     hf_[i] = (double*)dalloc((size_t)4 * D_[kphi_ + 1] * sizeof(double));
@@ -461,48 +491,84 @@ void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, co
   const int bl = t.f->b[n], br = t.f->b[n + 1];
   const int wl = t.w(n), wr = t.w(n + 1);
   const double* A = t.f->core(n);
+  double* X1 = lane_x1_[lane_];
+  double* X2 = lane_x2_[lane_];
   // X1[(w',a')][s][l] = sum_l' W_{n+1}[(w',a')][l'] Om[l][s][l']
-  gemm(wr * br, Ll, Lr, 1, 2, 1.0, mv(Wn1, Lr, 1), mv(Om, 1, 2LL * Lr, 0, Lr), 0.0, ov(X1_, 2LL * Ll, 1, 0, Ll), role);
+  gemm(wr * br, Ll, Lr, 1, 2, 1.0, mv(Wn1, Lr, 1), mv(Om, 1, 2LL * Lr, 0, Lr), 0.0, ov(X1, 2LL * Ll, 1, 0, Ll), role);
   if (!t.diag(n)) {
     // X2[w'][(a,s')][(s,l)] = sum_a' A[(a,s')][a'] X1[(w',a')][(s,l)]
-    gemm(2 * bl, 2 * Ll, br, wr, 1, 1.0, mv(A, br, 1), mv(X1_, 2LL * Ll, 1, (long long)br * 2 * Ll), 0.0,
-         ov(X2_, 2LL * Ll, 1, 4LL * bl * Ll), role);
+    gemm(2 * bl, 2 * Ll, br, wr, 1, 1.0, mv(A, br, 1), mv(X1, 2LL * Ll, 1, (long long)br * 2 * Ll), 0.0,
+         ov(X2, 2LL * Ll, 1, 4LL * bl * Ll), role);
     // W_n[(w,a)][l] = sum_{s,s',w'} W[w][s*2+s'][w'] X2[w'][(a,s')][(s,l)]
     const double* Wss = t.op->Wss(n);
     for (int ss = 0; ss < 4; ++ss) {
       const int s = ss >> 1, sp = ss & 1;
       gemm(wl, Ll, wr, bl, 1, 1.0, mv(Wss + (size_t)ss * wl * wr, wr, 1),
-           mv(X2_ + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll), ss == 0 ? 0.0 : 1.0,
+           mv(X2 + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll), ss == 0 ? 0.0 : 1.0,
            ov(Wn, (long long)bl * Ll, 1, Ll), role);
     }
   } else {
     const double* H = t.H(n);
-    // X2[h'][a][s][l] = sum_a' A[a][s][a'] X1[(h',a')][s][l]
-    gemm(bl, Ll, br, wr, 2, 1.0, mv(A, 2LL * br, 1, 0, br), mv(X1_, 2LL * Ll, 1, (long long)br * 2 * Ll, Ll), 0.0,
-         ov(X2_, 2LL * Ll, 1, 2LL * bl * Ll, Ll), role);
-    // W_n[(h,a)][l] = sum_s sum_h' H[h][s][h'] X2[h'][a][s][l]
+    // X2[a][s][h'][l] = sum_a' A[a][s][a'] X1[(h',a')][s][l]
+    gemm(bl, Ll, br, wr, 2, 1.0, mv(A, 2LL * br, 1, 0, br), mv(X1, 2LL * Ll, 1, (long long)br * 2 * Ll, Ll), 0.0,
+         ov(X2, 2LL * wr * Ll, 1, Ll, (long long)wr * Ll), role);
+    // W_n[(h,a)][l] = sum_s sum_h' H[h][s][h'] X2[a][s][h'][l], one product per s
+    // accumulated in FP64 (H is shared by every a).  Fusing the two into one
+    // product over K = 2 w_{n+1} changes how the tensor cores' FP32
+    // accumulation is chunked, and with the BF16X3 form that raised the drift
+    // of <1> after ten 2^4-point steps from -2.1e-6 to -7.6e-5.
     for (int s = 0; s < 2; ++s)
-      gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1),
-           mv(X2_ + (size_t)s * Ll, 2LL * bl * Ll, 1, 2LL * Ll), s == 0 ? 0.0 : 1.0,
-           ov(Wn, (long long)bl * Ll, 1, Ll), role);
+      gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1), mv(X2 + (size_t)s * wr * Ll, Ll, 1, 2LL * wr * Ll),
+           s == 0 ? 0.0 : 1.0, ov(Wn, (long long)bl * Ll, 1, Ll), role);
   }
+}
+
+void Engine::fork_lanes(int n) {
+  QTT_CUDA(cudaEventRecord(ev_fork_, st_));
+  for (int l = 1; l <= n; ++l) QTT_CUDA(cudaStreamWaitEvent(lane_st_[l], ev_fork_, 0));
+}
+
+void Engine::join_lanes(int n) {
+  for (int l = 1; l <= n; ++l) {
+    QTT_CUDA(cudaEventRecord(ev_join_[l], lane_st_[l]));
+    QTT_CUDA(cudaStreamWaitEvent(st_, ev_join_[l], 0));
+  }
+}
+
+void Engine::sketch_pass(Term* terms, int nt, int n_stop, const DevMps& om) {
+  // right-to-left sketch of every term; the terms' chains are independent,
+  // so each runs on a lane of its own when there are enough lanes
+  const bool par = nt > 1 && nt < nlanes_;
+  if (par) fork_lanes(nt);
+  for (int i = 0; i < nt; ++i) {
+    lane_ = par ? 1 + i : 0;
+    const Term& t = terms[i];
+    double* W = Wslot_[t.slot];
+    fill_value(cur(), W + Woff_[t.slot][N_], 1, 1.0);
+    for (int n = N_ - 1; n > n_stop; --n)
+      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], om.core(n), ell_[n], ell_[n + 1],
+                  exact_ ? GEMM_STATE : GEMM_SKETCH);
+  }
+  lane_ = 0;
+  if (par) join_lanes(nt);
 }
 
 void Engine::zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha) {
   const int bl = t.f->b[n], br = t.f->b[n + 1];
   const int wl = t.w(n), wr = t.w(n + 1);
   const double* A = t.f->core(n);
+  double* P = lane_p_[lane_];
   // P[(rho,w)][(s',a')] = sum_a C[(rho,w)][a] A[a][(s',a')]
-  gemm(r * wl, 2 * br, bl, 1, 1, 1.0, mv(C, bl, 1), mv(A, 2LL * br, 1), 0.0, ov(P_, 2LL * br, 1));
+  gemm(r * wl, 2 * br, bl, 1, 1, 1.0, mv(C, bl, 1), mv(A, 2LL * br, 1), 0.0, ov(P, 2LL * br, 1));
   if (!t.diag(n)) {
     // T[(rho,s)][(w',a')] = sum_{(w,s')} Wt[s][w'][(w,s')] P[rho][(w,s')][a']
     const double* Wt = t.op->Wt(n);
     gemm(wr, br, 2 * wl, r, 2, alpha, mv(Wt, 2LL * wl, 1, 0, (long long)wr * 2 * wl),
-         mv(P_, br, 1, 2LL * wl * br, 0), 0.0, ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
+         mv(P, br, 1, 2LL * wl * br, 0), 0.0, ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
   } else {
     const double* H = t.H(n);
     // T[(rho,s)][(h',a')] = sum_h H[h][s][h'] P[(rho,h)][(s,a')]
-    gemm(wr, br, wl, r, 2, alpha, mv(H, 1, 2LL * wr, 0, wr), mv(P_, 2LL * br, 1, (long long)wl * 2 * br, br), 0.0,
+    gemm(wr, br, wl, r, 2, alpha, mv(H, 1, 2LL * wr, 0, wr), mv(P, 2LL * br, 1, (long long)wl * 2 * br, br), 0.0,
          ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
   }
 }
@@ -541,20 +607,29 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
     fill_gaussian_sketch(st_, omega_.chain(), omega_.max_core_elems(), p_.seed, dstep_, stage);
   }
   // 1. right-to-left sketch: W_n = (right part of the term) x (right part of the random MPS)
-  for (int i = 0; i < nt; ++i) {
-    const Term& t = terms[i];
-    double* W = Wslot_[t.slot];
-    fill_value(st_, W + Woff_[t.slot][N], 1, 1.0);
-    for (int n = N - 1; n >= 1; --n)
-      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], omega_.core(n), ell_[n], ell_[n + 1],
-                  GEMM_SKETCH);
-  }
-  // 2. left-to-right orthogonalisation of the sketched site tensors
+  sketch_pass(terms, nt, 0, omega_);
+  // 2. left-to-right orthogonalisation of the sketched site tensors.  The
+  // terms' site tensors T_i (and, after the QR, C_i = Q^T T_i together with
+  // the next site's T_i) are independent, so each term runs on a lane of its
+  // own between the Y = sum_i T_i W_i / QR steps on st_.
+  const bool par = nt > 1 && nt < nlanes_;
   for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
+  auto zip_all = [&](int n, int r, bool project, int rn) {
+    if (par) fork_lanes(nt);
+    for (int i = 0; i < nt; ++i) {
+      lane_ = par ? 1 + i : 0;
+      const Term& t = terms[i];
+      if (project)  // C_i = Q^T T_i at the previous site
+        gemm(rn, (int)t.B(n), 2 * r, 1, 1, 1.0, mv(mid_.core(n - 1), 1, rn), mv(T_[t.slot], t.B(n), 1), 0.0,
+             ov(C_[t.slot], t.B(n), 1));
+      zip_site(t, n, project ? rn : r, C_[t.slot], T_[t.slot], n == 0 ? t.scale : 1.0);
+    }
+    lane_ = 0;
+    if (par) join_lanes(nt);
+  };
   int r = 1;
+  zip_all(0, 1, false, 0);
   for (int n = 0; n < N; ++n) {
-    for (int i = 0; i < nt; ++i)
-      zip_site(terms[i], n, r, C_[terms[i].slot], T_[terms[i].slot], n == 0 ? terms[i].scale : 1.0);
     if (n == N - 1) {  // all terms close with bond 1: the last core is their sum
       for (int i = 0; i < nt; ++i) {
         const Term& t = terms[i];
@@ -570,6 +645,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
         fill_identity_left(st_, mid_.core(n), r);
       }
       for (int i = 0; i < nt; ++i) std::swap(C_[terms[i].slot], T_[terms[i].slot]);
+      zip_all(n + 1, rn, false, 0);
     } else {
       const int L = ell_[n + 1];
       for (int i = 0; i < nt; ++i) {
@@ -591,11 +667,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
         gemm64(rn, rn, 2 * r, 1, 1, -0.5, mv(X1_, 1, rn), mv(X1_, rn, 1), 1.5, ov(gq_, rn, 1));
         gemm64(2 * r, rn, rn, 1, 1, 1.0, mv(X1_, rn, 1), mv(gq_, rn, 1), 0.0, ov(mid_.core(n), rn, 1));
       }
-      for (int i = 0; i < nt; ++i) {
-        const Term& t = terms[i];
-        gemm(rn, (int)t.B(n + 1), 2 * r, 1, 1, 1.0, mv(mid_.core(n), 1, rn), mv(T_[t.slot], t.B(n + 1), 1), 0.0,
-             ov(C_[t.slot], t.B(n + 1), 1));
-      }
+      if (n + 1 < N) zip_all(n + 1, r, true, rn);
     }
     r = rn;
   }
@@ -651,14 +723,7 @@ void Engine::run_stage_exact(Term* terms, int nt, DevMps& out) {
     TimeScope ts(timer_, TM_OTHER, st_);
     for (int n = nc + 1; n < N; ++n) fill_identity_right(st_, out.core(n), ell_[n + 1]);
   }
-  for (int i = 0; i < nt; ++i) {
-    const Term& t = terms[i];
-    double* W = Wslot_[t.slot];
-    fill_value(st_, W + Woff_[t.slot][N], 1, 1.0);
-    for (int n = N - 1; n > nc; --n)
-      sketch_site(t, n, W + Woff_[t.slot][n + 1], W + Woff_[t.slot][n], out.core(n), ell_[n], ell_[n + 1],
-                  GEMM_STATE);
-  }
+  sketch_pass(terms, nt, nc, out);
   for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
   int r = 1;
   for (int n = 0; n <= nc; ++n) {

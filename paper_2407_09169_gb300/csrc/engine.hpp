@@ -114,6 +114,7 @@ class Engine {
   void cond_means(const DevMps& f, double* v);
   void make_hfirst(const DevMps& f, double* v, double* hf);
   void sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr, int role);
+  void sketch_pass(Term* terms, int nt, int n_stop, const DevMps& om);  // right-to-left, sites N-1 .. n_stop+1
   void zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha);
   void run_stage(Term* terms, int nterms, DevMps& out, int stage);
   void step_body();      // one RK2 step from f_ into g_ (launches only)
@@ -152,8 +153,24 @@ class Engine {
   EigProblem* trunc_probs_ = nullptr;
   int trunc_nmax_ = 1, trunc_kmax_ = 0;
   size_t ws_elems_ = 0;
-  void* pack_ws_ = nullptr;
-  size_t pack_bytes_ = 0;
+  // Lanes: lane 0 is st_; lanes 1..kLanes-1 are streams of their own on which
+  // the terms' independent work (sketch chains; site tensors and projections
+  // of the zip-up) runs concurrently, forked from and joined back into st_
+  // with events (also inside a captured graph).  Each lane has its own GEMM
+  // workspaces and scratch.
+  static constexpr int kLanes = 5;
+  int lane_ = 0, nlanes_ = 1;
+  cudaStream_t lane_st_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork_ = nullptr, ev_join_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* lane_ws_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *lane_x1_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *lane_x2_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *lane_p_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* pack_ws_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t pack_bytes_[kLanes] = {0, 0, 0, 0, 0};
+  cudaStream_t cur() const { return lane_st_[lane_]; }
+  void fork_lanes(int n);  // lanes 1..n wait for st_
+  void join_lanes(int n);  // st_ waits for lanes 1..n
   int tc_mode_[3] = {-1, -1, -1};  // per GEMM role; -1: FP64 kernel
   int max_bond_ = 1;
   unsigned long long* dstep_ = nullptr;  // device copy of the step count (sketch draws)

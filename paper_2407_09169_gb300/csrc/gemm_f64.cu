@@ -18,6 +18,8 @@ constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(int M, int N, int K, int inner, int splitk, int kchunk,
                                                       double alpha, MatView A, MatView B, double beta,
                                                       OutView C, double* ws) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -96,6 +98,8 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(int M, int N, int K, int i
 
 __global__ void splitk_reduce_kernel(int M, int N, int inner, int splitk, int batch, double alpha, const double* ws,
                                      double beta, OutView C) {
+  pdl_trigger();
+  pdl_wait();
   const long long MN = (long long)M * N;
   const long long total = MN * batch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -111,6 +115,8 @@ __global__ void splitk_reduce_kernel(int M, int N, int inner, int splitk, int ba
   }
 }
 __global__ void scale_out_kernel(int M, int N, int inner, int batch, double beta, OutView C) {
+  pdl_trigger();
+  pdl_wait();
   const long long MN = (long long)M * N;
   const long long total = MN * batch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -130,7 +136,8 @@ void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int bat
   const long long total = (long long)M * N * batch;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, inner, splitk, batch, alpha, ws, beta, C);
+  launch_pdl(splitk_reduce_kernel, dim3((unsigned)blocks), dim3(256), 0, st, M, N, inner, splitk, batch, alpha,
+             (const double*)ws, beta, C);
 }
 
 int gemm_split_k(int M, int N, int K, int batch) {
@@ -164,13 +171,15 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splitk);
   count_launches(splitk == 1 ? 1 : 2);
   if (splitk == 1) {
-    gemm_f64_kernel<<<grid, NT, 0, st>>>(M, N, K, inner, 1, kchunk, alpha, A, B, beta, C, nullptr);
+    launch_pdl(gemm_f64_kernel, grid, dim3(NT), 0, st, M, N, K, inner, 1, kchunk, alpha, A, B, beta, C,
+               (double*)nullptr);
   } else {
-    gemm_f64_kernel<<<grid, NT, 0, st>>>(M, N, K, inner, splitk, kchunk, alpha, A, B, beta, C, ws);
+    launch_pdl(gemm_f64_kernel, grid, dim3(NT), 0, st, M, N, K, inner, splitk, kchunk, alpha, A, B, beta, C, ws);
     const long long total = (long long)M * N * batch;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, inner, splitk, batch, alpha, ws, beta, C);
+    launch_pdl(splitk_reduce_kernel, dim3((unsigned)blocks), dim3(256), 0, st, M, N, inner, splitk, batch, alpha,
+             (const double*)ws, beta, C);
   }
 }
 

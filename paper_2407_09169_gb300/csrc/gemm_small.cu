@@ -61,6 +61,8 @@ __device__ __forceinline__ double to_d(T x) {
 template <typename T, int MT>
 __global__ void __launch_bounds__(SG_THREADS) small_gemm_kernel(int M, int N, int K, int inner, double alpha,
                                                                 MatView A, MatView B, double beta, OutView C) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ T As[SG_MAXM * SG_MAXK];
   const int b = blockIdx.y;
   const int bo = b / inner, bi = b - bo * inner;
@@ -99,11 +101,11 @@ void launch_small(cudaStream_t st, int M, int N, int K, int outer, int inner, do
                   double beta, OutView C) {
   const dim3 grid((unsigned)((N + SG_THREADS - 1) / SG_THREADS), (unsigned)(outer * inner));
   if (M <= 8)
-    small_gemm_kernel<T, 8><<<grid, SG_THREADS, 0, st>>>(M, N, K, inner, alpha, A, B, beta, C);
+    launch_pdl(small_gemm_kernel<T, 8>, grid, dim3(SG_THREADS), 0, st, M, N, K, inner, alpha, A, B, beta, C);
   else if (M <= 16)
-    small_gemm_kernel<T, 16><<<grid, SG_THREADS, 0, st>>>(M, N, K, inner, alpha, A, B, beta, C);
+    launch_pdl(small_gemm_kernel<T, 16>, grid, dim3(SG_THREADS), 0, st, M, N, K, inner, alpha, A, B, beta, C);
   else
-    small_gemm_kernel<T, 32><<<grid, SG_THREADS, 0, st>>>(M, N, K, inner, alpha, A, B, beta, C);
+    launch_pdl(small_gemm_kernel<T, 32>, grid, dim3(SG_THREADS), 0, st, M, N, K, inner, alpha, A, B, beta, C);
 }
 }  // namespace
 

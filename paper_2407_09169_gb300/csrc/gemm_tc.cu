@@ -41,6 +41,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <stdexcept>
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
                    const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, int M, int N,
                    int kblocks, int kb_per_split, int splitk, int inner, double alpha, double beta, OutView C,
-                   double* ws, const int* __restrict__ ea, const int* __restrict__ eb, int* err) {
+                   double* ws, const int* __restrict__ ea, const int* __restrict__ eb, int a_bs, int b_bs, int* err) {
   using Tr = ModeTraits<MODE>;
   constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
   constexpr int STAGE_BYTES = Tr::na * A_BYTES + Tr::nb * B_BYTES;
@@ -276,6 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   __shared__ int s_abort, s_issued;
 
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
   const int z = blockIdx.z;
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();  // operands and outputs are touched only from here on
 
   if (warp == 0 && lane == 0) {
     // TMA producer; a stage holds the na A tiles, then the nb B tiles
@@ -318,9 +321,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_expect_tx(&full[s], STAGE_BYTES);
       const int kx = kb * (128 / Tr::esize);
 #pragma unroll
-      for (int t = 0; t < Tr::na; ++t) tma_load_3d(st + t * A_BYTES, ma[t], &full[s], kx, m0, b);
+      for (int t = 0; t < Tr::na; ++t) tma_load_3d(st + t * A_BYTES, ma[t], &full[s], kx, m0, b * a_bs);
 #pragma unroll
-      for (int t = 0; t < Tr::nb; ++t) tma_load_3d(st + Tr::na * A_BYTES + t * B_BYTES, mb[t], &full[s], kx, n0, b);
+      for (int t = 0; t < Tr::nb; ++t)
+        tma_load_3d(st + Tr::na * A_BYTES + t * B_BYTES, mb[t], &full[s], kx, n0, b * b_bs);
       s_issued = i + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     double* Cb = C.p + bo * C.so + bi * C.si;
     double* W = ws ? ws + ((long long)b * splitk + ks) * (long long)M * N : nullptr;
     const int m_pad = (int)gridDim.y * BM, n_pad = (int)gridDim.x * BN;
-    const int erow = (Tr::sliced && wrow0 + lane < M) ? ea[(long long)b * m_pad + wrow0 + lane] : 0;
+    const int erow = (Tr::sliced && wrow0 + lane < M) ? ea[(long long)(b * a_bs) * m_pad + wrow0 + lane] : 0;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     // 32 x 32 staging tile per warp in the (drained) pipeline buffers: rows are
     // TMEM lanes on the way in, columns are lanes on the way out (coalesced stores)
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int g = 0; g < Tr::ngroups; ++g) tmem_ld32(lane_base + (uint32_t)(g * BN + c0), r[g]);
       tmem_ld_wait();
-      const int ecol = (Tr::sliced && n0 + c0 + lane < N) ? eb[(long long)b * n_pad + n0 + c0 + lane] : 0;
+      const int ecol = (Tr::sliced && n0 + c0 + lane < N) ? eb[(long long)(b * b_bs) * n_pad + n0 + c0 + lane] : 0;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         unsigned long long bits;
@@ -501,6 +505,7 @@ struct PackJob {
   long long batch, units;  // units: row tiles * batch (cols) or rows * batch (warp layout)
   int cols, ksign;
   const int* kshift;               // K-index balancing shifts (BF16X6), or null
+  long long kshift_bstride;        // k_pad, or 0 when the shifts are common to the batch
   unsigned long long* maxbits;     // per packed row: largest balanced magnitude (BF16X6)
   void *o0, *o1, *o2;
   int* expo;
@@ -522,7 +527,7 @@ __device__ void opmax_job(const PackJob& J, int bx) {
     const int r0 = (int)(u - b * tiles_r) * 32;
     const long long bo = b / J.inner, bi = b - bo * J.inner;
     const double* src = J.p + bo * J.so + bi * J.si;
-    const int* ksh = J.kshift + b * J.k_pad;
+    const int* ksh = J.kshift + b * J.kshift_bstride;
     const int tx = lane, ty = threadIdx.x >> 5;
     unsigned long long mx = 0;
     if (r0 + tx < J.rows) {
@@ -547,7 +552,7 @@ __device__ void opmax_job(const PackJob& J, int bx) {
       if (r >= J.rows) continue;  // warp-uniform
       const long long bo = b / J.inner, bi = b - bo * J.inner;
       const double* row = J.p + bo * J.so + bi * J.si + (long long)r * J.rstr;
-      const int* ksh = J.kshift + b * J.k_pad;
+      const int* ksh = J.kshift + b * J.kshift_bstride;
       unsigned long long mx = 0;
       const int k1 = min(J.K, (seg + 1) * J.kseg);
       for (int k = seg * J.kseg + lane; k < k1; k += 32)
@@ -574,7 +579,7 @@ __device__ void pack_job(const PackJob& J, int bx) {
     const double* src = J.p + bo * J.so + bi * J.si;
     const int tx = lane, ty = threadIdx.x >> 5;  // 32 x 8
     const bool rlive = r0 + tx < J.rows;
-    const int* ksh = J.kshift ? J.kshift + b * J.k_pad : nullptr;
+    const int* ksh = J.kshift ? J.kshift + b * J.kshift_bstride : nullptr;
     if constexpr (MODE == TC_BF16X6) {
       if (ty == 0) {
         const int e = row_exponent(J.maxbits[b * J.rows_pad + r0 + tx]);
@@ -611,7 +616,7 @@ __device__ void pack_job(const PackJob& J, int bx) {
       const int r = (int)(rowid - b * J.rows_pad);
       const long long bo = b / J.inner, bi = b - bo * J.inner;
       const double* row = J.p + bo * J.so + bi * J.si + (long long)r * J.rstr;
-      const int* ksh = J.kshift ? J.kshift + b * J.k_pad : nullptr;
+      const int* ksh = J.kshift ? J.kshift + b * J.kshift_bstride : nullptr;
       const bool live = r < J.rows;
       int e = 0;
       if constexpr (MODE == TC_BF16X6) {
@@ -629,6 +634,8 @@ __device__ void pack_job(const PackJob& J, int bx) {
 
 // Both operands in one launch each: blocks [0, a.blocks) serve a, the rest b.
 __global__ void __launch_bounds__(256) opmax2_kernel(const PackJob a, const PackJob b) {
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < a.blocks)
     opmax_job(a, blockIdx.x);
   else
@@ -636,6 +643,8 @@ __global__ void __launch_bounds__(256) opmax2_kernel(const PackJob a, const Pack
 }
 template <int MODE>
 __global__ void __launch_bounds__(256) pack2_kernel(const PackJob a, const PackJob b) {
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < a.blocks)
     pack_job<MODE>(a, blockIdx.x);
   else
@@ -651,20 +660,25 @@ __global__ void __launch_bounds__(256) pack2_kernel(const PackJob a, const PackJ
 // the bond's singular values.)  B(k, n) at k * rs + n * cs; a warp per k when
 // n is contiguous, 32 k per block otherwise.
 __global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long long cs, long long so, long long si,
-                                int inner, int K, int N, int k_pad, long long batch, int* kshift,
+                                int inner, int K, int N, int k_pad, long long batch, int common, int* kshift,
                                 unsigned long long* zero_me, long long nzero) {
+  // common = 1: one shift per k over the whole batch (batch entries loop inside)
+  const long long nb_out = common ? 1 : batch, nb_in = common ? batch : 1;
+  pdl_trigger();
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nzero; x += (long long)gridDim.x * blockDim.x)
     zero_me[x] = 0ull;  // the row-maximum buffer of the next pass
   if (cs == 1) {
-    const long long warps_total = (long long)k_pad * batch;
+    const long long warps_total = (long long)k_pad * nb_out;
     for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < warps_total;
          w += ((long long)gridDim.x * blockDim.x) >> 5) {
-      const long long b = w / k_pad;
-      const int k = (int)(w - b * k_pad);
-      const long long bo = b / inner, bi = b - bo * inner;
+      const long long b0 = w / k_pad;
+      const int k = (int)(w - b0 * k_pad);
       unsigned long long mx = 0;
-      if (k < K) {
+      for (long long bb = 0; bb < nb_in && k < K; ++bb) {
+        const long long b = b0 + bb;
+        const long long bo = b / inner, bi = b - bo * inner;
         const double* row = p + bo * so + bi * si + (long long)k * rs;
         for (int n = lane; n < N; n += 32) mx = max(mx, abs_bits(row[n]));
       }
@@ -677,13 +691,14 @@ __global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long
     __shared__ unsigned long long red[8][32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int ktiles = (k_pad + 31) / 32;
-    const long long tiles = (long long)ktiles * batch;
+    const long long tiles = (long long)ktiles * nb_out;
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-      const long long b = t / ktiles;
-      const int k = (int)(t - b * ktiles) * 32 + tx;
-      const long long bo = b / inner, bi = b - bo * inner;
+      const long long b0 = t / ktiles;
+      const int k = (int)(t - b0 * ktiles) * 32 + tx;
       unsigned long long mx = 0;
-      if (k < K) {
+      for (long long bb = 0; bb < nb_in && k < K; ++bb) {
+        const long long b = b0 + bb;
+        const long long bo = b / inner, bi = b - bo * inner;
         const double* row = p + bo * so + bi * si + (long long)k * rs;
         for (int n = ty; n < N; n += 8) mx = max(mx, abs_bits(row[(long long)n * cs]));
       }
@@ -691,7 +706,7 @@ __global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long
       __syncthreads();
       if (ty == 0) {
         for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tx]);
-        if (k < k_pad) kshift[b * k_pad + k] = row_exponent(mx);
+        if (k < k_pad) kshift[b0 * k_pad + k] = row_exponent(mx);
       }
       __syncthreads();
     }
@@ -730,7 +745,8 @@ CUtensorMap make_map(const void* base, int esize, int k_pad, int rows_pad, long 
 
 template <int MODE, int BN, int STAGES>
 void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, int kbps, int splitk, int inner,
-               long long batch, double alpha, double beta, OutView C, double* ws, int* err) {
+               long long batch, long long batch_a, long long batch_b, double alpha, double beta, OutView C, double* ws,
+               int* err) {
   using Tr = ModeTraits<MODE>;
   constexpr int SMEM = STAGES * (Tr::na * BM * 128 + Tr::nb * BN * 128) + 1024 + 256;
   static_assert(SMEM <= 232448, "shared memory budget");
@@ -742,13 +758,13 @@ void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, i
   }
   CUtensorMap a[3], bm[3];
   for (int i = 0; i < 3; ++i) {
-    a[i] = make_map(pk.a[i < Tr::na ? i : 0], Tr::esize, pk.k_pad, pk.m_pad, batch, BM);
-    bm[i] = make_map(pk.b[i < Tr::nb ? i : 0], Tr::esize, pk.k_pad, pk.n_pad, batch, BN);
+    a[i] = make_map(pk.a[i < Tr::na ? i : 0], Tr::esize, pk.k_pad, pk.m_pad, batch_a, BM);
+    bm[i] = make_map(pk.b[i < Tr::nb ? i : 0], Tr::esize, pk.k_pad, pk.n_pad, batch_b, BN);
   }
   dim3 grid(pk.n_pad / BN, pk.m_pad / BM, (unsigned)(batch * splitk));
-  tc_gemm_kernel<MODE, BN, STAGES><<<grid, TC_THREADS, SMEM, st>>>(a[0], a[1], a[2], bm[0], bm[1], bm[2], M, N,
-                                                                    kblocks, kbps, splitk, inner, alpha, beta, C, ws,
-                                                                    pk.ea, pk.eb, err);
+  launch_pdl(tc_gemm_kernel<MODE, BN, STAGES>, grid, dim3(TC_THREADS), SMEM, st, a[0], a[1], a[2], bm[0], bm[1],
+             bm[2], M, N, kblocks, kbps, splitk, inner, alpha, beta, C, ws, (const int*)pk.ea, (const int*)pk.eb,
+             batch_a == batch ? 1 : 0, batch_b == batch ? 1 : 0, err);
 }
 
 // Packs one operand (rows x K, element (r, k) at r * rstr + k * kstr) into the
@@ -756,9 +772,10 @@ void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, i
 // Fills the geometry of one packing job: k segments so that about two waves
 // of 152 SMs' worth of blocks exist.
 PackJob make_job(const MatView& v, long long rstr, long long kstr, int inner, int rows, int K, int rows_pad,
-                 int k_pad, long long batch, void* const* o, int* expo, const int* kshift, int ksign,
-                 unsigned long long* maxbits) {
+                 int k_pad, long long batch, void* const* o, int* expo, const int* kshift, long long kshift_bstride,
+                 int ksign, unsigned long long* maxbits) {
   PackJob J;
+  J.kshift_bstride = kshift_bstride;
   J.p = v.p;
   J.rstr = rstr;
   J.kstr = kstr;
@@ -862,6 +879,10 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   const ModeInfo mi = mode_info(mode);
   const PackLayout L = pack_layout(M, N, K, batch, mode);
   if (L.total > pack_bytes) return false;
+  // an operand identical for every batch entry (zero batch strides) is packed once
+  const long long batch_a = (A.so == 0 && A.si == 0) ? 1 : batch;
+  const long long batch_b = (B.so == 0 && B.si == 0) ? 1 : batch;
+  const bool common_shift = batch_a != batch || batch_b != batch;
   TcPacked pk;
   pk.k_pad = L.k_pad;
   pk.m_pad = L.m_pad;
@@ -885,27 +906,33 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     maxb = maxa + (size_t)L.m_pad * batch;
   }
   // A(m, k) = A.p[m * rs + k * cs]; B is packed as B^T: (n, k) = B.p[k * rs + n * cs]
-  const PackJob ja = make_job(A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch, pk.a, pk.ea, kshift, 1, maxa);
-  const PackJob jb = make_job(B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch, pk.b, pk.eb, kshift, -1, maxb);
+  const long long ksb = common_shift ? 0 : L.k_pad;
+  const PackJob ja = make_job(A, A.rs, A.cs, inner, M, K, L.m_pad, L.k_pad, batch_a, pk.a, pk.ea, kshift, ksb, 1, maxa);
+  const PackJob jb = make_job(B, B.cs, B.rs, inner, N, K, L.n_pad, L.k_pad, batch_b, pk.b, pk.eb, kshift, ksb, -1, maxb);
   const unsigned pack_blocks = (unsigned)(ja.blocks + jb.blocks);
   if (mi.sliced) {
-    const long long items = B.cs == 1 ? 32LL * L.k_pad * batch : 256LL * ((L.k_pad + 31) / 32) * batch;
+    const long long kb_batch = common_shift ? 1 : batch;
+    const long long items = B.cs == 1 ? 32LL * L.k_pad * kb_batch : 256LL * ((L.k_pad + 31) / 32) * kb_batch;
     long long blocks = (items + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    kbalance_kernel<<<(int)blocks, 256, 0, st>>>(B.p, B.rs, B.cs, B.so, B.si, inner, K, N, L.k_pad, batch, kshift,
-                                                 maxa, (long long)(L.m_pad + L.n_pad) * batch);
-    opmax2_kernel<<<pack_blocks, 256, 0, st>>>(ja, jb);
+    launch_pdl(kbalance_kernel, dim3((unsigned)blocks), dim3(256), 0, st, B.p, B.rs, B.cs, B.so, B.si, inner, K, N,
+               L.k_pad, batch_b, (common_shift && batch_b == batch) ? 1 : 0, kshift, maxa,
+               (long long)(L.m_pad + L.n_pad) * batch);
+    launch_pdl(opmax2_kernel, dim3(pack_blocks), dim3(256), 0, st, ja, jb);
   }
   switch (mode) {
-    case TC_BF16: pack2_kernel<TC_BF16><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
-    case TC_BF16X3: pack2_kernel<TC_BF16X3><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
-    case TC_TF32: pack2_kernel<TC_TF32><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
-    case TC_TF32X3: pack2_kernel<TC_TF32X3><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
-    default: pack2_kernel<TC_BF16X6><<<pack_blocks, 256, 0, st>>>(ja, jb); break;
+    case TC_BF16: launch_pdl(pack2_kernel<TC_BF16>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
+    case TC_BF16X3: launch_pdl(pack2_kernel<TC_BF16X3>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
+    case TC_TF32: launch_pdl(pack2_kernel<TC_TF32>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
+    case TC_TF32X3: launch_pdl(pack2_kernel<TC_TF32X3>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
+    default: launch_pdl(pack2_kernel<TC_BF16X6>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
   }
   const int kblocks = L.k_pad / L.kb;
   // split K when the tile grid is small; the exact-slice modes also cap the
-  // depth one accumulator sums so that its partial sums stay exact integers
+  // depth one accumulator sums so that its partial sums stay exact integers.
+  // (Capping the floating modes' accumulation depth as well -- two k-blocks
+  // per accumulator -- made the BF16X3 drift of <1> worse, -2.1e-6 -> -6.6e-5
+  // after ten 2^4-point steps, so they keep the tile-grid split only.)
   int cap = max_kb_per_split;
   if (mi.exact_kb > 0 && (cap <= 0 || cap > mi.exact_kb)) cap = mi.exact_kb;
   const long long tiles = (long long)(L.m_pad / BM) * (L.n_pad / L.bn) * batch;
@@ -928,7 +955,8 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   double* wsp = splitk > 1 ? ws : nullptr;
   count_launches(1 + (mi.sliced ? 2 : 0) + (splitk > 1 ? 2 : 1));
 #define QTT_TC_LAUNCH(MODE_, BN_, ST_) \
-  launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kbps, splitk, inner, batch, alpha, beta, C, wsp, err)
+  launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kbps, splitk, inner, batch, batch_a, batch_b, alpha, beta, C, wsp, \
+                             err)
 #define QTT_TC_BN(MODE_, S256, S160, S128, S64)       \
   switch (L.bn) {                                     \
     case 256: QTT_TC_LAUNCH(MODE_, 256, S256); break; \

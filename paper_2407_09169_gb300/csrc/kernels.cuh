@@ -12,6 +12,37 @@ constexpr int kMaxSites = 64;
 unsigned long long launch_count();
 void count_launches(int n);
 
+// Programmatic dependent launch (optional).  The step is a long chain of
+// small kernels on one stream; with programmatic stream serialisation the
+// next kernel can be scheduled, and run its prologue (barrier init, TMEM
+// allocation), while the previous one finishes.  Every kernel launched
+// through launch_pdl calls pdl_trigger() first and pdl_wait() before its first
+// global-memory access (read or write), which returns once the preceding
+// kernel has completed and its memory is visible.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Whether launch_pdl sets the attribute (environment QTT_PDL=1 turns it on;
+// read once).
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Operand view for the strided batched GEMM: element (i, j) of batch
 // (bo, bi) lives at p[bo * so + bi * si + i * rs + j * cs].
 struct MatView {

@@ -243,6 +243,8 @@ __device__ __forceinline__ bool qrr_wait(volatile int* ready, int j, int lane, i
 template <int RPL, int CPW>
 __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const double* __restrict__ A,
                                                              double* __restrict__ Qout, int* status) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char qr_smem[];
   constexpr int LDV = 32 * RPL;
   float* V = (float*)qr_smem;        // [n][LDV] reflectors; first the input, last the output staging
@@ -386,7 +388,7 @@ bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, in
                          (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + 2 * QRR_WARPS * CPW) * sizeof(float)));
     attr = true;
   }
-  qr_reg_kernel<RPL, CPW><<<1, QRR_THREADS, smem, st>>>(m, n, A, Qout, status);
+  launch_pdl(qr_reg_kernel<RPL, CPW>, dim3(1), dim3(QRR_THREADS), smem, st, m, n, A, Qout, status);
   return true;
 }
 

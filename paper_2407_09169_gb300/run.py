@@ -1,0 +1,51 @@
+"""Command-line stepping of one workload through the C ABI.
+
+    python -m paper_2407_09169_gb300.run --workload large --precision fp32 --steps 1
+
+Builds the library if needed, creates a context for the named workload
+(workload.WORKLOADS, or --paper for the paper's flow case), advances it and
+prints the scalar observables as one JSON line.  Used as the profiled command
+of the ncu summaries (with QTT_GRAPHS=0 every step runs eagerly, so every
+kernel launch appears individually).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+from . import _binding as q  # noqa: E402
+from . import build as qbuild  # noqa: E402
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="large", choices=list(workload.WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=list(workload.PRECISIONS))
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--paper", action="store_true", help="the paper's flow case at the workload's grid and chi")
+    args = ap.parse_args(argv)
+    qbuild.build()
+    w = workload.WORKLOADS[args.workload]
+    if args.paper:
+        p = workload.make_paper_params(bits=w["bits"], chi=w["chi_max"], seed=args.seed, precision=args.precision)
+    else:
+        p = workload.make_params(args.workload, seed=args.seed, precision=args.precision)
+    t0 = time.perf_counter()
+    with q.qtt_init(p) as ctx:
+        ctx.step(args.steps)
+        s = ctx.scalars()
+    s["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(s))
+
+
+if __name__ == "__main__":
+    main()
