@@ -403,6 +403,12 @@ void Engine::init() {
   const size_t rmax = (size_t)max_bond_;
   qrwork_ = (double*)dalloc((2 * (2 * rmax) * rmax + rmax) * sizeof(double));
   gq_ = (double*)dalloc(rmax * rmax * sizeof(double));
+  {  // the six weight chains as a device array for the batched environment kernel
+    std::vector<Chain> wc(6);
+    for (int w = 0; w < 6; ++w) wc[w] = wphi_[w].chain();
+    wchains_dev_ = (Chain*)dalloc(6 * sizeof(Chain));
+    QTT_CUDA(cudaMemcpy(wchains_dev_, wc.data(), 6 * sizeof(Chain), cudaMemcpyHostToDevice));
+  }
   ws_elems_ = (size_t)8 << 20;
   ws_ = (double*)dalloc(ws_elems_ * sizeof(double));
   // lanes for the terms' concurrent work (at most 2 terms in the first stage
@@ -412,6 +418,7 @@ void Engine::init() {
   lane_x1_[0] = X1_;
   lane_x2_[0] = X2_;
   lane_p_[0] = P_;
+  lane_y_[0] = (double*)dalloc(yy * sizeof(double));
   nlanes_ = 1 + (p_.rk_variant == 0 ? 3 : 4);
   if (const char* e = std::getenv("QTT_LANES"))
     if (e[0] == '0') nlanes_ = 1;
@@ -423,6 +430,7 @@ void Engine::init() {
     lane_x1_[l] = (double*)dalloc(x1 * sizeof(double));
     lane_x2_[l] = (double*)dalloc(x2 * sizeof(double));
     lane_p_[l] = (double*)dalloc(pp * sizeof(double));
+    lane_y_[l] = (double*)dalloc(yy * sizeof(double));
   }
   for (int i = 0; i < 2; ++i) {
     v_[i] = (double*)dalloc((size_t)2 * D_[kphi_] * sizeof(double));
@@ -475,9 +483,8 @@ void Engine::init() {
 void Engine::cond_means(const DevMps& f, double* v) {
   // v[a][b] = h1 h2 sum over phi indices of phi_a f(..)[b] at the phi/x cut (Eq. 2)
   TimeScope ts(timer_, TM_OTHER, st_);
-  const Chain fc = f.chain();
-  for (int a = 0; a < 2; ++a)
-    left_weight_env(st_, fc, wphi_[1 + a].chain(), kphi_, max_bond_, v + (size_t)a * D_[kphi_], D_[kphi_], envw_);
+  // both alpha in one launch (weight chains 1 and 2)
+  left_weight_envs(st_, f.chain(), wchains_dev_ + 1, 2, kphi_, max_bond_, v, D_[kphi_], D_[kphi_]);
 }
 
 void Engine::make_hfirst(const DevMps& f, double* v, double* hf) {
@@ -614,7 +621,12 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
   // own between the Y = sum_i T_i W_i / QR steps on st_.
   const bool par = nt > 1 && nt < nlanes_;
   for (int i = 0; i < nt; ++i) fill_value(st_, C_[terms[i].slot], 1, 1.0);
+  // zip_all(n): each term's site tensor T_i at site n (after C_i = Q^T T_i of
+  // site n-1 when `project`), and, when site n truncates, its range product
+  // Y_i = T_i W_i; the Y_i are summed on st_ after the join.
   auto zip_all = [&](int n, int r, bool project, int rn) {
+    const int rs = project ? rn : r;  // bond entering site n
+    const bool range = n + 1 < N && rz_[n + 1] != 2 * rs;
     if (par) fork_lanes(nt);
     for (int i = 0; i < nt; ++i) {
       lane_ = par ? 1 + i : 0;
@@ -622,10 +634,21 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
       if (project)  // C_i = Q^T T_i at the previous site
         gemm(rn, (int)t.B(n), 2 * r, 1, 1, 1.0, mv(mid_.core(n - 1), 1, rn), mv(T_[t.slot], t.B(n), 1), 0.0,
              ov(C_[t.slot], t.B(n), 1));
-      zip_site(t, n, project ? rn : r, C_[t.slot], T_[t.slot], n == 0 ? t.scale : 1.0);
+      zip_site(t, n, rs, C_[t.slot], T_[t.slot], n == 0 ? t.scale : 1.0);
+      if (range) {
+        const int L = ell_[n + 1];
+        gemm(2 * rs, L, (int)t.B(n + 1), 1, 1, 1.0, mv(T_[t.slot], t.B(n + 1), 1),
+             mv(Wslot_[t.slot] + Woff_[t.slot][n + 1], L, 1), par || i == 0 ? 0.0 : 1.0,
+             ov(par ? lane_y_[1 + i] : Y_, L, 1), GEMM_RANGE);
+      }
     }
     lane_ = 0;
     if (par) join_lanes(nt);
+    if (range && par) {
+      const double* ys[4] = {lane_y_[1], lane_y_[2], lane_y_[3], lane_y_[4]};
+      TimeScope ts(timer_, TM_OTHER, st_);
+      sum_arrays(st_, Y_, ys, nt, (size_t)2 * rs * ell_[n + 1]);
+    }
   };
   int r = 1;
   zip_all(0, 1, false, 0);
@@ -647,12 +670,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
       for (int i = 0; i < nt; ++i) std::swap(C_[terms[i].slot], T_[terms[i].slot]);
       zip_all(n + 1, rn, false, 0);
     } else {
-      const int L = ell_[n + 1];
-      for (int i = 0; i < nt; ++i) {
-        const Term& t = terms[i];
-        gemm(2 * r, L, (int)t.B(n + 1), 1, 1, 1.0, mv(T_[t.slot], t.B(n + 1), 1),
-             mv(Wslot_[t.slot] + Woff_[t.slot][n + 1], L, 1), i == 0 ? 0.0 : 1.0, ov(Y_, L, 1), GEMM_RANGE);
-      }
+      // Y = sum_i T_i W_i is in Y_ (zip_all)
       {
         TimeScope ts(timer_, TM_QR, st_);
         qr_thin(st_, 2 * r, rn, Y_, qr_refine_ ? X1_ : mid_.core(n), qrwork_, prec_bits_, status_);
@@ -893,7 +911,7 @@ void Engine::scalars(double out[12]) {
   double* E = u + b;                // b x b
   double* res = E + (size_t)b * b;  // 6 + b + 1
   const Chain fc = f_.chain();
-  for (int w = 0; w < 6; ++w) left_weight_env(st_, fc, wphi_[w].chain(), kphi_, max_bond_, V + (size_t)w * b, b, envw_);
+  left_weight_envs(st_, fc, wchains_dev_, 6, kphi_, max_bond_, V, b, b);
   right_ones_env(st_, fc, kphi_, max_bond_, u, envw_);
   xgram(f_, E);
   gemm64(6, 1, b, 1, 1, 1.0, mv(V, b, 1), mv(u, 1, 1), 0.0, ov(res, 1, 1));                 // <w> sums

@@ -138,6 +138,7 @@ class Engine {
   std::vector<void*> allocs_;
   std::vector<int> D_, ell_, rz_;
   DevMps f_, fs_, g_, mid_, omega_, wphi_[6];
+  Chain* wchains_dev_ = nullptr;  // wphi_ chains on the device
   DevOp op_lin_, had_, ident_;
   // scratch
   double *Wslot_[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -166,6 +167,7 @@ class Engine {
   double *lane_x1_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *lane_x2_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *lane_p_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *lane_y_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   void* pack_ws_[kLanes] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t pack_bytes_[kLanes] = {0, 0, 0, 0, 0};
   cudaStream_t cur() const { return lane_st_[lane_]; }

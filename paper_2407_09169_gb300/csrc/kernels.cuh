@@ -129,6 +129,8 @@ void fill_gaussian(cudaStream_t st, double* p, size_t n, double sigma, unsigned 
 // restart from a checkpoint (which restores the count) draws the same ones.
 void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, unsigned long long seed,
                           const unsigned long long* step, int stage);
+// out[x] = in[0][x] + ... + in[n_in - 1][x], n_in <= 4.
+void sum_arrays(cudaStream_t st, double* out, const double* const* in, int n_in, size_t n);
 // p = the n x n identity (row-major).
 void fill_eye(cudaStream_t st, double* p, int n);
 // *c += 1 on the device.
@@ -140,6 +142,11 @@ void bump_counter(cudaStream_t st, unsigned long long* c);
 // work holds 16 * max_bond doubles.
 void left_weight_env(cudaStream_t st, const Chain& f, const Chain& w, int nsites, int max_bond, double* out,
                      int ldo, double* work);
+// The same for nw weight chains (device array wchains_dev[0..nw)) in one
+// launch, one block per chain, chain i writing out + i * out_stride;
+// environments in shared memory (16 * max_bond doubles, max_bond <= 1600).
+void left_weight_envs(cudaStream_t st, const Chain& f, const Chain* wchains_dev, int nw, int nsites, int max_bond,
+                      double* out, long long out_stride, int ldo);
 // u[b] = sum over the indices of sites [n0, N) of f(..)[b]: right environment
 // with the all-ones vector.  One block; work holds 2 * max_bond doubles.
 void right_ones_env(cudaStream_t st, const Chain& f, int n0, int max_bond, double* out, double* work);

@@ -92,6 +92,19 @@ __global__ void gaussian_sketch_kernel(Chain om, unsigned long long seed, const 
 
 __global__ void bump_kernel(unsigned long long* c) { *c += 1ull; }
 
+// out = sum of up to four arrays (the terms' range products of one site).
+struct SumArgs {
+  const double* in[4];
+  int n_in;
+};
+__global__ void sum_kernel(double* out, SumArgs a, size_t n) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+    double v = a.in[0][x];
+    for (int i = 1; i < a.n_in; ++i) v += a.in[i][x];
+    out[x] = v;
+  }
+}
+
 __global__ void eye_kernel(double* p, int n) {
   pdl_trigger();
   pdl_wait();
@@ -136,6 +149,51 @@ __global__ void left_weight_env_kernel(Chain f, Chain w, int nsites, int max_bon
   for (int x = threadIdx.x; x < qn * bn; x += blockDim.x) {
     const int q = x / bn, b = x - q * bn;
     out[(size_t)q * ldo + b] = E[q * max_bond + b];
+  }
+}
+
+// Several weight chains at once, one block per chain (block b takes chain
+// wchains[b] and writes out + b * out_stride); the environments live in
+// shared memory (16 * max_bond doubles).
+__global__ void left_weight_envs_kernel(Chain f, const Chain* __restrict__ wchains, int nsites, int max_bond,
+                                        double* out, long long out_stride, int ldo) {
+  extern __shared__ double env_smem[];
+  double* E = env_smem;          // [4][max_bond]
+  double* X = E + 4 * max_bond;  // [4][2][max_bond]
+  double* E2 = X + 8 * max_bond; // [4][max_bond]
+  const Chain& w = wchains[blockIdx.x];
+  if (threadIdx.x == 0) E[0] = 1.0;
+  __syncthreads();
+  for (int n = 0; n < nsites; ++n) {
+    const int bl = f.bond[n], br = f.bond[n + 1], ql = w.bond[n], qr = w.bond[n + 1];
+    const double* A = f.core[n];
+    const double* W = w.core[n];
+    for (int x = threadIdx.x; x < ql * 2 * br; x += blockDim.x) {
+      const int q = x / (2 * br), sb = x - q * 2 * br;
+      double acc = 0.0;
+      for (int b = 0; b < bl; ++b) acc += E[q * max_bond + b] * A[(size_t)b * 2 * br + sb];
+      X[q * 2 * max_bond + sb] = acc;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < qr * br; x += blockDim.x) {
+      const int q2 = x / br, b2 = x - q2 * br;
+      double acc = 0.0;
+      for (int q = 0; q < ql; ++q)
+        for (int s = 0; s < 2; ++s) acc += W[(q * 2 + s) * qr + q2] * X[q * 2 * max_bond + s * br + b2];
+      E2[q2 * max_bond + b2] = acc;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < qr * br; x += blockDim.x) {
+      const int q2 = x / br, b2 = x - q2 * br;
+      E[q2 * max_bond + b2] = E2[q2 * max_bond + b2];
+    }
+    __syncthreads();
+  }
+  const int qn = w.bond[nsites], bn = f.bond[nsites];
+  double* o = out + (long long)blockIdx.x * out_stride;
+  for (int x = threadIdx.x; x < qn * bn; x += blockDim.x) {
+    const int q = x / bn, b = x - q * bn;
+    o[(size_t)q * ldo + b] = E[q * max_bond + b];
   }
 }
 
@@ -258,6 +316,14 @@ void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, uns
   if (bx > 64) bx = 64;
   gaussian_sketch_kernel<<<dim3((unsigned)bx, (unsigned)om.n), 256, 0, st>>>(om, seed, step, stage);
 }
+void sum_arrays(cudaStream_t st, double* out, const double* const* in, int n_in, size_t n) {
+  if (n == 0 || n_in <= 0) return;
+  SumArgs a{};
+  for (int i = 0; i < n_in && i < 4; ++i) a.in[i] = in[i];
+  a.n_in = n_in < 4 ? n_in : 4;
+  count_launches(1);
+  sum_kernel<<<grid_for(n), 256, 0, st>>>(out, a, n);
+}
 void fill_eye(cudaStream_t st, double* p, int n) {
   if (n <= 0) return;
   count_launches(1);
@@ -271,6 +337,18 @@ void left_weight_env(cudaStream_t st, const Chain& f, const Chain& w, int nsites
                      int ldo, double* work) {
   count_launches(1);
   left_weight_env_kernel<<<1, 256, 0, st>>>(f, w, nsites, max_bond, out, ldo, work);
+}
+void left_weight_envs(cudaStream_t st, const Chain& f, const Chain* wchains_dev, int nw, int nsites, int max_bond,
+                      double* out, long long out_stride, int ldo) {
+  if (nw <= 0) return;
+  const size_t smem = (size_t)16 * max_bond * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(left_weight_envs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  count_launches(1);
+  left_weight_envs_kernel<<<nw, 256, smem, st>>>(f, wchains_dev, nsites, max_bond, out, out_stride, ldo);
 }
 void right_ones_env(cudaStream_t st, const Chain& f, int n0, int max_bond, double* out, double* work) {
   count_launches(1);

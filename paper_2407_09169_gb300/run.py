@@ -3,10 +3,10 @@
     python -m paper_2407_09169_gb300.run --workload large --precision fp32 --steps 1
 
 Builds the library if needed, creates a context for the named workload
-(workload.WORKLOADS, or --paper for the paper's flow case), advances it and
-prints the scalar observables as one JSON line.  Used as the profiled command
-of the ncu summaries (with QTT_GRAPHS=0 every step runs eagerly, so every
-kernel launch appears individually).
+(workload.WORKLOADS, or --paper for the paper's flow case at that grid and
+chi), advances it and prints the scalar observables as one JSON line.  Used
+as the profiled command of the ncu summaries (with QTT_GRAPHS=0 every step
+runs eagerly, so every kernel launch appears individually).
 """
 from __future__ import annotations
 
