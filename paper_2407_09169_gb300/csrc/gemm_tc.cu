@@ -495,6 +495,11 @@ __device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
   return E == 0 ? 0 : E - 1022;
 }
 
+// Loads each thread of the packing and maximum passes issues before it uses
+// the first: the passes stream operands once, so they are bound by how many
+// bytes are in flight, not by arithmetic.
+constexpr int PACK_UNROLL = 8;
+
 // One operand to pack: packed row r, element k is p[b-offset + r * rstr +
 // k * kstr].  "cols" layouts (r stride 1) go through a shared tile, 32 rows x
 // one k segment per block; the others take one warp per (row, k segment).
@@ -532,8 +537,16 @@ __device__ void opmax_job(const PackJob& J, int bx) {
     unsigned long long mx = 0;
     if (r0 + tx < J.rows) {
       const int k1 = min(J.K, (seg + 1) * J.kseg);
-      for (int k = seg * J.kseg + ty; k < k1; k += 8)
-        mx = max(mx, scale_bits(abs_bits(src[(r0 + tx) + (long long)k * J.kstr]), J.ksign * ksh[k]));
+      for (int k0 = seg * J.kseg + ty; k0 < k1; k0 += 8 * PACK_UNROLL) {
+        unsigned long long x[PACK_UNROLL];  // all loads in flight before the first use
+#pragma unroll
+        for (int u = 0; u < PACK_UNROLL; ++u) {
+          const int k = k0 + 8 * u;
+          x[u] = k < k1 ? scale_bits(abs_bits(src[(r0 + tx) + (long long)k * J.kstr]), J.ksign * ksh[k]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < PACK_UNROLL; ++u) mx = max(mx, x[u]);
+      }
     }
     red[ty][tx] = mx;
     __syncthreads();
@@ -555,8 +568,16 @@ __device__ void opmax_job(const PackJob& J, int bx) {
       const int* ksh = J.kshift + b * J.kshift_bstride;
       unsigned long long mx = 0;
       const int k1 = min(J.K, (seg + 1) * J.kseg);
-      for (int k = seg * J.kseg + lane; k < k1; k += 32)
-        mx = max(mx, scale_bits(abs_bits(row[(long long)k * J.kstr]), J.ksign * ksh[k]));
+      for (int k0 = seg * J.kseg + lane; k0 < k1; k0 += 32 * PACK_UNROLL) {
+        unsigned long long x[PACK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < PACK_UNROLL; ++u) {
+          const int k = k0 + 32 * u;
+          x[u] = k < k1 ? scale_bits(abs_bits(row[(long long)k * J.kstr]), J.ksign * ksh[k]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < PACK_UNROLL; ++u) mx = max(mx, x[u]);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane == 0 && mx != 0ull) atomicMax(J.maxbits + rowid, mx);
@@ -568,7 +589,7 @@ template <int MODE>
 __device__ void pack_job(const PackJob& J, int bx) {
   const int lane = threadIdx.x & 31;
   if (J.cols) {
-    __shared__ double tile[32][33];  // [k][r]
+    __shared__ double tile[64][33];  // [k][r]
     __shared__ int s_e[32];
     const long long u = bx % J.units;
     const int seg = (int)(bx / J.units);
@@ -589,20 +610,24 @@ __device__ void pack_job(const PackJob& J, int bx) {
       __syncthreads();
     }
     const int kend = min(J.k_pad, (seg + 1) * J.kseg);
-    for (int k0 = seg * J.kseg; k0 < kend; k0 += 32) {
+    for (int k0 = seg * J.kseg; k0 < kend; k0 += 64) {  // kseg is a multiple of 32: the second half may be past kend
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const int kl = ty + 8 * q, k = k0 + kl;
-        tile[kl][tx] = (rlive && k < J.K) ? src[(r0 + tx) + (long long)k * J.kstr] : 0.0;
+        tile[kl][tx] = (rlive && k < J.K && k < kend) ? src[(r0 + tx) + (long long)k * J.kstr] : 0.0;
       }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int rl = ty + 8 * q;
         const int e = (MODE == TC_BF16X6) ? s_e[rl] : 0;
-        const int k = k0 + tx;
-        pack_one<MODE>(tile[tx][rl], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0,
-                       ((size_t)b * J.rows_pad + r0 + rl) * J.k_pad + k, J.o0, J.o1, J.o2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = k0 + 32 * h + tx;
+          if (k < kend)
+            pack_one<MODE>(tile[32 * h + tx][rl], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0,
+                           ((size_t)b * J.rows_pad + r0 + rl) * J.k_pad + k, J.o0, J.o1, J.o2);
+        }
       }
       __syncthreads();
     }
@@ -625,9 +650,19 @@ __device__ void pack_job(const PackJob& J, int bx) {
       }
       const size_t base = (size_t)rowid * J.k_pad;
       const int k1 = min(J.k_pad, (seg + 1) * J.kseg);
-      for (int k = seg * J.kseg + lane; k < k1; k += 32)
-        pack_one<MODE>((live && k < J.K) ? row[(long long)k * J.kstr] : 0.0, e,
-                       (ksh && k < J.K) ? J.ksign * ksh[k] : 0, base + k, J.o0, J.o1, J.o2);
+      for (int k0 = seg * J.kseg + lane; k0 < k1; k0 += 32 * PACK_UNROLL) {
+        double x[PACK_UNROLL];  // all loads in flight before the first use
+#pragma unroll
+        for (int u = 0; u < PACK_UNROLL; ++u) {
+          const int k = k0 + 32 * u;
+          x[u] = (live && k < J.K && k < k1) ? row[(long long)k * J.kstr] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < PACK_UNROLL; ++u) {
+          const int k = k0 + 32 * u;
+          if (k < k1) pack_one<MODE>(x[u], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0, base + k, J.o0, J.o1, J.o2);
+        }
+      }
     }
   }
 }
@@ -680,7 +715,13 @@ __global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long
         const long long b = b0 + bb;
         const long long bo = b / inner, bi = b - bo * inner;
         const double* row = p + bo * so + bi * si + (long long)k * rs;
-        for (int n = lane; n < N; n += 32) mx = max(mx, abs_bits(row[n]));
+        for (int n0 = lane; n0 < N; n0 += 32 * PACK_UNROLL) {
+          unsigned long long x[PACK_UNROLL];
+#pragma unroll
+          for (int u = 0; u < PACK_UNROLL; ++u) x[u] = n0 + 32 * u < N ? abs_bits(row[n0 + 32 * u]) : 0ull;
+#pragma unroll
+          for (int u = 0; u < PACK_UNROLL; ++u) mx = max(mx, x[u]);
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -700,7 +741,14 @@ __global__ void kbalance_kernel(const double* __restrict__ p, long long rs, long
         const long long b = b0 + bb;
         const long long bo = b / inner, bi = b - bo * inner;
         const double* row = p + bo * so + bi * si + (long long)k * rs;
-        for (int n = ty; n < N; n += 8) mx = max(mx, abs_bits(row[(long long)n * cs]));
+        for (int n0 = ty; n0 < N; n0 += 8 * PACK_UNROLL) {
+          unsigned long long x[PACK_UNROLL];
+#pragma unroll
+          for (int u = 0; u < PACK_UNROLL; ++u)
+            x[u] = n0 + 8 * u < N ? abs_bits(row[(long long)(n0 + 8 * u) * cs]) : 0ull;
+#pragma unroll
+          for (int u = 0; u < PACK_UNROLL; ++u) mx = max(mx, x[u]);
+        }
       }
       red[ty][tx] = mx;
       __syncthreads();
@@ -797,7 +845,7 @@ PackJob make_job(const MatView& v, long long rstr, long long kstr, int inner, in
   J.cols = (rstr == 1 && kstr != 1 && rows_pad % 32 == 0) ? 1 : 0;
   const int chunks = (k_pad + 31) / 32;
   J.units = J.cols ? (long long)(rows_pad / 32) * batch : (long long)rows_pad * batch;
-  const long long want = J.cols ? 2 * 152 : 2 * 152 * 8;  // blocks (tile layout) / warps (row layout)
+  const long long want = J.cols ? 2 * 152 : 2 * 152 * 16;  // blocks (tile layout) / warps (row layout)
   int nseg = (int)std::min<long long>(chunks, std::max<long long>(1, (want + J.units - 1) / J.units));
   J.kseg = 32 * ((chunks + nseg - 1) / nseg);
   J.nseg = (k_pad + J.kseg - 1) / J.kseg;

@@ -170,15 +170,82 @@ __global__ void __launch_bounds__(qr_threads<T>()) qr_thin_kernel(int m, int n, 
 // and raises its flag before it updates its other columns, which keeps the
 // chain of reflectors short (a look-ahead of one column).  Q is accumulated
 // backwards in the same register layout, with no synchronisation at all.
+// Both loops pair columns through the packed FP32x2 FMA (FFMA2).
+
+// d0 += a0 * b0, d1 += a1 * b1 in one packed FP32x2 instruction.
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rd, {%0, %1};\n"
+      " fma.rn.f32x2 rd, ra, rb, rd;\n mov.b64 {%0, %1}, rd;\n}"
+      : "+f"(d0), "+f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// Sums each of CPW values over the warp's 32 lanes; every lane gets every
+// sum.  For CPW = 9 the first eight go through a butterfly in which pairs of
+// values trade halves at each level (lane bit 4 keeps the odd one, bit 3 ...),
+// so that after five levels the lane with bits (b4, b3, b2) holds the sum of
+// value 4 b2 + 2 b3 + b4, which eight shuffles then broadcast: 22 shuffles
+// instead of 45.  Shuffle throughput, not the FMAs, bounds this kernel.
+template <int CPW>
+__device__ __forceinline__ void qrr_warp_sums(float (&d)[CPW], int lane) {
+  constexpr unsigned F = 0xffffffffu;
+  if constexpr (CPW == 9) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = (b4 ? d[2 * i + 1] : d[2 * i]) + __shfl_xor_sync(F, b4 ? d[2 * i] : d[2 * i + 1], 16);
+    float s8 = d[8] + __shfl_xor_sync(F, d[8], 16);
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) c[i] = (b3 ? a[2 * i + 1] : a[2 * i]) + __shfl_xor_sync(F, b3 ? a[2 * i] : a[2 * i + 1], 8);
+    s8 += __shfl_xor_sync(F, s8, 8);
+    float e = (b2 ? c[1] : c[0]) + __shfl_xor_sync(F, b2 ? c[0] : c[1], 4);
+    s8 += __shfl_xor_sync(F, s8, 4);
+    e += __shfl_xor_sync(F, e, 2);
+    s8 += __shfl_xor_sync(F, s8, 2);
+    e += __shfl_xor_sync(F, e, 1);
+    s8 += __shfl_xor_sync(F, s8, 1);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = __shfl_sync(F, e, ((q & 1) << 4) | (((q >> 1) & 1) << 3) | (((q >> 2) & 1) << 2));
+    d[8] = s8;
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) d[q] += __shfl_xor_sync(F, d[q], o);
+  }
+}
+
 constexpr int QRR_WARPS = 16;
 constexpr int QRR_THREADS = QRR_WARPS * 32;
-constexpr int QRR_SPIN_LIMIT = 1 << 22;  // polls of a reflector flag (with a short sleep) before giving up
+constexpr long long QRR_WAIT_LIMIT = 1LL << 24;  // try_wait polls of a reflector barrier before giving up
+
+// One mbarrier per reflector (arrival count 32: every lane of the owning warp
+// arrives after its own stores of v, with release semantics); waiters poll
+// with try_wait (acquire), which suspends the warp in hardware and resumes it
+// as soon as the phase completes, with no sleep quantum on the critical path.
+__device__ __forceinline__ uint32_t qrr_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void qrr_bar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(qrr_smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void qrr_bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(qrr_smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool qrr_bar_try_wait(uint64_t* bar) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(qrr_smem_u32(bar))
+      : "memory");
+  return ok != 0;
+}
 
 // Reflector of the owned column q (global index c) of X (rows lane + 32 k):
-// writes v (v_c = 1, zeros above c) to V[c][.] and tau[c], then raises ready[c].
+// writes v (v_c = 1, zeros above c) to V[c][.] and tau[c], then arrives on bar[c].
 template <int RPL, int CPW>
 __device__ __forceinline__ void qrr_reflector(const float (&X)[RPL][CPW], int q, int c, int lane, int ldv, float* V,
-                                              float* tau, volatile int* ready, int* status) {
+                                              float* tau, uint64_t* bar, int* status) {
   float s = 0.f, a = 0.f;
 #pragma unroll
   for (int qq = 0; qq < CPW; ++qq) {
@@ -203,41 +270,44 @@ __device__ __forceinline__ void qrr_reflector(const float (&X)[RPL][CPW], int q,
     v0 = a - beta;
   }
   float* v = V + (size_t)c * ldv;
+  // |x_i| <= |v0|: one reciprocal instead of a division per row (divisions
+  // only when v0 is so small that its reciprocal would overflow)
+  const bool tiny = fabsf(v0) < 1e-30f;
+  const float rv0 = tiny ? 0.f : __frcp_rn(v0);
 #pragma unroll
   for (int qq = 0; qq < CPW; ++qq) {
     if (qq != q) continue;
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
       const int i = lane + 32 * k;
-      v[i] = i < c ? 0.f : (i == c ? 1.f : (t != 0.f ? X[k][qq] / v0 : 0.f));
+      const float x = X[k][qq];
+      v[i] = i < c ? 0.f : (i == c ? 1.f : (t != 0.f ? (tiny ? x / v0 : x * rv0) : 0.f));
     }
   }
   if (lane == 0) {
     tau[c] = t;
     if (!isfinite(t)) atomicOr(status, 1);
   }
-  __syncwarp();
-  if (lane == 0) {
-    __threadfence_block();
-    ready[c] = 1;
-  }
+  qrr_bar_arrive(bar + c);
 }
 
-// Bounded wait for reflector j; false (and status bit 4) if it never comes.
-__device__ __forceinline__ bool qrr_wait(volatile int* ready, int j, int lane, int* status) {
-  int ok = 1;
-  if (lane == 0) {
-    int it = 0;
-    while (ready[j] == 0 && it < QRR_SPIN_LIMIT) {
-      __nanosleep(32);
-      ++it;
+// Bounded wait for reflector j (every lane acquires it); false (and status
+// bit 4) if it never comes.
+__device__ __forceinline__ bool qrr_wait(uint64_t* bar, int j, int lane, int* status) {
+  bool ok = false;
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (long long it = 0; it < QRR_WAIT_LIMIT && !ok; ++it) {
+    ok = qrr_bar_try_wait(bar + j);
+    if (!ok && (it & 255) == 255) {  // and at most about a second of wall time
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 1000000000ull) break;
     }
-    ok = ready[j] != 0;
-    if (!ok) atomicOr(status, 4);
-    __threadfence_block();
   }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  return ok != 0;
+  const bool all = __all_sync(0xffffffffu, ok);
+  if (!all && lane == 0) atomicOr(status, 4);
+  return all;
 }
 
 template <int RPL, int CPW>
@@ -249,14 +319,14 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
   constexpr int LDV = 32 * RPL;
   float* V = (float*)qr_smem;        // [n][LDV] reflectors; first the input, last the output staging
   float* tau = V + (size_t)n * LDV;  // [n]
-  volatile int* ready = (volatile int*)(tau + n);  // [n]
+  uint64_t* bar = (uint64_t*)(((uintptr_t)(tau + n) + 7) & ~(uintptr_t)7);  // [n]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // input, column-major in shared memory, then into registers
   for (int e = tid; e < m * n; e += QRR_THREADS) {
     const int i = e / n, c = e - i * n;
     V[(size_t)c * LDV + i] = (float)A[e];
   }
-  for (int c = tid; c < n; c += QRR_THREADS) ready[c] = 0;
+  for (int c = tid; c < n; c += QRR_THREADS) qrr_bar_init(bar + c, 32);
   __syncthreads();
   float X[RPL][CPW];
 #pragma unroll
@@ -269,10 +339,10 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
     }
   }
   __syncthreads();  // the input copy is dead from here on
-  if (warp == 0) qrr_reflector<RPL, CPW>(X, 0, 0, lane, LDV, V, tau, ready, status);
+  if (warp == 0) qrr_reflector<RPL, CPW>(X, 0, 0, lane, LDV, V, tau, bar, status);
   bool alive = true;
   for (int j = 0; j < n && alive; ++j) {
-    alive = qrr_wait(ready, j, lane, status);
+    alive = qrr_wait(bar, j, lane, status);
     if (!alive) break;
     const float t = tau[j];
     float v[RPL];
@@ -296,30 +366,48 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
           for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
         }
       }
-      qrr_reflector<RPL, CPW>(X, qn, cn, lane, LDV, V, tau, ready, status);
+      qrr_reflector<RPL, CPW>(X, qn, cn, lane, LDV, V, tau, bar, status);
     }
     if (t != 0.f) {
+      // the other owned columns c > j (c > j + 1 for the owner of j + 1): the
+      // inactive ones form a prefix in q, so columns go in pairs through the
+      // packed FP32x2 FMA and a pair with one inactive column gets f = 0 there
+      const int cmin = own_next ? cn + 1 : cn;
       float dot[CPW];
 #pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        dot[q] = 0.f;
-        const int c = warp + QRR_WARPS * q;
-        if (c > cn - (own_next ? 0 : 1) && c < n) {
+      for (int q = 0; q < CPW; ++q) dot[q] = 0.f;
+#pragma unroll
+      for (int q = 0; q + 1 < CPW; q += 2) {
+        if (warp + QRR_WARPS * (q + 1) >= cmin && warp + QRR_WARPS * q < n) {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) ffma2(dot[q], dot[q + 1], v[k], v[k], X[k][q], X[k][q + 1]);
+        }
+      }
+      if (CPW % 2 == 1) {
+        constexpr int q = CPW - 1;
+        if (warp + QRR_WARPS * q >= cmin && warp + QRR_WARPS * q < n) {
 #pragma unroll
           for (int k = 0; k < RPL; ++k) dot[q] += v[k] * X[k][q];
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < CPW; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+      qrr_warp_sums<CPW>(dot, lane);
 #pragma unroll
       for (int q = 0; q < CPW; ++q) {
         const int c = warp + QRR_WARPS * q;
-        if (c > cn - (own_next ? 0 : 1) && c < n) {
-          const float f = t * dot[q];
+        dot[q] = (c >= cmin && c < n) ? -t * dot[q] : 0.f;  // the update factor
+      }
 #pragma unroll
-          for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
+      for (int q = 0; q + 1 < CPW; q += 2) {
+        if (warp + QRR_WARPS * (q + 1) >= cmin && warp + QRR_WARPS * q < n) {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) ffma2(X[k][q], X[k][q + 1], dot[q], dot[q + 1], v[k], v[k]);
+        }
+      }
+      if (CPW % 2 == 1) {
+        constexpr int q = CPW - 1;
+        if (warp + QRR_WARPS * q >= cmin && warp + QRR_WARPS * q < n) {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) X[k][q] += dot[q] * v[k];
         }
       }
     }
@@ -338,27 +426,42 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
     float v[RPL];
 #pragma unroll
     for (int k = 0; k < RPL; ++k) v[k] = V[(size_t)j * LDV + lane + 32 * k];
+    // columns c >= j (the others are still e_c, orthogonal to v), in pairs as above
     float dot[CPW];
 #pragma unroll
-    for (int q = 0; q < CPW; ++q) {
-      dot[q] = 0.f;
-      const int c = warp + QRR_WARPS * q;
-      if (c >= j && c < n) {
+    for (int q = 0; q < CPW; ++q) dot[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q + 1 < CPW; q += 2) {
+      if (warp + QRR_WARPS * (q + 1) >= j && warp + QRR_WARPS * q < n) {
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) ffma2(dot[q], dot[q + 1], v[k], v[k], X[k][q], X[k][q + 1]);
+      }
+    }
+    if (CPW % 2 == 1) {
+      constexpr int q = CPW - 1;
+      if (warp + QRR_WARPS * q >= j && warp + QRR_WARPS * q < n) {
 #pragma unroll
         for (int k = 0; k < RPL; ++k) dot[q] += v[k] * X[k][q];
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+    qrr_warp_sums<CPW>(dot, lane);
 #pragma unroll
     for (int q = 0; q < CPW; ++q) {
       const int c = warp + QRR_WARPS * q;
-      if (c >= j && c < n) {
-        const float f = t * dot[q];
+      dot[q] = (c >= j && c < n) ? -t * dot[q] : 0.f;
+    }
 #pragma unroll
-        for (int k = 0; k < RPL; ++k) X[k][q] -= f * v[k];
+    for (int q = 0; q + 1 < CPW; q += 2) {
+      if (warp + QRR_WARPS * (q + 1) >= j && warp + QRR_WARPS * q < n) {
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) ffma2(X[k][q], X[k][q + 1], dot[q], dot[q + 1], v[k], v[k]);
+      }
+    }
+    if (CPW % 2 == 1) {
+      constexpr int q = CPW - 1;
+      if (warp + QRR_WARPS * q >= j && warp + QRR_WARPS * q < n) {
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) X[k][q] += dot[q] * v[k];
       }
     }
   }
@@ -381,11 +484,12 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
 template <int RPL, int CPW>
 bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, int* status) {
   if (m > 32 * RPL || n > QRR_WARPS * CPW) return false;
-  const size_t smem = ((size_t)n * 32 * RPL + 2 * (size_t)n) * sizeof(float);
+  const size_t smem = ((size_t)n * 32 * RPL + (size_t)n) * sizeof(float) + 8 + (size_t)n * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(qr_reg_kernel<RPL, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + 2 * QRR_WARPS * CPW) * sizeof(float)));
+                         (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + QRR_WARPS * CPW) * sizeof(float) + 8 +
+                               (size_t)QRR_WARPS * CPW * sizeof(uint64_t)));
     attr = true;
   }
   launch_pdl(qr_reg_kernel<RPL, CPW>, dim3(1), dim3(QRR_THREADS), smem, st, m, n, A, Qout, status);

@@ -24,8 +24,15 @@ def lib(gpu_available):
 # operations (e.g. only the operator-bond products in FP32, all else FP64)
 # already gives 9.6e-6, because the truncation to chi amplifies any change of
 # the near-degenerate singular directions it cuts.  The bounds leave a factor
-# 2 to 4; the mass bounds follow the measured drift (FP64 re-orthonormalised
-# QR in every reduced form).
+# 2 to 4.  Mass: the FP32 and TF32 bounds follow the measured drift (FP64
+# re-orthonormalised QR in every reduced form).  BF16X3's products are biased
+# low by up to 5e-6 of their magnitude (test_accumulation_bias: the tensor
+# cores' FP32 accumulation rounds toward zero), and the mass after 10 steps
+# passes through about 40 such products in sequence (two per stage along the
+# chain, two stages a step), so |<1> - 1| <= 40 * 5e-6 = 2e-4.  Which part of
+# that bias survives the truncation depends on the rounding of everything
+# else: two builds whose QR differs only in the last bit measured -2.1e-6 and
+# -8.1e-5.
 @pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-4), ("fp32", 4e-5), ("tf32", 3e-2)])
 def test_precision_form_vs_fp64_small(prec, tol):
     p64 = workload.make_params("small")
@@ -43,7 +50,7 @@ def test_precision_form_vs_fp64_small(prec, tol):
     print(f"{prec}: rel-L2 vs fp64 {rel:.2e}, vs oracle {vs_oracle:.2e}, "
           f"norm err {sb['norm_avg'] - 1:.1e}, d<Phi1> {sb['mean1_avg'] - sa['mean1_avg']:.1e}")
     assert rel < tol
-    assert abs(sb["norm_avg"] - 1.0) < {"tf32": 2e-2, "bf16x3": 2e-5, "fp32": 2e-5}[prec]
+    assert abs(sb["norm_avg"] - 1.0) < {"tf32": 2e-2, "bf16x3": 2e-4, "fp32": 2e-5}[prec]
 
 
 def test_accumulation_bias():
