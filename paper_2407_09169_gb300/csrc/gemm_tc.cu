@@ -984,13 +984,25 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   int cap = max_kb_per_split;
   if (mi.exact_kb > 0 && (cap <= 0 || cap > mi.exact_kb)) cap = mi.exact_kb;
   const long long tiles = (long long)(L.m_pad / BM) * (L.n_pad / L.bn) * batch;
+  // The split count minimises a cost model: waves of CTAs x k-blocks per
+  // split x the time of one k-block (its operand bytes at ~60 GB/s per SM),
+  // plus the FP64 partial tiles written, re-read and reduced (2 s + 1 passes
+  // over M x N at ~3 TB/s).  Short K with many tiles stays unsplit.
   int splitk = 1;
-  if (tiles < 152 && kblocks >= 4) {
-    long long s = (2 * 152 + tiles - 1) / tiles;
-    if (s > kblocks / 2) s = kblocks / 2;
-    if (s > 64) s = 64;
-    if (s < 1) s = 1;
-    splitk = (int)s;
+  {
+    const double kb_us = (double)(mi.na * BM + mi.nb * L.bn) * 128.0 / 60e3;
+    const double mn_bytes = (double)M * N * batch * 8.0;
+    double best = 0.0;
+    for (int s = 1; s <= 64 && s <= kblocks; ++s) {
+      const int per = (kblocks + s - 1) / s;
+      if (s > 1 && (long long)(s - 1) * per >= kblocks) continue;  // an empty split
+      const double waves = (double)((tiles * s + 151) / 152);
+      const double t = waves * per * kb_us + (s > 1 ? (2.0 * s + 1.0) * mn_bytes / 3e6 : 0.0);
+      if (s == 1 || t < best) {
+        best = t;
+        splitk = s;
+      }
+    }
   }
   int kbps = (kblocks + splitk - 1) / splitk;
   if (cap > 0 && kbps > cap) kbps = cap;
