@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64,
                     help="instances of the batched configuration stepped together (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--adjoint-steps", type=int, default=20,
+                    help="Heun steps of the timed gradient (qtt_grad) on the adjoint configuration (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -440,6 +442,35 @@ def run_mine(args, rank, world, local_rank):
             "max_abs_norm_err": max(abs(v - 1.0) for v in norms), "sum_cells": cells,
         }
 
+    # ---- discrete adjoint (qtt_grad) on the adjoint configuration, rank 0 at N = 1 only
+    adjoint = None
+    if rank == 0 and world == 1 and args.adjoint_steps > 0:
+        pa = workload.make_adjoint_params(seed=0, precision="fp32")
+        ns = args.adjoint_steps
+        ck = max(1, min(workload.ADJOINT["ckpt_every"], ns // 4))
+        with q.qtt_init(pa) as ca:
+            ca.grad(2, 1)  # untimed: sizes the workspaces
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Ja, ga = ca.grad(ns, ck)
+            torch.cuda.synchronize()
+            tg = time.perf_counter() - t0
+            ca.step(2)  # the forward alone on the same context (graph capture first)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ca.step(ns)
+            torch.cuda.synchronize()
+            tf = time.perf_counter() - t0
+        adjoint = {
+            "config": "2^6 points per dimension, chi 64, FP32 form, gradient in Omega, Da, gamma, 4 velocity and "
+                      "16 initial-condition amplitudes (workload.make_adjoint_params)",
+            "steps": ns, "ckpt_every": ck, "n_params": int(len(ga)), "seconds": tg,
+            "gradient_steps_per_s": ns / tg, "forward_steps_per_s": ns / tf, "gradient_over_forward_time": tg / tf,
+            "J": Ja, "dJ_dOmega": float(ga[0]), "dJ_dDa": float(ga[1]), "dJ_dgamma": float(ga[2]),
+            "timing": "host clock around one qtt_grad call (forward with checkpoints, recompute, backward) with a "
+                      "device synchronize on both sides, after an untimed 2-step call",
+        }
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -451,7 +482,7 @@ def run_mine(args, rank, world, local_rank):
             "clocks": clocks, "gpu_launches": int(launches),
             "state": {"norm_avg": scal["norm_avg"], "mean1_avg": scal["mean1_avg"], "nvpp": nvpp,
                       "discarded_weight_last_step": scal["discarded_weight"]},
-            "parity": parity, "fp64_path": fp64_path, "batched": batched,
+            "parity": parity, "fp64_path": fp64_path, "batched": batched, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
 

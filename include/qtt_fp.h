@@ -129,6 +129,25 @@ qtt_status qtt_init(const qtt_params* params, qtt_ctx** out);
  * by randomized rounding and truncates it by an SVD sweep to chi_max. */
 qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps);
 
+/* Discrete adjoint (paper: the observables of Eqs. 2 and spaceAvg; the
+ * gradient is of the discretised Heun map of Eq. FP2, not of the continuous
+ * equation).  Restarts the context from its initial PDF, takes nsteps Heun
+ * steps and returns in out[0] the mean product J = avg_x (<1> - <Phi_1> -
+ * <Phi_2>) of the final state and in out[1 ..] dJ/dtheta for theta = Omega,
+ * Da, gamma, the amplitude of each velocity mode (params.umode_amp order)
+ * and of each initial-condition mode (params.icmode_amp order), dt held
+ * fixed: 1 + 3 + n_umodes + n_icmodes values (cap >= that, else QTT_EINVAL;
+ * *written receives the count).  The backward sweep applies the transposed
+ * stage operators (MPO transposes, the transposed mixing drift and the
+ * transpose of its dependence through <Phi_a>) to the adjoint state and
+ * rounds each adjoint stage to chi like a forward stage; in exact mode
+ * nothing is rounded and the result is the exact gradient of the discrete
+ * map.  Forward states are kept every ckpt_every steps (<= 0: only the
+ * first) and each segment is recomputed before its backward sweep.  The
+ * context is left at the final state (time nsteps * dt).  Heun only
+ * (rk_variant 0). */
+qtt_status qtt_grad(qtt_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* out, int64_t cap, int64_t* written);
+
 /* Batched stepping of independent PDFs (no counterpart in the paper, which
  * steps one PDF): advances each of ctxs[0..n) by nsteps steps, enqueueing the
  * work of every context before synchronising any of them, so that contexts

@@ -81,6 +81,7 @@ def load_library(path: str | None = None):
     lib.qtt_init.argtypes = [P(QttParams), P(C.c_void_p)]
     lib.qtt_step.argtypes = [C.c_void_p, C.c_int32]
     lib.qtt_step_many.argtypes = [P(C.c_void_p), C.c_int32, C.c_int32, P(C.c_int32)]
+    lib.qtt_grad.argtypes = [C.c_void_p, C.c_int32, C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
     lib.qtt_observe.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
     lib.qtt_compare.argtypes = [C.c_void_p, C.c_void_p, P(C.c_double)]
     lib.qtt_save.argtypes = [C.c_void_p, C.c_char_p]
@@ -93,7 +94,7 @@ def load_library(path: str | None = None):
     lib.qtt_version.restype = C.c_char_p
     lib.qtt_host_dense.argtypes = [P(QttParams), C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
     lib.qtt_selftest.argtypes = [C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
-    for fn in ("qtt_init", "qtt_step", "qtt_step_many", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense",
+    for fn in ("qtt_init", "qtt_step", "qtt_step_many", "qtt_grad", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense",
                "qtt_selftest"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
@@ -178,6 +179,17 @@ class Context:
     def step(self, nsteps: int = 1):
         _check(load_library().qtt_step(self._handle(), int(nsteps)), self._h)
 
+    def grad(self, nsteps: int, ckpt_every: int = 0):
+        """(J, dJ/dtheta) after nsteps Heun steps from the initial PDF; theta in
+        the order of grad_param_names(params).  Leaves the context at the final state."""
+        n = 1 + len(grad_param_names(self.params))
+        out = np.zeros(n, dtype=np.float64)
+        written = C.c_int64(0)
+        _check(load_library().qtt_grad(self._handle(), int(nsteps), int(ckpt_every),
+                                       out.ctypes.data_as(C.POINTER(C.c_double)), out.size, C.byref(written)),
+               self._h)
+        return float(out[0]), out[1:written.value].copy()
+
     def observe(self, what: int, cap: int | None = None, out: np.ndarray | None = None) -> np.ndarray:
         Kx = sum(self.params["bits"][2:])
         if out is None:
@@ -254,6 +266,16 @@ def qtt_step_many(ctxs, nsteps: int = 1):
     if st != QTT_OK:
         i = failed.value
         _check(st, ctxs[i]._h if 0 <= i < len(ctxs) else None)
+
+
+def grad_param_names(params: dict) -> list:
+    """Order of the gradient of qtt_grad: omega, da, gamma, umode<i>, icmode<i>."""
+    return (["omega", "da", "gamma"] + [f"umode{i}" for i in range(len(params.get("umodes") or []))]
+            + [f"icmode{i}" for i in range(len(params.get("icmodes") or []))])
+
+
+def qtt_grad(ctx: Context, nsteps: int, ckpt_every: int = 0):
+    return ctx.grad(nsteps, ckpt_every)
 
 
 def qtt_observe(ctx: Context, what: int, cap: int | None = None) -> np.ndarray:

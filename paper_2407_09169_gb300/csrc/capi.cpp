@@ -205,6 +205,31 @@ qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps) {
   }
 }
 
+qtt_status qtt_grad(qtt_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* out, int64_t cap, int64_t* written) {
+  if (written) *written = 0;
+  if (!ctx || !ctx->eng) return QTT_EINVAL;
+  const int64_t need = 1 + ctx->eng->n_grad_params();
+  if (written) *written = need;
+  if (nsteps < 1 || !out || cap < need) {
+    ctx->err = "EINVAL: qtt_grad needs nsteps >= 1 and room for 1 + n_params values";
+    return QTT_EINVAL;
+  }
+  try {
+    const std::vector<double> g = ctx->eng->grad(nsteps, ckpt_every);
+    std::string msg;
+    const int st = ctx->eng->check_status(msg);
+    if (st != 0) {
+      ctx->err = msg;
+      return (qtt_status)st;
+    }
+    for (size_t i = 0; i < g.size(); ++i) out[i] = g[i];
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return classify(ctx->err);
+  }
+}
+
 qtt_status qtt_step_many(qtt_ctx* const* ctxs, int32_t n, int32_t nsteps, int32_t* failed) {
   if (failed) *failed = -1;
   if (n < 0 || nsteps < 0 || (n > 0 && !ctxs)) return QTT_EINVAL;

@@ -39,14 +39,6 @@
 
 namespace qtt {
 
-#define QTT_CUDA(call)                                                                         \
-  do {                                                                                         \
-    cudaError_t _e = (call);                                                                   \
-    if (_e != cudaSuccess)                                                                     \
-      throw std::runtime_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + " at " + \
-                               __FILE__ + ":" + std::to_string(__LINE__));                     \
-  } while (0)
-
 struct KernelTimer {
   bool on = false;
   struct Rec {
@@ -285,25 +277,6 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
     throw std::runtime_error("EINVAL: tensor-core GEMM shape outside the supported grid or workspace");
 }
 
-static MatView mv(const double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
-  MatView v;
-  v.p = p;
-  v.rs = rs;
-  v.cs = cs;
-  v.so = so;
-  v.si = si;
-  return v;
-}
-static OutView ov(double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
-  OutView v;
-  v.p = p;
-  v.rs = rs;
-  v.cs = cs;
-  v.so = so;
-  v.si = si;
-  return v;
-}
-
 void Engine::init() {
   std::string why = validate(p_);
   if (!why.empty()) throw std::runtime_error("EINVAL: " + why);
@@ -396,6 +369,7 @@ void Engine::init() {
     x1 = std::max(x1, (size_t)2 * rz_[n] * rz_[n + 1]);
     x2 = std::max(x2, (size_t)D_[n] * 2 * rz_[n + 1]);
   }
+  pp_elems_ = pp;
   P_ = (double*)dalloc(pp * sizeof(double));
   X1_ = (double*)dalloc(x1 * sizeof(double));
   X2_ = (double*)dalloc(x2 * sizeof(double));
@@ -495,9 +469,9 @@ void Engine::make_hfirst(const DevMps& f, double* v, double* hf) {
 
 void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr,
                          int role) {
-  const int bl = t.f->b[n], br = t.f->b[n + 1];
-  const int wl = t.w(n), wr = t.w(n + 1);
-  const double* A = t.f->core(n);
+  const int bl = t.bl(n), br = t.br(n);
+  const int wl = t.wl(n), wr = t.wr(n);
+  const double* A = t.A(n);
   double* X1 = lane_x1_[lane_];
   double* X2 = lane_x2_[lane_];
   // X1[(w',a')][s][l] = sum_l' W_{n+1}[(w',a')][l'] Om[l][s][l']
@@ -561,9 +535,9 @@ void Engine::sketch_pass(Term* terms, int nt, int n_stop, const DevMps& om) {
 }
 
 void Engine::zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha) {
-  const int bl = t.f->b[n], br = t.f->b[n + 1];
-  const int wl = t.w(n), wr = t.w(n + 1);
-  const double* A = t.f->core(n);
+  const int bl = t.bl(n), br = t.br(n);
+  const int wl = t.wl(n), wr = t.wr(n);
+  const double* A = t.A(n);
   double* P = lane_p_[lane_];
   // P[(rho,w)][(s',a')] = sum_a C[(rho,w)][a] A[a][(s',a')]
   gemm(r * wl, 2 * br, bl, 1, 1, 1.0, mv(C, bl, 1), mv(A, 2LL * br, 1), 0.0, ov(P, 2LL * br, 1));

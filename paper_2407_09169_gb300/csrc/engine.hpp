@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -11,6 +12,15 @@
 #include "model.hpp"
 
 namespace qtt {
+
+// Throws std::runtime_error("CUDA error: ...") when a runtime call fails.
+#define QTT_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t _e = (call);                                                                   \
+    if (_e != cudaSuccess)                                                                     \
+      throw std::runtime_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + " at " + \
+                               __FILE__ + ":" + std::to_string(__LINE__));                     \
+  } while (0)
 
 // MPS with a static bond profile b[0..N], cores [b[n]][2][b[n+1]] in one allocation.
 struct DevMps {
@@ -47,21 +57,60 @@ enum GemmRole { GEMM_STATE = 0, GEMM_SKETCH = 1, GEMM_RANGE = 2 };
 
 // One summand c * Op * f of a stage.  kind 0: dense MPO over all sites;
 // kind 1: mixing Hadamard term -- dense composition-space MPO on the phi
-// sites, then the diagonal operator diag(<Phi_a>(x)) whose cores are f's own
-// x cores (the first one mixed with the conditional-mean vectors).
+// sites, then the diagonal operator diag(<Phi_a>(x)) whose cores are the x
+// cores of hsrc (the first one mixed with the conditional-mean vectors);
+// hsrc is f itself in the forward step and the state the adjoint is
+// linearised at in the backward step.  kind 2 (adjoint of the mixing term's
+// dependence through <Phi_a>): the output h1 h2 phi_a (x) sum_phi hsrc
+// (D1phi_a^T f), i.e. the fixed train aux (weights phi_a on the phi sites,
+// then at the first x site a core that already holds the contraction over
+// the phi sites) followed by diag(hsrc's x cores) applied to f's x cores.
 struct Term {
   const DevMps* f = nullptr;
   int kind = 0;
   const DevOp* op = nullptr;
   const double* hfirst = nullptr;
+  const DevMps* hsrc = nullptr;  // kinds 1, 2: source of the diagonal cores (null: f)
+  const DevMps* aux = nullptr;   // kind 2: cores 0 .. kphi
   int kphi = 0;
-  int slot = 0;  // scratch slot: 0 / 3 identity, 1 linear, 2 mixing
+  int slot = 0;  // scratch slot: 0 / 3 identity, 1 linear, 2 mixing, 4 adjoint mixing
   double scale = 1.0;
-  int w(int n) const { return kind == 0 ? op->w[n] : (n <= kphi ? op->w[n] : f->b[n]); }
-  bool diag(int n) const { return kind == 1 && n >= kphi; }
-  const double* H(int n) const { return n == kphi ? hfirst : f->core(n); }
-  long long B(int n) const { return (long long)w(n) * f->b[n]; }
+  const DevMps* hs() const { return hsrc ? hsrc : f; }
+  // operated core of site n and its bonds
+  const double* A(int n) const { return (kind == 2 && n <= kphi) ? aux->core(n) : f->core(n); }
+  int bl(int n) const { return (kind == 2 && n <= kphi) ? aux->b[n] : f->b[n]; }
+  int br(int n) const { return (kind == 2 && n <= kphi) ? aux->b[n + 1] : f->b[n + 1]; }
+  // operator bond on the left of site n / on the right of site n
+  int wl(int n) const {
+    if (kind == 0) return op->w[n];
+    if (kind == 1) return n <= kphi ? op->w[n] : hs()->b[n];
+    return n <= kphi ? 1 : hs()->b[n];
+  }
+  int wr(int n) const { return (kind == 2 && n == kphi) ? 1 : wl(n + 1); }
+  bool diag(int n) const { return (kind == 1 && n >= kphi) || (kind == 2 && n > kphi); }
+  const double* H(int n) const { return (kind == 1 && n == kphi) ? hfirst : hs()->core(n); }
+  long long B(int n) const { return (long long)wl(n) * bl(n); }
 };
+
+// strided views for the contraction calls
+inline MatView mv(const double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
+  MatView v;
+  v.p = p;
+  v.rs = rs;
+  v.cs = cs;
+  v.so = so;
+  v.si = si;
+  return v;
+}
+inline OutView ov(double* p, long long rs, long long cs, long long so = 0, long long si = 0) {
+  OutView v;
+  v.p = p;
+  v.rs = rs;
+  v.cs = cs;
+  v.so = so;
+  v.si = si;
+  return v;
+}
 
 struct KernelTimer;
 
@@ -98,6 +147,14 @@ class Engine {
   double discarded_last() const { return discarded_last_; }
   cudaStream_t stream() const { return st_; }
   void set_time(double t, long long s);
+  // Discrete adjoint (gradient of J = avg_x (<1> - <Phi_1> - <Phi_2>) after
+  // nsteps Heun steps from the initial PDF): out[0] = J, out[1..] = dJ/dtheta
+  // for Omega, Da, gamma, each velocity mode amplitude and each IC mode
+  // amplitude.  The forward states are kept every ckpt_every steps and each
+  // segment is recomputed before it is swept backwards.  Leaves the context
+  // at the final state.
+  std::vector<double> grad(int nsteps, int ckpt_every);
+  int n_grad_params() const { return 3 + (int)p_.umodes.size() + (int)p_.icmodes.size(); }
 
  private:
   void* dalloc(size_t bytes);
@@ -126,6 +183,15 @@ class Engine {
   Term term_dense(int slot, const DevOp* op, const DevMps* f, double scale) const;
   Term term_mix(const DevMps* f, const double* hf, double scale) const;
   void chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out);
+  // adjoint (adjoint.cu)
+  void grad_setup();
+  void copy_mps(const DevMps& from, DevMps& to);
+  void mix_env_core(const DevMps& lam, const DevMps& f);  // the kind-2 core of aux_ at site kphi
+  Term term_mix_adj(const DevMps* lam, const DevMps* f, const double* hf, double scale) const;
+  Term term_mix_env(const DevMps* lam, const DevMps* f, double scale) const;
+  void sandwich_acc(const DevMps& a, const Term& t, double w, double* acc);  // acc += w <a| Term |t.f>
+  void grad_terms(const DevMps& a, const DevMps& f, const double* hf, double w);
+  void set_step_counter(unsigned long long s);
 
   Params p_;
   Model model_;
@@ -141,9 +207,9 @@ class Engine {
   Chain* wchains_dev_ = nullptr;  // wphi_ chains on the device
   DevOp op_lin_, had_, ident_;
   // scratch
-  double *Wslot_[4] = {nullptr, nullptr, nullptr, nullptr};
-  std::vector<size_t> Woff_[4];
-  double *C_[4] = {nullptr, nullptr, nullptr, nullptr}, *T_[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *Wslot_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<size_t> Woff_[5];
+  double *C_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr}, *T_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *P_ = nullptr, *X1_ = nullptr, *X2_ = nullptr, *Y_ = nullptr;
   double *v_[2] = {nullptr, nullptr}, *hf_[2] = {nullptr, nullptr};
   double *envw_ = nullptr, *envout_ = nullptr, *ws_ = nullptr, *qrwork_ = nullptr, *gq_ = nullptr;
@@ -187,6 +253,18 @@ class Engine {
   double discarded_last_ = 0.0;
   KernelTimer* timer_ = nullptr;
   double tc_issued_flops_ = 0.0;
+  // adjoint state (allocated by grad_setup on the first grad call)
+  bool adj_ready_ = false;
+  AdjointModel adjm_;
+  DevOp op_lin_t_, had_t_, had_unit_;
+  std::vector<DevOp> dL_;
+  std::vector<DevMps> dic_;
+  DevMps lamT_, lam_[2], mu_, aux_, f0_, fin_;
+  std::vector<DevMps> ckpt_, segf_, segfs_;
+  double *sw_ = nullptr, *sx1_ = nullptr, *sx2_ = nullptr, *senv_[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* gacc_ = nullptr;  // [0] J, [1..] dJ/dtheta, [last] the constant 1
+  std::vector<size_t> swoff_;
+  size_t pp_elems_ = 0;
 };
 
 }  // namespace qtt

@@ -359,4 +359,74 @@ Model build_model(const Params& p) {
   return m;
 }
 
+// ------------------------------------------------------------- adjoint
+TT mpo_transpose(const TT& op) {
+  TT t = op;
+  for (size_t n = 0; n < t.c.size(); ++n) {
+    const int L = t.r[n], R = t.r[n + 1];
+    for (int l = 0; l < L; ++l)
+      for (int r = 0; r < R; ++r) std::swap(t.c[n][((size_t)l * 4 + 1) * R + r], t.c[n][((size_t)l * 4 + 2) * R + r]);
+  }
+  return t;
+}
+
+AdjointModel build_adjoint_model(const Params& p, const Model& m) {
+  AdjointModel a;
+  a.op_lin_t = mpo_transpose(m.op_lin);
+  a.had_phi_t = mpo_transpose(m.had_phi);
+  TT d1a = tt_kron(op_d1_zero_sum(p.bits[0], 1.0 / (double)(1 << p.bits[0])), mpo_identity(p.bits[1]));
+  TT d1b = tt_kron(mpo_identity(p.bits[0]), op_d1_zero_sum(p.bits[1], 1.0 / (double)(1 << p.bits[1])));
+  a.had_unit = tt_stack_right(d1a, d1b);
+  tt_scale(a.had_unit, -1.0);
+  a.c_stack = tt_stack_right(m.wphi[1], m.wphi[2]);
+  const int Kphi = p.bits[0] + p.bits[1];
+  TT idphi = mpo_identity(Kphi);
+  const double h12 = (1.0 / (double)(1 << p.bits[0])) * (1.0 / (double)(1 << p.bits[1]));
+  // dL/dOmega (linear part) = sum_a D1phi_a diag(phi_a); dL/dDa = sum_a D1phi_a diag(phi1 phi2)
+  auto drift = [&](int e1a, int e2a, int e1b, int e2b) {
+    TT out;
+    for (int q = 0; q < 2; ++q) {
+      const int K = p.bits[q];
+      TT c = scaled(phi_weight(p, q == 0 ? e1a : e1b, q == 0 ? e2a : e2b), 1.0 / h12);
+      TT op = mpo_mul(embed_op(p, op_d1_zero_sum(K, 1.0 / (double)(1 << K)), q), mpo_diag(tt_kron(c, ones_x(p))));
+      out = q == 0 ? op : tt_add(out, op);
+    }
+    return tt_round(out, kTol, 0);
+  };
+  a.dL.push_back(drift(1, 0, 0, 1));
+  a.dL.push_back(drift(1, 1, 1, 1));
+  {
+    TT g;
+    for (int i = 0; i < 3; ++i) {
+      const int K = p.bits[2 + i];
+      TT d2 = embed_op(p, op_d2_periodic(K, 2.0 * kPi / (double)(1 << K)), 2 + i);
+      g = i == 0 ? d2 : tt_add(g, d2);
+    }
+    a.dL.push_back(tt_round(g, kTol, 0));
+  }
+  for (const Mode& md : p.umodes) {  // dL/da_m = -sin(k_m . x + t_m) D1x_c
+    const int K = p.bits[2 + md.comp];
+    TT ds = tt_kron(idphi, mpo_diag(fourier_tt(p, md.k, md.phase, true)));
+    TT op = mpo_mul(ds, embed_op(p, op_d1_periodic(K, 2.0 * kPi / (double)(1 << K)), 2 + md.comp));
+    tt_scale(op, -1.0);
+    a.dL.push_back(tt_round(op, kTol, 0));
+  }
+  {
+    Params p0 = p;
+    p0.icmodes.clear();
+    TT g = initial_pdf(p0);
+    TT phi1 = tt_kron(tt_constant(p.bits[0], 1.0), tt_constant(p.bits[1], 1.0));
+    for (const Mode& md : p.icmodes)
+      a.dic.push_back(tt_round(tt_hadamard(g, tt_kron(phi1, fourier_tt(p, md.k, md.phase, false))), kTol, 0));
+  }
+  {
+    TT w = tt_add(m.wphi[0], scaled(m.wphi[1], -1.0));
+    w = tt_add(w, scaled(m.wphi[2], -1.0));
+    const double nx = (double)(1LL << (p.bits[2] + p.bits[3] + p.bits[4]));
+    a.lam_T = tt_round(tt_kron(w, ones_x(p)), kTol, 0);
+    tt_scale(a.lam_T, 1.0 / nx);
+  }
+  return a;
+}
+
 }  // namespace qtt

@@ -47,6 +47,20 @@ struct Model {
   TT u[3];      // velocity components over the x sites (for checks)
 };
 
+// Trains of the discrete adjoint of the Heun step (gradient of the mean
+// product J = avg_x (<1> - <Phi_1> - <Phi_2>), Eqs. 2 and spaceAvg).
+struct AdjointModel {
+  TT op_lin_t;          // (I + dt W_lin)^T
+  TT had_phi_t;         // had_phi with every core transposed (open right bond 2)
+  TT had_unit;          // -[D1phi1 (+) D1phi2] (open right bond 2): d/dOmega of the mixing drift
+  TT c_stack;           // h1 h2 [phi1 (+) phi2] over the phi sites (open right bond 2)
+  std::vector<TT> dL;   // dL/dtheta (linear part) for Omega, Da, gamma, each velocity mode
+  std::vector<TT> dic;  // f0 without modulation times cos(q_m . x + p_m), each IC mode
+  TT lam_T;             // dJ/df = (h1 h2 / n_x) (1 - phi1 - phi2)
+};
+AdjointModel build_adjoint_model(const Params& p, const Model& m);
+TT mpo_transpose(const TT& op);
+
 // Single-dimension building blocks (exposed for the host debug entry points).
 TT op_shift(int K, int dir, bool periodic);   // (S f)_i = f_{i + dir}, dir = +1 / -1
 TT op_d1_periodic(int K, double h);

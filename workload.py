@@ -145,3 +145,30 @@ def make_batch_params(n: int = BATCH["n"], seed: int = 0, precision: str = "fp32
         out.append(make_params(w, seed=i, precision=precision, da=da, omega=omega, d_phi=BATCH["mu"] * omega))
     return out
 
+
+
+def draw_ic_modes(seed: int, n_modes: int = 16, kmax: int = 2):
+    """Initial-condition modulation modes f0 *= 1 + sum_m b_m cos(q_m . x + psi_m):
+    integer q_m in [-kmax, kmax]^3 without 0, psi_m ~ U[0, 2pi), b_m = 0
+    (the nominal point of the gradient)."""
+    rng = np.random.default_rng(seed + 7919)
+    modes = []
+    for _ in range(n_modes):
+        while True:
+            q = [int(v) for v in rng.integers(-kmax, kmax + 1, size=3)]
+            if any(q):
+                break
+        modes.append(dict(k=q, phase=float(rng.uniform(0.0, 2.0 * math.pi)), amp=0.0))
+    return modes
+
+
+# Adjoint configuration: 2^6 points per dimension, chi 64, FP32 form, the
+# gradient in Omega, Da, gamma, 4 velocity and 16 initial-condition amplitudes.
+ADJOINT = {"bits": 6, "chi_max": 64, "steps": 200, "ckpt_every": 20, "n_ic": 16}
+
+
+def make_adjoint_params(seed: int = 0, precision: str = "fp32") -> dict:
+    p = make_params({"bits": ADJOINT["bits"], "chi_max": ADJOINT["chi_max"], "steps": ADJOINT["steps"]}, seed=seed,
+                    precision=precision)
+    p["icmodes"] = draw_ic_modes(seed, ADJOINT["n_ic"])
+    return p
