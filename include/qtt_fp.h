@@ -89,7 +89,13 @@ typedef struct {
                             (shear_amp unused; seeded modes, if any, are added) */
   double u0;             /* velocity scale of flow 1 */
   int32_t ic_kind;       /* 0: blend in x2 (above); 1: the paper's Gaussian step function in x1
-                            (Eq. initPDF) smoothed by tanh edges of width ic_blend_width */
+                            (Eq. initPDF) smoothed by tanh edges of width ic_blend_width;
+                            2 (no counterpart in the paper): a Gaussian of std ic_sigma whose
+                            centre moves with x, c1 = ic_c_hi[0] + A sin(x1) cos(x2),
+                            c2 = ic_c_hi[1] - A sin(x2 + x3), A = ic_blend_width >= 0, each factor
+                            normalised on the phi grid; it couples phi with x, and is encoded
+                            by tensor cross from point samples (paper: initial states by the
+                            tensor-cross algorithm, "Computational complexity") */
   void* stream;          /* cudaStream_t or NULL (the context then creates its own stream) */
 } qtt_params;
 

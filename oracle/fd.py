@@ -101,12 +101,37 @@ def _gaussian2(grid: Grid, centre, sigma):
     return g / (g.sum() * grid.h_phi[0] * grid.h_phi[1])
 
 
+def _moving_gaussian(params, grid: Grid):
+    """ic_kind 2: Gaussian in phi (std ic_sigma) centred at
+    c1 = ic_c_hi[0] + A sin(x1) cos(x2), c2 = ic_c_hi[1] - A sin(x2 + x3),
+    A = ic_blend_width, each 1-D factor normalised on the phi grid."""
+    X1, X2, X3 = np.meshgrid(*grid.x, indexing="ij")
+    A, s = params["ic_blend_width"], params["ic_sigma"]
+    c1 = params["ic_c_hi"][0] + A * np.sin(X1) * np.cos(X2)
+    c2 = params["ic_c_hi"][1] - A * np.sin(X2 + X3)
+    g1 = np.exp(-(grid.phi[0][:, None, None, None] - c1[None]) ** 2 / (2 * s * s))
+    g2 = np.exp(-(grid.phi[1][:, None, None, None] - c2[None]) ** 2 / (2 * s * s))
+    g1 = g1 / (g1.sum(axis=0, keepdims=True) * grid.h_phi[0])
+    g2 = g2 / (g2.sum(axis=0, keepdims=True) * grid.h_phi[1])
+    f = g1[:, None] * g2[None, :]
+    if params.get("icmodes"):
+        mod = np.ones(grid.M[2:])
+        for m in params["icmodes"]:
+            q = m["k"]
+            mod += m["amp"] * np.cos(q[0] * X1 + q[1] * X2 + q[2] * X3 + m["phase"])
+        f = f * mod[None, None]
+    return np.ascontiguousarray(f)
+
+
 def initial_pdf(params, grid: Grid):
     """f0 = w G_hi(phi) + (1 - w) G_lo(phi), G normalised so that
     h_phi1 h_phi2 sum G = 1.  ic_kind 0: w(x2) = (1 + tanh((x2 - pi)/width))/2.
     ic_kind 1 (Eq. initPDF, smoothed): w(x1) = 1 on l0/4 <= x1 < 3 l0/4
     (l0 = 2 pi), with tanh edges of the given width.  Optionally multiplied
-    by (1 + sum_m b_m cos(q_m . x + psi_m))."""
+    by (1 + sum_m b_m cos(q_m . x + psi_m)).  ic_kind 2 (ours): see
+    _moving_gaussian."""
+    if params.get("ic_kind", 0) == 2:
+        return _moving_gaussian(params, grid)
     g_hi = _gaussian2(grid, params["ic_c_hi"], params["ic_sigma"])
     g_lo = _gaussian2(grid, params["ic_c_lo"], params["ic_sigma"])
     width = params["ic_blend_width"]

@@ -10,6 +10,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 namespace qtt {
@@ -45,5 +46,18 @@ TT mpo_diag(const TT& v);
 TT mpo_mul(const TT& A, const TT& B);  // operator product A * B
 std::vector<double> tt_dense(const TT& a);  // all d^N entries, site 0 most significant
 double tt_norm(const TT& a);
+
+// Tensor-train cross interpolation (cross.cpp) of F over N binary indices
+// (bits[n] in {0, 1}, site 0 first): two-site sweeps with SVD rank selection
+// (relative tolerance rel_tol, cap max_rank) and maximum-volume pivots, at
+// most max_sweeps left-to-right sweeps, stopping when the relative error on
+// 256 random samples is below 10 rel_tol.  The result is not rounded.
+struct CrossStats {
+  long long evaluations = 0;
+  int sweeps = 0;
+  double sample_rel_err = 0.0;
+};
+TT tt_cross(int N, const std::function<double(const uint8_t*)>& F, int max_rank, double rel_tol, int max_sweeps,
+            uint64_t seed, CrossStats* stats);
 
 }  // namespace qtt

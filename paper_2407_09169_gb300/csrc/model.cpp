@@ -11,6 +11,7 @@
 //                        each dimension coarse-to-fine (most significant bit first).
 #include "model.hpp"
 
+#include <algorithm>
 #include <cmath>
 #include <sstream>
 #include <stdexcept>
@@ -30,9 +31,10 @@ std::string validate(const Params& p) {
   if (p.precision < 0 || p.precision > 3) e << "unknown precision " << p.precision << "; ";
   if (!(p.dt > 0.0) || !std::isfinite(p.dt)) e << "dt must be positive; ";
   if (!(p.ic_sigma > 0.0)) e << "ic_sigma must be positive; ";
-  if (!(p.ic_blend_width > 0.0)) e << "ic_blend_width must be positive; ";
+  if (p.ic_kind == 2 ? !(p.ic_blend_width >= 0.0) : !(p.ic_blend_width > 0.0))
+    e << "ic_blend_width must be positive (ic_kind 2: non-negative); ";
   if (p.flow != 0 && p.flow != 1) e << "flow must be 0 or 1; ";
-  if (p.ic_kind != 0 && p.ic_kind != 1) e << "ic_kind must be 0 or 1; ";
+  if (p.ic_kind < 0 || p.ic_kind > 2) e << "ic_kind must be 0, 1 or 2; ";
   if (!std::isfinite(p.u0)) e << "u0 must be finite; ";
   if (p.oversample < 0 || p.oversample > 256) e << "oversample outside 0..256; ";
   if (p.rk_variant != 0 && p.rk_variant != 1) e << "rk_variant must be 0 or 1; ";
@@ -270,6 +272,55 @@ static TT gaussian_phi(const Params& p, const double c[2]) {
   return out;
 }
 
+// ic_kind 2 (ours, not the paper's): a composition-space Gaussian whose
+// centre moves with x, c1 = ic_c_hi[0] + A sin(x1) cos(x2),
+// c2 = ic_c_hi[1] - A sin(x2 + x3), A = ic_blend_width, std ic_sigma, each
+// factor normalised on the phi grid (h_a sum_i G = 1) so that <1>(x) = 1.
+// It couples phi with x (not a short sum of products), so it is encoded by
+// tensor cross from point evaluations.
+static TT moving_gaussian_pdf(const Params& p) {
+  const int N = p.N();
+  const int K[5] = {p.bits[0], p.bits[1], p.bits[2], p.bits[3], p.bits[4]};
+  const size_t M[5] = {(size_t)1 << K[0], (size_t)1 << K[1], (size_t)1 << K[2], (size_t)1 << K[3], (size_t)1 << K[4]};
+  const std::vector<double> ph1 = grid_phi(K[0]), ph2 = grid_phi(K[1]);
+  const std::vector<double> x1 = grid_x(K[2]), x2 = grid_x(K[3]), x3 = grid_x(K[4]);
+  const double A = p.ic_blend_width, s2 = 2.0 * p.ic_sigma * p.ic_sigma;
+  auto g = [&](double d) { return std::exp(-d * d / s2); };
+  // centres and 1-D normalisations on the x planes they depend on
+  std::vector<double> c1(M[2] * M[3]), z1(M[2] * M[3]), c2(M[3] * M[4]), z2(M[3] * M[4]);
+  for (size_t a = 0; a < M[2]; ++a)
+    for (size_t b = 0; b < M[3]; ++b) {
+      const double c = p.ic_c_hi[0] + A * std::sin(x1[a]) * std::cos(x2[b]);
+      double z = 0.0;
+      for (double v : ph1) z += g(v - c);
+      c1[a * M[3] + b] = c;
+      z1[a * M[3] + b] = z / (double)M[0];
+    }
+  for (size_t b = 0; b < M[3]; ++b)
+    for (size_t e = 0; e < M[4]; ++e) {
+      const double c = p.ic_c_hi[1] - A * std::sin(x2[b] + x3[e]);
+      double z = 0.0;
+      for (double v : ph2) z += g(v - c);
+      c2[b * M[4] + e] = c;
+      z2[b * M[4] + e] = z / (double)M[1];
+    }
+  auto F = [&](const uint8_t* bits) {
+    size_t idx[5];
+    int o = 0;
+    for (int d = 0; d < 5; ++d) {
+      size_t v = 0;
+      for (int k = 0; k < K[d]; ++k) v = (v << 1) | bits[o + k];
+      idx[d] = v;
+      o += K[d];
+    }
+    const size_t i1 = idx[2] * M[3] + idx[3], i2 = idx[3] * M[4] + idx[4];
+    return g(ph1[idx[0]] - c1[i1]) / z1[i1] * g(ph2[idx[1]] - c2[i2]) / z2[i2];
+  };
+  // the state keeps at most chi_max per bond, so the cross needs a little more
+  TT t = tt_cross(N, F, p.chi_max + 16, 1e-12, 8, p.seed ^ 0x5eedc0deULL, nullptr);
+  return tt_round(t, kTol, 0);
+}
+
 static TT initial_pdf(const Params& p) {
   const int Kx[3] = {p.bits[2], p.bits[3], p.bits[4]};
   // ic_kind 0: w(x2) = (1 + tanh((x2 - pi) / width)) / 2.  ic_kind 1 (Eq. initPDF):
@@ -286,9 +337,14 @@ static TT initial_pdf(const Params& p) {
     parts[d] = encode(Kx[d], grid_x(Kx[d]), [&](double x) { return hi ? w(x) : 1.0 - w(x); });
     return kron3(parts[0], parts[1], parts[2]);
   };
-  TT whi = blend(true), wlo = blend(false);
-  TT f = tt_add(tt_kron(gaussian_phi(p, p.ic_c_hi), whi), tt_kron(gaussian_phi(p, p.ic_c_lo), wlo));
-  f = tt_round(f, kTol, 0);
+  TT f;
+  if (p.ic_kind == 2) {
+    f = moving_gaussian_pdf(p);
+  } else {
+    TT whi = blend(true), wlo = blend(false);
+    f = tt_add(tt_kron(gaussian_phi(p, p.ic_c_hi), whi), tt_kron(gaussian_phi(p, p.ic_c_lo), wlo));
+    f = tt_round(f, kTol, 0);
+  }
   bool any = false;
   for (const Mode& m : p.icmodes) any = any || (m.amp != 0.0);
   if (any) {

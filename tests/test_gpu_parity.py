@@ -186,3 +186,34 @@ def test_paper_flow_truncated_vs_oracle():
         assert err < 5e-2
         assert abs(s["norm_avg"] - 1.0) < 1e-4
         assert abs(s["mean1_avg"] - o["mean1_avg"]) < 1e-3
+
+
+# ------------------------------------------------- tensor-cross initial PDF
+@pytest.mark.parametrize("K,steps", [(2, 4), ([2, 2, 3, 2, 3], 3)])
+def test_exact_mode_moving_gaussian_matches_oracle(K, steps):
+    """ic_kind 2 (encoded by tensor cross on the host) stepped untruncated."""
+    p = exact_params(K, ic_kind=2, ic_sigma=0.12, ic_blend_width=0.2, ic_c_hi=[0.45, 0.55])
+    with pkg.qtt_init(p) as ctx:
+        g = oracle.make_grid(p["bits"])
+        assert rel_l2(ctx.observe(pkg.OBS_DENSE), oracle.initial_pdf(p, g).ravel()) < 1e-12
+        ctx.step(steps)
+        got = ctx.observe(pkg.OBS_DENSE)
+    err = rel_l2(got, oracle.solve(p, steps).ravel())
+    assert err <= 1e-10, err
+
+
+def test_truncated_moving_gaussian_against_oracle():
+    """2^4 points per dimension, chi 64: the non-separable initial PDF (its
+    rank at the x1 | x2 cut is ~110 at 1e-12) stepped with truncation, against
+    the dense oracle."""
+    p = workload.make_params({"bits": 4, "chi_max": 64}, ic_kind=2, ic_sigma=0.25, ic_blend_width=0.1,
+                             ic_c_hi=[0.45, 0.55])
+    with pkg.qtt_init(p) as ctx:
+        g = oracle.make_grid(p["bits"])
+        e0 = rel_l2(ctx.observe(pkg.OBS_DENSE), oracle.initial_pdf(p, g).ravel())
+        ctx.step(10)
+        got = ctx.observe(pkg.OBS_DENSE)
+        s = ctx.scalars()
+    err = rel_l2(got, oracle.solve(p, 10).ravel())
+    print(f"\nmoving Gaussian, chi 64: initial {e0:.2e}, after 10 steps {err:.2e}, <1>-1 {s['norm_avg'] - 1:.1e}")
+    assert e0 <= 1e-6 and err <= 1e-4 and abs(s["norm_avg"] - 1.0) <= 1e-6

@@ -61,6 +61,25 @@ def test_initial_pdf_with_modulation():
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("bits,sigma,amp", [([3, 3, 3, 3, 3], 0.1, 0.2), ([4, 3, 3, 2, 3], 0.08, 0.25),
+                                             ([3, 3, 3, 3, 3], 0.1, 0.0)])
+def test_moving_gaussian_by_tensor_cross(bits, sigma, amp):
+    """ic_kind 2 couples phi with x (the Gaussian's centre moves with x), so
+    the library encodes it by tensor cross from point samples; the encoding
+    must reproduce the oracle's dense array to the cross tolerance."""
+    p = _params(bits, ic_kind=2, ic_sigma=sigma, ic_blend_width=amp, ic_c_hi=[0.45, 0.55])
+    g = oracle.make_grid(bits)
+    ref = oracle.initial_pdf(p, g).ravel()
+    got = pkg.qtt_host_dense(p, 0, ref.size)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    ranks = pkg.qtt_host_dense(p, 41, sum(bits) + 1)
+    print(f"\nbits {bits} sigma {sigma} amp {amp}: rel err {err:.2e}, max rank {int(ranks.max())}")
+    assert err <= 1e-10
+    if amp == 0.0:  # separable: rank 1 between the dimensions
+        cuts = np.cumsum(bits)[:-1]
+        assert all(int(ranks[c]) == 1 for c in cuts), ranks
+
+
 def test_velocity_encoding():
     p = _params([1, 1, 4, 3, 5])
     g = oracle.make_grid(p["bits"])

@@ -343,3 +343,24 @@ def test_paper_velocity_moment_equation_da0():
     assert np.abs(f1 - m1).max() < 1e-12
     assert np.abs(f2 - m2).max() < 1e-12
 
+
+
+def test_moving_gaussian_initial_pdf():
+    """ic_kind 2: every x has <1>(x) = 1; with no centre modulation it is the
+    separable corner Gaussian of ic_kind 0's construction at the same centre."""
+    p = workload.make_params({"bits": 3, "chi_max": 8}, ic_kind=2, ic_sigma=0.1, ic_blend_width=0.2, ic_c_hi=[0.4, 0.6])
+    g = oracle.make_grid(p["bits"])
+    f = oracle.initial_pdf(p, g)
+    norm = f.sum(axis=(0, 1)) * g.h_phi[0] * g.h_phi[1]
+    assert np.max(np.abs(norm - 1.0)) < 1e-13
+    p0 = dict(p, ic_blend_width=0.0)
+    f0 = oracle.initial_pdf(p0, g)
+    P1, P2 = np.meshgrid(g.phi[0], g.phi[1], indexing="ij")
+    G = np.exp(-((P1 - 0.4) ** 2 + (P2 - 0.6) ** 2) / (2 * 0.1 ** 2))
+    G = G / (G.sum() * g.h_phi[0] * g.h_phi[1])
+    assert np.max(np.abs(f0 - G[:, :, None, None, None])) < 1e-12 * G.max()
+    # the centre moves: the conditional mean of phi1 follows c1 = 0.4 + 0.2 sin(x1) cos(x2) away from the walls
+    m1, _ = oracle.conditional_means(f, g)
+    X1, X2, _ = np.meshgrid(*g.x, indexing="ij")
+    c1 = 0.4 + 0.2 * np.sin(X1) * np.cos(X2)
+    assert np.max(np.abs(m1 - c1)) < 0.02
