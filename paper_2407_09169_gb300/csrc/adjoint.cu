@@ -53,6 +53,7 @@ void Engine::grad_setup() {
   upload_op(had_unit_, adjm_.had_unit);
   dL_.resize(adjm_.dL.size());
   for (size_t i = 0; i < dL_.size(); ++i) upload_op(dL_[i], adjm_.dL[i]);
+  upload_op(dL_stack_, adjm_.dL_stack);
   dic_.resize(adjm_.dic.size());
   for (size_t i = 0; i < dic_.size(); ++i) {
     alloc_mps(dic_[i], adjm_.dic[i].r);
@@ -114,6 +115,7 @@ void Engine::grad_setup() {
     sb[n] = (size_t)D_[n];
     for (const DevMps& m : dic_) sb[n] = std::max(sb[n], (size_t)m.b[n]);
     for (const DevOp& o : dL_) wm[n] = std::max(wm[n], (size_t)o.w[n]);
+    wm[n] = std::max(wm[n], (size_t)dL_stack_.w[n]);
     wm[n] = std::max(wm[n], n <= kp ? (size_t)had_unit_.w[n] : (size_t)D_[n]);
   }
   swoff_.assign(N + 1, 0);
@@ -228,7 +230,7 @@ void Engine::sandwich_acc(const DevMps& a, const Term& t, double w, double* acc)
   std::swap(lane_x2_[0], sx2_);
   lane_ = lane0;
   const double* one = gacc_ + n_grad_params() + 1;
-  gemm64(1, 1, 1, 1, 1, w, mv(sw_ + swoff_[0], 1, 1), mv(one, 1, 1), 1.0, ov(acc, 1, 1));
+  gemm64(t.wl(0), 1, 1, 1, 1, w, mv(sw_ + swoff_[0], 1, 1), mv(one, 1, 1), 1.0, ov(acc, 1, 1));
 }
 
 // acc[theta] += w <a| dL/dtheta(f) |f> for Omega, Da, gamma and the velocity
@@ -236,11 +238,12 @@ void Engine::sandwich_acc(const DevMps& a, const Term& t, double w, double* acc)
 // dL/dOmega = sum_a D1phi_a[(phi_a - <Phi_a>) f]).
 void Engine::grad_terms(const DevMps& a, const DevMps& f, const double* hf, double w) {
   double* g = gacc_ + 1;
-  sandwich_acc(a, term_dense(1, &dL_[0], &f, 1.0), w, g + 0);
+  // the linear parts of every parameter in one contraction: the stacked
+  // operator's open left bond carries the parameter index
+  sandwich_acc(a, term_dense(1, &dL_stack_, &f, 1.0), w, g);
   Term mix = term_mix(&f, hf, 1.0);
   mix.op = &had_unit_;
   sandwich_acc(a, mix, w, g + 0);
-  for (size_t i = 1; i < dL_.size(); ++i) sandwich_acc(a, term_dense(1, &dL_[i], &f, 1.0), w, g + i);
 }
 
 std::vector<double> Engine::grad(int nsteps, int ckpt_every) {

@@ -189,7 +189,8 @@ class Engine {
   void mix_env_core(const DevMps& lam, const DevMps& f);  // the kind-2 core of aux_ at site kphi
   Term term_mix_adj(const DevMps* lam, const DevMps* f, const double* hf, double scale) const;
   Term term_mix_env(const DevMps* lam, const DevMps* f, double scale) const;
-  void sandwich_acc(const DevMps& a, const Term& t, double w, double* acc);  // acc += w <a| Term |t.f>
+  // acc[0 .. w0) += w <a| Term |t.f> (w0 = the term's open left operator bond)
+  void sandwich_acc(const DevMps& a, const Term& t, double w, double* acc);
   void grad_terms(const DevMps& a, const DevMps& f, const double* hf, double w);
   void set_step_counter(unsigned long long s);
 
@@ -256,7 +257,7 @@ class Engine {
   // adjoint state (allocated by grad_setup on the first grad call)
   bool adj_ready_ = false;
   AdjointModel adjm_;
-  DevOp op_lin_t_, had_t_, had_unit_;
+  DevOp op_lin_t_, had_t_, had_unit_, dL_stack_;
   std::vector<DevOp> dL_;
   std::vector<DevMps> dic_;
   DevMps lamT_, lam_[2], mu_, aux_, f0_, fin_;

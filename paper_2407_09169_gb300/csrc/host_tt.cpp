@@ -192,7 +192,7 @@ TT tt_kron(const TT& a, const TT& b) {
   return t;
 }
 
-static TT tt_direct_sum(const TT& a, const TT& b, bool open_right) {
+static TT tt_direct_sum(const TT& a, const TT& b, bool open_right, bool open_left = false) {
   if (a.N() != b.N() || a.d != b.d) throw std::runtime_error("tt_add: shape mismatch");
   const int N = a.N(), d = a.d;
   TT t;
@@ -200,8 +200,10 @@ static TT tt_direct_sum(const TT& a, const TT& b, bool open_right) {
   t.r.resize(N + 1);
   t.c.resize(N);
   for (int n = 0; n <= N; ++n) t.r[n] = a.r[n] + b.r[n];
-  t.r[0] = 1;
-  if (a.r[0] != 1 || b.r[0] != 1) throw std::runtime_error("tt_add: left boundary must be 1");
+  if (!open_left) {
+    t.r[0] = 1;
+    if (a.r[0] != 1 || b.r[0] != 1) throw std::runtime_error("tt_add: left boundary must be 1");
+  }
   if (!open_right) {
     if (a.r[N] != 1 || b.r[N] != 1) throw std::runtime_error("tt_add: right boundary must be 1");
     t.r[N] = 1;
@@ -209,7 +211,7 @@ static TT tt_direct_sum(const TT& a, const TT& b, bool open_right) {
   for (int n = 0; n < N; ++n) {
     const int L = t.r[n], R = t.r[n + 1];
     t.c[n].assign((size_t)L * d * R, 0.0);
-    const bool first = (n == 0), last = (n == N - 1) && !open_right;
+    const bool first = (n == 0) && !open_left, last = (n == N - 1) && !open_right;
     for (int which = 0; which < 2; ++which) {
       const TT& s = which ? b : a;
       const int l0 = first ? 0 : (which ? a.r[n] : 0);
@@ -225,6 +227,7 @@ static TT tt_direct_sum(const TT& a, const TT& b, bool open_right) {
 
 TT tt_add(const TT& a, const TT& b) { return tt_direct_sum(a, b, false); }
 TT tt_stack_right(const TT& a, const TT& b) { return tt_direct_sum(a, b, true); }
+TT tt_stack_left(const TT& a, const TT& b) { return tt_direct_sum(a, b, false, true); }
 
 void tt_scale(TT& a, double s) {
   for (double& x : a.c[0]) x *= s;

@@ -38,6 +38,7 @@ TT tt_constant(int K, double value);
 TT tt_kron(const TT& a, const TT& b);
 TT tt_add(const TT& a, const TT& b);
 TT tt_stack_right(const TT& a, const TT& b);  // direct sum with an open right bond ra + rb
+TT tt_stack_left(const TT& a, const TT& b);   // direct sum with an open left bond ra + rb (right ends summed)
 void tt_scale(TT& a, double s);
 TT tt_round(const TT& a, double rel_tol, int max_rank);  // drop sigma < rel_tol * sigma_1 per bond
 TT tt_hadamard(const TT& a, const TT& b);

@@ -467,6 +467,8 @@ AdjointModel build_adjoint_model(const Params& p, const Model& m) {
     tt_scale(op, -1.0);
     a.dL.push_back(tt_round(op, kTol, 0));
   }
+  a.dL_stack = a.dL[0];
+  for (size_t i = 1; i < a.dL.size(); ++i) a.dL_stack = tt_stack_left(a.dL_stack, a.dL[i]);
   {
     Params p0 = p;
     p0.icmodes.clear();

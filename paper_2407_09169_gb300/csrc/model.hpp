@@ -55,6 +55,7 @@ struct AdjointModel {
   TT had_unit;          // -[D1phi1 (+) D1phi2] (open right bond 2): d/dOmega of the mixing drift
   TT c_stack;           // h1 h2 [phi1 (+) phi2] over the phi sites (open right bond 2)
   std::vector<TT> dL;   // dL/dtheta (linear part) for Omega, Da, gamma, each velocity mode
+  TT dL_stack;          // the dL stacked with an open left bond (one per parameter)
   std::vector<TT> dic;  // f0 without modulation times cos(q_m . x + p_m), each IC mode
   TT lam_T;             // dJ/df = (h1 h2 / n_x) (1 - phi1 - phi2)
 };
