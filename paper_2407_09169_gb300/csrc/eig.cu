@@ -51,6 +51,18 @@ __device__ T warp_sum_e(T v) {
 
 __device__ __forceinline__ double rhyp(double a, double b) { return rhypot(a, b); }
 __device__ __forceinline__ float rhyp(float a, float b) { return rhypotf(a, b); }
+// 1 / sqrt(a^2 + b^2) on the QL recurrence's dependency chain: the plain
+// reciprocal square root of the sum of squares (fewer dependent operations
+// than the scaled rhypot) while the sum stays inside the normal range, else
+// the scaled form.
+__device__ __forceinline__ double rhyp_fast(double a, double b) {
+  const double q = fma(a, a, b * b);
+  return (q > 1e-300 && q < 1e300) ? rsqrt(q) : rhypot(a, b);
+}
+__device__ __forceinline__ float rhyp_fast(float a, float b) {
+  const float q = fmaf(a, a, b * b);
+  return (q > 1e-35f && q < 1e35f) ? rsqrtf(q) : rhypotf(a, b);
+}
 
 // Work layout, in elements of T: A n*n | Z n*n | rot_c R | rot_s R; then
 // ints: seg_lo S | seg_hi S | seg_off S | order n | nseg.  R = 4 n^2 + 64 n
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
           const T ei = e[i];
           g = c * ei;
           h = c * p;
-          const T rr = rhyp(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
+          const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
           const T cn = p * rr, sn = ei * rr;
           r = p * cn + ei * sn;  // hypot(p, e_i)
           e[i + 1] = s * r;      // previous sine
