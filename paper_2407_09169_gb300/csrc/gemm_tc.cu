@@ -43,9 +43,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "gemm_tc.cuh"
 
@@ -911,6 +913,49 @@ PackLayout pack_layout(int M, int N, int K, long long batch, int mode) {
   return L;
 }
 
+// shape key of the split-K autotuner and its process-wide cache
+struct TuneKey {
+  int mode, M, N, K;
+  long long batch, ba, bb;
+  int cap;
+  bool operator<(const TuneKey& o) const {
+    if (mode != o.mode) return mode < o.mode;
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    if (K != o.K) return K < o.K;
+    if (batch != o.batch) return batch < o.batch;
+    if (ba != o.ba) return ba < o.ba;
+    if (bb != o.bb) return bb < o.bb;
+    return cap < o.cap;
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune;
+
+bool tune_lookup(const TuneKey& k, int& s) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  s = it->second;
+  return true;
+}
+void tune_store(const TuneKey& k, int s) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune[k] = s;
+}
+bool tune_enabled() {
+  const char* e = std::getenv("QTT_TUNE");
+  return !(e && e[0] == '0');
+}
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown: do not time
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 }  // namespace
 
 size_t tc_workspace_bytes(int M, int N, int K, long long batch, int mode) {
@@ -1004,19 +1049,20 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
       }
     }
   }
-  int kbps = (kblocks + splitk - 1) / splitk;
-  if (cap > 0 && kbps > cap) kbps = cap;
-  splitk = (kblocks + kbps - 1) / kbps;
-  if (splitk > 1 && (ws == nullptr || (size_t)splitk * batch * (size_t)M * N > ws_elems || splitk * batch > 65535)) {
-    if (mi.exact_kb > 0) return false;  // exactness needs the FP64 reduction of the chunks
-    splitk = 1;
-    kbps = kblocks;
-  }
-  double* wsp = splitk > 1 ? ws : nullptr;
-  count_launches(1 + (mi.sliced ? 2 : 0) + (splitk > 1 ? 2 : 1));
+  // a split count as launched: k-blocks per split within the exactness cap,
+  // partial tiles that fit the workspace (0: not launchable)
+  auto legal = [&](int s_req, int& kbps_out) -> int {
+    int kb = (kblocks + s_req - 1) / s_req;
+    if (cap > 0 && kb > cap) kb = cap;
+    const int s2 = (kblocks + kb - 1) / kb;
+    if (s2 > 1 && (ws == nullptr || (size_t)s2 * batch * (size_t)M * N > ws_elems || s2 * batch > 65535)) return 0;
+    kbps_out = kb;
+    return s2;
+  };
+  auto run = [&](int sk, int kb, double beta_, OutView C_) {
+    double* wsp = sk > 1 ? ws : nullptr;
 #define QTT_TC_LAUNCH(MODE_, BN_, ST_) \
-  launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kbps, splitk, inner, batch, batch_a, batch_b, alpha, beta, C, wsp, \
-                             err)
+  launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kb, sk, inner, batch, batch_a, batch_b, alpha, beta_, C_, wsp, err)
 #define QTT_TC_BN(MODE_, S256, S160, S128, S64)       \
   switch (L.bn) {                                     \
     case 256: QTT_TC_LAUNCH(MODE_, 256, S256); break; \
@@ -1030,18 +1076,93 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
     default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
   }
-  // stages: as many as fit in 227 KB of shared memory
-  switch (mode) {
-    case TC_BF16X3: QTT_TC_BN(TC_BF16X3, 2, 3, 3, 4); break;
-    case TC_BF16X6: QTT_TC_BN3(TC_BF16X6, 2, 2, 3); break;
-    case TC_BF16: QTT_TC_BN(TC_BF16, 4, 4, 6, 8); break;
-    case TC_TF32: QTT_TC_BN(TC_TF32, 4, 4, 6, 8); break;
-    default: QTT_TC_BN(TC_TF32X3, 2, 3, 3, 4); break;
-  }
+    // stages: as many as fit in 227 KB of shared memory
+    switch (mode) {
+      case TC_BF16X3: QTT_TC_BN(TC_BF16X3, 2, 3, 3, 4); break;
+      case TC_BF16X6: QTT_TC_BN3(TC_BF16X6, 2, 2, 3); break;
+      case TC_BF16: QTT_TC_BN(TC_BF16, 4, 4, 6, 8); break;
+      case TC_TF32: QTT_TC_BN(TC_TF32, 4, 4, 6, 8); break;
+      default: QTT_TC_BN(TC_TF32X3, 2, 3, 3, 4); break;
+    }
 #undef QTT_TC_BN3
 #undef QTT_TC_BN
 #undef QTT_TC_LAUNCH
-  if (splitk > 1) splitk_reduce(st, M, N, inner, splitk, (int)batch, alpha, ws, beta, C);
+    if (sk > 1) splitk_reduce(st, M, N, inner, sk, (int)batch, alpha, ws, beta_, C_);
+  };
+  int kbps = kblocks;
+  splitk = legal(splitk, kbps);
+  if (splitk == 0) {
+    if (mi.exact_kb > 0) return false;  // exactness needs the FP64 reduction of the chunks
+    splitk = 1;
+    kbps = kblocks;
+  }
+  // Split-K autotuner: the first time a shape is seen outside a graph
+  // capture, the cost model's split, half and double of it and no split are
+  // each timed (CUDA events, three launches after one warm-up, output into
+  // a scratch buffer), and the fastest is kept for every later call of that
+  // shape.  Later steps (and the captured graphs) reuse the choice.
+  {
+    const TuneKey key{mode, M, N, K, batch, batch_a, batch_b, cap};
+    int cached = 0;
+    if (tune_lookup(key, cached)) {
+      int kb2 = kblocks;
+      const int s2 = legal(cached, kb2);
+      if (s2 > 0) {
+        splitk = s2;
+        kbps = kb2;
+      }
+    } else if (tune_enabled() && !stream_capturing(st)) {
+      std::vector<int> cands{splitk};
+      for (int c : {1, splitk / 2, splitk * 2}) {
+        int kb2 = kblocks;
+        const int s2 = c >= 1 ? legal(c, kb2) : 0;
+        if (s2 > 0 && std::find(cands.begin(), cands.end(), s2) == cands.end()) cands.push_back(s2);
+      }
+      int best = splitk;
+      if (cands.size() > 1) {
+        double* scratch = nullptr;
+        const size_t sbytes = (size_t)M * N * batch * sizeof(double);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaMalloc(&scratch, sbytes) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess) {
+          OutView Cs;
+          Cs.p = scratch;
+          Cs.rs = N;
+          Cs.cs = 1;
+          Cs.si = (long long)M * N;
+          Cs.so = Cs.si * inner;
+          float best_ms = 1e30f;
+          for (int c : cands) {
+            int kb2 = kblocks;
+            const int s2 = legal(c, kb2);
+            run(s2, kb2, 0.0, Cs);  // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3; ++r) run(s2, kb2, 0.0, Cs);
+            cudaEventRecord(e1, st);
+            float ms = 1e30f;
+            if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+              best_ms = ms;
+              best = s2;
+            }
+          }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (scratch) {
+          cudaStreamSynchronize(st);
+          cudaFree(scratch);
+        }
+        cudaGetLastError();
+      }
+      tune_store(key, best);
+      int kb2 = kblocks;
+      splitk = legal(best, kb2);
+      kbps = kb2;
+    }
+  }
+  count_launches(1 + (mi.sliced ? 2 : 0) + (splitk > 1 ? 2 : 1));
+  run(splitk, kbps, beta, C);
   return true;
 }
 
