@@ -652,6 +652,31 @@ __device__ void pack_job(const PackJob& J, int bx) {
       }
       const size_t base = (size_t)rowid * J.k_pad;
       const int k1 = min(J.k_pad, (seg + 1) * J.kseg);
+      if (MODE == TC_BF16X3 && J.kstr == 1 && !ksh && ((uintptr_t)row & 15) == 0 && (J.kseg & 63) == 0) {
+        // contiguous rows: two elements per lane (16-byte loads, 4-byte bf16x2 stores)
+        for (int k0 = seg * J.kseg + 2 * lane; k0 < k1; k0 += 64 * (PACK_UNROLL / 2)) {
+          double2 x[PACK_UNROLL / 2];
+#pragma unroll
+          for (int u = 0; u < PACK_UNROLL / 2; ++u) {
+            const int k = k0 + 64 * u;
+            x[u] = make_double2(0.0, 0.0);
+            if (live && k + 1 < J.K && k < k1) x[u] = *reinterpret_cast<const double2*>(row + k);
+            else if (live && k < J.K && k < k1) x[u].x = row[k];
+          }
+#pragma unroll
+          for (int u = 0; u < PACK_UNROLL / 2; ++u) {
+            const int k = k0 + 64 * u;
+            if (k >= k1) continue;
+            const float f0 = double_bits_to_float((unsigned long long)__double_as_longlong(x[u].x));
+            const float f1 = double_bits_to_float((unsigned long long)__double_as_longlong(x[u].y));
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(f0 - __low2float(h), f1 - __high2float(h));
+            *reinterpret_cast<__nv_bfloat162*>((__nv_bfloat16*)J.o0 + base + k) = h;
+            *reinterpret_cast<__nv_bfloat162*>((__nv_bfloat16*)J.o1 + base + k) = l;
+          }
+        }
+        continue;
+      }
       for (int k0 = seg * J.kseg + lane; k0 < k1; k0 += 32 * PACK_UNROLL) {
         double x[PACK_UNROLL];  // all loads in flight before the first use
 #pragma unroll

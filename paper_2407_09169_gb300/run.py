@@ -1,6 +1,7 @@
 """Command-line stepping of one workload through the C ABI.
 
     python -m paper_2407_09169_gb300.run --workload large --precision fp32 --steps 1
+    python -m paper_2407_09169_gb300.run --adjoint --precision fp32 --steps 4 --ckpt 2
 
 Builds the library if needed, creates a context for the named workload
 (workload.WORKLOADS, or --paper for the paper's flow case at that grid and
@@ -32,9 +33,20 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--paper", action="store_true", help="the paper's flow case at the workload's grid and chi")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="run qtt_grad on the adjoint configuration (workload.make_adjoint_params) instead")
+    ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval of --adjoint")
     args = ap.parse_args(argv)
     qbuild.build()
     w = workload.WORKLOADS[args.workload]
+    if args.adjoint:
+        p = workload.make_adjoint_params(seed=args.seed, precision=args.precision)
+        t0 = time.perf_counter()
+        with q.qtt_init(p) as ctx:
+            J, g = ctx.grad(args.steps, args.ckpt)
+        print(json.dumps({"J": J, "grad": g.tolist(), "names": q.grad_param_names(p),
+                          "wall_s": time.perf_counter() - t0}))
+        return
     if args.paper:
         p = workload.make_paper_params(bits=w["bits"], chi=w["chi_max"], seed=args.seed, precision=args.precision)
     else:
