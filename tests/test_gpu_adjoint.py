@@ -39,11 +39,21 @@ def exact_params(bits, **kw):
     return p
 
 
-@pytest.mark.parametrize("bits,steps,ckpt", [([2, 2, 2, 2, 2], 4, 0), ([2, 2, 3, 2, 3], 3, 2)])
-def test_exact_adjoint_matches_oracle(bits, steps, ckpt):
+@pytest.mark.parametrize("bits,steps,ckpt,flow", [([2, 2, 2, 2, 2], 4, 0, 0), ([2, 2, 3, 2, 3], 3, 2, 0),
+                                                  ([2, 2, 2, 2, 2], 3, 1, 1)])
+def test_exact_adjoint_matches_oracle(bits, steps, ckpt, flow):
     """Untruncated FP64: the GPU adjoint is the exact gradient of the
-    discrete map, like the oracle's."""
-    p = with_ic_modes(exact_params(bits), 3)
+    discrete map, like the oracle's (flow 1: the paper's jet through a
+    Taylor-Green vortex and its Gaussian step initial PDF, with seeded
+    velocity modes added)."""
+    if flow == 1:
+        p = workload.make_paper_params(bits=2, chi=32, umodes=workload.draw_velocity_modes(0), da=0.7)
+        p["bits"] = list(bits)
+        N = sum(p["bits"])
+        p["chi_max"], p["svd_rel_tol"], p["exact"] = 2 ** (N // 2), 0.0, 1
+        p = with_ic_modes(p, 3)
+    else:
+        p = with_ic_modes(exact_params(bits), 3)
     with pkg.qtt_init(p) as ctx:
         J, g = ctx.grad(steps, ckpt)
         s = ctx.scalars()

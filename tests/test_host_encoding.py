@@ -80,6 +80,15 @@ def test_moving_gaussian_by_tensor_cross(bits, sigma, amp):
         assert all(int(ranks[c]) == 1 for c in cuts), ranks
 
 
+def test_moving_gaussian_with_modulation():
+    p = _params([3, 2, 3, 2, 2], ic_kind=2, ic_sigma=0.12, ic_blend_width=0.15, ic_c_hi=[0.5, 0.45],
+                icmodes=[dict(k=[1, 0, -1], phase=0.3, amp=0.2), dict(k=[0, 2, 1], phase=1.1, amp=-0.1)])
+    g = oracle.make_grid(p["bits"])
+    ref = oracle.initial_pdf(p, g).ravel()
+    got = pkg.qtt_host_dense(p, 0, ref.size)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
 def test_velocity_encoding():
     p = _params([1, 1, 4, 3, 5])
     g = oracle.make_grid(p["bits"])
