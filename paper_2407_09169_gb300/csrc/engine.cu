@@ -494,10 +494,7 @@ void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, co
     gemm(bl, Ll, br, wr, 2, 1.0, mv(A, 2LL * br, 1, 0, br), mv(X1, 2LL * Ll, 1, (long long)br * 2 * Ll, Ll), 0.0,
          ov(X2, 2LL * wr * Ll, 1, Ll, (long long)wr * Ll), role);
     // W_n[(h,a)][l] = sum_s sum_h' H[h][s][h'] X2[a][s][h'][l], one product per s
-    // accumulated in FP64 (H is shared by every a).  Fusing the two into one
-    // product over K = 2 w_{n+1} changes how the tensor cores' FP32
-    // accumulation is chunked, and with the BF16X3 form that raised the drift
-    // of <1> after ten 2^4-point steps from -2.1e-6 to -7.6e-5.
+    // accumulated in FP64 (H is shared by every a).
     for (int s = 0; s < 2; ++s)
       gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1), mv(X2 + (size_t)s * wr * Ll, Ll, 1, 2LL * wr * Ll),
            s == 0 ? 0.0 : 1.0, ov(Wn, (long long)bl * Ll, 1, Ll), role);

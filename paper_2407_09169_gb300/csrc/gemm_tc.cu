@@ -1048,9 +1048,9 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   const int kblocks = L.k_pad / L.kb;
   // split K when the tile grid is small; the exact-slice modes also cap the
   // depth one accumulator sums so that its partial sums stay exact integers.
-  // (Capping the floating modes' accumulation depth as well -- two k-blocks
-  // per accumulator -- made the BF16X3 drift of <1> worse, -2.1e-6 -> -6.6e-5
-  // after ten 2^4-point steps, so they keep the tile-grid split only.)
+  // (Capping the floating modes' accumulation depth as well -- 1, 2 or 4
+  // k-blocks per accumulator -- did not make BF16X3 more accurate: its error
+  // is that of its 16-bit operands; so they keep the tile-grid split only.)
   int cap = max_kb_per_split;
   if (mi.exact_kb > 0 && (cap <= 0 || cap > mi.exact_kb)) cap = mi.exact_kb;
   const long long tiles = (long long)(L.m_pad / BM) * (L.n_pad / L.bn) * batch;
