@@ -649,12 +649,8 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
       if (qr_refine_) {
         // one Newton-Schulz step in FP64, Q <- Q (3 I - Q^T Q) / 2: the span of
         // the float Q, orthonormal to double round-off
-        {
-          TimeScope ts(timer_, TM_OTHER, st_);
-          fill_eye(st_, gq_, rn);
-        }
-        gemm64(rn, rn, 2 * r, 1, 1, -0.5, mv(X1_, 1, rn), mv(X1_, rn, 1), 1.5, ov(gq_, rn, 1));
-        gemm64(2 * r, rn, rn, 1, 1, 1.0, mv(X1_, rn, 1), mv(gq_, rn, 1), 0.0, ov(mid_.core(n), rn, 1));
+        TimeScope ts(timer_, TM_GEMM, st_, 4.0 * (2.0 * r) * rn * rn);
+        newton_schulz_step(st_, 2 * r, rn, X1_, gq_, mid_.core(n));
       }
       if (n + 1 < N) zip_all(n + 1, r, true, rn);
     }

@@ -129,6 +129,54 @@ __global__ void scale_out_kernel(int M, int N, int inner, int batch, double beta
     *c = (beta == 0.0) ? 0.0 : beta * (*c);
   }
 }
+// One Newton-Schulz step of an almost-orthonormal Q (m x n, row-major):
+// out = Q (3 I - Q^T Q) / 2, in two launches without a K split (the factors
+// of the reduced forms' QR are at most 288 x 144, so every dot product fits
+// one thread): G = 1.5 I - 0.5 Q^T Q, then out = Q G; 16 x 16 output tile per
+// block, operand strips staged through shared memory in chunks of 32.
+constexpr int NS_T = 16;
+
+__global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, const double* __restrict__ Q,
+                                                      double* __restrict__ G) {
+  __shared__ double A[32][NS_T + 1], B[32][NS_T + 1];
+  const int tx = threadIdx.x & (NS_T - 1), ty = threadIdx.x / NS_T;
+  const int i0 = blockIdx.y * NS_T, j0 = blockIdx.x * NS_T;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    for (int e = threadIdx.x; e < 32 * NS_T; e += blockDim.x) {
+      const int kk = e / NS_T, c = e - kk * NS_T, k = k0 + kk;
+      A[kk][c] = (k < m && i0 + c < n) ? Q[(size_t)k * n + i0 + c] : 0.0;
+      B[kk][c] = (k < m && j0 + c < n) ? Q[(size_t)k * n + j0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc = fma(A[kk][ty], B[kk][tx], acc);
+    __syncthreads();
+  }
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < n && j < n) G[(size_t)i * n + j] = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+}
+
+__global__ void __launch_bounds__(256) ns_apply_kernel(int m, int n, const double* __restrict__ Q,
+                                                       const double* __restrict__ G, double* __restrict__ out) {
+  __shared__ double A[NS_T][33], B[32][NS_T + 1];
+  const int tx = threadIdx.x & (NS_T - 1), ty = threadIdx.x / NS_T;
+  const int r0 = blockIdx.y * NS_T, c0 = blockIdx.x * NS_T;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int e = threadIdx.x; e < NS_T * 32; e += blockDim.x) {
+      const int rr = e / 32, kk = e - rr * 32;  // A[rr][kk] = Q[r0 + rr][k0 + kk]
+      A[rr][kk] = (r0 + rr < m && k0 + kk < n) ? Q[(size_t)(r0 + rr) * n + k0 + kk] : 0.0;
+      const int kb = e / NS_T, cc = e - kb * NS_T;  // B[kb][cc] = G[k0 + kb][c0 + cc]
+      B[kb][cc] = (k0 + kb < n && c0 + cc < n) ? G[(size_t)(k0 + kb) * n + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc = fma(A[ty][kk], B[kk][tx], acc);
+    __syncthreads();
+  }
+  if (r0 + ty < m && c0 + tx < n) out[(size_t)(r0 + ty) * n + c0 + tx] = acc;
+}
 }  // namespace
 
 void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int batch, double alpha, const double* ws,
@@ -181,6 +229,14 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
     launch_pdl(splitk_reduce_kernel, dim3((unsigned)blocks), dim3(256), 0, st, M, N, inner, splitk, batch, alpha,
              (const double*)ws, beta, C);
   }
+}
+
+void newton_schulz_step(cudaStream_t st, int m, int n, const double* Q, double* G, double* out) {
+  if (m <= 0 || n <= 0) return;
+  count_launches(2);
+  const unsigned bn = (unsigned)((n + NS_T - 1) / NS_T), bm = (unsigned)((m + NS_T - 1) / NS_T);
+  ns_gram_kernel<<<dim3(bn, bn), 256, 0, st>>>(m, n, Q, G);
+  ns_apply_kernel<<<dim3(bn, bm), 256, 0, st>>>(m, n, Q, G, out);
 }
 
 }  // namespace qtt

@@ -133,6 +133,9 @@ void fill_gaussian_sketch(cudaStream_t st, const Chain& om, size_t max_core, uns
 void sum_arrays(cudaStream_t st, double* out, const double* const* in, int n_in, size_t n);
 // p = the n x n identity (row-major).
 void fill_eye(cudaStream_t st, double* p, int n);
+// One Newton-Schulz step in FP64 of an almost-orthonormal Q (m x n,
+// row-major): out = Q (3 I - Q^T Q) / 2, G (n x n) receives 1.5 I - 0.5 Q^T Q.
+void newton_schulz_step(cudaStream_t st, int m, int n, const double* Q, double* G, double* out);
 // *c += 1 on the device.
 void bump_counter(cudaStream_t st, unsigned long long* c);
 
