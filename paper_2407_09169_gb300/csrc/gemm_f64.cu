@@ -129,6 +129,41 @@ __global__ void scale_out_kernel(int M, int N, int inner, int batch, double beta
     *c = (beta == 0.0) ? 0.0 : beta * (*c);
   }
 }
+// Products whose 64 x 64 tile grid is too small for the GPU (the bond-sized
+// FP64 products: right Grams of the truncation, 136 x 136 x 272) otherwise
+// need a K split and a reduction launch.  16 x 16 output tiles give them
+// enough blocks instead, each thread summing its whole dot product (K in
+// chunks of 32 staged through shared memory), with the strided views and
+// alpha / beta of gemm_f64.
+__global__ void __launch_bounds__(256) gemm_f64_t16_kernel(int M, int N, int K, int inner, double alpha, MatView A,
+                                                           MatView B, double beta, OutView C) {
+  pdl_trigger();
+  pdl_wait();
+  __shared__ double As[16][33], Bs[32][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16;
+  const int b = blockIdx.z, bo = b / inner, bi = b - bo * inner;
+  const double* Ap = A.p + bo * A.so + bi * A.si;
+  const double* Bp = B.p + bo * B.so + bi * B.si;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int e = threadIdx.x; e < 512; e += 256) {
+      const int rr = e >> 5, kk = e & 31;  // As[rr][kk] = A(m0 + rr, k0 + kk)
+      As[rr][kk] = (m0 + rr < M && k0 + kk < K) ? Ap[(long long)(m0 + rr) * A.rs + (long long)(k0 + kk) * A.cs] : 0.0;
+      const int kb = e >> 4, cc = e & 15;  // Bs[kb][cc] = B(k0 + kb, n0 + cc)
+      Bs[kb][cc] = (k0 + kb < K && n0 + cc < N) ? Bp[(long long)(k0 + kb) * B.rs + (long long)(n0 + cc) * B.cs] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  if (m0 + ty < M && n0 + tx < N) {
+    double* c = C.p + bo * C.so + bi * C.si + (long long)(m0 + ty) * C.rs + (long long)(n0 + tx) * C.cs;
+    *c = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*c);
+  }
+}
+
 // One Newton-Schulz step of an almost-orthonormal Q (m x n, row-major):
 // out = Q (3 I - Q^T Q) / 2, in two launches without a K split (the factors
 // of the reduced forms' QR are at most 288 x 144, so every dot product fits
@@ -212,6 +247,15 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
     return;
   }
   int splitk = gemm_split_k(M, N, K, batch);
+  {
+    const long long t16 = (long long)((M + 15) / 16) * ((N + 15) / 16) * batch;
+    if (splitk > 1 && t16 >= 64 && K <= 2048 && batch <= 65535) {
+      count_launches(1);
+      launch_pdl(gemm_f64_t16_kernel, dim3((N + 15) / 16, (M + 15) / 16, batch), dim3(256), 0, st, M, N, K, inner, alpha,
+                 A, B, beta, C);
+      return;
+    }
+  }
   if (splitk > 1 && (ws == nullptr || (size_t)splitk * batch * (size_t)M * N > ws_elems)) splitk = 1;
   int kchunk = (K + splitk - 1) / splitk;
   kchunk = ((kchunk + BK - 1) / BK) * BK;
