@@ -1053,16 +1053,16 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
   // is that of its 16-bit operands; so they keep the tile-grid split only.)
   int cap = max_kb_per_split;
   if (mi.exact_kb > 0 && (cap <= 0 || cap > mi.exact_kb)) cap = mi.exact_kb;
-  const long long tiles = (long long)(L.m_pad / BM) * (L.n_pad / L.bn) * batch;
   // The split count minimises a cost model: waves of CTAs x k-blocks per
   // split x the time of one k-block (its operand bytes at ~60 GB/s per SM),
   // plus the FP64 partial tiles written, re-read and reduced (2 s + 1 passes
   // over M x N at ~3 TB/s).  Short K with many tiles stays unsplit.
-  int splitk = 1;
-  {
-    const double kb_us = (double)(mi.na * BM + mi.nb * L.bn) * 128.0 / 60e3;
+  auto model_split = [&](int bn) {
+    const long long tiles = (long long)(L.m_pad / BM) * (L.n_pad / bn) * batch;
+    const double kb_us = (double)(mi.na * BM + mi.nb * bn) * 128.0 / 60e3;
     const double mn_bytes = (double)M * N * batch * 8.0;
     double best = 0.0;
+    int sbest = 1;
     for (int s = 1; s <= 64 && s <= kblocks; ++s) {
       const int per = (kblocks + s - 1) / s;
       if (s > 1 && (long long)(s - 1) * per >= kblocks) continue;  // an empty split
@@ -1070,10 +1070,12 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
       const double t = waves * per * kb_us + (s > 1 ? (2.0 * s + 1.0) * mn_bytes / 3e6 : 0.0);
       if (s == 1 || t < best) {
         best = t;
-        splitk = s;
+        sbest = s;
       }
     }
-  }
+    return sbest;
+  };
+  int splitk = model_split(L.bn);
   // a split count as launched: k-blocks per split within the exactness cap,
   // partial tiles that fit the workspace (0: not launchable)
   auto legal = [&](int s_req, int& kbps_out) -> int {
@@ -1084,19 +1086,19 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     kbps_out = kb;
     return s2;
   };
-  auto run = [&](int sk, int kb, double beta_, OutView C_) {
+  auto run = [&](int bn, int sk, int kb, double beta_, OutView C_) {
     double* wsp = sk > 1 ? ws : nullptr;
 #define QTT_TC_LAUNCH(MODE_, BN_, ST_) \
   launch_tc<MODE_, BN_, ST_>(st, pk, M, N, kblocks, kb, sk, inner, batch, batch_a, batch_b, alpha, beta_, C_, wsp, err)
 #define QTT_TC_BN(MODE_, S256, S160, S128, S64)       \
-  switch (L.bn) {                                     \
+  switch (bn) {                                       \
     case 256: QTT_TC_LAUNCH(MODE_, 256, S256); break; \
     case 160: QTT_TC_LAUNCH(MODE_, 160, S160); break; \
     case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
     default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
   }
 #define QTT_TC_BN3(MODE_, S160, S128, S64)            \
-  switch (L.bn) {                                     \
+  switch (bn) {                                       \
     case 160: QTT_TC_LAUNCH(MODE_, 160, S160); break; \
     case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
     default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
@@ -1121,29 +1123,42 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     splitk = 1;
     kbps = kblocks;
   }
-  // Split-K autotuner: the first time a shape is seen outside a graph
-  // capture, the cost model's split, half and double of it and no split are
-  // each timed (CUDA events, three launches after one warm-up, output into
-  // a scratch buffer), and the fastest is kept for every later call of that
-  // shape.  Later steps (and the captured graphs) reuse the choice.
+  // Autotuner of the tile width and the split-K count: the first time a
+  // shape is seen outside a graph capture, the cost model's split for the
+  // padding-chosen tile width, half, double and no split of it, and each
+  // other tile width whose padded N is the same (the packed operands then
+  // serve it unchanged) with its model split and no split, are each timed
+  // (CUDA events, three launches after one warm-up, output into a scratch
+  // buffer), and the fastest is kept for every later call of that shape.
+  // Later steps (and the captured graphs) reuse the choice.
+  int bn = L.bn;
   {
     const TuneKey key{mode, M, N, K, batch, batch_a, batch_b, cap};
     int cached = 0;
     if (tune_lookup(key, cached)) {
       int kb2 = kblocks;
-      const int s2 = legal(cached, kb2);
+      const int s2 = legal(cached % 1000, kb2);
       if (s2 > 0) {
+        bn = cached / 1000;
         splitk = s2;
         kbps = kb2;
       }
     } else if (tune_enabled() && !stream_capturing(st)) {
-      std::vector<int> cands{splitk};
-      for (int c : {1, splitk / 2, splitk * 2}) {
+      std::vector<std::pair<int, int>> cands{{bn, splitk}};
+      auto add = [&](int b, int c) {
         int kb2 = kblocks;
         const int s2 = c >= 1 ? legal(c, kb2) : 0;
-        if (s2 > 0 && std::find(cands.begin(), cands.end(), s2) == cands.end()) cands.push_back(s2);
+        if (s2 > 0 && std::find(cands.begin(), cands.end(), std::make_pair(b, s2)) == cands.end())
+          cands.push_back({b, s2});
+      };
+      for (int c : {1, splitk / 2, splitk * 2}) add(bn, c);
+      for (int b : {256, 160, 128, 64}) {
+        if (b == L.bn || mi.ngroups * b > 512 || (mode == TC_BF16X6 && b == 256)) continue;
+        if ((N + b - 1) / b * b != L.n_pad) continue;
+        add(b, model_split(b));
+        add(b, 1);
       }
-      int best = splitk;
+      std::pair<int, int> best = cands[0];
       if (cands.size() > 1) {
         double* scratch = nullptr;
         const size_t sbytes = (size_t)M * N * batch * sizeof(double);
@@ -1157,18 +1172,18 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
           Cs.si = (long long)M * N;
           Cs.so = Cs.si * inner;
           float best_ms = 1e30f;
-          for (int c : cands) {
+          for (const auto& c : cands) {
             int kb2 = kblocks;
-            const int s2 = legal(c, kb2);
-            run(s2, kb2, 0.0, Cs);  // warm-up
+            const int s2 = legal(c.second, kb2);
+            run(c.first, s2, kb2, 0.0, Cs);  // warm-up
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 3; ++r) run(s2, kb2, 0.0, Cs);
+            for (int r = 0; r < 3; ++r) run(c.first, s2, kb2, 0.0, Cs);
             cudaEventRecord(e1, st);
             float ms = 1e30f;
             if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best_ms) {
               best_ms = ms;
-              best = s2;
+              best = {c.first, s2};
             }
           }
         }
@@ -1180,14 +1195,15 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
         }
         cudaGetLastError();
       }
-      tune_store(key, best);
+      tune_store(key, best.first * 1000 + best.second);
       int kb2 = kblocks;
-      splitk = legal(best, kb2);
+      bn = best.first;
+      splitk = legal(best.second, kb2);
       kbps = kb2;
     }
   }
   count_launches(1 + (mi.sliced ? 2 : 0) + (splitk > 1 ? 2 : 1));
-  run(splitk, kbps, beta, C);
+  run(bn, splitk, kbps, beta, C);
   return true;
 }
 
