@@ -8,9 +8,10 @@
 // Three kernels, so that the FP64 work does not all sit on one SM:
 //   1. eig_tridiag_ql (one block): Householder reduction to tridiagonal form
 //      (matrix in shared memory when it fits, lower-triangle updates), then
-//      the implicit-shift QL iteration on (d, e) run by one thread, which
-//      records every Givens rotation of every sweep in a list, and a stable
-//      descending order of the eigenvalues;
+//      the implicit-shift QL iteration on (d, e) run by one warp (one lane
+//      carries the rotation chain, which records every Givens rotation of
+//      every sweep in a list), and a stable descending order of the
+//      eigenvalues;
 //   2. eig_apply_rotations (one thread per row of the eigenvector matrix Z of
 //      the tridiagonal problem, over several blocks): replays the rotation
 //      list on its row;
@@ -215,8 +216,12 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
     else if (c == i) W[L.A + x] = tauv[i];
   }
 
-  // ---- implicit QL with a Wilkinson-type shift, rotations recorded per sweep
-  if (tid == 0) {
+  // ---- implicit QL with a Wilkinson-type shift, rotations recorded per sweep.
+  // Warp 0 runs it: lane 0 carries the rotation chain; the search for the
+  // next negligible off-diagonal (32 entries per ballot) and the shift of the
+  // trailing diagonal are spread over the lanes.  The loop control is the
+  // same in every lane (computed from the same shared values).
+  if (warp == 0) {
     const T eps = Eps<T>::v();
     T f = 0, tst1 = 0;
     int nseg = 0;
@@ -225,57 +230,76 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
       const T hl = fabs(d[l]) + fabs(e[l]);
       tst1 = hl > tst1 ? hl : tst1;
       for (int iter = 0;; ++iter) {
-        int m = l;
-        while (m < n - 1 && fabs(e[m]) > eps * tst1) ++m;
+        int m = n - 1;
+        for (int base = l; base < n - 1; base += 32) {
+          const int i = base + lane;
+          const bool small = i < n - 1 && !(fabs(e[i]) > eps * tst1);
+          const unsigned bal = __ballot_sync(0xffffffffu, small);
+          if (bal) {
+            m = base + __ffs(bal) - 1;
+            break;
+          }
+        }
         if (m == l) break;
         if (iter >= QL_MAX_SWEEPS || nseg >= (int)L.S || off + (size_t)(m - l) > L.R) {
-          atomicOr(status, 2);
+          if (lane == 0) atomicOr(status, 2);
           break;
         }
         T g = d[l];
         T p = (d[l + 1] - g) / ((T)2 * e[l]);
         T r = (T)1 / rhyp(p, (T)1);
         if (p < 0) r = -r;
-        d[l] = e[l] / (p + r);
-        d[l + 1] = e[l] * (p + r);
-        const T dl1 = d[l + 1];
-        T h = g - d[l];
-        for (int i = l + 2; i < n; ++i) d[i] -= h;
+        const T dl0 = e[l] / (p + r);
+        const T dl1 = e[l] * (p + r);
+        const T h = g - dl0;
+        __syncwarp();
+        if (lane == 0) {
+          d[l] = dl0;
+          d[l + 1] = dl1;
+        }
+        for (int i = l + 2 + lane; i < n; i += 32) d[i] -= h;
         f += h;
-        p = d[m];
-        T c = 1, c2 = 1, c3 = 1, s = 0, s2 = 0;
-        const T el1 = e[l + 1];
-        seg_lo[nseg] = l;
-        seg_hi[nseg] = m - 1;
-        seg_off[nseg] = (int)off;
-        for (int i = m - 1; i >= l; --i) {
-          c3 = c2;
-          c2 = c;
-          s2 = s;
-          const T ei = e[i];
-          g = c * ei;
-          h = c * p;
-          const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
-          const T cn = p * rr, sn = ei * rr;
-          r = p * cn + ei * sn;  // hypot(p, e_i)
-          e[i + 1] = s * r;      // previous sine
-          s = sn;
-          c = cn;
-          p = c * d[i] - s * g;
-          d[i + 1] = h + s * (c * g + s * d[i]);
-          rcg[off + (size_t)(m - 1 - i)] = c;
-          rsg[off + (size_t)(m - 1 - i)] = s;
+        __syncwarp();
+        if (lane == 0) {
+          p = d[m];
+          T c = 1, c2 = 1, c3 = 1, s = 0, s2 = 0;
+          const T el1 = e[l + 1];
+          seg_lo[nseg] = l;
+          seg_hi[nseg] = m - 1;
+          seg_off[nseg] = (int)off;
+          for (int i = m - 1; i >= l; --i) {
+            c3 = c2;
+            c2 = c;
+            s2 = s;
+            const T ei = e[i];
+            g = c * ei;
+            const T hh = c * p;
+            const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
+            const T cn = p * rr, sn = ei * rr;
+            r = p * cn + ei * sn;  // hypot(p, e_i)
+            e[i + 1] = s * r;      // previous sine
+            s = sn;
+            c = cn;
+            p = c * d[i] - s * g;
+            d[i + 1] = hh + s * (c * g + s * d[i]);
+            rcg[off + (size_t)(m - 1 - i)] = c;
+            rsg[off + (size_t)(m - 1 - i)] = s;
+          }
+          p = -s * s2 * c3 * el1 * e[l] / dl1;
+          e[l] = s * p;
+          d[l] = c * p;
         }
         off += (size_t)(m - l);
         ++nseg;
-        p = -s * s2 * c3 * el1 * e[l] / dl1;
-        e[l] = s * p;
-        d[l] = c * p;
+        __syncwarp();
       }
-      d[l] += f;
-      e[l] = 0;
+      if (lane == 0) {
+        d[l] += f;
+        e[l] = 0;
+      }
+      __syncwarp();
     }
-    I[L.nseg] = nseg;
+    if (lane == 0) I[L.nseg] = nseg;
   }
   __syncthreads();
   // ---- stable descending order of the eigenvalues
