@@ -58,7 +58,9 @@ __device__ __forceinline__ float rhyp(float a, float b) { return rhypotf(a, b); 
 // the scaled form.
 __device__ __forceinline__ double rhyp_fast(double a, double b) {
   const double q = fma(a, a, b * b);
-  return (q > 1e-300 && q < 1e300) ? rsqrt(q) : rhypot(a, b);
+  // normal range test on the exponent bits (integer pipe): 2^-996 .. 2^996
+  const int ex = (__double2hiint(q) >> 20) & 0x7ff;
+  return (ex > 27 && ex < 2019) ? rsqrt(q) : rhypot(a, b);
 }
 __device__ __forceinline__ float rhyp_fast(float a, float b) {
   const float q = fmaf(a, a, b * b);

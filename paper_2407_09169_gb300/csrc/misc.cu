@@ -126,9 +126,19 @@ __global__ void left_weight_env_kernel(Chain f, Chain w, int nsites, int max_bon
     const double* W = w.core[n];
     for (int x = threadIdx.x; x < ql * 2 * br; x += blockDim.x) {
       const int q = x / (2 * br), sb = x - q * 2 * br;
-      double acc = 0.0;
-      for (int b = 0; b < bl; ++b) acc += E[q * max_bond + b] * A[(size_t)b * 2 * br + sb];
-      X[q * 2 * max_bond + sb] = acc;
+      // four independent partial sums: four loads of A in flight per thread
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int b = 0;
+      for (; b + 3 < bl; b += 4) {
+        const double v0 = A[(size_t)b * 2 * br + sb], v1 = A[(size_t)(b + 1) * 2 * br + sb];
+        const double v2 = A[(size_t)(b + 2) * 2 * br + sb], v3 = A[(size_t)(b + 3) * 2 * br + sb];
+        a0 += E[q * max_bond + b] * v0;
+        a1 += E[q * max_bond + b + 1] * v1;
+        a2 += E[q * max_bond + b + 2] * v2;
+        a3 += E[q * max_bond + b + 3] * v3;
+      }
+      for (; b < bl; ++b) a0 += E[q * max_bond + b] * A[(size_t)b * 2 * br + sb];
+      X[q * 2 * max_bond + sb] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < qr * br; x += blockDim.x) {
@@ -170,9 +180,19 @@ __global__ void left_weight_envs_kernel(Chain f, const Chain* __restrict__ wchai
     const double* W = w.core[n];
     for (int x = threadIdx.x; x < ql * 2 * br; x += blockDim.x) {
       const int q = x / (2 * br), sb = x - q * 2 * br;
-      double acc = 0.0;
-      for (int b = 0; b < bl; ++b) acc += E[q * max_bond + b] * A[(size_t)b * 2 * br + sb];
-      X[q * 2 * max_bond + sb] = acc;
+      // four independent partial sums: four loads of A in flight per thread
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int b = 0;
+      for (; b + 3 < bl; b += 4) {
+        const double v0 = A[(size_t)b * 2 * br + sb], v1 = A[(size_t)(b + 1) * 2 * br + sb];
+        const double v2 = A[(size_t)(b + 2) * 2 * br + sb], v3 = A[(size_t)(b + 3) * 2 * br + sb];
+        a0 += E[q * max_bond + b] * v0;
+        a1 += E[q * max_bond + b + 1] * v1;
+        a2 += E[q * max_bond + b + 2] * v2;
+        a3 += E[q * max_bond + b + 3] * v3;
+      }
+      for (; b < bl; ++b) a0 += E[q * max_bond + b] * A[(size_t)b * 2 * br + sb];
+      X[q * 2 * max_bond + sb] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < qr * br; x += blockDim.x) {
