@@ -684,22 +684,30 @@ void Engine::gram_pass(const DevMps& g) {
 }
 
 void Engine::project_cores(const DevMps& g, DevMps& out) {
-  // out core n = U_n^T A_n U_{n+1}, with U = identity on bonds that keep all directions
+  // out core n = U_n^T A_n U_{n+1}, with U = identity on bonds that keep all
+  // directions.  The cores are independent: they are spread over the main
+  // stream and the lanes (each with its own scratch), then joined.
+  const int nl = nlanes_;
+  if (nl > 1) fork_lanes(nl - 1);
   for (int n = 0; n < N_; ++n) {
+    lane_ = n % nl;
+    double* scratch = lane_x2_[lane_];
     const int rl = g.b[n], rr = g.b[n + 1], Dl = out.b[n], Dr = out.b[n + 1];
     const double* U_l = tU_[n];
     const double* U_r = tU_[n + 1];
     const double* X = g.core(n);
     if (U_l) {  // X = U_l^T A_n : [Dl x 2 rr]
-      gemm(Dl, 2 * rr, rl, 1, 1, 1.0, mv(U_l, 1, Dl), mv(g.core(n), 2LL * rr, 1), 0.0, ov(X2_, 2LL * rr, 1));
-      X = X2_;
+      gemm(Dl, 2 * rr, rl, 1, 1, 1.0, mv(U_l, 1, Dl), mv(g.core(n), 2LL * rr, 1), 0.0, ov(scratch, 2LL * rr, 1));
+      X = scratch;
     }
     if (U_r) {  // out = X U_r : [(2 Dl) x Dr]
       gemm(2 * Dl, Dr, rr, 1, 1, 1.0, mv(X, rr, 1), mv(U_r, Dr, 1), 0.0, ov(out.core(n), Dr, 1));
     } else {
-      QTT_CUDA(cudaMemcpyAsync(out.core(n), X, sizeof(double) * (size_t)Dl * 2 * Dr, cudaMemcpyDeviceToDevice, st_));
+      QTT_CUDA(cudaMemcpyAsync(out.core(n), X, sizeof(double) * (size_t)Dl * 2 * Dr, cudaMemcpyDeviceToDevice, cur()));
     }
   }
+  lane_ = 0;
+  if (nl > 1) join_lanes(nl - 1);
 }
 
 void Engine::run_stage_exact(Term* terms, int nt, DevMps& out) {
