@@ -81,7 +81,7 @@ void small_gemm(cudaStream_t st, bool fp32, int M, int N, int K, int outer, int 
 
 // Thin Householder QR of an m x n row-major matrix (m >= n): Q (m x n,
 // row-major) overwrites Qout.  Computed in float (prec_bits 32) or double;
-// work must hold 2 * m * n + n elements of that type.  *status != 0 on failure.
+// work must hold 2 * m * n + n doubles.  *status != 0 on failure.
 void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void* work, int prec_bits,
              int* status);
 

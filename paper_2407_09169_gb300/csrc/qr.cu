@@ -312,7 +312,8 @@ __device__ __forceinline__ bool qrr_wait(uint64_t* bar, int j, int lane, int* st
 
 template <int RPL, int CPW>
 __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const double* __restrict__ A,
-                                                             double* __restrict__ Qout, int* status) {
+                                                             double* __restrict__ Qout, float* __restrict__ Vg,
+                                                             int* status) {
   pdl_trigger();
   pdl_wait();
   extern __shared__ __align__(16) unsigned char qr_smem[];
@@ -413,6 +414,12 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
     }
   }
   __syncthreads();  // every reflector is published and every warp is done with its columns
+  if (Vg) {  // Q is formed by qr_formq_kernel over several blocks: hand over the reflectors and tau
+    const int nv = n * LDV / 4;
+    for (int e = tid; e < nv; e += QRR_THREADS) reinterpret_cast<float4*>(Vg)[e] = reinterpret_cast<const float4*>(V)[e];
+    for (int c = tid; c < n; c += QRR_THREADS) Vg[(size_t)n * LDV + c] = tau[c];
+    return;
+  }
   // Q = H_0 ... H_{n-1} [I; 0], accumulated backwards in the same registers
 #pragma unroll
   for (int q = 0; q < CPW; ++q) {
@@ -481,18 +488,83 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
   for (int e = tid; e < m * n; e += QRR_THREADS) Qout[e] = (double)V[e];
 }
 
+// Q = H_0 ... H_{n-1} [I; 0] from the reflectors that qr_reg_kernel hands over
+// (Vg: n rows of LDV = 32 RPL floats, then tau[n]).  The columns of Q are
+// independent, Q e_c = H_0 ... H_c e_c (H_j e_c = e_c for j > c, since v_j
+// vanishes above row j), so each warp forms one column, 16 per block, over
+// ceil(n / 16) blocks; the block stages the reflectors 0 .. its last column in
+// shared memory and writes its 16 columns of Q row by row.
+template <int RPL>
+__global__ void __launch_bounds__(QRR_THREADS) qr_formq_kernel(int m, int n, const float* __restrict__ Vg,
+                                                               double* __restrict__ Qout) {
+  pdl_trigger();
+  pdl_wait();
+  constexpr int LDV = 32 * RPL;
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  const int c0 = blockIdx.x * QRR_WARPS;
+  const int nr = min(n, c0 + QRR_WARPS);  // reflectors 0 .. nr - 1 are needed
+  float* V = (float*)qr_smem;               // [nr][LDV]
+  float* tau = V + (size_t)nr * LDV;        // [nr]
+  float* S = tau + ((nr + 3) & ~3);         // [32 RPL][QRR_WARPS] staging of the block's columns
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nv = nr * LDV / 4;
+  for (int e = tid; e < nv; e += QRR_THREADS) reinterpret_cast<float4*>(V)[e] = reinterpret_cast<const float4*>(Vg)[e];
+  for (int c = tid; c < nr; c += QRR_THREADS) tau[c] = Vg[(size_t)n * LDV + c];
+  __syncthreads();
+  const int c = c0 + warp;
+  float x[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) x[k] = (lane + 32 * k == c) ? 1.f : 0.f;
+  if (c < n) {
+    for (int j = c; j >= 0; --j) {
+      const float t = tau[j];
+      if (t == 0.f) continue;
+      float v[RPL], d = 0.f;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        v[k] = V[(size_t)j * LDV + lane + 32 * k];
+        d += v[k] * x[k];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const float f = -t * d;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) x[k] += f * v[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) S[(size_t)(lane + 32 * k) * QRR_WARPS + warp] = x[k];
+  __syncthreads();
+  const int nc = nr - c0;
+  for (int e = tid; e < m * QRR_WARPS; e += QRR_THREADS) {
+    const int i = e / QRR_WARPS, cc = e - i * QRR_WARPS;
+    if (cc < nc) Qout[(size_t)i * n + c0 + cc] = (double)S[e];
+  }
+}
+
+// split: hand the reflectors over to qr_formq_kernel (work: n (32 RPL + 1)
+// floats) instead of accumulating Q in the factorising block.
 template <int RPL, int CPW>
-bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, int* status) {
+bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, int* status, float* split) {
   if (m > 32 * RPL || n > QRR_WARPS * CPW) return false;
   const size_t smem = ((size_t)n * 32 * RPL + (size_t)n) * sizeof(float) + 8 + (size_t)n * sizeof(uint64_t);
+  constexpr int NMAX = QRR_WARPS * CPW;
+  auto formq_smem = [](int nr) {
+    return ((size_t)nr * 32 * RPL + (size_t)((nr + 3) & ~3) + (size_t)32 * RPL * QRR_WARPS) * sizeof(float);
+  };
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(qr_reg_kernel<RPL, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(((size_t)QRR_WARPS * CPW * 32 * RPL + QRR_WARPS * CPW) * sizeof(float) + 8 +
-                               (size_t)QRR_WARPS * CPW * sizeof(uint64_t)));
+                         (int)(((size_t)NMAX * 32 * RPL + NMAX) * sizeof(float) + 8 + (size_t)NMAX * sizeof(uint64_t)));
+    cudaFuncSetAttribute(qr_formq_kernel<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)formq_smem(NMAX));
     attr = true;
   }
-  launch_pdl(qr_reg_kernel<RPL, CPW>, dim3(1), dim3(QRR_THREADS), smem, st, m, n, A, Qout, status);
+  launch_pdl(qr_reg_kernel<RPL, CPW>, dim3(1), dim3(QRR_THREADS), smem, st, m, n, A, Qout, split, status);
+  if (split) {
+    const int nb = (n + QRR_WARPS - 1) / QRR_WARPS;
+    launch_pdl(qr_formq_kernel<RPL>, dim3(nb), dim3(QRR_THREADS), formq_smem(n), st, m, n, (const float*)split, Qout);
+    count_launches(1);
+  }
   return true;
 }
 
@@ -519,8 +591,9 @@ void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void*
   }
   count_launches(1);
   if (prec_bits == 32) {
-    if (try_qr_reg<3, 3>(st, m, n, A, Qout, status) || try_qr_reg<5, 5>(st, m, n, A, Qout, status) ||
-        try_qr_reg<9, 9>(st, m, n, A, Qout, status))
+    float* split = (float*)work;  // n (32 RPL + 1) floats <= 2 m n + n doubles, as m >= 8 RPL where used
+    if (try_qr_reg<3, 3>(st, m, n, A, Qout, status, nullptr) || try_qr_reg<5, 5>(st, m, n, A, Qout, status, split) ||
+        try_qr_reg<9, 9>(st, m, n, A, Qout, status, split))
       return;
     launch_qr<float>(st, m, n, A, Qout, work, status);
   }

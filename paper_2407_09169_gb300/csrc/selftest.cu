@@ -105,7 +105,8 @@ std::vector<double> run_selftest(int which) {
     }
     cudaFree(pack);
   } else if (which == 1) {
-    const int shapes[][2] = {{272, 136}, {64, 33}, {256, 256}, {40, 1}, {288, 143}, {150, 77}, {200, 120}, {96, 2}};
+    const int shapes[][2] = {{272, 136}, {64, 33}, {256, 256}, {40, 1}, {288, 143}, {150, 77}, {200, 120}, {96, 2},
+                             {288, 144}, {160, 80}, {97, 49}, {161, 81}, {144, 72}};
     for (auto& sh : shapes) {
       const int m = sh[0], n = sh[1];
       DBuf Y((size_t)m * n), Q((size_t)m * n), W((size_t)2 * m * n + n + 64);
