@@ -234,8 +234,9 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
  * implementation, not the method.  Values written (then one error-flag word):
  *   0  tensor-core GEMM: for 7 shapes x 4 modes (BF16X3, TF32, TF32X3, BF16)
  *      max |C_tc - C_fp64| / max |C_fp64| (-1 when a shape is not supported)
- *   1  Householder QR: for 4 shapes x (FP64, FP32) the orthogonality
- *      max |Q^T Q - I| and the projection residual ||Y - Q Q^T Y|| / ||Y||
+ *   1  Householder QR: for 13 shapes x (FP64, FP32, FP32 followed by one
+ *      FP64 Newton-Schulz step) the orthogonality max |Q^T Q - I| and the
+ *      projection residual ||Y - Q Q^T Y|| / ||Y||
  *   2  eigensolver: for 5 sizes x (FP64, FP32) max |G U - U diag(lam)| / max |G|,
  *      max |U^T U - I| and 1 if the eigenvalues are not descending
  *   3  accumulation bias of the tensor-core GEMM: positive operands, K = 32,

@@ -376,7 +376,7 @@ void Engine::init() {
   Y_ = (double*)dalloc(yy * sizeof(double));
   const size_t rmax = (size_t)max_bond_;
   qrwork_ = (double*)dalloc((2 * (2 * rmax) * rmax + rmax) * sizeof(double));
-  gq_ = (double*)dalloc(rmax * rmax * sizeof(double));
+  gq_ = (double*)dalloc(8 * rmax * rmax * sizeof(double));  // Newton-Schulz partial Grams
   {  // the six weight chains as a device array for the batched environment kernel
     std::vector<Chain> wc(6);
     for (int w = 0; w < 6; ++w) wc[w] = wphi_[w].chain();

@@ -8,6 +8,8 @@
 // every reshape / transpose of the contraction is a view, not a copy.
 // Split-K writes partial tiles to a workspace that a second kernel reduces
 // in a fixed order (deterministic).
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace qtt {
@@ -165,23 +167,40 @@ __global__ void __launch_bounds__(256) gemm_f64_t16_kernel(int M, int N, int K, 
 }
 
 // One Newton-Schulz step of an almost-orthonormal Q (m x n, row-major):
-// out = Q (3 I - Q^T Q) / 2, in two launches without a K split (the factors
-// of the reduced forms' QR are at most 288 x 144, so every dot product fits
-// one thread): G = 1.5 I - 0.5 Q^T Q, then out = Q G; 16 x 16 output tile per
-// block, operand strips staged through shared memory in chunks of 32.
-constexpr int NS_T = 16;
+// out = Q (3 I - Q^T Q) / 2, in two launches.  FP64 issues at two operations
+// per clock per SM, so both are sized to one wave of at most 152 blocks with
+// one block per SM:
+//   ns_gram_kernel: the upper-triangular 16 x 16 tiles of P = Q^T Q only (P is
+//     symmetric), each over a slice of the m rows of Q (split s of S), raw
+//     partial sums to P_s;
+//   ns_apply_kernel: out = Q G with G = 1.5 I - 0.5 sum_s P_s read from the
+//     partials (mirrored below the diagonal tiles), 16 x 17 output tiles
+//     (17 columns: 136 = 8 x 17 fills 136 blocks where 16 x 16 tiles would
+//     make 153, one more than the SMs).
+// Operand strips are staged through shared memory in chunks of 32.
+constexpr int NS_T = 16;      // Gram tile, and rows of the apply tile
+constexpr int NS_C = 17;      // columns of the apply tile
+constexpr int NS_MAX_SPLIT = 8;
 
-__global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, const double* __restrict__ Q,
-                                                      double* __restrict__ G) {
+__global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, int nt, int rows_per_split,
+                                                      const double* __restrict__ Q, double* __restrict__ P) {
   __shared__ double A[32][NS_T + 1], B[32][NS_T + 1];
+  // upper-triangular tile pair (ti <= tj) from the linear block index
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= nt - ti) {
+    rem -= nt - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
   const int tx = threadIdx.x & (NS_T - 1), ty = threadIdx.x / NS_T;
-  const int i0 = blockIdx.y * NS_T, j0 = blockIdx.x * NS_T;
+  const int i0 = ti * NS_T, j0 = tj * NS_T;
+  const int kbeg = blockIdx.y * rows_per_split, kend = min(m, kbeg + rows_per_split);
   double acc = 0.0;
-  for (int k0 = 0; k0 < m; k0 += 32) {
+  for (int k0 = kbeg; k0 < kend; k0 += 32) {
     for (int e = threadIdx.x; e < 32 * NS_T; e += blockDim.x) {
       const int kk = e / NS_T, c = e - kk * NS_T, k = k0 + kk;
-      A[kk][c] = (k < m && i0 + c < n) ? Q[(size_t)k * n + i0 + c] : 0.0;
-      B[kk][c] = (k < m && j0 + c < n) ? Q[(size_t)k * n + j0 + c] : 0.0;
+      A[kk][c] = (k < kend && i0 + c < n) ? Q[(size_t)k * n + i0 + c] : 0.0;
+      B[kk][c] = (k < kend && j0 + c < n) ? Q[(size_t)k * n + j0 + c] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
@@ -189,21 +208,33 @@ __global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, const double
     __syncthreads();
   }
   const int i = i0 + ty, j = j0 + tx;
-  if (i < n && j < n) G[(size_t)i * n + j] = (i == j ? 1.5 : 0.0) - 0.5 * acc;
+  if (i < n && j < n) P[(size_t)blockIdx.y * n * n + (size_t)i * n + j] = acc;
 }
 
-__global__ void __launch_bounds__(256) ns_apply_kernel(int m, int n, const double* __restrict__ Q,
-                                                       const double* __restrict__ G, double* __restrict__ out) {
-  __shared__ double A[NS_T][33], B[32][NS_T + 1];
-  const int tx = threadIdx.x & (NS_T - 1), ty = threadIdx.x / NS_T;
-  const int r0 = blockIdx.y * NS_T, c0 = blockIdx.x * NS_T;
+__global__ void __launch_bounds__(NS_T * NS_C) ns_apply_kernel(int m, int n, int splits, const double* __restrict__ Q,
+                                                               const double* __restrict__ P, double* __restrict__ out) {
+  __shared__ double A[NS_T][33], B[32][NS_C + 1];
+  const int tx = threadIdx.x % NS_C, ty = threadIdx.x / NS_C;
+  const int r0 = blockIdx.y * NS_T, c0 = blockIdx.x * NS_C;
   double acc = 0.0;
   for (int k0 = 0; k0 < n; k0 += 32) {
     for (int e = threadIdx.x; e < NS_T * 32; e += blockDim.x) {
       const int rr = e / 32, kk = e - rr * 32;  // A[rr][kk] = Q[r0 + rr][k0 + kk]
       A[rr][kk] = (r0 + rr < m && k0 + kk < n) ? Q[(size_t)(r0 + rr) * n + k0 + kk] : 0.0;
-      const int kb = e / NS_T, cc = e - kb * NS_T;  // B[kb][cc] = G[k0 + kb][c0 + cc]
-      B[kb][cc] = (k0 + kb < n && c0 + cc < n) ? G[(size_t)(k0 + kb) * n + c0 + cc] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 32 * NS_C; e += blockDim.x) {
+      const int kb = e / NS_C, cc = e - kb * NS_C;  // B[kb][cc] = G[k0 + kb][c0 + cc]
+      const int k = k0 + kb, c = c0 + cc;
+      double g = 0.0;
+      if (k < n && c < n) {
+        // P holds the tiles with tile(row) <= tile(col); the others by symmetry
+        const bool upper = (k / NS_T) <= (c / NS_T);
+        const size_t idx = upper ? (size_t)k * n + c : (size_t)c * n + k;
+        double p = 0.0;
+        for (int sp = 0; sp < splits; ++sp) p += P[(size_t)sp * n * n + idx];
+        g = (k == c ? 1.5 : 0.0) - 0.5 * p;
+      }
+      B[kb][cc] = g;
     }
     __syncthreads();
 #pragma unroll 8
@@ -278,9 +309,16 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
 void newton_schulz_step(cudaStream_t st, int m, int n, const double* Q, double* G, double* out) {
   if (m <= 0 || n <= 0) return;
   count_launches(2);
-  const unsigned bn = (unsigned)((n + NS_T - 1) / NS_T), bm = (unsigned)((m + NS_T - 1) / NS_T);
-  ns_gram_kernel<<<dim3(bn, bn), 256, 0, st>>>(m, n, Q, G);
-  ns_apply_kernel<<<dim3(bn, bm), 256, 0, st>>>(m, n, Q, G, out);
+  const int nt = (n + NS_T - 1) / NS_T;
+  const int pairs = nt * (nt + 1) / 2;
+  const int chunks = (m + 31) / 32;  // K slices come in chunks of 32 rows
+  int splits = 152 / pairs;
+  splits = std::max(1, std::min({splits, chunks, NS_MAX_SPLIT}));
+  const int rows = ((chunks + splits - 1) / splits) * 32;
+  splits = (m + rows - 1) / rows;
+  ns_gram_kernel<<<dim3((unsigned)pairs, (unsigned)splits), 256, 0, st>>>(m, n, nt, rows, Q, G);
+  const unsigned bc = (unsigned)((n + NS_C - 1) / NS_C), bm = (unsigned)((m + NS_T - 1) / NS_T);
+  ns_apply_kernel<<<dim3(bc, bm), NS_T * NS_C, 0, st>>>(m, n, splits, Q, G, out);
 }
 
 }  // namespace qtt

@@ -30,7 +30,8 @@ std::vector<double> down(const double* d, size_t n) {
 // which = 0: tensor-core GEMM modes against the FP64 GEMM.  For every case
 // and mode (BF16X3, TF32, TF32X3, BF16, BF16X6) one value:
 // max |C_tc - C_64| / max |C_64|.
-// which = 1: QR (FP64 and FP32): ||Q^T Q - I||_max and ||Q Q^T Y - Y|| / ||Y|| per case.
+// which = 1: QR (FP64, FP32, FP32 + one FP64 Newton-Schulz step): ||Q^T Q - I||_max and
+//   ||Q Q^T Y - Y|| / ||Y|| per case and run.
 // which = 2: eigensolver (FP64 and FP32): ||G U - U diag(lam)|| / ||G|| and ||U^T U - I||_max.
 // which = 3: bias of the tensor-core modes (TF32X3, BF16X3, BF16X6) on positive
 // operands, K in {32, 256, 2048}, with and without a one-k-block cap per
@@ -109,10 +110,17 @@ std::vector<double> run_selftest(int which) {
                              {288, 144}, {160, 80}, {97, 49}, {161, 81}, {144, 72}};
     for (auto& sh : shapes) {
       const int m = sh[0], n = sh[1];
-      DBuf Y((size_t)m * n), Q((size_t)m * n), W((size_t)2 * m * n + n + 64);
+      DBuf Y((size_t)m * n), Q((size_t)m * n), W((size_t)2 * m * n + n + 64), Qf((size_t)m * n),
+          G((size_t)8 * n * n);
       fill_gaussian(st, Y.p, (size_t)m * n, 1.0, 99 + m, 5);
-      for (int prec : {64, 32}) {
-        qr_thin(st, m, n, Y.p, Q.p, W.p, prec, err);
+      // FP64 QR; float QR; float QR + one FP64 Newton-Schulz step
+      for (int run = 0; run < 3; ++run) {
+        if (run < 2) {
+          qr_thin(st, m, n, Y.p, Q.p, W.p, run == 0 ? 64 : 32, err);
+        } else {
+          qr_thin(st, m, n, Y.p, Qf.p, W.p, 32, err);
+          newton_schulz_step(st, m, n, Qf.p, G.p, Q.p);
+        }
         if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest qr");
         std::vector<double> y = down(Y.p, (size_t)m * n), q = down(Q.p, (size_t)m * n);
         double orth = 0;
