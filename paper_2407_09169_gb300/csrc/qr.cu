@@ -493,7 +493,21 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_reg_kernel(int m, int n, const
 // independent, Q e_c = H_0 ... H_c e_c (H_j e_c = e_c for j > c, since v_j
 // vanishes above row j), so each warp forms one column, 16 per block, over
 // ceil(n / 16) blocks; the block stages the reflectors 0 .. its last column in
-// shared memory and writes its 16 columns of Q row by row.
+// shared memory and writes its 16 columns of Q row by row.  The reflectors
+// are applied FQ_B at a time in compact form, H_j0 ... H_j0+3 = I - V T V^T
+// (T upper triangular: T_kk = tau_k, column k above the diagonal
+// -tau_k T V^T v_k, formed once per block of reflectors in the prologue), so
+// that one warp reduction of FQ_B dot products replaces FQ_B dependent ones.
+// Starting at the block that holds reflector c is exact: the reflectors after
+// c in that block meet x = e_c in exact zeros.
+constexpr int FQ_B = 4;
+
+template <int RPL>
+__host__ __device__ constexpr size_t formq_smem_floats(int nr) {
+  return (size_t)nr * 32 * RPL + (size_t)((nr + 3) & ~3) + (size_t)32 * RPL * QRR_WARPS +
+         (size_t)((nr + FQ_B - 1) / FQ_B) * FQ_B * FQ_B;
+}
+
 template <int RPL>
 __global__ void __launch_bounds__(QRR_THREADS) qr_formq_kernel(int m, int n, const float* __restrict__ Vg,
                                                                double* __restrict__ Qout) {
@@ -503,33 +517,91 @@ __global__ void __launch_bounds__(QRR_THREADS) qr_formq_kernel(int m, int n, con
   extern __shared__ __align__(16) unsigned char qr_smem[];
   const int c0 = blockIdx.x * QRR_WARPS;
   const int nr = min(n, c0 + QRR_WARPS);  // reflectors 0 .. nr - 1 are needed
+  const int nbr = (nr + FQ_B - 1) / FQ_B;  // blocks of FQ_B reflectors
   float* V = (float*)qr_smem;               // [nr][LDV]
   float* tau = V + (size_t)nr * LDV;        // [nr]
   float* S = tau + ((nr + 3) & ~3);         // [32 RPL][QRR_WARPS] staging of the block's columns
+  float* T = S + (size_t)32 * RPL * QRR_WARPS;  // [nbr][FQ_B][FQ_B]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nv = nr * LDV / 4;
   for (int e = tid; e < nv; e += QRR_THREADS) reinterpret_cast<float4*>(V)[e] = reinterpret_cast<const float4*>(Vg)[e];
   for (int c = tid; c < nr; c += QRR_THREADS) tau[c] = Vg[(size_t)n * LDV + c];
+  __syncthreads();
+  // T of each block of reflectors (those at or past nr are absent: tau 0, v 0)
+  for (int bb = warp; bb < nbr; bb += QRR_WARPS) {
+    const int j0 = bb * FQ_B;
+    float g[FQ_B][FQ_B];
+#pragma unroll
+    for (int r = 0; r < FQ_B; ++r)
+#pragma unroll
+      for (int k = 0; k < FQ_B; ++k) g[r][k] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < RPL; ++kk) {
+      float v[FQ_B];
+#pragma unroll
+      for (int r = 0; r < FQ_B; ++r) v[r] = (j0 + r < nr) ? V[(size_t)(j0 + r) * LDV + lane + 32 * kk] : 0.f;
+#pragma unroll
+      for (int k = 1; k < FQ_B; ++k)
+#pragma unroll
+        for (int r = 0; r < k; ++r) g[r][k] += v[r] * v[k];
+    }
+#pragma unroll
+    for (int k = 1; k < FQ_B; ++k)
+#pragma unroll
+      for (int r = 0; r < k; ++r)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g[r][k] += __shfl_xor_sync(0xffffffffu, g[r][k], o);
+    if (lane == 0) {
+      float* Tb = T + (size_t)bb * FQ_B * FQ_B;
+      float tk[FQ_B];
+#pragma unroll
+      for (int k = 0; k < FQ_B; ++k) tk[k] = (j0 + k < nr) ? tau[j0 + k] : 0.f;
+#pragma unroll
+      for (int k = 0; k < FQ_B; ++k) {
+#pragma unroll
+        for (int p = 0; p < FQ_B; ++p) Tb[p * FQ_B + k] = 0.f;
+        Tb[k * FQ_B + k] = tk[k];
+#pragma unroll
+        for (int p = 0; p < k; ++p) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = p; r < k; ++r) acc += Tb[p * FQ_B + r] * g[r][k];
+          Tb[p * FQ_B + k] = -tk[k] * acc;
+        }
+      }
+    }
+  }
   __syncthreads();
   const int c = c0 + warp;
   float x[RPL];
 #pragma unroll
   for (int k = 0; k < RPL; ++k) x[k] = (lane + 32 * k == c) ? 1.f : 0.f;
   if (c < n) {
-    for (int j = c; j >= 0; --j) {
-      const float t = tau[j];
-      if (t == 0.f) continue;
-      float v[RPL], d = 0.f;
+    for (int bb = c / FQ_B; bb >= 0; --bb) {
+      const int j0 = bb * FQ_B;
+      float v[FQ_B][RPL], w[FQ_B];
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) {
-        v[k] = V[(size_t)j * LDV + lane + 32 * k];
-        d += v[k] * x[k];
+      for (int p = 0; p < FQ_B; ++p) {
+        w[p] = 0.f;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          v[p][k] = (j0 + p < nr) ? V[(size_t)(j0 + p) * LDV + lane + 32 * k] : 0.f;
+          w[p] += v[p][k] * x[k];
+        }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      const float f = -t * d;
+      for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) x[k] += f * v[k];
+        for (int p = 0; p < FQ_B; ++p) w[p] += __shfl_xor_sync(0xffffffffu, w[p], o);
+      const float* Tb = T + (size_t)bb * FQ_B * FQ_B;
+#pragma unroll
+      for (int p = 0; p < FQ_B; ++p) {  // z = T w, then x -= V z
+        float z = 0.f;
+#pragma unroll
+        for (int q = p; q < FQ_B; ++q) z += Tb[p * FQ_B + q] * w[q];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) x[k] -= v[p][k] * z;
+      }
     }
   }
 #pragma unroll
@@ -549,9 +621,7 @@ bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, in
   if (m > 32 * RPL || n > QRR_WARPS * CPW) return false;
   const size_t smem = ((size_t)n * 32 * RPL + (size_t)n) * sizeof(float) + 8 + (size_t)n * sizeof(uint64_t);
   constexpr int NMAX = QRR_WARPS * CPW;
-  auto formq_smem = [](int nr) {
-    return ((size_t)nr * 32 * RPL + (size_t)((nr + 3) & ~3) + (size_t)32 * RPL * QRR_WARPS) * sizeof(float);
-  };
+  auto formq_smem = [](int nr) { return formq_smem_floats<RPL>(nr) * sizeof(float); };
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(qr_reg_kernel<RPL, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
