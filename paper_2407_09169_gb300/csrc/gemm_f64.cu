@@ -133,35 +133,26 @@ __global__ void scale_out_kernel(int M, int N, int inner, int batch, double beta
 }
 // Products whose 64 x 64 tile grid is too small for the GPU (the bond-sized
 // FP64 products: right Grams of the truncation, 136 x 136 x 272) otherwise
-// need a K split and a reduction launch.  Output tiles of 16 rows x nc
-// columns give them enough blocks instead, each thread summing its whole dot
-// product (K in chunks of 32 staged through shared memory), with the strided
-// views and alpha / beta of gemm_f64.  FP64 issues at two operations per clock
-// per SM, so nc is chosen to fill one wave of 152 blocks (one block per SM)
-// where the rows allow: 16 x 16 tiles would make 153 blocks of a 272 x 136
-// product (two waves) and 81 of a 136 x 136 one (half the SMs idle).
-constexpr int T16_MAX_NC = 32;
-
-__global__ void __launch_bounds__(16 * T16_MAX_NC) gemm_f64_t16_kernel(int M, int N, int K, int inner, int nc,
-                                                                        double alpha, MatView A, MatView B, double beta,
-                                                                        OutView C) {
+// need a K split and a reduction launch.  16 x 16 output tiles give them
+// enough blocks instead, each thread summing its whole dot product (K in
+// chunks of 32 staged through shared memory), with the strided views and
+// alpha / beta of gemm_f64.
+__global__ void __launch_bounds__(256) gemm_f64_t16_kernel(int M, int N, int K, int inner, double alpha, MatView A,
+                                                           MatView B, double beta, OutView C) {
   pdl_trigger();
   pdl_wait();
-  __shared__ double As[16][33], Bs[32][T16_MAX_NC + 1];
-  const int nt = 16 * nc;
-  const int tx = threadIdx.x % nc, ty = threadIdx.x / nc;
-  const int m0 = blockIdx.y * 16, n0 = blockIdx.x * nc;
+  __shared__ double As[16][33], Bs[32][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16;
   const int b = blockIdx.z, bo = b / inner, bi = b - bo * inner;
   const double* Ap = A.p + bo * A.so + bi * A.si;
   const double* Bp = B.p + bo * B.so + bi * B.si;
   double acc = 0.0;
   for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = threadIdx.x; e < 512; e += nt) {
+    for (int e = threadIdx.x; e < 512; e += 256) {
       const int rr = e >> 5, kk = e & 31;  // As[rr][kk] = A(m0 + rr, k0 + kk)
       As[rr][kk] = (m0 + rr < M && k0 + kk < K) ? Ap[(long long)(m0 + rr) * A.rs + (long long)(k0 + kk) * A.cs] : 0.0;
-    }
-    for (int e = threadIdx.x; e < 32 * nc; e += nt) {
-      const int kb = e / nc, cc = e - kb * nc;  // Bs[kb][cc] = B(k0 + kb, n0 + cc)
+      const int kb = e >> 4, cc = e & 15;  // Bs[kb][cc] = B(k0 + kb, n0 + cc)
       Bs[kb][cc] = (k0 + kb < K && n0 + cc < N) ? Bp[(long long)(k0 + kb) * B.rs + (long long)(n0 + cc) * B.cs] : 0.0;
     }
     __syncthreads();
@@ -290,16 +281,9 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
   {
     const long long t16 = (long long)((M + 15) / 16) * ((N + 15) / 16) * batch;
     if (splitk > 1 && t16 >= 64 && K <= 2048 && batch <= 65535) {
-      // column tile width: one wave of 152 blocks where the row tiles allow it
-      const long long rows = (long long)((M + 15) / 16) * batch;
-      int nc = 16;
-      if (rows <= 152) {
-        const long long cols = 152 / rows;
-        nc = (int)std::min<long long>(T16_MAX_NC, std::max<long long>(4, (N + cols - 1) / cols));
-      }
       count_launches(1);
-      launch_pdl(gemm_f64_t16_kernel, dim3((N + nc - 1) / nc, (M + 15) / 16, batch), dim3(16 * nc), 0, st, M, N, K,
-                 inner, nc, alpha, A, B, beta, C);
+      launch_pdl(gemm_f64_t16_kernel, dim3((N + 15) / 16, (M + 15) / 16, batch), dim3(256), 0, st, M, N, K, inner, alpha,
+                 A, B, beta, C);
       return;
     }
   }
