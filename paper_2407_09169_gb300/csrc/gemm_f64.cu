@@ -172,9 +172,9 @@ __global__ void __launch_bounds__(256) gemm_f64_t16_kernel(int M, int N, int K, 
 // one block per SM:
 //   ns_gram_kernel: the upper-triangular 16 x 16 tiles of P = Q^T Q only (P is
 //     symmetric), each over a slice of the m rows of Q (split s of S), raw
-//     partial sums to P_s;
-//   ns_apply_kernel: out = Q G with G = 1.5 I - 0.5 sum_s P_s read from the
-//     partials (mirrored below the diagonal tiles), 16 x 17 output tiles
+//     partial sums to P_s, written to the tile and to its mirror image;
+//   ns_apply_kernel: out = Q G with G = 1.5 I - 0.5 sum_s P_s read row-wise
+//     from the partials, 16 x 17 output tiles
 //     (17 columns: 136 = 8 x 17 fills 136 blocks where 16 x 16 tiles would
 //     make 153, one more than the SMs).
 // Operand strips are staged through shared memory in chunks of 32.
@@ -208,7 +208,11 @@ __global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, int nt, int 
     __syncthreads();
   }
   const int i = i0 + ty, j = j0 + tx;
-  if (i < n && j < n) P[(size_t)blockIdx.y * n * n + (size_t)i * n + j] = acc;
+  if (i < n && j < n) {
+    double* Ps = P + (size_t)blockIdx.y * n * n;
+    Ps[(size_t)i * n + j] = acc;
+    if (ti != tj) Ps[(size_t)j * n + i] = acc;  // the mirrored tile, so that the apply reads rows
+  }
 }
 
 __global__ void __launch_bounds__(NS_T * NS_C) ns_apply_kernel(int m, int n, int splits, const double* __restrict__ Q,
@@ -227,11 +231,8 @@ __global__ void __launch_bounds__(NS_T * NS_C) ns_apply_kernel(int m, int n, int
       const int k = k0 + kb, c = c0 + cc;
       double g = 0.0;
       if (k < n && c < n) {
-        // P holds the tiles with tile(row) <= tile(col); the others by symmetry
-        const bool upper = (k / NS_T) <= (c / NS_T);
-        const size_t idx = upper ? (size_t)k * n + c : (size_t)c * n + k;
         double p = 0.0;
-        for (int sp = 0; sp < splits; ++sp) p += P[(size_t)sp * n * n + idx];
+        for (int sp = 0; sp < splits; ++sp) p += P[(size_t)sp * n * n + (size_t)k * n + c];
         g = (k == c ? 1.5 : 0.0) - 0.5 * p;
       }
       B[kb][cc] = g;

@@ -135,7 +135,7 @@ void sum_arrays(cudaStream_t st, double* out, const double* const* in, int n_in,
 void fill_eye(cudaStream_t st, double* p, int n);
 // One Newton-Schulz step in FP64 of an almost-orthonormal Q (m x n,
 // row-major): out = Q (3 I - Q^T Q) / 2.  G is work space of 8 n n doubles
-// (partial sums of the upper tiles of Q^T Q).
+// (split partial sums of Q^T Q).
 void newton_schulz_step(cudaStream_t st, int m, int n, const double* Q, double* G, double* out);
 // *c += 1 on the device.
 void bump_counter(cudaStream_t st, unsigned long long* c);
