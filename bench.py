@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path beside the form")
     ap.add_argument("--also", default="fp32,tf32",
                     help="other reduced forms timed and compared with the FP64 path (comma-separated)")
-    ap.add_argument("--batch", type=int, default=64,
+    ap.add_argument("--batch", type=int, default=256,
                     help="instances of the batched configuration stepped together (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--adjoint-steps", type=int, default=20,
