@@ -273,17 +273,21 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
             c3 = c2;
             c2 = c;
             s2 = s;
-            const T ei = e[i];
+            const T ei = e[i], di = d[i];
             g = c * ei;
             const T hh = c * p;
+            // the next p = c' d_i - s' g = rr (p d_i - e_i g): the bracket does
+            // not wait for rr, so the chain per rotation is the sum of squares,
+            // its reciprocal square root and one product
+            const T tq = fma(p, di, -(ei * g));
             const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
             const T cn = p * rr, sn = ei * rr;
             r = p * cn + ei * sn;  // hypot(p, e_i)
             e[i + 1] = s * r;      // previous sine
             s = sn;
             c = cn;
-            p = c * d[i] - s * g;
-            d[i + 1] = hh + s * (c * g + s * d[i]);
+            p = rr * tq;
+            d[i + 1] = hh + s * (c * g + s * di);
             rcg[off + (size_t)(m - 1 - i)] = c;
             rsg[off + (size_t)(m - 1 - i)] = s;
           }
