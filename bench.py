@@ -26,6 +26,8 @@ import tempfile
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -312,6 +314,15 @@ def run_mine(args, rank, world, local_rank):
         roofline["avg_launch_us"] = g["ms_per_step"] * 1e3 / max(g["launches_per_step"], 1)
         roofline["timing"] = ("separate eager pass after the timed region: CUDA events on the launching stream "
                               "around every launch of the class, averaged over the pass's steps")
+        if args.precision != "fp64":
+            # the same tensor-core GEMM (packing included) on square products that fill the GPU
+            big = {}
+            for n_, mode_, tfl, err_ in np.array(q.qtt_selftest(4)[:-1]).reshape(-1, 4):
+                name = {3: "bf16", 0: "bf16x3"}.get(int(mode_), str(int(mode_)))
+                mma_passes = 3.0 if name == "bf16x3" else 1.0
+                big[f"{name}_n{int(n_)}"] = {"tflops": float(tfl), "frac": float(tfl) * mma_passes / bf16,
+                                             "max_rel_err_sampled": float(err_)}
+            roofline["same_kernel_large_square"] = big
 
     # ---- the plain FP64 GPU path at equal chi: steps/s, and the form's distance to it
     fp64_path = None
@@ -392,8 +403,6 @@ def run_mine(args, rank, world, local_rank):
                              f"extrapolated by cell count to 2^{sum(p['bits'])} cells ({cell_rate:.3e} cell-steps/s)"}
     if rank == 0 and world == 1 and not args.no_parity:
         try:
-            import numpy as np
-
             import oracle
             ps = workload.make_params("small", precision=args.precision)
             with q.qtt_init(ps, stream=stream.cuda_stream) as cs:

@@ -241,7 +241,12 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
  *      max |U^T U - I| and 1 if the eigenvalues are not descending
  *   3  accumulation bias of the tensor-core GEMM: positive operands, K = 32,
  *      256, 2048, modes (TF32X3, BF16X3), accumulation (one FP32 accumulator,
- *      FP64 sum of per-k-block accumulators): mean signed and max relative error */
+ *      FP64 sum of per-k-block accumulators): mean signed and max relative error
+ *   4  throughput of the tensor-core GEMM on square products n = 4096, 8192
+ *      in modes BF16 and BF16X3 (calls including the operand packing): per
+ *      case n, the mode's enum value (BF16 3, BF16X3 0), TFLOP/s at 2 n^3 per
+ *      call, and the max of |C - C_fp64| / sum_k |A_ik B_kj| over 16 sampled
+ *      entries (needs ~3 GiB of device memory) */
 qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written);
 
 #ifdef __cplusplus

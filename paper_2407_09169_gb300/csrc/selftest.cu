@@ -235,6 +235,72 @@ std::vector<double> run_selftest(int which) {
         }
     }
     cudaFree(pack);
+  } else if (which == 4) {
+    // throughput of the tensor-core GEMM on large square products (the
+    // contraction kernel on a shape that fills the GPU), per call including the
+    // operand packing: for n in {4096, 8192} and modes (BF16, BF16X3):
+    // n, mode, TFLOP/s (2 n^3 per call, mean of 5 timed calls after 2 untimed
+    // ones), max relative error of 16 sampled entries against FP64 dot products
+    const size_t ws_elems = (size_t)32 << 20;
+    DBuf ws(ws_elems);
+    for (int n : {4096, 8192}) {
+      const size_t sz = (size_t)n * n;  // 8192^2 FP64: 512 MiB per operand
+      DBuf A(sz), B(sz), C(sz);
+      fill_gaussian(st, A.p, sz, 1.0, 4242 + n, 9);
+      fill_gaussian(st, B.p, sz, 1.0, 4343 + n, 10);
+      MatView av, bv;
+      av.p = A.p; av.rs = n; av.cs = 1;
+      bv.p = B.p; bv.rs = n; bv.cs = 1;
+      OutView cv;
+      cv.p = C.p; cv.rs = n; cv.cs = 1;
+      const int modes[2] = {TC_BF16, TC_BF16X3};
+      for (int mode : modes) {
+        const size_t pack_bytes = tc_workspace_bytes(n, n, n, 1, mode);
+        void* pack = nullptr;
+        if (cudaMalloc(&pack, pack_bytes) != cudaSuccess) throw std::runtime_error("ENOMEM: selftest pack");
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        bool ok = true;
+        for (int it = 0; it < 2 && ok; ++it)
+          ok = gemm_tc(st, mode, n, n, n, 1, 1, 1.0, av, bv, 0.0, cv, pack, pack_bytes, ws.p, ws_elems, err);
+        float ms = 0.f;
+        if (ok) {
+          cudaEventRecord(e0, st);
+          for (int it = 0; it < 5; ++it)
+            gemm_tc(st, mode, n, n, n, 1, 1, 1.0, av, bv, 0.0, cv, pack, pack_bytes, ws.p, ws_elems, err);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) throw std::runtime_error("CUDA error: selftest gemm timing");
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(pack);
+        double err_max = -1.0;
+        if (ok) {  // row i of A, column j of B and C(i, j) only
+          err_max = 0.0;
+          std::vector<double> ar(n), bc(n);
+          for (int q = 0; q < 16; ++q) {
+            const size_t i = ((size_t)q * 2654435761u) % n, j = ((size_t)q * 40503u + 7) % n;
+            double cij = 0.0;
+            if (cudaMemcpy(ar.data(), A.p + i * n, (size_t)n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy2D(bc.data(), 8, B.p + j, (size_t)n * 8, 8, n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(&cij, C.p + i * n + j, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+              throw std::runtime_error("CUDA error: selftest gemm sample");
+            double ref = 0.0, mag = 0.0;
+            for (int k = 0; k < n; ++k) {
+              ref += ar[k] * bc[k];
+              mag += std::fabs(ar[k] * bc[k]);
+            }
+            err_max = std::fmax(err_max, std::fabs(cij - ref) / mag);
+          }
+        }
+        out.push_back((double)n);
+        out.push_back((double)mode);
+        out.push_back(ok && ms > 0.f ? 2.0 * n * (double)n * n * 5.0 / (ms * 1e-3) / 1e12 : -1.0);
+        out.push_back(err_max);
+      }
+    }
   } else {
     cudaFree(err);
     throw std::runtime_error("EINVAL: unknown selftest");

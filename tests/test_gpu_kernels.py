@@ -54,3 +54,17 @@ def test_eigensolver():
         (r64, o64, ord64), (r32, o32, ord32) = case
         assert r64 < 1e-12 and o64 < 1e-12 and ord64 == 0
         assert r32 < 5e-5 and o32 < 5e-5 and ord32 == 0
+
+
+def test_tensor_core_gemm_large_square():
+    """The tensor-core GEMM on square products n = 4096 and 8192 (the shapes
+    the contraction kernel reaches its throughput on): sampled entries against
+    FP64 dot products, |C - C_fp64| / sum_k |A_ik B_kj|.  BF16: each operand
+    rounded to 8 significant bits (2^-8 per product) plus FP32 accumulation
+    over K = 8192 (<= K 2^-24 = 4.9e-4): 5e-3.  BF16X3: 16-bit operands
+    (2^-16 per product) plus the same accumulation bound: 1e-3."""
+    v = np.array(pkg.qtt_selftest(4)[:-1]).reshape(-1, 4)  # n, mode, TFLOP/s, error
+    print("\n" + "\n".join(f"n={int(n)} mode={int(m)}: {t:.1f} TFLOP/s, err {e:.2e}" for n, m, t, e in v))
+    for n, mode, tflops, err in v:
+        assert tflops > 0
+        assert 0 <= err <= (5e-3 if int(mode) == 3 else 1e-3), (n, mode, err)
