@@ -264,24 +264,38 @@ __device__ __forceinline__ void qrr_reflector(const float (&X)[RPL][CPW], int q,
   }
   float t = 0.f, v0 = 1.f;
   if (s != 0.f) {
-    const float mu = sqrtf(a * a + s);
+    // On the reflector chain: the approximate reciprocal square root and
+    // quotient (a few ulp) where the sum of squares is a normal number.  H
+    // stays orthogonal to that level (tau v^T v = 2 up to the error of beta),
+    // as with float round-off, which the FP64 Newton-Schulz step removes.
+    const float q2 = fmaf(a, a, s);
+    const bool normal = q2 > 1e-30f && q2 < 1e30f;
+    const float mu = normal ? q2 * rsqrtf(q2) : sqrtf(q2);
     const float beta = a <= 0.f ? mu : -mu;
-    t = (beta - a) / beta;
+    t = normal ? __fdividef(beta - a, beta) : (beta - a) / beta;
     v0 = a - beta;
   }
   float* v = V + (size_t)c * ldv;
-  // |x_i| <= |v0|: one reciprocal instead of a division per row (divisions
-  // only when v0 is so small that its reciprocal would overflow)
+  // |x_i| <= |v0|: one reciprocal instead of a division per row; the
+  // (warp-uniform) branch keeps divisions out of the common case, they run
+  // only when v0 is so small that its reciprocal would overflow
   const bool tiny = fabsf(v0) < 1e-30f;
-  const float rv0 = tiny ? 0.f : __frcp_rn(v0);
+  const float rv0 = (t != 0.f && !tiny) ? __fdividef(1.f, v0) : 0.f;
 #pragma unroll
   for (int qq = 0; qq < CPW; ++qq) {
     if (qq != q) continue;
+    if (!tiny || t == 0.f) {
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-      const int i = lane + 32 * k;
-      const float x = X[k][qq];
-      v[i] = i < c ? 0.f : (i == c ? 1.f : (t != 0.f ? (tiny ? x / v0 : x * rv0) : 0.f));
+      for (int k = 0; k < RPL; ++k) {
+        const int i = lane + 32 * k;
+        v[i] = i < c ? 0.f : (i == c ? 1.f : X[k][qq] * rv0);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int i = lane + 32 * k;
+        v[i] = i < c ? 0.f : (i == c ? 1.f : X[k][qq] / v0);
+      }
     }
   }
   if (lane == 0) {
