@@ -122,26 +122,33 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   __shared__ T s_tau, s_v0, s_K;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = TRI_THREADS / 32;
 
+  // row stride of the working copy: n + 1 in shared memory (rows of
+  // consecutive threads then fall on different banks), n in global memory
+  const int lda = use_smem ? n + 1 : n;
   for (size_t x = tid; x < (size_t)n * n; x += TRI_THREADS) {
     const int i = (int)(x / n), c = (int)(x - (size_t)i * n);
-    A[x] = (T)(0.5 * (G[x] + G[(size_t)c * n + i]));
+    A[(size_t)i * lda + c] = (T)(0.5 * (G[x] + G[(size_t)c * n + i]));
   }
   __syncthreads();
 
   // ---- Householder tridiagonalisation.  Only the lower triangle (c <= i) of
   // the trailing block is kept current; reflector j is stored in row j,
-  // columns > j + 1 (the strict upper part, unused otherwise).
+  // columns > j + 1 (the strict upper part, unused otherwise).  FP64 issues
+  // at a fraction of a lane per clock per scheduler, so the products are laid
+  // out to keep whole warps busy: A22 v with four threads per row (no
+  // reduction over a warp per row), the rank-2 update over the flattened lower
+  // triangle (no lanes idle on short rows).
   for (int j = 0; j + 2 < n; ++j) {
-    T* Aj = A + (size_t)j * n;
+    T* Aj = A + (size_t)j * lda;
     if (warp == 0) {
       T s = 0;
       for (int i = j + 2 + lane; i < n; i += 32) {
-        const T v = A[(size_t)i * n + j];
+        const T v = A[(size_t)i * lda + j];
         s += v * v;
       }
       s = warp_sum_e(s);
       if (lane == 0) {
-        const T alpha = A[(size_t)(j + 1) * n + j];
+        const T alpha = A[(size_t)(j + 1) * lda + j];
         d[j] = Aj[j];
         if (s == (T)0) {
           s_tau = 0;
@@ -166,21 +173,31 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
     {
       const T inv = (T)1 / s_v0;
       for (int i = j + 2 + tid; i < n; i += TRI_THREADS) {
-        const T v = A[(size_t)i * n + j] * inv;
+        const T v = A[(size_t)i * lda + j] * inv;
         vb[i] = v;
         Aj[i] = v;
       }
       if (tid == 0) vb[j + 1] = (T)1;
     }
     __syncthreads();
-    // p = tau * A22 v, A22 symmetric with its lower triangle stored
-    for (int i = j + 1 + warp; i < n; i += nwarps) {
-      const T* Ai = A + (size_t)i * n;
+    // p = tau * A22 v, A22 symmetric with its lower triangle stored: four
+    // threads per row (lanes 4r .. 4r + 3), each over every fourth column
+    const int m = n - j - 1;
+    const int m4 = (4 * m + 31) & ~31;  // whole warps enter each pass (the shuffles)
+    for (int x = tid; x < m4; x += TRI_THREADS) {
+      const bool ok = x < 4 * m;
+      const int i = j + 1 + (x >> 2), q = x & 3;
       T acc = 0;
-      for (int c = j + 1 + lane; c <= i; c += 32) acc += Ai[c] * vb[c];
-      for (int c = i + 1 + lane; c < n; c += 32) acc += A[(size_t)c * n + i] * vb[c];
-      acc = warp_sum_e(acc);
-      if (lane == 0) pb[i] = tau * acc;
+      if (ok) {
+        for (int c = j + 1 + q; c < n; c += 4) {
+          const T a = c <= i ? A[(size_t)i * lda + c] : A[(size_t)c * lda + i];
+          acc += a * vb[c];
+        }
+      }
+      // the four partial sums of a row sit in lanes 4r .. 4r + 3 of one warp
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2, 4);
+      if (ok && q == 0) pb[i] = tau * acc;
     }
     __syncthreads();
     if (warp == 0) {
@@ -192,21 +209,25 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
     __syncthreads();
     for (int i = j + 1 + tid; i < n; i += TRI_THREADS) wb[i] = pb[i] - s_K * vb[i];
     __syncthreads();
-    // lower-triangle rank-2 update: rows i >= j+1, columns j+1 <= c <= i
-    for (int i = j + 1 + warp; i < n; i += nwarps) {
-      T* Ai = A + (size_t)i * n;
-      const T vi = vb[i], wi = wb[i];
-      for (int c = j + 1 + lane; c <= i; c += 32) Ai[c] -= vi * wb[c] + wi * vb[c];
+    // lower-triangle rank-2 update, rows i >= j+1, columns j+1 <= c <= i,
+    // over the flattened triangle: element x is (r, c') with r (r + 1) / 2 <= x
+    const int tri = m * (m + 1) / 2;
+    for (int x = tid; x < tri; x += TRI_THREADS) {
+      int r = (int)((sqrtf(8.f * (float)x + 1.f) - 1.f) * 0.5f);
+      while (r * (r + 1) / 2 > x) --r;
+      while ((r + 1) * (r + 2) / 2 <= x) ++r;
+      const int i = j + 1 + r, c = j + 1 + (x - r * (r + 1) / 2);
+      A[(size_t)i * lda + c] -= vb[i] * wb[c] + wb[i] * vb[c];
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
-      d[n - 2] = A[(size_t)(n - 2) * n + (n - 2)];
-      e[n - 2] = A[(size_t)(n - 1) * n + (n - 2)];
+      d[n - 2] = A[(size_t)(n - 2) * lda + (n - 2)];
+      e[n - 2] = A[(size_t)(n - 1) * lda + (n - 2)];
       tauv[n - 2] = 0;
     }
-    d[n - 1] = A[(size_t)(n - 1) * n + (n - 1)];
+    d[n - 1] = A[(size_t)(n - 1) * lda + (n - 1)];
     e[n - 1] = 0;
     tauv[n - 1] = 0;
   }
@@ -214,7 +235,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   // reflectors (and tau in the diagonal of A) for the back-transform kernel
   for (size_t x = tid; x < (size_t)n * n; x += TRI_THREADS) {
     const int i = (int)(x / n), c = (int)(x - (size_t)i * n);
-    if (c > i + 1) W[L.A + x] = A[x];
+    if (c > i + 1) W[L.A + x] = A[(size_t)i * lda + c];
     else if (c == i) W[L.A + x] = tauv[i];
   }
 
@@ -389,7 +410,7 @@ __global__ void eig_back_transform(const EigProblem* __restrict__ probs) {
 
 template <typename T>
 void eig_launch(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nmax, int kmax, int* status) {
-  const size_t smem_A = (size_t)nmax * nmax * sizeof(T);
+  const size_t smem_A = (size_t)nmax * (nmax + 1) * sizeof(T);  // row stride n + 1 in shared memory
   const int use_smem = smem_A <= EIG_SMEM_LIMIT ? 1 : 0;
   static bool attr = false;
   if (!attr) {
