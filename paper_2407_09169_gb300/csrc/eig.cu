@@ -67,6 +67,56 @@ __device__ __forceinline__ float rhyp_fast(float a, float b) {
   return (q > 1e-35f && q < 1e35f) ? rsqrtf(q) : rhypotf(a, b);
 }
 
+// Bounded spins on a flag in shared memory, between the QL chain and its
+// helper lane: at most ~2^26 polls and about a second of wall time; on expiry
+// the abort word is set so that the other side stops too.
+constexpr long long QL_SPIN_LIMIT = 1LL << 26;
+__device__ __forceinline__ bool ql_spin_expired(long long it, unsigned long long t0) {
+  if ((it & 1023) != 1023) return it >= QL_SPIN_LIMIT;
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return it >= QL_SPIN_LIMIT || t - t0 > 1000000000ull;
+}
+__device__ __forceinline__ unsigned long long ql_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// waits for *w == v; false if it expired or the abort word was set
+__device__ inline bool ql_wait_eq(volatile int* w, int v, volatile int* abort_w) {
+  const unsigned long long t0 = ql_now();
+  for (long long it = 0;; ++it) {
+    if (*w == v) return true;
+    if (*abort_w || ql_spin_expired(it, t0)) {
+      *abort_w = 1;
+      return false;
+    }
+  }
+}
+// waits for *w >= v
+__device__ inline bool ql_wait_ge(volatile int* w, int v, volatile int* abort_w) {
+  const unsigned long long t0 = ql_now();
+  for (long long it = 0;; ++it) {
+    if (*w >= v) return true;
+    if (*abort_w || ql_spin_expired(it, t0)) {
+      *abort_w = 1;
+      return false;
+    }
+  }
+}
+// waits for *w != seen; returns the new value, or -2 on expiry / abort
+__device__ inline int ql_wait_change(volatile int* w, int seen, volatile int* abort_w) {
+  const unsigned long long t0 = ql_now();
+  for (long long it = 0;; ++it) {
+    const int v = *w;
+    if (v != seen) return v;
+    if (*abort_w || ql_spin_expired(it, t0)) {
+      *abort_w = 1;
+      return -2;
+    }
+  }
+}
+
 // Work layout, in elements of T: A n*n | Z n*n | rot_c R | rot_s R; then
 // ints: seg_lo S | seg_hi S | seg_off S | order n | nseg.  R = 4 n^2 + 64 n
 // rotations, S = 60 n sweeps.
@@ -120,6 +170,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   int* order = I + L.order;
   __shared__ T d[EIG_MAXN], e[EIG_MAXN], vb[EIG_MAXN], pb[EIG_MAXN], wb[EIG_MAXN], tauv[EIG_MAXN];
   __shared__ T s_tau, s_v0, s_K;
+  __shared__ int ql_ctl[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = TRI_THREADS / 32;
 
   // row stride of the working copy: n + 1 in shared memory (rows of
@@ -240,93 +291,170 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   }
 
   // ---- implicit QL with a Wilkinson-type shift, rotations recorded per sweep.
-  // Warp 0 runs it: lane 0 carries the rotation chain; the search for the
-  // next negligible off-diagonal (32 entries per ballot) and the shift of the
-  // trailing diagonal are spread over the lanes.  The loop control is the
-  // same in every lane (computed from the same shared values).
-  if (warp == 0) {
-    const T eps = Eps<T>::v();
-    T f = 0, tst1 = 0;
-    int nseg = 0;
-    size_t off = 0;
-    for (int l = 0; l < n; ++l) {
-      const T hl = fabs(d[l]) + fabs(e[l]);
-      tst1 = hl > tst1 ? hl : tst1;
-      for (int iter = 0;; ++iter) {
-        int m = n - 1;
-        for (int base = l; base < n - 1; base += 32) {
-          const int i = base + lane;
-          const bool small = i < n - 1 && !(fabs(e[i]) > eps * tst1);
-          const unsigned bal = __ballot_sync(0xffffffffu, small);
-          if (bal) {
-            m = base + __ffs(bal) - 1;
+  // Warp 0 runs it: the search for the next negligible off-diagonal (32
+  // entries per ballot) and the shift of the trailing diagonal are spread over
+  // its lanes, and lane 0 carries the rotation chain.  FP64 instructions cost
+  // the same whatever the number of active lanes, so the chain lane keeps only
+  // the operations the next rotation depends on (sum of squares, reciprocal
+  // square root, cosine, next p) and hands (p, 1/hypot) of every rotation to
+  // lane 0 of warp 1, which runs on another scheduler's FP64 pipe one rotation
+  // behind: it forms the cosine and sine, updates d[i+1] and e[i+1] (positions
+  // the chain has passed) and records the rotation.  The chain waits for it at
+  // the end of each sweep.  Every wait is bounded (status bit 8 on expiry).
+  {
+    T* qlP = vb;  // the tridiagonalisation's vectors are dead from here on
+    T* qlR = pb;
+    volatile int* ctl = ql_ctl;  // 0 sweep number (-1: end), 1 l, 2 m, 3 off, 4 published, 5 done, 6 abort
+    if (tid == 0) {
+      ctl[0] = 0;
+      ctl[4] = 0;
+      ctl[5] = 0;
+      ctl[6] = 0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const T eps = Eps<T>::v();
+      T f = 0, tst1 = 0;
+      int nseg = 0, sweep = 0;
+      size_t off = 0;
+      bool aborted = false;  // warp-uniform (lane 0's view of the abort word)
+      for (int l = 0; l < n && !aborted; ++l) {
+        const T hl = fabs(d[l]) + fabs(e[l]);
+        tst1 = hl > tst1 ? hl : tst1;
+        for (int iter = 0;; ++iter) {
+          int m = n - 1;
+          for (int base = l; base < n - 1; base += 32) {
+            const int i = base + lane;
+            const bool small = i < n - 1 && !(fabs(e[i]) > eps * tst1);
+            const unsigned bal = __ballot_sync(0xffffffffu, small);
+            if (bal) {
+              m = base + __ffs(bal) - 1;
+              break;
+            }
+          }
+          if (m == l) break;
+          if (iter >= QL_MAX_SWEEPS || nseg >= (int)L.S || off + (size_t)(m - l) > L.R) {
+            if (lane == 0) atomicOr(status, 2);
             break;
           }
-        }
-        if (m == l) break;
-        if (iter >= QL_MAX_SWEEPS || nseg >= (int)L.S || off + (size_t)(m - l) > L.R) {
-          if (lane == 0) atomicOr(status, 2);
-          break;
-        }
-        T g = d[l];
-        T p = (d[l + 1] - g) / ((T)2 * e[l]);
-        T r = (T)1 / rhyp(p, (T)1);
-        if (p < 0) r = -r;
-        const T dl0 = e[l] / (p + r);
-        const T dl1 = e[l] * (p + r);
-        const T h = g - dl0;
-        __syncwarp();
-        if (lane == 0) {
-          d[l] = dl0;
-          d[l + 1] = dl1;
-        }
-        for (int i = l + 2 + lane; i < n; i += 32) d[i] -= h;
-        f += h;
-        __syncwarp();
-        if (lane == 0) {
-          p = d[m];
-          T c = 1, c2 = 1, c3 = 1, s = 0, s2 = 0;
-          const T el1 = e[l + 1];
-          seg_lo[nseg] = l;
-          seg_hi[nseg] = m - 1;
-          seg_off[nseg] = (int)off;
-          for (int i = m - 1; i >= l; --i) {
-            c3 = c2;
-            c2 = c;
-            s2 = s;
-            const T ei = e[i], di = d[i];
-            g = c * ei;
-            const T hh = c * p;
-            // the next p = c' d_i - s' g = rr (p d_i - e_i g): the bracket does
-            // not wait for rr, so the chain per rotation is the sum of squares,
-            // its reciprocal square root and one product
-            const T tq = fma(p, di, -(ei * g));
-            const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
-            const T cn = p * rr, sn = ei * rr;
-            r = p * cn + ei * sn;  // hypot(p, e_i)
-            e[i + 1] = s * r;      // previous sine
-            s = sn;
-            c = cn;
-            p = rr * tq;
-            d[i + 1] = hh + s * (c * g + s * di);
-            rcg[off + (size_t)(m - 1 - i)] = c;
-            rsg[off + (size_t)(m - 1 - i)] = s;
+          T g = d[l];
+          T p = (d[l + 1] - g) / ((T)2 * e[l]);
+          T r = (T)1 / rhyp(p, (T)1);
+          if (p < 0) r = -r;
+          const T dl0 = e[l] / (p + r);
+          const T dl1 = e[l] * (p + r);
+          const T h = g - dl0;
+          __syncwarp();
+          if (lane == 0) {
+            d[l] = dl0;
+            d[l + 1] = dl1;
           }
-          p = -s * s2 * c3 * el1 * e[l] / dl1;
-          e[l] = s * p;
-          d[l] = c * p;
+          for (int i = l + 2 + lane; i < n; i += 32) d[i] -= h;
+          f += h;
+          __syncwarp();
+          ++sweep;
+          if (lane == 0) {
+            p = d[m];
+            const T el1 = e[l + 1];
+            seg_lo[nseg] = l;
+            seg_hi[nseg] = m - 1;
+            seg_off[nseg] = (int)off;
+            ctl[1] = l;
+            ctl[2] = m;
+            ctl[3] = (int)off;
+            ctl[4] = 0;
+            __threadfence_block();
+            ctl[0] = sweep;
+            // c: cosine of the previous rotation (1 before the first); c2, c3
+            // the two before it; (e_i, rr) of the last two for the sines
+            T c = 1, c2 = 1, c3 = 1, e1 = 0, r1 = 0, e2 = 0, r2 = 0;
+            int k = 0;
+            for (int i = m - 1; i >= l; --i, ++k) {
+              c3 = c2;
+              c2 = c;
+              e2 = e1;
+              r2 = r1;
+              const T ei = e[i], di = d[i];
+              // the next p = c' d_i - s' g = rr (p d_i - e_i g), g = c e_i:
+              // the bracket does not wait for rr
+              const T tq = fma(p, di, -(ei * (c * ei)));
+              const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
+              qlP[i] = p;
+              qlR[i] = rr;
+              __threadfence_block();
+              ctl[4] = k + 1;
+              c = p * rr;
+              p = rr * tq;
+              e1 = ei;
+              r1 = rr;
+            }
+            const T s = e1 * r1, s2 = e2 * r2;  // sines of the last two rotations (0 when absent)
+            p = -s * s2 * c3 * el1 * e[l] / dl1;
+            // the helper reads e[l] and d[l] in the last rotation and writes
+            // d[l+1 ..], e[l+1 ..]: wait for it before e[l], d[l] and the next search
+            if (!ql_wait_eq(ctl + 5, sweep, ctl + 6)) atomicOr(status, 8);
+            __threadfence_block();
+            e[l] = s * p;
+            d[l] = c * p;
+          }
+          off += (size_t)(m - l);
+          ++nseg;
+          __syncwarp();
+          __threadfence_block();  // the helper's d and e, seen by lane 0, for every lane
+          aborted = __shfl_sync(0xffffffffu, ctl[6], 0) != 0;
+          if (aborted) break;
         }
-        off += (size_t)(m - l);
-        ++nseg;
+        if (lane == 0) {
+          d[l] += f;
+          e[l] = 0;
+        }
         __syncwarp();
       }
       if (lane == 0) {
-        d[l] += f;
-        e[l] = 0;
+        I[L.nseg] = nseg;
+        __threadfence_block();
+        ctl[0] = -1;
       }
-      __syncwarp();
+    } else if (warp == 1 && lane == 0) {
+      int seen = 0;
+      for (;;) {
+        const int sw = ql_wait_change(ctl, seen, ctl + 6);
+        if (sw == -2) {  // expired
+          atomicOr(status, 8);
+          break;
+        }
+        if (sw < 0) break;
+        seen = sw;
+        __threadfence_block();
+        const int l = ctl[1], m = ctl[2];
+        const size_t off = (size_t)ctl[3];
+        T c = 1, s = 0;
+        bool ok = true;
+        for (int k = 0; k < m - l && ok; ++k) {
+          ok = ql_wait_ge(ctl + 4, k + 1, ctl + 6);
+          if (!ok) break;
+          __threadfence_block();
+          const int i = m - 1 - k;
+          const T p = qlP[i], rr = qlR[i], ei = e[i], di = d[i];
+          const T g = c * ei;
+          const T hh = c * p;
+          const T cn = p * rr, sn = ei * rr;
+          const T r = p * cn + ei * sn;  // hypot(p, e_i)
+          e[i + 1] = s * r;               // previous sine
+          s = sn;
+          c = cn;
+          d[i + 1] = hh + s * (c * g + s * di);
+          rcg[off + (size_t)k] = c;
+          rsg[off + (size_t)k] = s;
+        }
+        if (!ok) {
+          atomicOr(status, 8);
+          break;
+        }
+        __threadfence_block();
+        ctl[5] = seen;
+      }
     }
-    if (lane == 0) I[L.nseg] = nseg;
   }
   __syncthreads();
   // ---- stable descending order of the eigenvalues
