@@ -62,6 +62,16 @@ __device__ __forceinline__ double rhyp_fast(double a, double b) {
   const int ex = (__double2hiint(q) >> 20) & 0x7ff;
   return (ex > 27 && ex < 2019) ? rsqrt(q) : rhypot(a, b);
 }
+// the same with b^2 given (b2 = b * b, computed off the chain)
+__device__ __forceinline__ double rhyp_fast_sq(double a, double b, double b2) {
+  const double q = fma(a, a, b2);
+  const int ex = (__double2hiint(q) >> 20) & 0x7ff;
+  return (ex > 27 && ex < 2019) ? rsqrt(q) : rhypot(a, b);
+}
+__device__ __forceinline__ float rhyp_fast_sq(float a, float b, float b2) {
+  const float q = fmaf(a, a, b2);
+  return (q > 1e-35f && q < 1e35f) ? rsqrtf(q) : rhypotf(a, b);
+}
 __device__ __forceinline__ float rhyp_fast(float a, float b) {
   const float q = fmaf(a, a, b * b);
   return (q > 1e-35f && q < 1e35f) ? rsqrtf(q) : rhypotf(a, b);
@@ -304,6 +314,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   {
     T* qlP = vb;  // the tridiagonalisation's vectors are dead from here on
     T* qlR = pb;
+    T* qlE2 = wb;
     volatile int* ctl = ql_ctl;  // 0 sweep number (-1: end), 1 l, 2 m, 3 off, 4 published, 5 done, 6 abort
     if (tid == 0) {
       ctl[0] = 0;
@@ -350,6 +361,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
             d[l + 1] = dl1;
           }
           for (int i = l + 2 + lane; i < n; i += 32) d[i] -= h;
+          for (int i = l + lane; i < m; i += 32) qlE2[i] = e[i] * e[i];  // e_i^2 for the chain
           f += h;
           __syncwarp();
           ++sweep;
@@ -374,11 +386,11 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
               c2 = c;
               e2 = e1;
               r2 = r1;
-              const T ei = e[i], di = d[i];
-              // the next p = c' d_i - s' g = rr (p d_i - e_i g), g = c e_i:
+              const T ei = e[i], di = d[i], e2 = qlE2[i];
+              // the next p = c' d_i - s' g = rr (p d_i - e_i g), e_i g = c e_i^2:
               // the bracket does not wait for rr
-              const T tq = fma(p, di, -(ei * (c * ei)));
-              const T rr = rhyp_fast(p, ei);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
+              const T tq = fma(p, di, -(c * e2));
+              const T rr = rhyp_fast_sq(p, ei, e2);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
               qlP[i] = p;
               qlR[i] = rr;
               __threadfence_block();
