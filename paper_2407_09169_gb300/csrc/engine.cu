@@ -480,27 +480,13 @@ void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, co
     // X2[w'][(a,s')][(s,l)] = sum_a' A[(a,s')][a'] X1[(w',a')][(s,l)]
     gemm(2 * bl, 2 * Ll, br, wr, 1, 1.0, mv(A, br, 1), mv(X1, 2LL * Ll, 1, (long long)br * 2 * Ll), 0.0,
          ov(X2, 2LL * Ll, 1, 4LL * bl * Ll), role);
-    // W_n[(w,a)][l] = sum_{s,s',w'} W[w][s*2+s'][w'] X2[w'][(a,s')][(s,l)]:
-    // the four (s, s') products in one launch where they fit the CUDA-core
-    // kernel (the operator bond always does), else one product each
+    // W_n[(w,a)][l] = sum_{s,s',w'} W[w][s*2+s'][w'] X2[w'][(a,s')][(s,l)]
     const double* Wss = t.op->Wss(n);
-    if (small_gemm_fits(wl, Ll, wr, bl, 1)) {
-      SumViews V;
-      V.nt = 4;
-      for (int ss = 0; ss < 4; ++ss) {
-        const int s = ss >> 1, sp = ss & 1;
-        V.A[ss] = mv(Wss + (size_t)ss * wl * wr, wr, 1);
-        V.B[ss] = mv(X2 + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll);
-      }
-      TimeScope ts(timer_, TM_SMALL, cur(), 2.0 * 4 * wl * (double)Ll * wr * bl);
-      small_gemm_sum(cur(), tc_mode_[role] >= 0, wl, Ll, wr, bl, 1, V, ov(Wn, (long long)bl * Ll, 1, Ll));
-    } else {
-      for (int ss = 0; ss < 4; ++ss) {
-        const int s = ss >> 1, sp = ss & 1;
-        gemm(wl, Ll, wr, bl, 1, 1.0, mv(Wss + (size_t)ss * wl * wr, wr, 1),
-             mv(X2 + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll), ss == 0 ? 0.0 : 1.0,
-             ov(Wn, (long long)bl * Ll, 1, Ll), role);
-      }
+    for (int ss = 0; ss < 4; ++ss) {
+      const int s = ss >> 1, sp = ss & 1;
+      gemm(wl, Ll, wr, bl, 1, 1.0, mv(Wss + (size_t)ss * wl * wr, wr, 1),
+           mv(X2 + (size_t)sp * 2 * Ll + (size_t)s * Ll, 4LL * bl * Ll, 1, 4LL * Ll), ss == 0 ? 0.0 : 1.0,
+           ov(Wn, (long long)bl * Ll, 1, Ll), role);
     }
   } else {
     const double* H = t.H(n);
@@ -508,23 +494,10 @@ void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, co
     gemm(bl, Ll, br, wr, 2, 1.0, mv(A, 2LL * br, 1, 0, br), mv(X1, 2LL * Ll, 1, (long long)br * 2 * Ll, Ll), 0.0,
          ov(X2, 2LL * wr * Ll, 1, Ll, (long long)wr * Ll), role);
     // W_n[(h,a)][l] = sum_s sum_h' H[h][s][h'] X2[a][s][h'][l], one product per s
-    // accumulated in FP64 (H is shared by every a); both in one launch where
-    // they fit the CUDA-core kernel
-    if (small_gemm_fits(wl, Ll, wr, bl, 1)) {
-      SumViews V;
-      V.nt = 2;
-      for (int s = 0; s < 2; ++s) {
-        V.A[s] = mv(H + (size_t)s * wr, 2LL * wr, 1);
-        V.B[s] = mv(X2 + (size_t)s * wr * Ll, Ll, 1, 2LL * wr * Ll);
-      }
-      TimeScope ts(timer_, TM_SMALL, cur(), 2.0 * 2 * wl * (double)Ll * wr * bl);
-      small_gemm_sum(cur(), tc_mode_[role] >= 0, wl, Ll, wr, bl, 1, V, ov(Wn, (long long)bl * Ll, 1, Ll));
-    } else {
-      for (int s = 0; s < 2; ++s)
-        gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1),
-             mv(X2 + (size_t)s * wr * Ll, Ll, 1, 2LL * wr * Ll), s == 0 ? 0.0 : 1.0, ov(Wn, (long long)bl * Ll, 1, Ll),
-             role);
-    }
+    // accumulated in FP64 (H is shared by every a).
+    for (int s = 0; s < 2; ++s)
+      gemm(wl, Ll, wr, bl, 1, 1.0, mv(H + (size_t)s * wr, 2LL * wr, 1), mv(X2 + (size_t)s * wr * Ll, Ll, 1, 2LL * wr * Ll),
+           s == 0 ? 0.0 : 1.0, ov(Wn, (long long)bl * Ll, 1, Ll), role);
   }
 }
 

@@ -96,67 +96,6 @@ __global__ void __launch_bounds__(SG_THREADS) small_gemm_kernel(int M, int N, in
   }
 }
 
-// C = sum_t A_t B_t over up to four (A_t, B_t) pairs of the same shape in one
-// launch (the four physical-index pairs of an MPO core applied in the sketch
-// pass): each pair's product is summed in T as in small_gemm_kernel, and the
-// pairs' results are added in FP64 in order, C = P_0 + P_1 + ..., the same
-// arithmetic as one small_gemm per pair accumulating into C.
-template <typename T, int MT>
-__global__ void __launch_bounds__(SG_THREADS) small_gemm_sum_kernel(int M, int N, int K, int inner, SumViews V,
-                                                                    OutView C) {
-  pdl_trigger();
-  pdl_wait();
-  __shared__ T As[SG_MAXM * SG_MAXK];
-  const int b = blockIdx.y;
-  const int bo = b / inner, bi = b - bo * inner;
-  const int n = blockIdx.x * SG_THREADS + threadIdx.x;
-  const bool on = n < N;
-  double accd[MT];
-#pragma unroll
-  for (int m = 0; m < MT; ++m) accd[m] = 0.0;
-  for (int t = 0; t < V.nt; ++t) {
-    const MatView& A = V.A[t];
-    const MatView& B = V.B[t];
-    const double* Ab = A.p + bo * A.so + bi * A.si;
-    __syncthreads();  // the previous pair's A is no longer read
-    for (int x = threadIdx.x; x < M * K; x += SG_THREADS) {
-      const int m = x / K, k = x - m * K;
-      As[x] = to_t<T>(Ab[(long long)m * A.rs + (long long)k * A.cs]);
-    }
-    __syncthreads();
-    if (on) {
-      const double* Bb = B.p + bo * B.so + bi * B.si + (long long)n * B.cs;
-      T acc[MT];
-#pragma unroll
-      for (int m = 0; m < MT; ++m) acc[m] = (T)0;
-      for (int k = 0; k < K; ++k) {
-        const T bk = to_t<T>(Bb[(long long)k * B.rs]);
-#pragma unroll
-        for (int m = 0; m < MT; ++m)
-          if (m < M) acc[m] += As[m * K + k] * bk;
-      }
-#pragma unroll
-      for (int m = 0; m < MT; ++m) accd[m] = t == 0 ? to_d<T>(acc[m]) : to_d<T>(acc[m]) + accd[m];
-    }
-  }
-  if (!on) return;
-  double* Cb = C.p + bo * C.so + bi * C.si + (long long)n * C.cs;
-#pragma unroll
-  for (int m = 0; m < MT; ++m)
-    if (m < M) Cb[(long long)m * C.rs] = accd[m];
-}
-
-template <typename T>
-void launch_small_sum(cudaStream_t st, int M, int N, int K, int outer, int inner, const SumViews& V, OutView C) {
-  const dim3 grid((unsigned)((N + SG_THREADS - 1) / SG_THREADS), (unsigned)(outer * inner));
-  if (M <= 8)
-    launch_pdl(small_gemm_sum_kernel<T, 8>, grid, dim3(SG_THREADS), 0, st, M, N, K, inner, V, C);
-  else if (M <= 16)
-    launch_pdl(small_gemm_sum_kernel<T, 16>, grid, dim3(SG_THREADS), 0, st, M, N, K, inner, V, C);
-  else
-    launch_pdl(small_gemm_sum_kernel<T, 32>, grid, dim3(SG_THREADS), 0, st, M, N, K, inner, V, C);
-}
-
 template <typename T>
 void launch_small(cudaStream_t st, int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B,
                   double beta, OutView C) {
@@ -172,15 +111,6 @@ void launch_small(cudaStream_t st, int M, int N, int K, int outer, int inner, do
 
 bool small_gemm_fits(int M, int N, int K, int outer, int inner) {
   return M >= 1 && M <= SG_MAXM && K >= 1 && K <= SG_MAXK && N >= 1 && (long long)outer * inner <= 65535;
-}
-
-void small_gemm_sum(cudaStream_t st, bool fp32, int M, int N, int K, int outer, int inner, const SumViews& V,
-                    OutView C) {
-  count_launches(1);
-  if (fp32)
-    launch_small_sum<float>(st, M, N, K, outer, inner, V, C);
-  else
-    launch_small_sum<double>(st, M, N, K, outer, inner, V, C);
 }
 
 void small_gemm(cudaStream_t st, bool fp32, int M, int N, int K, int outer, int inner, double alpha, MatView A,

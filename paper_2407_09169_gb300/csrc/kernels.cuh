@@ -78,16 +78,6 @@ void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int bat
 bool small_gemm_fits(int M, int N, int K, int outer, int inner);
 void small_gemm(cudaStream_t st, bool fp32, int M, int N, int K, int outer, int inner, double alpha, MatView A,
                 MatView B, double beta, OutView C);
-// C = A_0 B_0 + ... + A_{nt-1} B_{nt-1} (nt <= 4 pairs of the same shape) in
-// one launch: each product in the same arithmetic as small_gemm, the sum over
-// pairs in FP64 in order (equal to nt small_gemm calls accumulating into C).
-struct SumViews {
-  MatView A[4];
-  MatView B[4];
-  int nt;
-};
-void small_gemm_sum(cudaStream_t st, bool fp32, int M, int N, int K, int outer, int inner, const SumViews& V,
-                    OutView C);
 
 // Thin Householder QR of an m x n row-major matrix (m >= n): Q (m x n,
 // row-major) overwrites Qout.  Computed in float (prec_bits 32) or double;
