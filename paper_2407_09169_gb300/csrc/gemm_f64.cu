@@ -184,6 +184,8 @@ constexpr int NS_MAX_SPLIT = 8;
 
 __global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, int nt, int rows_per_split,
                                                       const double* __restrict__ Q, double* __restrict__ P) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double A[32][NS_T + 1], B[32][NS_T + 1];
   // upper-triangular tile pair (ti <= tj) from the linear block index
   int ti = 0, rem = blockIdx.x;
@@ -217,6 +219,8 @@ __global__ void __launch_bounds__(256) ns_gram_kernel(int m, int n, int nt, int 
 
 __global__ void __launch_bounds__(NS_T * NS_C) ns_apply_kernel(int m, int n, int splits, const double* __restrict__ Q,
                                                                const double* __restrict__ P, double* __restrict__ out) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double A[NS_T][33], B[32][NS_C + 1];
   const int tx = threadIdx.x % NS_C, ty = threadIdx.x / NS_C;
   const int r0 = blockIdx.y * NS_T, c0 = blockIdx.x * NS_C;
@@ -317,9 +321,9 @@ void newton_schulz_step(cudaStream_t st, int m, int n, const double* Q, double* 
   splits = std::max(1, std::min({splits, chunks, NS_MAX_SPLIT}));
   const int rows = ((chunks + splits - 1) / splits) * 32;
   splits = (m + rows - 1) / rows;
-  ns_gram_kernel<<<dim3((unsigned)pairs, (unsigned)splits), 256, 0, st>>>(m, n, nt, rows, Q, G);
+  launch_pdl_chain(ns_gram_kernel, dim3((unsigned)pairs, (unsigned)splits), dim3(256), 0, st, m, n, nt, rows, Q, G);
   const unsigned bc = (unsigned)((n + NS_C - 1) / NS_C), bm = (unsigned)((m + NS_T - 1) / NS_T);
-  ns_apply_kernel<<<dim3(bc, bm), NS_T * NS_C, 0, st>>>(m, n, splits, Q, G, out);
+  launch_pdl_chain(ns_apply_kernel, dim3(bc, bm), dim3(NS_T * NS_C), 0, st, m, n, splits, Q, (const double*)G, out);
 }
 
 }  // namespace qtt

@@ -42,6 +42,25 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   cfg.numAttrs = pdl_enabled() ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
+// The same with the attribute always set: for the short chain QR factorisation
+// -> Q formation -> Newton-Schulz Gram -> apply, whose kernels occupy few SMs
+// each, so that the next one is resident (waiting in pdl_wait) when the
+// previous one ends.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // Operand view for the strided batched GEMM: element (i, j) of batch
 // (bo, bi) lives at p[bo * so + bi * si + i * rs + j * cs].

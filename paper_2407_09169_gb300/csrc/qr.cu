@@ -646,7 +646,8 @@ bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, in
   launch_pdl(qr_reg_kernel<RPL, CPW>, dim3(1), dim3(QRR_THREADS), smem, st, m, n, A, Qout, split, status);
   if (split) {
     const int nb = (n + QRR_WARPS - 1) / QRR_WARPS;
-    launch_pdl(qr_formq_kernel<RPL>, dim3(nb), dim3(QRR_THREADS), formq_smem(n), st, m, n, (const float*)split, Qout);
+    launch_pdl_chain(qr_formq_kernel<RPL>, dim3(nb), dim3(QRR_THREADS), formq_smem(n), st, m, n, (const float*)split,
+                     Qout);
     count_launches(1);
   }
   return true;
