@@ -12,9 +12,10 @@ static unsigned long long g_launches = 0;
 unsigned long long launch_count() { return g_launches; }
 void count_launches(int n) { g_launches += (unsigned long long)n; }
 // Off unless QTT_PDL=1: measured on the 2^8-point chi = 128 workload, the
-// early launch of dependents cost 4-5% of the step (12.4 -> 11.7 steps/s for
-// BF16X3, 9.95 -> 9.5 for FP32) -- waiting CTAs hold SM slots that the
-// running kernel's later CTAs need.
+// early launch of dependents for every kernel cost 4-5% of the step when it
+// was built (12.4 -> 11.7 steps/s for BF16X3) and 10% on later kernels (22.3
+// -> 20.0) -- waiting CTAs hold SM slots that the running kernel's later CTAs
+// need.  (launch_pdl_chain sets it for one short chain regardless.)
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("QTT_PDL");
