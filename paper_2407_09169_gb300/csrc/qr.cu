@@ -168,9 +168,11 @@ __global__ void __launch_bounds__(qr_threads<T>()) qr_thin_kernel(int m, int n, 
 // barrier: a warp waits only for the flag of the reflector it applies next.
 // The owner of column j + 1 applies H_j to that column first, forms H_{j+1}
 // and raises its flag before it updates its other columns, which keeps the
-// chain of reflectors short (a look-ahead of one column).  Q is accumulated
-// backwards in the same register layout, with no synchronisation at all.
-// Both loops pair columns through the packed FP32x2 FMA (FFMA2).
+// chain of reflectors short (a look-ahead of one column).  For the small
+// shapes Q is then accumulated backwards in the same register layout, with no
+// synchronisation at all; for the larger ones (Vg given) the block hands the
+// reflectors to qr_formq_kernel, which forms the columns of Q over several
+// blocks.  Both loops pair columns through the packed FP32x2 FMA (FFMA2).
 
 // d0 += a0 * b0, d1 += a1 * b1 in one packed FP32x2 instruction.
 __device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
