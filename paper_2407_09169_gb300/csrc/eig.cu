@@ -8,18 +8,19 @@
 // Three kernels, so that the FP64 work does not all sit on one SM:
 //   1. eig_tridiag_ql (one block): Householder reduction to tridiagonal form
 //      (matrix in shared memory when it fits, lower-triangle updates), then
-//      the implicit-shift QL iteration on (d, e) run by one warp (one lane
-//      carries the rotation chain, which records every Givens rotation of
-//      every sweep in a list), and a stable descending order of the
-//      eigenvalues;
+//      the implicit-shift QL iteration on (d, e) run by warp 0 (one lane
+//      carries the rotation chain; a lane of warp 1 applies each rotation to
+//      d and e and records it in a list of every sweep's rotations), and a
+//      stable descending order of the eigenvalues;
 //   2. eig_apply_rotations (one thread per row of the eigenvector matrix Z of
 //      the tridiagonal problem, over several blocks): replays the rotation
 //      list on its row;
 //   3. eig_back_transform (one warp per kept eigenvector): applies the
 //      Householder reflectors, U[:, r] = H_0 ... H_{n-3} Z[:, order[r]].
 // Every loop is bounded; the QL iteration stops after 60 sweeps per
-// eigenvalue (or when the rotation list is full) and reports that through the
-// status word.
+// eigenvalue (or when the rotation list is full), and the two QL lanes wait
+// on each other for at most about a second; both report through the status
+// word (bits 2 and 8).
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"

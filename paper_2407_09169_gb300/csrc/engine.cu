@@ -852,6 +852,12 @@ int Engine::check_status(std::string& msg) {
     msg = "non-finite value in the state after step " + std::to_string(steps_);
     return 6;  // QTT_ENAN
   }
+  if (h[0] & (4 | 8)) {
+    msg = (h[0] & 8) ? "eigensolver: the two QL lanes gave up waiting on each other"
+                     : "QR: a warp gave up waiting on a reflector";
+    QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), st_));
+    return 5;  // QTT_ETIMEOUT
+  }
   if (h[0] & 2) {
     msg = "eigen-decomposition hit its QL sweep cap";
     QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), st_));
