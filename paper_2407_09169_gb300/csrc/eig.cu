@@ -9,8 +9,8 @@
 //   1. eig_tridiag_ql (one block): Householder reduction to tridiagonal form
 //      (matrix in shared memory when it fits, lower-triangle updates), then
 //      the implicit-shift QL iteration on (d, e) run by warp 0 (one lane
-//      carries the rotation chain; a lane of warp 1 applies each rotation to
-//      d and e and records it in a list of every sweep's rotations), and a
+//      carries the rotation chain; lanes of warps 1 and 2 apply each rotation
+//      to e and d and record it in a list of every sweep's rotations), and a
 //      stable descending order of the eigenvalues;
 //   2. eig_apply_rotations (one thread per row of the eigenvector matrix Z of
 //      the tridiagonal problem, over several blocks): replays the rotation
@@ -307,21 +307,24 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   // its lanes, and lane 0 carries the rotation chain.  FP64 instructions cost
   // the same whatever the number of active lanes, so the chain lane keeps only
   // the operations the next rotation depends on (sum of squares, reciprocal
-  // square root, cosine, next p) and hands (p, 1/hypot) of every rotation to
-  // lane 0 of warp 1, which runs on another scheduler's FP64 pipe one rotation
-  // behind: it forms the cosine and sine, updates d[i+1] and e[i+1] (positions
-  // the chain has passed) and records the rotation.  The chain waits for it at
-  // the end of each sweep.  Every wait is bounded (status bit 8 on expiry).
+  // square root, cosine, next p) and hands (p, 1/hypot, e_i) of every
+  // rotation to lane 0 of warps 1 and 2, which run on two other schedulers'
+  // FP64 pipes one rotation behind: both form the cosine and sine, warp 1
+  // updates e[i+1] and records the rotation, warp 2 updates d[i+1] (positions
+  // the chain has passed).  The chain waits for both at the end of each
+  // sweep.  Every wait is bounded (status bit 8 on expiry).
   {
     T* qlP = vb;  // the tridiagonalisation's vectors are dead from here on
     T* qlR = pb;
     T* qlE2 = wb;
-    volatile int* ctl = ql_ctl;  // 0 sweep number (-1: end), 1 l, 2 m, 3 off, 4 published, 5 done, 6 abort
+    T* qlEi = tauv;
+    volatile int* ctl = ql_ctl;  // 0 sweep number (-1: end), 1 l, 2 m, 3 off, 4 published, 5 / 7 done (e / d), 6 abort
     if (tid == 0) {
       ctl[0] = 0;
       ctl[4] = 0;
       ctl[5] = 0;
       ctl[6] = 0;
+      ctl[7] = 0;
     }
     __syncthreads();
     if (warp == 0) {
@@ -394,6 +397,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
               const T rr = rhyp_fast_sq(p, ei, e2);  // 1 / hypot(p, e_i); e_i != 0 inside an unreduced block
               qlP[i] = p;
               qlR[i] = rr;
+              qlEi[i] = ei;
               __threadfence_block();
               ctl[4] = k + 1;
               c = p * rr;
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
             p = -s * s2 * c3 * el1 * e[l] / dl1;
             // the helper reads e[l] and d[l] in the last rotation and writes
             // d[l+1 ..], e[l+1 ..]: wait for it before e[l], d[l] and the next search
-            if (!ql_wait_eq(ctl + 5, sweep, ctl + 6)) atomicOr(status, 8);
+            if (!ql_wait_eq(ctl + 5, sweep, ctl + 6) || !ql_wait_eq(ctl + 7, sweep, ctl + 6)) atomicOr(status, 8);
             __threadfence_block();
             e[l] = s * p;
             d[l] = c * p;
@@ -428,7 +432,12 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
         __threadfence_block();
         ctl[0] = -1;
       }
-    } else if (warp == 1 && lane == 0) {
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+      // warp 1: e[i+1] and the rotation list; warp 2: d[i+1] (two schedulers'
+      // FP64 pipes).  Each reads the original e_i and d_i of its own
+      // positions; warp 2 takes e_i from the chain's copy, since warp 1 may
+      // already have overwritten it.
+      const bool upd_e = warp == 1;
       int seen = 0;
       for (;;) {
         const int sw = ql_wait_change(ctl, seen, ctl + 6);
@@ -448,24 +457,32 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
           if (!ok) break;
           __threadfence_block();
           const int i = m - 1 - k;
-          const T p = qlP[i], rr = qlR[i], ei = e[i], di = d[i];
-          const T g = c * ei;
-          const T hh = c * p;
-          const T cn = p * rr, sn = ei * rr;
-          const T r = p * cn + ei * sn;  // hypot(p, e_i)
-          e[i + 1] = s * r;               // previous sine
-          s = sn;
-          c = cn;
-          d[i + 1] = hh + s * (c * g + s * di);
-          rcg[off + (size_t)k] = c;
-          rsg[off + (size_t)k] = s;
+          const T p = qlP[i], rr = qlR[i];
+          if (upd_e) {
+            const T ei = e[i];
+            const T cn = p * rr, sn = ei * rr;
+            const T r = p * cn + ei * sn;  // hypot(p, e_i)
+            e[i + 1] = s * r;               // previous sine
+            s = sn;
+            c = cn;
+            rcg[off + (size_t)k] = c;
+            rsg[off + (size_t)k] = s;
+          } else {
+            const T ei = qlEi[i], di = d[i];
+            const T g = c * ei;
+            const T hh = c * p;
+            const T cn = p * rr, sn = ei * rr;
+            s = sn;
+            c = cn;
+            d[i + 1] = hh + s * (c * g + s * di);
+          }
         }
         if (!ok) {
           atomicOr(status, 8);
           break;
         }
         __threadfence_block();
-        ctl[5] = seen;
+        ctl[upd_e ? 5 : 7] = seen;
       }
     }
   }
