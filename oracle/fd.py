@@ -37,7 +37,11 @@ What it computes (plain FP64 numpy, no blocking or fusion):
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, Fourier-exact solutions, conservation laws, the moment
-equation, brute-force sums and the paper's NVPP values).
+equation, brute-force sums and the paper's NVPP values).  The integrated
+statistics of ``observables`` (<Phi_1 Phi_2>, R12 of Eq. RACov, Y12 of
+Eq. SGSCov, J) are pinned by closed forms of a phi-separable PDF (Y12 = 0),
+an x-uniform two-point PDF (R12 = 0, Y12 = the two-point covariance) and the
+interior tanh blend (R12 and Y12 from the blend weights alone).
 """
 from __future__ import annotations
 

@@ -364,3 +364,86 @@ def test_moving_gaussian_initial_pdf():
     X1, X2, _ = np.meshgrid(*g.x, indexing="ij")
     c1 = 0.4 + 0.2 * np.sin(X1) * np.cos(X2)
     assert np.max(np.abs(m1 - c1)) < 0.02
+
+
+# ------------- integrated statistics (Eqs. spaceAvg, RACov, SGSCov), closed forms
+def _blend_pdf_params(**kw):
+    return _params([5, 5, 2, 4, 2], ic_c_hi=[0.62, 0.41], ic_c_lo=[0.35, 0.58], **kw)
+
+
+def test_statistics_of_phi_separable_pdf():
+    """f(phi1, phi2; x) = g1(phi1; x) g2(phi2; x) with each 1-D factor
+    normalised on its phi grid: <1> = 1, <Phi_1 Phi_2>(x) = m1(x) m2(x) exactly,
+    so Y12 = 0 and the space average of <Phi_1 Phi_2> is avg(m1 m2), with
+    m_a(x) = h_a sum_i phi_i g_a(phi_i; x) taken from the 1-D factors alone.
+    The centres move with x in step, so R12 = Cov_x(m1, m2) is far from zero
+    (an R12 / Y12 mix-up or a dropped h_phi factor fails here)."""
+    bits = [4, 5, 2, 3, 2]
+    g = oracle.make_grid(bits)
+    X1, X2, X3 = np.meshgrid(*g.x, indexing="ij")
+    c1 = 0.5 + 0.2 * np.sin(X2) * np.cos(X1)
+    c2 = 0.45 + 0.15 * np.sin(X2) * np.cos(X1) + 0.05 * np.cos(X3)
+    s1, s2 = 0.11, 0.07
+    g1 = np.exp(-(g.phi[0][:, None, None, None] - c1[None]) ** 2 / (2 * s1 * s1))
+    g2 = np.exp(-(g.phi[1][:, None, None, None] - c2[None]) ** 2 / (2 * s2 * s2))
+    g1 /= g1.sum(axis=0, keepdims=True) * g.h_phi[0]
+    g2 /= g2.sum(axis=0, keepdims=True) * g.h_phi[1]
+    f = g1[:, None] * g2[None, :]
+    m1 = g.h_phi[0] * (g.phi[0][:, None, None, None] * g1).sum(axis=0)
+    m2 = g.h_phi[1] * (g.phi[1][:, None, None, None] * g2).sum(axis=0)
+    o = oracle.observables(f, g)
+    assert abs(o["norm_avg"] - 1.0) < 1e-14
+    assert abs(o["Y12"]) < 1e-15
+    assert abs(o["phi12_avg"] - float((m1 * m2).mean())) < 1e-14
+    r12 = float((m1 * m2).mean() - m1.mean() * m2.mean())
+    assert abs(o["R12"] - r12) < 1e-14
+    assert r12 > 1e-3
+
+
+def test_statistics_of_x_uniform_two_point_pdf():
+    """A PDF that does not depend on x and puts weight 1/2 on each of the two
+    cells (i1, i2) = (a1, a2) and (b1, b2): R12 = 0 (no spatial fluctuation of
+    the means), and Y12 is the covariance of a two-point distribution,
+    (phi1_a - phi1_b)(phi2_a - phi2_b) / 4; <Phi_1 Phi_2> is the mean of the
+    two products."""
+    bits = [3, 4, 2, 1, 2]
+    g = oracle.make_grid(bits)
+    a, b = (1, 12), (6, 3)
+    f = np.zeros(g.shape)
+    w = 0.5 / (g.h_phi[0] * g.h_phi[1])
+    f[a[0], a[1]] = w
+    f[b[0], b[1]] = w
+    pa = (g.phi[0][a[0]], g.phi[1][a[1]])
+    pb = (g.phi[0][b[0]], g.phi[1][b[1]])
+    o = oracle.observables(f, g)
+    assert abs(o["norm_avg"] - 1.0) < 1e-14
+    assert abs(o["R12"]) < 1e-16
+    assert abs(o["Y12"] - (pa[0] - pb[0]) * (pa[1] - pb[1]) / 4) < 1e-15
+    assert abs(o["phi12_avg"] - (pa[0] * pa[1] + pb[0] * pb[1]) / 2) < 1e-15
+    assert abs(o["phi11_avg"] - (pa[0] ** 2 + pb[0] ** 2) / 2) < 1e-15
+    assert abs(o["Y12"]) > 0.05
+
+
+def test_statistics_of_interior_tanh_blend():
+    """f = w(x2) G_hi + (1 - w(x2)) G_lo with two interior Gaussians (centres
+    c_hi, c_lo; uncorrelated, so E[phi1 phi2] = c1 c2 for each): with
+    d_a = c_hi,a - c_lo,a the statistics follow from the blend weights alone,
+      R12 = d1 d2 (avg(w^2) - avg(w)^2)          (Eq. RACov)
+      Y12 = d1 d2 avg(w (1 - w))                 (Eq. SGSCov)
+      avg <Phi_1 Phi_2> = avg(w) c_hi,1 c_hi,2 + (1 - avg(w)) c_lo,1 c_lo,2
+      J = avg(<1 - phi1 - phi2>) = 1 - sum_a [avg(w) c_hi,a + (1 - avg(w)) c_lo,a]
+    (discrete Gaussian moments are exact to e^{-2 pi^2 sigma^2 / h^2} and the
+    wall truncation of the tails is below 1e-12)."""
+    p = _blend_pdf_params()
+    g = oracle.make_grid(p["bits"])
+    o = oracle.observables(oracle.initial_pdf(p, g), g)
+    w = 0.5 * (1 + np.tanh((g.x[1] - math.pi) / p["ic_blend_width"]))
+    hi, lo = p["ic_c_hi"], p["ic_c_lo"]
+    d1, d2 = hi[0] - lo[0], hi[1] - lo[1]
+    aw, aw2 = float(w.mean()), float((w * w).mean())
+    assert abs(o["R12"] - d1 * d2 * (aw2 - aw * aw)) < 1e-12
+    assert abs(o["Y12"] - d1 * d2 * float((w * (1 - w)).mean())) < 1e-12
+    assert abs(o["phi12_avg"] - (aw * hi[0] * hi[1] + (1 - aw) * lo[0] * lo[1])) < 1e-12
+    assert abs(o["product_J"] - (1 - sum(aw * hi[k] + (1 - aw) * lo[k] for k in range(2)))) < 1e-12
+    # both covariances are exercised (negative: the centres move in opposite directions)
+    assert o["R12"] < -1e-2 and o["Y12"] < -5e-4 and abs(o["R12"] - o["Y12"]) > 1e-3
