@@ -655,6 +655,266 @@ bool try_qr_reg(cudaStream_t st, int m, int n, const double* A, double* Qout, in
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 QR over a cluster of CTAs.  FP64 issues at two FMAs per clock per SM
+// on this GPU, so one block needs ~1 ms for the 272 x 136 factorisation
+// alone; the factorisation is spread over the P CTAs of a thread-block
+// cluster instead.  Column c belongs to warp c / P of CTA c % P (cyclic, so
+// every CTA keeps work until the end) and lives in that warp's registers
+// (rows lane + 32 k).  A warp applies the reflectors 0 .. c-1 as they appear
+// and then forms reflector c itself: the owner of column j + 1 is the first
+// to take H_j, which gives the one-column look-ahead with no further
+// arrangement.  Reflector c stays in its owner's shared memory (v_c with
+// v_c[c] = 1 and zeros above, tau_c); readiness is an mbarrier per reflector
+// in every CTA, on which the owner's lane r arrives remotely (release at
+// cluster scope) for CTA r, and the consumers read v_c through distributed
+// shared memory after an acquire-wait on their local barrier.  Waits are
+// bounded (status bit 4 when one gives up).  The reflectors then go to
+// global memory (work: n rows of m doubles, then tau), from which
+// qr64_formq_kernel forms the columns of Q over n blocks.
+constexpr long long QR64_WAIT_POLLS = 1LL << 24;
+
+__device__ __forceinline__ uint32_t qr64_mapa(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double qr64_ld_remote(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void qr64_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t qr64_cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+template <int RPL>
+__global__ void __launch_bounds__(512) qr64_cluster_kernel(int m, int n, int P, const double* __restrict__ A, double* __restrict__ Vg,
+                                    int ldv, int* status) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  const int wpc = blockDim.x >> 5;                                  // columns (warps) per CTA
+  double* V = (double*)qr_smem;                                     // [wpc][32 RPL] own reflectors
+  double* tau = V + (size_t)wpc * 32 * RPL;                         // [wpc]
+  uint64_t* bar = (uint64_t*)(tau + ((wpc + 1) & ~1));              // [n] one per reflector
+  const int rank = (int)qr64_cluster_rank();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int j = tid; j < n; j += blockDim.x)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(qrr_smem_u32(bar + j)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const int c = rank + P * w;  // the column this warp owns
+  double X[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int i = lane + 32 * k;
+    X[k] = (c < n && i < m) ? A[(size_t)i * n + c] : 0.0;
+  }
+  qr64_cluster_sync();  // every barrier of every CTA is initialised
+  const uint32_t V0 = qrr_smem_u32(V), T0 = qrr_smem_u32(tau);
+  bool alive = c < n;
+  for (int j = 0; j < c && alive; ++j) {
+    // bounded acquire-wait (cluster scope) on the local barrier of reflector j
+    const uint32_t b = qrr_smem_u32(bar + j);
+    bool ok = false;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (long long it = 0; it < QR64_WAIT_POLLS && !ok; ++it) {
+      uint32_t r;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(r)
+          : "r"(b)
+          : "memory");
+      ok = r != 0;
+      if (!ok && (it & 255) == 255) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) break;
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicOr(status, 4);
+      alive = false;
+      break;
+    }
+    const uint32_t owner = (uint32_t)(j % P), slot = (uint32_t)(j / P);
+    const uint32_t vb = qr64_mapa(V0 + slot * 32 * RPL * 8, owner);
+    const double t = qr64_ld_remote(qr64_mapa(T0 + slot * 8, owner));
+    if (t == 0.0) continue;
+    double v[RPL], d = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) v[k] = qr64_ld_remote(vb + (lane + 32 * k) * 8);
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) d = fma(v[k], X[k], d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const double f = -t * d;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) X[k] = fma(f, v[k], X[k]);
+  }
+  if (alive) {
+    // reflector of column c: v = (x - beta e_c) / (x_c - beta) on rows >= c
+    double s = 0.0, a = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = lane + 32 * k;
+      if (i > c) s = fma(X[k], X[k], s);
+      if (i == c) a = X[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+    }
+    double t = 0.0, v0 = 1.0;
+    if (s != 0.0) {
+      const double mu = sqrt(fma(a, a, s));
+      const double beta = a <= 0.0 ? mu : -mu;
+      t = (beta - a) / beta;
+      v0 = a - beta;  // |v0| >= mu >= |x_i|
+    }
+    double* vc = V + (size_t)w * 32 * RPL;
+    const double rv0 = t != 0.0 ? 1.0 / v0 : 0.0;
+    const bool tiny = fabs(v0) < 1e-300;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int i = lane + 32 * k;
+      const double vi = i < c ? 0.0 : (i == c ? 1.0 : (tiny ? X[k] / v0 : X[k] * rv0));
+      vc[i] = vi;
+      if (i < m) Vg[(size_t)c * ldv + i] = vi;
+    }
+    if (lane == 0) {
+      tau[w] = t;
+      Vg[(size_t)n * ldv + c] = t;
+      if (!isfinite(t)) atomicOr(status, 1);
+    }
+    // every lane's stores of v are ordered before the release-arrives below
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+    __syncwarp();
+    if (lane < P) {
+      const uint32_t rb = qr64_mapa(qrr_smem_u32(bar + c), (uint32_t)lane);
+      asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rb) : "memory");
+    }
+  }
+  qr64_cluster_sync();  // no CTA leaves while another may still read its reflectors
+}
+
+// Q = H_0 ... H_{n-1} [I; 0] column by column: block c forms Q e_c =
+// H_0 ... H_c e_c (128 threads, rows t + 128 r), one block reduction per
+// reflector; the next reflector's rows are loaded before the reduction.
+constexpr int QR64_FQ_THREADS = 128;
+__global__ void __launch_bounds__(QR64_FQ_THREADS) qr64_formq_kernel(int m, int n, const double* __restrict__ Vg,
+                                                                     int ldv, double* __restrict__ Qout) {
+  constexpr int R = 3;  // m <= 384
+  __shared__ double part[2][QR64_FQ_THREADS / 32];
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const double* tau = Vg + (size_t)n * ldv;
+  double x[R], v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = tid + QR64_FQ_THREADS * r;
+    x[r] = i == c ? 1.0 : 0.0;
+    v[r] = i < m ? Vg[(size_t)c * ldv + i] : 0.0;
+  }
+  int ph = 0;  // reduction slot: alternates with every block barrier taken
+  for (int j = c; j >= 0; --j) {
+    const double t = tau[j];
+    double vn[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = tid + QR64_FQ_THREADS * r;
+      vn[r] = (j > 0 && i < m) ? Vg[(size_t)(j - 1) * ldv + i] : 0.0;
+    }
+    if (t != 0.0) {  // uniform across the block
+      double d = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) d = fma(v[r], x[r], d);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) part[ph][w] = d;
+      __syncthreads();
+      d = 0.0;
+#pragma unroll
+      for (int q = 0; q < QR64_FQ_THREADS / 32; ++q) d += part[ph][q];
+      ph ^= 1;
+      const double f = -t * d;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = fma(f, v[r], x[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = vn[r];
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = tid + QR64_FQ_THREADS * r;
+    if (i < m) Qout[(size_t)i * n + c] = x[r];
+  }
+}
+
+// Launches the cluster factorisation and the Q formation; false when the
+// shape or the GPU does not take it (the caller then uses the one-block QR).
+// work: n (m + 1) doubles.
+template <int RPL>
+bool try_qr64_cluster(cudaStream_t st, int m, int n, const double* A, double* Qout, double* work, int* status) {
+  if (m > 32 * RPL || m > 3 * QR64_FQ_THREADS) return false;
+  static int P = -1;  // cluster size: 16 where the GPU takes it, else 8, else 0
+  const int wpc_max = 16;  // 512 threads: the register file takes every RPL used here
+  if (P < 0) {
+    P = 0;
+    cudaFuncSetAttribute(qr64_cluster_kernel<RPL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const size_t smem_max = (size_t)wpc_max * 32 * RPL * 8 + (wpc_max + 2) * 8 + (size_t)16 * wpc_max * 8;
+    cudaFuncSetAttribute(qr64_cluster_kernel<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    for (int cand : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cand);
+      cfg.blockDim = dim3(32 * 9);
+      cfg.dynamicSmemBytes = (size_t)9 * 32 * RPL * 8 + 16 * 8 + (size_t)cand * 9 * 8;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cand;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, qr64_cluster_kernel<RPL>, &cfg) == cudaSuccess && nclusters > 0) {
+        P = cand;
+        break;
+      }
+      cudaGetLastError();
+    }
+  }
+  if (P == 0) return false;
+  const int wpc = (n + P - 1) / P;
+  if (wpc > wpc_max) return false;
+  const int ldv = m;  // row stride of the reflectors in work (rows >= m are not stored)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P);
+  cfg.blockDim = dim3(32 * wpc);
+  // shared: wpc reflector slots of 32 RPL doubles, tau (rounded up to an even count), n barriers
+  cfg.dynamicSmemBytes = (size_t)wpc * 32 * RPL * 8 + (size_t)((wpc + 1) & ~1) * 8 + (size_t)n * 8;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, qr64_cluster_kernel<RPL>, m, n, P, A, work, ldv, status) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  qr64_formq_kernel<<<n, QR64_FQ_THREADS, 0, st>>>(m, n, (const double*)work, ldv, Qout);
+  count_launches(1);
+  return true;
+}
+
 template <typename T>
 void launch_qr(cudaStream_t st, int m, int n, const double* A, double* Qout, void* work, int* status) {
   static bool attr = false;
@@ -684,8 +944,14 @@ void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void*
       return;
     launch_qr<float>(st, m, n, A, Qout, work, status);
   }
-  else
+  else {
+    if (try_qr64_cluster<3>(st, m, n, A, Qout, (double*)work, status) ||
+        try_qr64_cluster<5>(st, m, n, A, Qout, (double*)work, status) ||
+        try_qr64_cluster<9>(st, m, n, A, Qout, (double*)work, status) ||
+        try_qr64_cluster<12>(st, m, n, A, Qout, (double*)work, status))
+      return;
     launch_qr<double>(st, m, n, A, Qout, work, status);
+  }
 }
 
 }  // namespace qtt
