@@ -940,6 +940,7 @@ void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_r
     R *= 2;
     bond = br;
   }
+  QTT_CUDA(cudaGetLastError());
   QTT_CUDA(cudaMemcpyAsync(out, a, sizeof(double) * R, cudaMemcpyDeviceToHost, st_));
   QTT_CUDA(cudaStreamSynchronize(st_));
   cudaFree(a);

@@ -273,6 +273,19 @@ int gemm_split_k(int M, int N, int K, int batch) {
 void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B,
               double beta, OutView C, double* ws, size_t ws_elems) {
   if (M <= 0 || N <= 0 || outer <= 0 || inner <= 0) return;
+  // The row tiles run along grid.y (at most 65535 blocks): taller products
+  // (the dense decompression of a large chain) are issued in row chunks.
+  constexpr int kRowsPerCall = 1 << 19;
+  if (M > kRowsPerCall) {
+    for (int m0 = 0; m0 < M; m0 += kRowsPerCall) {
+      MatView Ac = A;
+      OutView Cc = C;
+      Ac.p += (long long)m0 * A.rs;
+      Cc.p += (long long)m0 * C.rs;
+      gemm_f64(st, std::min(kRowsPerCall, M - m0), N, K, outer, inner, alpha, Ac, B, beta, Cc, ws, ws_elems);
+    }
+    return;
+  }
   const int batch = outer * inner;
   if (K <= 0) {  // empty contraction: C = beta * C
     const long long total = (long long)M * N * batch;
