@@ -81,6 +81,35 @@ struct Chain {
   int n;
 };
 
+#ifdef __CUDACC__
+// f at one grid point, evaluated by one warp: the row vector v (length of the
+// current bond) is carried through the chain, v <- v A_n[:, s_n, :], with s_n
+// the n-th index bit of the point, read by bit(n) (any flag type: bytes or
+// 0/1 doubles).  v and v2 are two scratch rows of max_bond doubles owned by
+// the warp; every entry read has been written first, so the scratch needs no
+// clearing.  Returns the value on every lane.
+template <typename BitFn>
+__device__ __forceinline__ double eval_point_warp(const Chain& f, BitFn bit, double* v, double* v2) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) v[0] = 1.0;
+  __syncwarp();
+  for (int n = 0; n < f.n; ++n) {
+    const int bl = f.bond[n], br = f.bond[n + 1];
+    const int s = bit(n) ? 1 : 0;
+    const double* A = f.core[n];
+    for (int c = lane; c < br; c += 32) {
+      double acc = 0.0;
+      for (int b = 0; b < bl; ++b) acc += v[b] * A[((size_t)b * 2 + s) * br + c];
+      v2[c] = acc;
+    }
+    __syncwarp();
+    for (int c = lane; c < br; c += 32) v[c] = v2[c];
+    __syncwarp();
+  }
+  return v[0];
+}
+#endif
+
 // C[b] = alpha * A[b] * B[b] + beta * C[b] for b in [0, outer * inner).
 // M x K times K x N.  A split of K accumulates partial products in `ws`
 // (reduced in a fixed order, so results are deterministic); ws must hold

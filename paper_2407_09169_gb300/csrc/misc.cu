@@ -244,23 +244,9 @@ __global__ void eval_points_kernel(Chain f, int npts, const unsigned char* bits,
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= npts) return;
   double* v = work + (size_t)warp * 2 * max_bond;
-  double* v2 = v + max_bond;
-  if (lane == 0) v[0] = 1.0;
-  __syncwarp();
-  for (int n = 0; n < f.n; ++n) {
-    const int bl = f.bond[n], br = f.bond[n + 1];
-    const int s = bits[(size_t)warp * f.n + n] ? 1 : 0;
-    const double* A = f.core[n];
-    for (int c = lane; c < br; c += 32) {
-      double acc = 0.0;
-      for (int b = 0; b < bl; ++b) acc += v[b] * A[((size_t)b * 2 + s) * br + c];
-      v2[c] = acc;
-    }
-    __syncwarp();
-    for (int c = lane; c < br; c += 32) v[c] = v2[c];
-    __syncwarp();
-  }
-  if (lane == 0) out[warp] = v[0];
+  const unsigned char* b = bits + (size_t)warp * f.n;
+  const double val = eval_point_warp(f, [b](int n) { return b[n] != 0; }, v, v + max_bond);
+  if (lane == 0) out[warp] = val;
 }
 
 __global__ void finite_kernel(const double* p, size_t n, int* flag) {
