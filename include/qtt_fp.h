@@ -184,17 +184,22 @@ qtt_status qtt_load(qtt_ctx* ctx, const char* path);
 /* Allocation-free variant of qtt_observe(ctx, QTT_OBS_POINTS, ...), same
  * arguments and result: inout holds n groups of N index bits (doubles 0/1,
  * most significant bit first per dimension), cap = n * N, and the first n
- * entries receive f at those points.  The paper has no counterpart; this
- * serves callers that must not allocate device memory during the call (for
- * example while a stream is being captured into a CUDA graph, or in a
- * per-step monitoring loop that cannot afford cudaFree's implicit device
- * synchronisation).  The query, scratch and results use one 4 MiB device
- * array fixed at compile time and shared by the whole process: at most
- * floor((4 MiB - 768) / (8 + 8 N + 16 (chi_max + oversample))) points per
- * call; larger requests return QTT_EINVAL with the limit in the message.
- * The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  Calls
- * whose work overlaps on the GPU race on the shared array: serialise them. */
+ * entries receive f at those points.  The paper has no counterpart.  It
+ * serves callers that cannot allocate device memory during the call: a
+ * process whose device memory is entirely held by its own pool allocator, or
+ * a per-step monitoring loop that cannot pay cudaFree's implicit device-wide
+ * synchronisation.  The call copies the query in and the values out on the
+ * context's stream and synchronises that stream before returning.  The query,
+ * scratch and results use one 4 MiB device array fixed at compile time and
+ * shared by the whole process, which limits a call to
+ * floor((4 MiB - 768) / (8 + 8 N + 16 B)) points, B the largest bond the
+ * context works with: chi_max + oversample for a truncating context (about
+ * 1670 points at N = 40, chi_max 128), 2^floor(N/2) in exact mode (about 250
+ * at N = 20).  Larger requests return QTT_EINVAL, the message giving the
+ * limit.  The first call on a device looks up that array's device address
+ * (with the device current); make that first call before any stream capture.
+ * Calls whose work overlaps on the GPU race on the shared array: serialise
+ * them. */
 qtt_status qtt_observe_points_noalloc(qtt_ctx* ctx, double* inout, int64_t cap, int64_t* written);
 
 void qtt_destroy(qtt_ctx* ctx);
@@ -246,7 +251,17 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
  *      in modes BF16 and BF16X3 (calls including the operand packing): per
  *      case n, the mode's enum value (BF16 3, BF16X3 0), TFLOP/s at 2 n^3 per
  *      call, and the max of |C - C_fp64| / sum_k |A_ik B_kj| over 16 sampled
- *      entries (needs ~3 GiB of device memory) */
+ *      entries (needs ~3 GiB of device memory)
+ *   5  tensor-core GEMM on seeded operands, for a check on the host: per case
+ *      a header (M, N, K, outer, inner, A transposed, B transposed, beta;
+ *      alpha = 1.5), A, B and the initial C as stored (batch-major; row-major,
+ *      or column-major when transposed), then C after each of the modes
+ *      BF16X3, TF32, TF32X3, BF16, BF16X6 (NaN where a mode does not take
+ *      the shape); four cases, about 9.1 million values
+ *   6  FP64 arithmetic throughput of the GPU: TFLOP/s of DFMA on the CUDA
+ *      cores and of mma.sync m8n8k4 f64 (each the best of three launches of
+ *      8 blocks of 256 threads per SM, 2 flops per FMA), the SM count and
+ *      the number of blocks */
 qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written);
 
 #ifdef __cplusplus

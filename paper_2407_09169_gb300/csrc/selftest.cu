@@ -19,6 +19,43 @@ struct DBuf {
   ~DBuf() { cudaFree(p); }
 };
 
+// FP64 throughput probes.  Every thread runs kChains independent dependency
+// chains (enough to hide the pipeline latency) for `iters` rounds; the final
+// values are summed into *sink so that nothing is dead code.
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) dfma_rate_kernel(int iters, double a, double b, double* sink) {
+  double x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == 12345.678) *sink = s;  // never true for the operands used; keeps the chains live
+}
+
+// mma.sync.m8n8k4 in FP64 (one warp: D = A B + C, 8 x 8 x 4, 256 FMAs), four
+// independent accumulators per warp.
+__global__ void __launch_bounds__(256) dmma_rate_kernel(int iters, double a, double b, double* sink) {
+  double d[4][2];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) d[c][0] = d[c][1] = 1e-3 * (threadIdx.x + c);
+  const double av = a + 1e-9 * threadIdx.x, bv = b;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(d[c][0]), "+d"(d[c][1])
+                   : "d"(av), "d"(bv));
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s += d[c][0] + d[c][1];
+  if (s == 12345.678) *sink = s;
+}
+
 std::vector<double> down(const double* d, size_t n) {
   std::vector<double> h(n);
   if (cudaMemcpy(h.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -301,6 +338,110 @@ std::vector<double> run_selftest(int which) {
         out.push_back(err_max);
       }
     }
+  } else if (which == 5) {
+    // tensor-core GEMM operands and results for a check on the host in FP64:
+    // per case the header (M, N, K, outer, inner, A transposed, B transposed,
+    // beta; alpha is 1.5), the operands A, B and the initial C as stored
+    // (batch-major, then row-major or, when transposed, column-major), then C
+    // after each mode (BF16X3, TF32, TF32X3, BF16, BF16X6; NaN when a mode
+    // does not take the shape)
+    struct Case {
+      int M, N, K, outer, inner;
+      bool ta, tb;
+      double beta;
+    };
+    const Case cases[] = {{272, 136, 2176, 1, 1, false, false, 0.0},
+                          {4352, 256, 136, 1, 1, false, false, 0.0},
+                          {130, 70, 100, 3, 2, true, false, 0.5},
+                          {136, 160, 272, 1, 1, true, true, 1.0}};
+    const size_t ws_elems = (size_t)32 << 20;
+    DBuf ws(ws_elems);
+    size_t pack_bytes = (size_t)256 << 20;
+    void* pack = nullptr;
+    if (cudaMalloc(&pack, pack_bytes) != cudaSuccess) throw std::runtime_error("ENOMEM: selftest pack");
+    unsigned long long seed = 24680;
+    for (const Case& c : cases) {
+      const long long batch = (long long)c.outer * c.inner;
+      const size_t asz = (size_t)c.M * c.K * batch, bsz = (size_t)c.K * c.N * batch, csz = (size_t)c.M * c.N * batch;
+      DBuf A(asz), B(bsz), C0(csz), C1(csz);
+      fill_gaussian(st, A.p, asz, 1.0, seed++, 1);
+      fill_gaussian(st, B.p, bsz, 1.0, seed++, 2);
+      fill_gaussian(st, C0.p, csz, 1.0, seed++, 3);
+      MatView av, bv;
+      av.p = A.p;
+      av.rs = c.ta ? 1 : c.K;
+      av.cs = c.ta ? c.M : 1;
+      av.si = (long long)c.M * c.K;
+      av.so = av.si * c.inner;
+      bv.p = B.p;
+      bv.rs = c.tb ? 1 : c.N;
+      bv.cs = c.tb ? c.K : 1;
+      bv.si = (long long)c.K * c.N;
+      bv.so = bv.si * c.inner;
+      OutView cv;
+      cv.p = C1.p;
+      cv.rs = c.N;
+      cv.cs = 1;
+      cv.si = (long long)c.M * c.N;
+      cv.so = cv.si * c.inner;
+      const double hdr[8] = {(double)c.M, (double)c.N, (double)c.K, (double)c.outer, (double)c.inner,
+                             c.ta ? 1.0 : 0.0, c.tb ? 1.0 : 0.0, c.beta};
+      out.insert(out.end(), hdr, hdr + 8);
+      for (const DBuf* d : {&A, &B, &C0}) {
+        const std::vector<double> h = down(d->p, d == &A ? asz : d == &B ? bsz : csz);
+        out.insert(out.end(), h.begin(), h.end());
+      }
+      const int tc_mode[5] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16, TC_BF16X6};
+      for (int mode = 0; mode < 5; ++mode) {
+        if (cudaMemcpy(C1.p, C0.p, csz * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess)
+          throw std::runtime_error("CUDA error: selftest copy");
+        if (!gemm_tc(st, tc_mode[mode], c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, cv, pack, pack_bytes,
+                     ws.p, ws_elems, err)) {
+          out.insert(out.end(), csz, std::nan(""));
+          continue;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest gemm");
+        const std::vector<double> h = down(C1.p, csz);
+        out.insert(out.end(), h.begin(), h.end());
+      }
+    }
+    cudaFree(pack);
+  } else if (which == 6) {
+    // FP64 arithmetic throughput of the whole GPU: DFMA (CUDA cores) and
+    // mma.sync m8n8k4 f64; per probe TFLOP/s (2 flops per FMA) of the best of
+    // three timed launches after one untimed one, then the SM count and the
+    // number of blocks launched
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    DBuf sink(1);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int probe = 0; probe < 2; ++probe) {
+      float best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, st);
+        if (probe == 0)
+          dfma_rate_kernel<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7, sink.p);
+        else
+          dmma_rate_kernel<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7, sink.p);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) throw std::runtime_error("CUDA error: FP64 rate probe");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+      }
+      const double fma_per_thread =
+          probe == 0 ? (double)iters * kChains : (double)iters * 4 * 256.0 / 32.0;  // 256 FMAs per warp-MMA
+      const double flops = 2.0 * fma_per_thread * threads * (double)blocks;
+      out.push_back(flops / (best * 1e-3) / 1e12);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out.push_back((double)sms);
+    out.push_back((double)blocks);
   } else {
     cudaFree(err);
     throw std::runtime_error("EINVAL: unknown selftest");

@@ -68,3 +68,68 @@ def test_tensor_core_gemm_large_square():
     for n, mode, tflops, err in v:
         assert tflops > 0
         assert 0 <= err <= (5e-3 if int(mode) == 3 else 1e-3), (n, mode, err)
+
+
+def _selftest5_cases(v):
+    """Split qtt_selftest(5) output into cases (operands as stored, results per mode)."""
+    out, i = [], 0
+    while i + 8 <= len(v):
+        M, N, K, outer, inner, ta, tb, beta = v[i:i + 8]
+        i += 8
+        M, N, K, b = int(M), int(N), int(K), int(outer) * int(inner)
+        take = lambda n: v[i:i + n]
+        A = take(M * K * b); i += M * K * b
+        B = take(K * N * b); i += K * N * b
+        C0 = take(M * N * b); i += M * N * b
+        Cs = []
+        for _ in MODES:
+            Cs.append(take(M * N * b).reshape(b, M, N)); i += M * N * b
+        A = A.reshape(b, K, M).transpose(0, 2, 1) if ta else A.reshape(b, M, K)
+        B = B.reshape(b, N, K).transpose(0, 2, 1) if tb else B.reshape(b, K, N)
+        out.append((K, beta, A, B, C0.reshape(b, M, N), Cs))
+    return out
+
+
+def test_tensor_core_gemm_against_host_fp64():
+    """Every tensor-core mode against a numpy FP64 product of the same seeded
+    operands (a long K with split-K, 34 row tiles, a batched product with a
+    transposed A and beta, both operands transposed with beta = 1), as
+    e = |C_tc - C| / (|alpha| sum_k |a_ik b_kj| + |beta| |c0_ij|).  Bounds from
+    the arithmetic: operand representation (unit roundoff of BF16 2^-8 per
+    operand, TF32 2^-11; the hi/lo splits leave 2^-16 (BF16X3) / 2^-22
+    (TF32X3) per operand plus the dropped lo*lo term of the same size) plus
+    FP32 accumulation, at most one rounding of 2^-23 per
+    tensor-core instruction (K / 16 of them for BF16, K / 8 for TF32); the
+    exact-slice form BF16X6 accumulates exactly and keeps each element to
+    three 8-bit slices of its row's (column's) largest power of two, which for
+    Gaussian rows (largest / mean magnitude below 5) is below
+    3 * 2^-24 * 25 = 4.5e-6 of sum |a b|.  A wrong index, transpose or packing
+    gives O(1) errors.  The signed mean error of the unbiased exact-slice form
+    must also stay far below its bound."""
+    v = np.asarray(pkg.qtt_selftest(5, cap=10_000_000))
+    assert v[-1] == 0, "a bounded wait gave up"
+    cases = _selftest5_cases(v[:-1])
+    assert len(cases) == 4
+    alpha, u = 1.5, 2.0 ** -23
+    for K, beta, A, B, C0, Cs in cases:
+        ref = alpha * np.matmul(A, B) + beta * C0
+        mag = abs(alpha) * np.matmul(np.abs(A), np.abs(B)) + abs(beta) * np.abs(C0)
+        bound = {"bf16x3": 3 * 2.0 ** -16 + (K / 16) * u, "tf32": 2 * 2.0 ** -11 + (K / 8) * u,
+                 "tf32x3": 3 * 2.0 ** -22 + (K / 8) * u, "bf16": 2 * 2.0 ** -8 + (K / 16) * u, "bf16x6": 4.5e-6}
+        for m, C in zip(MODES, Cs):
+            assert not np.isnan(C).any(), (m, K)
+            e = (C - ref) / mag
+            print(f"K={K} {m}: max {np.abs(e).max():.2e} (bound {bound[m]:.1e}), mean {e.mean():.1e}")
+            assert np.abs(e).max() <= bound[m], (m, K, np.abs(e).max())
+        e6 = (Cs[MODES.index("bf16x6")] - ref) / mag
+        assert abs(e6.mean()) <= 0.05 * bound["bf16x6"]
+
+
+def test_fp64_throughput_probe():
+    """DFMA and f64 mma.sync throughput of the whole GPU (the FP64 roofline's
+    denominator): both positive and below the nominal FP64 rate of a GB300
+    by a wide margin from above (no probe can beat the hardware: 2 TFLOP/s)."""
+    v = pkg.qtt_selftest(6)
+    dfma, dmma, sms, blocks = v[:4]
+    print(f"\nFP64: DFMA {dfma:.3f} TFLOP/s, DMMA {dmma:.3f} TFLOP/s on {int(sms)} SMs ({int(blocks)} blocks)")
+    assert 0.05 < dfma < 2.0 and 0.05 < dmma < 2.0
