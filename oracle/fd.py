@@ -31,8 +31,19 @@ What it computes (plain FP64 numpy, no blocking or fusion):
   midpoint  f_h = f + dt/2 L(f);  f_{n+1} = f + dt L(f_h)    (rk_variant 1)
 * Integrated statistics (Eqs. spaceAvg, RACov, SGSCov) with the space average
   normalised by the domain volume, so that the mean of <1> is one.
+* The subgrid closures of Eq. FP0 when params["sgs"] is 1: the Smagorinsky
+  diffusivity gamma_SGS(x) = C_s Delta^2/2 sqrt(sum_ij (d_j u_i + d_i u_j)^2)
+  (CFD2 derivatives of the sampled velocity) and the LMSE mixing rate
+  Omega_mix(x) = C_Omega (gamma + gamma_SGS(x)) / Delta^2, with the filter
+  width Delta = delta_cells (h1 h2 h3)^(1/3) (the paper: Delta = 3 l0 / M).
+  The diffusion d/dx_i [(gamma + gamma_SGS) df/dx_i] of Eq. FP2 is then taken
+  in flux form with face values averaged from the two neighbours,
+  [g_{+}(f_{+} - f) - g_{-}(f - f_{-})] / h^2, which for a constant field is
+  the CFD2 second difference used otherwise.
 * The moment equation Eq. FPMoms for Da = 0 (a separate 3-D RK2-CFD2 solver),
   used as an independent check of the composition-space operators.
+* The error measures of Eqs. RMSE0 and RMSE1 (time and space-time averages
+  of squared differences over the stored time samples).
 * The NVPP count of Eq. MPSdofs.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
@@ -53,7 +64,7 @@ __all__ = [
     "Grid", "make_grid", "velocity_field", "initial_pdf", "d1_periodic",
     "d2_periodic", "d1_zero_sum", "d2_zero_sum", "conditional_means", "rhs",
     "rk2_step", "solve", "observables", "moment_rhs", "moment_step", "nvpp",
-    "bond_profile",
+    "bond_profile", "filter_width", "subgrid_fields", "d2_flux_periodic", "error_measures",
 ]
 
 
@@ -188,6 +199,39 @@ def d2_zero_sum(f, axis, h):
             + np.take(fp, np.arange(0, n), axis=axis)) / (h * h)
 
 
+def d2_flux_periodic(f, g, axis, field_axis, h):
+    """d/dx [g df/dx] in flux form on a periodic axis: face value
+    g_{i+1/2} = (g_i + g_{i+1}) / 2, result [g_{i+1/2}(f_{i+1} - f_i) -
+    g_{i-1/2}(f_i - f_{i-1})] / h^2.  g lives on the 3 x axes (field_axis)
+    and is broadcast over the leading phi axes of f when f has more axes."""
+    gp = 0.5 * (g + np.roll(g, -1, field_axis))
+    lead = f.ndim - g.ndim
+    gp = gp.reshape((1,) * lead + gp.shape)
+    flux = gp * (np.roll(f, -1, axis) - f)
+    return (flux - np.roll(flux, 1, axis)) / (h * h)
+
+
+def filter_width(params, grid: Grid):
+    """LES filter width Delta = delta_cells (h1 h2 h3)^(1/3); the paper takes
+    Delta = 3 Delta x on an isotropic grid."""
+    return params.get("delta_cells", 3.0) * (grid.h_x[0] * grid.h_x[1] * grid.h_x[2]) ** (1.0 / 3.0)
+
+
+def subgrid_fields(params, grid: Grid, u):
+    """(gamma + gamma_SGS(x), Omega_mix(x)) on the x grid (Eq. FP0 and its
+    Smagorinsky / LMSE closures): gamma_SGS = C_s Delta^2 / 2 |S|,
+    |S| = sqrt(sum_ij (d_j u_i + d_i u_j)^2) from CFD2 derivatives of the
+    sampled velocity, Omega_mix = C_Omega (gamma + gamma_SGS) / Delta^2."""
+    D = filter_width(params, grid)
+    s2 = np.zeros(grid.M[2:])
+    for i in range(3):
+        for j in range(3):
+            sij = d1_periodic(u[i], j, grid.h_x[j]) + d1_periodic(u[j], i, grid.h_x[i])
+            s2 += sij * sij
+    gam = params["gamma"] + params["c_s"] * 0.5 * D * D * np.sqrt(s2)
+    return gam, params["c_omega"] * gam / (D * D)
+
+
 def conditional_means(f, grid: Grid):
     """<Phi_a>(x) = h1 h2 sum_{i1,i2} phi_a f  (Eq. 2, unnormalised)."""
     w = grid.h_phi[0] * grid.h_phi[1]
@@ -199,12 +243,18 @@ def conditional_means(f, grid: Grid):
 def rhs(f, grid: Grid, u, params):
     """L(f) of Eq. FP2 (see the module docstring)."""
     om, da, gam, dphi = params["omega"], params["da"], params["gamma"], params["d_phi"]
+    sgs = params.get("sgs", 0) == 1
+    if sgs:  # gamma(x) and Omega_mix(x) replace the constants
+        gam_x, om_x = subgrid_fields(params, grid, u)
+        om = om_x[None, None]
     out = np.zeros_like(f)
     for i in range(3):
         ax = 2 + i
         hx = grid.h_x[i]
         out -= u[i][None, None] * d1_periodic(f, ax, hx)
-        if gam != 0.0:
+        if sgs:
+            out += d2_flux_periodic(f, gam_x, ax, i, hx)
+        elif gam != 0.0:
             out += gam * d2_periodic(f, ax, hx)
     m1, m2 = conditional_means(f, grid)
     P1 = grid.phi[0][:, None, None, None, None]
@@ -266,17 +316,23 @@ def observables(f, grid: Grid):
 
 
 def moment_rhs(m, grid: Grid, u, gamma):
-    """Eq. FPMoms with S = 0 on the 3-D grid: -u . D1x m + gamma sum_i D2x_i m."""
+    """Eq. FPMoms with S = 0 on the 3-D grid: -u . D1x m + gamma sum_i D2x_i m;
+    gamma may be a field on the x grid (flux form, see d2_flux_periodic)."""
     out = np.zeros_like(m)
+    field = np.ndim(gamma) == 3
     for i in range(3):
         out -= u[i] * d1_periodic(m, i, grid.h_x[i])
-        if gamma != 0.0:
+        if field:
+            out += d2_flux_periodic(m, gamma, i, i, grid.h_x[i])
+        elif gamma != 0.0:
             out += gamma * d2_periodic(m, i, grid.h_x[i])
     return out
 
 
 def moment_step(m, grid: Grid, u, params):
     dt, gam = params["dt"], params["gamma"]
+    if params.get("sgs", 0) == 1:
+        gam = subgrid_fields(params, grid, u)[0]
     if params.get("rk_variant", 0) == 1:
         mh = m + 0.5 * dt * moment_rhs(m, grid, u, gam)
         return m + dt * moment_rhs(mh, grid, u, gam)
@@ -293,3 +349,28 @@ def nvpp(N, chi):
     """Number of variables parameterising the PDF, Eq. MPSdofs."""
     p = bond_profile(N, chi)
     return 2 * sum(p[n - 1] * p[n] for n in range(1, N + 1)) - sum(p[n] ** 2 for n in range(1, N))
+
+
+def error_measures(samples, exact=None):
+    """Eqs. RMSE0 / RMSE1: samples is a list (one entry per stored time, the
+    paper uses 17 equally spaced ones) of dicts with the space averages
+    mean1_avg, mean2_avg and the fields norm, mean1, mean2 (from observables);
+    exact the matching list of (<Phi_1>, <Phi_2>) fields of the moment
+    equation (or None).  E_t averages squared differences over the samples
+    (step quadrature), E_tx also over all grid points.  Returns
+    err_2b_up = sqrt(1/2 sum_a E_t[avg<Phi_a> - 1/2]),
+    err_2b_down = sqrt(1/2 sum_a E_tx[<Phi_a> - <Phi_a>_exact]) (None
+    without exact), err_2c_up = sqrt(E_t[avg<Phi_1> - avg<Phi_2>]),
+    err_2c_down = sqrt(E_tx[<1> - 1])."""
+    Et = lambda vals: float(np.mean(np.square(vals)))
+    out = {}
+    out["err_2b_up"] = math.sqrt(0.5 * sum(Et([s[f"mean{a}_avg"] - 0.5 for s in samples]) for a in (1, 2)))
+    if exact is not None:
+        out["err_2b_down"] = math.sqrt(0.5 * sum(
+            float(np.mean([np.mean(np.square(s[f"mean{a}"] - e[a - 1])) for s, e in zip(samples, exact)]))
+            for a in (1, 2)))
+    else:
+        out["err_2b_down"] = None
+    out["err_2c_up"] = math.sqrt(Et([s["mean1_avg"] - s["mean2_avg"] for s in samples]))
+    out["err_2c_down"] = math.sqrt(float(np.mean([np.mean(np.square(s["norm"] - 1.0)) for s in samples])))
+    return out

@@ -447,3 +447,154 @@ def test_statistics_of_interior_tanh_blend():
     assert abs(o["product_J"] - (1 - sum(aw * hi[k] + (1 - aw) * lo[k] for k in range(2)))) < 1e-12
     # both covariances are exercised (negative: the centres move in opposite directions)
     assert o["R12"] < -1e-2 and o["Y12"] < -5e-4 and abs(o["R12"] - o["Y12"]) > 1e-3
+
+
+# ---------------- subgrid closures (Eq. FP0: Smagorinsky gamma_SGS, LMSE Omega_mix)
+def _sgs_params(bits, **kw):
+    base = dict(sgs=1, c_s=0.11, c_omega=0.5, delta_cells=3.0, gamma=2 * math.pi / 1e3, da=0.0)
+    base.update(kw)
+    return _paper_case(bits, **base)
+
+
+def test_subgrid_constant_fields_reduce_to_constant_operator():
+    """C_s = 0 makes gamma(x) = gamma and, with C_Omega = Omega Delta^2 / gamma,
+    Omega_mix = Omega: the flux-form right-hand side then equals the one with
+    constant coefficients (compact CFD2 diffusion, constant Omega)."""
+    bits = [3, 3, 2, 3, 2]
+    p = _sgs_params(bits, da=0.7)
+    g = oracle.make_grid(bits)
+    D = oracle.filter_width(p, g)
+    p.update(c_s=0.0, c_omega=1.3 * D * D / p["gamma"])
+    q = dict(p, sgs=0, omega=1.3)
+    u = oracle.velocity_field(p, g)
+    f = np.random.default_rng(4).standard_normal(g.shape)
+    a, b = oracle.rhs(f, g, u, p), oracle.rhs(f, g, u, q)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+def test_smagorinsky_field_of_shear_modes():
+    """u1 = a sin(k x2 + t), u2 = b sin(q x1 + s): the only nonzero strain
+    entries are S12 = S21 = d2 u1 + d1 u2, whose CFD2 value is
+    a k_h cos(k x2 + t) + b q_h cos(q x1 + s) with k_h = sin(k h)/h, so
+    gamma_SGS = C_s Delta^2 / 2 * sqrt(2) |S12| and Omega_mix = C_Omega
+    (gamma + gamma_SGS) / Delta^2."""
+    bits = [1, 1, 4, 5, 3]
+    a, k, t, b, q, s = 0.3, 2, 0.4, -0.2, 3, 1.1
+    p = _params(bits, shear_amp=0.0, umodes=[dict(comp=0, k=[0, k, 0], phase=t, amp=a),
+                                             dict(comp=1, k=[q, 0, 0], phase=s, amp=b)],
+                sgs=1, c_s=0.11, c_omega=0.5, delta_cells=3.0, gamma=0.004)
+    g = oracle.make_grid(bits)
+    u = oracle.velocity_field(p, g)
+    gam, om = oracle.subgrid_fields(p, g, u)
+    X1, X2, _ = np.meshgrid(*g.x, indexing="ij")
+    s12 = (a * math.sin(k * g.h_x[1]) / g.h_x[1] * np.cos(k * X2 + t)
+           + b * math.sin(q * g.h_x[0]) / g.h_x[0] * np.cos(q * X1 + s))
+    D = 3.0 * (g.h_x[0] * g.h_x[1] * g.h_x[2]) ** (1 / 3)
+    gam_ref = 0.004 + 0.11 * D * D / 2 * math.sqrt(2.0) * np.abs(s12)
+    assert np.abs(gam - gam_ref).max() < 1e-14
+    assert np.abs(om - 0.5 * gam_ref / (D * D)).max() < 1e-13
+    assert np.abs(gam - 0.004).max() > 1e-3
+
+
+def test_flux_diffusion_conservative_symmetric_and_compact():
+    """The flux form d/dx[g df/dx] sums to zero over a periodic axis, is a
+    symmetric operator for any g > 0, and equals g D2 for constant g."""
+    rng = np.random.default_rng(8)
+    M, h = 16, 2 * math.pi / 16
+    gf = 1.0 + 0.5 * rng.random((M, 4, 2))
+    a, b = rng.standard_normal((M, 4, 2)), rng.standard_normal((M, 4, 2))
+    for ax in range(3):
+        La = oracle.d2_flux_periodic(a, gf, ax, ax, h)
+        Lb = oracle.d2_flux_periodic(b, gf, ax, ax, h)
+        assert np.abs(La.sum(axis=ax)).max() < 1e-12
+        assert abs(float((a * Lb).sum()) - float((La * b).sum())) < 1e-11 * float(np.abs(a * Lb).sum())
+    c = oracle.d2_flux_periodic(a, np.full(gf.shape, 0.7), 0, 0, h)
+    assert np.abs(c - 0.7 * oracle.d2_periodic(a, 0, h)).max() < 1e-12 * np.abs(c).max()
+
+
+def test_subgrid_mixing_rate_acts_pointwise():
+    """For an x-uniform PDF transport and diffusion vanish, so the right-hand
+    side at each x is the composition-space operator with the constant
+    Omega = Omega_mix(x) (and the same dissipation), as computed by the
+    constant-coefficient path on a one-point x grid."""
+    bits = [4, 4, 2, 2, 2]
+    p = _sgs_params(bits, da=0.4, ic_kind=0, ic_c_hi=[0.6, 0.4], ic_c_lo=[0.6, 0.4])
+    g = oracle.make_grid(bits)
+    u = oracle.velocity_field(p, g)
+    f = oracle.initial_pdf(p, g)
+    _, om = oracle.subgrid_fields(p, g, u)
+    assert np.ptp(om) > 1e-2
+    r = oracle.rhs(f, g, u, p)
+    g1 = oracle.make_grid([4, 4, 1, 1, 1])
+    u0 = [np.zeros((2, 2, 2))] * 3
+    for idx in [(0, 0, 0), (1, 2, 3), (3, 1, 2)]:
+        q = dict(p, sgs=0, omega=float(om[idx]), bits=[4, 4, 1, 1, 1])
+        f1 = np.broadcast_to(f[(slice(None), slice(None)) + idx][:, :, None, None, None], g1.shape).copy()
+        r1 = oracle.rhs(f1, g1, u0, q)[:, :, 0, 0, 0]
+        assert np.abs(r[(slice(None), slice(None)) + idx] - r1).max() < 1e-11 * np.abs(r1).max()
+
+
+def test_subgrid_norm_and_moment_equation():
+    """With gamma(x) and Omega_mix(x): <1>(x) stays 1 point-wise, and at Da = 0
+    the conditional means follow the 3-D flux-form solution of Eq. FPMoms
+    (interior Gaussians, so the phi walls add no boundary terms)."""
+    bits = [5, 5, 3, 3, 3]
+    p = _sgs_params(bits, ic_sigma=0.05, ic_c_hi=[0.62, 0.4], ic_c_lo=[0.38, 0.6])
+    g = oracle.make_grid(bits)
+    u = oracle.velocity_field(p, g)
+    gam, om = oracle.subgrid_fields(p, g, u)
+    p["dt"] = workload.cfl_dt(bits, float(om.max()), 0.0, float(gam.max()), p["d_phi"], workload.velocity_bound(p))
+    f = oracle.initial_pdf(p, g)
+    m1, m2 = oracle.conditional_means(f, g)
+    m1_0 = m1.copy()
+    for _ in range(6):
+        f = oracle.rk2_step(f, g, u, p)
+        m1 = oracle.moment_step(m1, g, u, p)
+        m2 = oracle.moment_step(m2, g, u, p)
+    o = oracle.observables(f, g)
+    assert np.abs(o["norm"] - 1.0).max() < 1e-12
+    # the Gaussians' tails at the phi walls (e^{-(0.38/0.05)^2/2} ~ 3e-13) enter
+    # the boundary terms of the first moment each step
+    assert np.abs(o["mean1"] - m1).max() < 5e-12 and np.abs(o["mean2"] - m2).max() < 5e-12
+    assert np.abs(m1 - m1_0).max() > 1e-4
+    # the field-diffusivity moment solution differs from the constant-gamma one
+    mc = m1_0.copy()
+    for _ in range(6):
+        mc = oracle.moment_step(mc, g, u, dict(p, sgs=0))
+    assert np.abs(mc - m1).max() > 1e-6
+
+
+def test_error_measures_closed_forms():
+    """Eqs. RMSE0 / RMSE1 on synthetic samples: constant offsets give the offsets
+    back, exact = MPS gives zero, and a norm field 1 + d cos(x) gives |d|/sqrt(2)
+    (space-time mean of d^2 cos^2)."""
+    x = np.linspace(0, 2 * math.pi, 16, endpoint=False)
+    fld = np.broadcast_to(x[:, None, None], (16, 2, 2))
+    samples, exact = [], []
+    for t in range(17):
+        m1 = 0.5 + 0.01 * np.cos(fld)
+        samples.append(dict(mean1_avg=0.53, mean2_avg=0.49, mean1=m1, mean2=1.0 - m1,
+                            norm=1.0 + 0.02 * np.cos(fld)))
+        exact.append((m1 - 0.003, 1.0 - m1 + 0.004))
+    e = oracle.error_measures(samples, exact)
+    assert abs(e["err_2b_up"] - math.sqrt(0.5 * (0.03 ** 2 + 0.01 ** 2))) < 1e-15
+    assert abs(e["err_2b_down"] - math.sqrt(0.5 * (0.003 ** 2 + 0.004 ** 2))) < 1e-15
+    assert abs(e["err_2c_up"] - 0.04) < 1e-15
+    assert abs(e["err_2c_down"] - 0.02 / math.sqrt(2)) < 1e-15
+    assert oracle.error_measures(samples, [(s["mean1"], s["mean2"]) for s in samples])["err_2b_down"] == 0.0
+
+
+def test_flux_diffusion_second_order_for_smooth_coefficient():
+    """Against the analytic d/dx[g f'] for g = 1 + sin(x)/2, f = cos(2x): the
+    centred face averages make the flux form second order (error ~h^2); a
+    one-sided or shifted face value would make it first order."""
+    errs = []
+    for M in (32, 64, 128):
+        h = 2 * math.pi / M
+        x = np.arange(M) * h
+        g = 1 + 0.5 * np.sin(x)
+        f = np.cos(2 * x)
+        exact = -4 * np.cos(2 * x) * (1 + 0.5 * np.sin(x)) - np.sin(2 * x) * np.cos(x)
+        errs.append(np.abs(oracle.d2_flux_periodic(f, g, 0, 0, h) - exact).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.9 < o < 2.1 for o in orders), (errs, orders)
