@@ -16,7 +16,10 @@
 // summed in FP64 by the split-K reduction.  The only errors left are the
 // dropped high-order slices and products, which are symmetric about zero.
 // BF16X6 keeps 3 x 3 slices and the 6 products with g <= 2: ~2^-24 relative
-// to the row and column maxima.
+// to the row and column maxima.  BF16X10 keeps 4 x 4 slices, cut from the
+// FP64 mantissa by integer arithmetic (x 2^-e_r rounded to a multiple of
+// 2^-31, written in balanced base-256 digits), and the 10 products with
+// g <= 3 in four accumulators: ~2^-31 relative to the row and column maxima.
 // Floating-point forms (FP32 accumulation on the tensor cores, which rounds
 // toward zero and therefore drifts):
 //   BF16X3 : A = A_hi + A_lo, B = B_hi + B_lo (bf16 each),
@@ -239,6 +242,11 @@ struct ModeTraits<TC_BF16X6> {
   static constexpr int na = 3, nb = 3, ngroups = 3, esize = 2;
 };
 template <>
+struct ModeTraits<TC_BF16X10> {
+  static constexpr bool tf32 = false, sliced = true;
+  static constexpr int na = 4, nb = 4, ngroups = 4, esize = 2;
+};
+template <>
 struct ModeTraits<TC_BF16> {
   static constexpr bool tf32 = false, sliced = false;
   static constexpr int na = 1, nb = 1, ngroups = 1, esize = 2;
@@ -261,8 +269,9 @@ __host__ __device__ constexpr int tmem_cols_for(int cols) {
 template <int MODE, int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
-                   const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, int M, int N,
+                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmA3,
+                   const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+                   const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ CUtensorMap tmB3, int M, int N,
                    int kblocks, int kb_per_split, int splitk, int inner, double alpha, double beta, OutView C,
                    double* ws, const int* __restrict__ ea, const int* __restrict__ eb, int a_bs, int b_bs, int* err) {
   using Tr = ModeTraits<MODE>;
@@ -309,8 +318,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // TMA producer; a stage holds the na A tiles, then the nb B tiles
-    const CUtensorMap* ma[3] = {&tmA0, &tmA1, &tmA2};
-    const CUtensorMap* mb[3] = {&tmB0, &tmB1, &tmB2};
+    const CUtensorMap* ma[4] = {&tmA0, &tmA1, &tmA2, &tmA3};
+    const CUtensorMap* mb[4] = {&tmB0, &tmB1, &tmB2, &tmB3};
     for (int kb = kb0, i = 0; kb < kb1; ++kb, ++i) {
       const int s = i % STAGES;
       const uint32_t ph = (uint32_t)((i / STAGES) & 1);
@@ -410,13 +419,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int j = 0; j < 32; ++j) {
         unsigned long long bits;
         if (Tr::sliced) {
-          // exact integer sums of weights 2^-14, 2^-22, 2^-30 -> one integer
-          // S = I0 2^16 + I1 2^8 + I2 (< 2^41) -> S 2^(e_row + e_col - 30)
+          // exact integer sums I_g of weight 2^-(14 + 8 g) -> one integer
+          // S = sum_g I_g 2^(8 (G - 1 - g)) (< 2^41 for G = 3, < 2^49 for
+          // G = 4) -> S 2^(e_row + e_col - 14 - 8 (G - 1))
           const int ec = __shfl_sync(0xffffffffu, ecol, j);
-          long long S = (long long)__float2int_rn(__uint_as_float(r[0][j])) << 16;
-          if (Tr::ngroups >= 2) S += (long long)__float2int_rn(__uint_as_float(r[1][j])) << 8;
-          if (Tr::ngroups >= 3) S += (long long)__float2int_rn(__uint_as_float(r[2][j]));
-          bits = int_to_double_bits(S, erow + ec - 30);
+          long long S = 0;
+#pragma unroll
+          for (int g = 0; g < Tr::ngroups; ++g)
+            S += (long long)__float2int_rn(__uint_as_float(r[g][j])) << (8 * (Tr::ngroups - 1 - g));
+          bits = int_to_double_bits(S, erow + ec - 14 - 8 * (Tr::ngroups - 1));
         } else {
           bits = float_to_double_bits(r[0][j]);
         }
@@ -461,8 +472,36 @@ __device__ __forceinline__ float to_tf32(float x) {
 // magnitude, so |t| < 128), then t = s1 + 2^-8 s2 + 2^-16 s3 + O(2^-17) with
 // integers |s_p| <= 128 from round-to-nearest; all in FP32.
 template <int MODE>
-__device__ __forceinline__ void pack_one(double x, int e, int ks, size_t idx, void* o0, void* o1, void* o2) {
-  if constexpr (MODE == TC_BF16X6) {
+__device__ __forceinline__ void pack_one(double x, int e, int ks, size_t idx, void* o0, void* o1, void* o2,
+                                         void* o3) {
+  if constexpr (MODE == TC_BF16X10) {
+    // T = round(x 2^(31 - e + ks)) from the FP64 bits (|T| <= 2^31), then
+    // balanced base-256 digits T = d1 2^24 + d2 2^16 + d3 2^8 + d4 with
+    // |d_p| <= 128 (integers, exact in bf16); no FP64 arithmetic.
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((u >> 52) & 0x7FFull);
+    long long T = 0;
+    if (E != 0) {
+      const int sh = 52 - (E - 1023 + 31 - e + ks);  // right shift of the 53-bit mantissa
+      const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      unsigned long long a = 0;
+      if (sh <= 0) a = m << (-sh > 10 ? 10 : -sh);  // |x| 2^(31-e) < 2^31: cannot happen, kept in range
+      else if (sh < 64) a = (m >> sh) + ((m >> (sh - 1)) & 1ull);
+      T = (u >> 63) ? -(long long)a : (long long)a;
+    }
+    long long q = (T + 128) >> 8;
+    const long long d4 = T - (q << 8);
+    T = q;
+    q = (T + 128) >> 8;
+    const long long d3 = T - (q << 8);
+    T = q;
+    q = (T + 128) >> 8;
+    const long long d2 = T - (q << 8);
+    ((__nv_bfloat16*)o0)[idx] = __float2bfloat16_rn((float)q);
+    ((__nv_bfloat16*)o1)[idx] = __float2bfloat16_rn((float)d2);
+    ((__nv_bfloat16*)o2)[idx] = __float2bfloat16_rn((float)d3);
+    ((__nv_bfloat16*)o3)[idx] = __float2bfloat16_rn((float)d4);
+  } else if constexpr (MODE == TC_BF16X6) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const float t = double_bits_to_float(scale_bits(u, 7 - e + ks));
     const float a1 = rintf(t);
@@ -514,7 +553,7 @@ struct PackJob {
   const int* kshift;               // K-index balancing shifts (BF16X6), or null
   long long kshift_bstride;        // k_pad, or 0 when the shifts are common to the batch
   unsigned long long* maxbits;     // per packed row: largest balanced magnitude (BF16X6)
-  void *o0, *o1, *o2;
+  void *o0, *o1, *o2, *o3;
   int* expo;
   int blocks;                      // blocks of this job in the fused launch
 };
@@ -603,7 +642,7 @@ __device__ void pack_job(const PackJob& J, int bx) {
     const int tx = lane, ty = threadIdx.x >> 5;  // 32 x 8
     const bool rlive = r0 + tx < J.rows;
     const int* ksh = J.kshift ? J.kshift + b * J.kshift_bstride : nullptr;
-    if constexpr (MODE == TC_BF16X6) {
+    if constexpr (MODE == TC_BF16X6 || MODE == TC_BF16X10) {
       if (ty == 0) {
         const int e = row_exponent(J.maxbits[b * J.rows_pad + r0 + tx]);
         s_e[tx] = e;
@@ -622,13 +661,13 @@ __device__ void pack_job(const PackJob& J, int bx) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int rl = ty + 8 * q;
-        const int e = (MODE == TC_BF16X6) ? s_e[rl] : 0;
+        const int e = (MODE == TC_BF16X6 || MODE == TC_BF16X10) ? s_e[rl] : 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int k = k0 + 32 * h + tx;
           if (k < kend)
             pack_one<MODE>(tile[32 * h + tx][rl], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0,
-                           ((size_t)b * J.rows_pad + r0 + rl) * J.k_pad + k, J.o0, J.o1, J.o2);
+                           ((size_t)b * J.rows_pad + r0 + rl) * J.k_pad + k, J.o0, J.o1, J.o2, J.o3);
         }
       }
       __syncthreads();
@@ -646,7 +685,7 @@ __device__ void pack_job(const PackJob& J, int bx) {
       const int* ksh = J.kshift ? J.kshift + b * J.kshift_bstride : nullptr;
       const bool live = r < J.rows;
       int e = 0;
-      if constexpr (MODE == TC_BF16X6) {
+      if constexpr (MODE == TC_BF16X6 || MODE == TC_BF16X10) {
         e = row_exponent(J.maxbits[rowid]);
         if (lane == 0 && seg == 0) J.expo[rowid] = e;
       }
@@ -687,7 +726,7 @@ __device__ void pack_job(const PackJob& J, int bx) {
 #pragma unroll
         for (int u = 0; u < PACK_UNROLL; ++u) {
           const int k = k0 + 32 * u;
-          if (k < k1) pack_one<MODE>(x[u], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0, base + k, J.o0, J.o1, J.o2);
+          if (k < k1) pack_one<MODE>(x[u], e, (ksh && k < J.K) ? J.ksign * ksh[k] : 0, base + k, J.o0, J.o1, J.o2, J.o3);
         }
       }
     }
@@ -831,14 +870,14 @@ void launch_tc(cudaStream_t st, const TcPacked& pk, int M, int N, int kblocks, i
     cudaFuncSetAttribute(tc_gemm_kernel<MODE, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     attr = true;
   }
-  CUtensorMap a[3], bm[3];
-  for (int i = 0; i < 3; ++i) {
+  CUtensorMap a[4], bm[4];
+  for (int i = 0; i < 4; ++i) {
     a[i] = make_map(pk.a[i < Tr::na ? i : 0], Tr::esize, pk.k_pad, pk.m_pad, batch_a, BM);
     bm[i] = make_map(pk.b[i < Tr::nb ? i : 0], Tr::esize, pk.k_pad, pk.n_pad, batch_b, BN);
   }
   dim3 grid(pk.n_pad / BN, pk.m_pad / BM, (unsigned)(batch * splitk));
-  launch_pdl(tc_gemm_kernel<MODE, BN, STAGES>, grid, dim3(TC_THREADS), SMEM, st, a[0], a[1], a[2], bm[0], bm[1],
-             bm[2], M, N, kblocks, kbps, splitk, inner, alpha, beta, C, ws, (const int*)pk.ea, (const int*)pk.eb,
+  launch_pdl(tc_gemm_kernel<MODE, BN, STAGES>, grid, dim3(TC_THREADS), SMEM, st, a[0], a[1], a[2], a[3], bm[0],
+             bm[1], bm[2], bm[3], M, N, kblocks, kbps, splitk, inner, alpha, beta, C, ws, (const int*)pk.ea, (const int*)pk.eb,
              batch_a == batch ? 1 : 0, batch_b == batch ? 1 : 0, err);
 }
 
@@ -868,6 +907,7 @@ PackJob make_job(const MatView& v, long long rstr, long long kstr, int inner, in
   J.o0 = o[0];
   J.o1 = o[1];
   J.o2 = o[2];
+  J.o3 = o[3];
   J.expo = expo;
   J.cols = (rstr == 1 && kstr != 1 && rows_pad % 32 == 0) ? 1 : 0;
   const int chunks = (k_pad + 31) / 32;
@@ -892,6 +932,8 @@ ModeInfo mode_info(int mode) {
   switch (mode) {
     case TC_BF16X3: return {2, 2, 1, 2, false, 0};
     case TC_BF16X6: return {3, 3, 3, 2, true, 5};
+    // group 3 sums 4 slice products (|.| <= 2^14 each) per k: 4 k-blocks of 64 stay <= 2^24
+    case TC_BF16X10: return {4, 4, 4, 2, true, 4};
     case TC_BF16: return {1, 1, 1, 2, false, 0};
     case TC_TF32: return {1, 1, 1, 4, false, 0};
     default: return {2, 2, 1, 4, false, 0};  // TC_TF32X3
@@ -1043,6 +1085,7 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     case TC_BF16X3: launch_pdl(pack2_kernel<TC_BF16X3>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
     case TC_TF32: launch_pdl(pack2_kernel<TC_TF32>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
     case TC_TF32X3: launch_pdl(pack2_kernel<TC_TF32X3>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
+    case TC_BF16X10: launch_pdl(pack2_kernel<TC_BF16X10>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
     default: launch_pdl(pack2_kernel<TC_BF16X6>, dim3(pack_blocks), dim3(256), 0, st, ja, jb); break;
   }
   const int kblocks = L.k_pad / L.kb;
@@ -1097,6 +1140,11 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
     default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
   }
+#define QTT_TC_BN2(MODE_, S128, S64)                  \
+  switch (bn) {                                       \
+    case 128: QTT_TC_LAUNCH(MODE_, 128, S128); break; \
+    default: QTT_TC_LAUNCH(MODE_, 64, S64); break;    \
+  }
 #define QTT_TC_BN3(MODE_, S160, S128, S64)            \
   switch (bn) {                                       \
     case 160: QTT_TC_LAUNCH(MODE_, 160, S160); break; \
@@ -1107,10 +1155,12 @@ bool gemm_tc(cudaStream_t st, int mode, int M, int N, int K, int outer, int inne
     switch (mode) {
       case TC_BF16X3: QTT_TC_BN(TC_BF16X3, 2, 3, 3, 4); break;
       case TC_BF16X6: QTT_TC_BN3(TC_BF16X6, 2, 2, 3); break;
+      case TC_BF16X10: QTT_TC_BN2(TC_BF16X10, 1, 2); break;
       case TC_BF16: QTT_TC_BN(TC_BF16, 4, 4, 6, 8); break;
       case TC_TF32: QTT_TC_BN(TC_TF32, 4, 4, 6, 8); break;
       default: QTT_TC_BN(TC_TF32X3, 2, 3, 3, 4); break;
     }
+#undef QTT_TC_BN2
 #undef QTT_TC_BN3
 #undef QTT_TC_BN
 #undef QTT_TC_LAUNCH

@@ -10,12 +10,16 @@ namespace qtt {
 // -- unbiased, ~2^-24 relative to the row and column maxima.  BF16X3 / TF32 /
 // TF32X3 / BF16: floating-point operands (hi+lo 3-pass, 1-pass, hi+lo 3-pass,
 // 1-pass) accumulated by the tensor cores in FP32, which rounds toward zero.
-enum TcMode { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2, TC_BF16 = 3, TC_BF16X6 = 4 };
+// BF16X10: 4 x 4 exact slices taken from the FP64 mantissa by integer
+// arithmetic (each element to 2^-31 of its row's largest power of two), the
+// 10 slice products of weight >= 2^-30 in four exact accumulators, ~2^-31
+// relative to the row and column maxima.
+enum TcMode { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2, TC_BF16 = 3, TC_BF16X6 = 4, TC_BF16X10 = 5 };
 
 // Packed K-major operand buffers of one product.
 struct TcPacked {
-  void* a[3] = {nullptr, nullptr, nullptr};
-  void* b[3] = {nullptr, nullptr, nullptr};
+  void* a[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* b[4] = {nullptr, nullptr, nullptr, nullptr};
   int* ea = nullptr;  // per-row power-of-two exponents (sliced modes)
   int* eb = nullptr;
   int m_pad = 0, n_pad = 0, k_pad = 0;

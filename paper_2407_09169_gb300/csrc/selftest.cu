@@ -65,7 +65,7 @@ std::vector<double> down(const double* d, size_t n) {
 }  // namespace
 
 // which = 0: tensor-core GEMM modes against the FP64 GEMM.  For every case
-// and mode (BF16X3, TF32, TF32X3, BF16, BF16X6) one value:
+// and mode (BF16X3, TF32, TF32X3, BF16, BF16X6, BF16X10) one value:
 // max |C_tc - C_64| / max |C_64|.
 // which = 1: QR (FP64, FP32, FP32 + one FP64 Newton-Schulz step): ||Q^T Q - I||_max and
 //   ||Q Q^T Y - Y|| / ||Y|| per case and run.
@@ -113,7 +113,7 @@ std::vector<double> run_selftest(int which) {
       bv.cs = c.tb ? c.K : 1;
       bv.si = (long long)c.K * c.N;
       bv.so = bv.si * c.inner;
-      for (int mode = 0; mode < 5; ++mode) {
+      for (int mode = 0; mode < 6; ++mode) {
         fill_gaussian(st, C0.p, csz, 1.0, 777, 3);
         fill_gaussian(st, C1.p, csz, 1.0, 777, 3);
         OutView c0, c1;
@@ -125,7 +125,7 @@ std::vector<double> run_selftest(int which) {
         c1 = c0;
         c1.p = C1.p;
         gemm_f64(st, c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, c0, ws.p, ws_elems);
-        const int tc_mode[5] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16, TC_BF16X6};
+        const int tc_mode[6] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16, TC_BF16X6, TC_BF16X10};
         if (!gemm_tc(st, tc_mode[mode], c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, c1, pack, pack_bytes,
                      ws.p, ws_elems, err)) {
           out.push_back(-1.0);
@@ -343,7 +343,7 @@ std::vector<double> run_selftest(int which) {
     // per case the header (M, N, K, outer, inner, A transposed, B transposed,
     // beta; alpha is 1.5), the operands A, B and the initial C as stored
     // (batch-major, then row-major or, when transposed, column-major), then C
-    // after each mode (BF16X3, TF32, TF32X3, BF16, BF16X6; NaN when a mode
+    // after each mode (BF16X3, TF32, TF32X3, BF16, BF16X6, BF16X10; NaN when a mode
     // does not take the shape)
     struct Case {
       int M, N, K, outer, inner;
@@ -391,8 +391,8 @@ std::vector<double> run_selftest(int which) {
         const std::vector<double> h = down(d->p, d == &A ? asz : d == &B ? bsz : csz);
         out.insert(out.end(), h.begin(), h.end());
       }
-      const int tc_mode[5] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16, TC_BF16X6};
-      for (int mode = 0; mode < 5; ++mode) {
+      const int tc_mode[6] = {TC_BF16X3, TC_TF32, TC_TF32X3, TC_BF16, TC_BF16X6, TC_BF16X10};
+      for (int mode = 0; mode < 6; ++mode) {
         if (cudaMemcpy(C1.p, C0.p, csz * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess)
           throw std::runtime_error("CUDA error: selftest copy");
         if (!gemm_tc(st, tc_mode[mode], c.M, c.N, c.K, c.outer, c.inner, 1.5, av, bv, c.beta, cv, pack, pack_bytes,
