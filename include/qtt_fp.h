@@ -50,10 +50,14 @@ typedef enum {
  * matrices and eigensolves of the SVD truncation and for all norm / mass
  * accumulation; their QR factorisations run in FP32 followed by one FP64
  * re-orthonormalisation step.  FP32: exact-slice bf16 tensor-core products
- * (unbiased); TF32 and BF16X3 (hi/lo split): tensor cores with FP32
- * accumulation.  Contractions with an operator bond <= 32 run on the CUDA
- * cores (FP32 in the reduced forms). */
-typedef enum { QTT_FP64 = 0, QTT_FP32 = 1, QTT_TF32 = 2, QTT_BF16X3 = 3 } qtt_precision;
+ * (3 x 3 slices, unbiased, ~2^-24 of the row maxima); TF32 and BF16X3 (hi/lo
+ * split): tensor cores with FP32 accumulation.  Contractions with an
+ * operator bond <= 32 run on the CUDA cores (FP32 in those three forms).
+ * BF16X10: the products carrying the state as 4 x 4 exact bf16 slices cut
+ * from the FP64 mantissa (10 slice products, exact FP32 accumulation,
+ * ~2^-31 of the row maxima), the sketch products hi/lo TF32, the
+ * operator-bond contractions in FP64. */
+typedef enum { QTT_FP64 = 0, QTT_FP32 = 1, QTT_TF32 = 2, QTT_BF16X3 = 3, QTT_BF16X10 = 4 } qtt_precision;
 
 typedef struct {
   int32_t bits[5];       /* K per dimension, order phi1, phi2, x1, x2, x3; 1..12 */
@@ -96,15 +100,32 @@ typedef struct {
                             normalised on the phi grid; it couples phi with x, and is encoded
                             by tensor cross from point samples (paper: initial states by the
                             tensor-cross algorithm, "Computational complexity") */
+  int32_t sgs;           /* 1: the subgrid closures of Eq. FP0 replace gamma and omega by fields:
+                            gamma(x) = gamma + gamma_SGS(x), gamma_SGS = c_s Delta^2 / 2 *
+                            sqrt(sum_ij (d_j u_i + d_i u_j)^2) (Smagorinsky; CFD2 derivatives of
+                            the sampled velocity), the diffusion taken in flux form with face
+                            values averaged from the two neighbours, and the mixing rate
+                            Omega_mix(x) = c_omega gamma(x) / Delta^2 (LMSE); Delta = delta_cells
+                            (h1 h2 h3)^(1/3); omega unused.  Needs K3 + K4 + K5 <= 18; not
+                            available for qtt_grad */
+  double c_s;            /* Smagorinsky constant (paper: 0.11) */
+  double c_omega;        /* SGS mixing-rate constant C_Omega (paper: 0.25 .. 1) */
+  double delta_cells;    /* filter width in cells (paper: 3) */
+  int32_t moment_ref;    /* 1: also step the first-moment equation Eq. FPMoms with S = 0 (the
+                            "numerically exact" <Phi_a>(x) of the error measures, Eqs. RMSE0/1)
+                            on the dense x grid, by the same RK2 and CFD2 stencils (flux form
+                            under sgs), from the initial <Phi_a>(x); K3 + K4 + K5 <= 26 */
   void* stream;          /* cudaStream_t or NULL (the context then creates its own stream) */
 } qtt_params;
 
 /* What qtt_observe returns (all FP64, space averages normalised by the
  * number of x points; paper Eqs. 2, spaceAvg, RACov, SGSCov). */
 typedef enum {
-  QTT_OBS_SCALARS = 0,   /* 12 values: time, norm_avg, mean1_avg, mean2_avg,
+  QTT_OBS_SCALARS = 0,   /* 13 values: time, norm_avg, mean1_avg, mean2_avg,
                             phi11_avg, phi22_avg, phi12_avg, R12, Y12,
-                            product_J, discarded_weight (last step), steps */
+                            product_J, discarded_weight (sum over the bonds of the
+                            discarded squared singular values in the last step),
+                            steps, norm2 (sum of f^2 over every grid cell) */
   QTT_OBS_BONDS = 1,     /* N+1 values: bond dimensions b_0..b_N (b_0 = b_N = 1) */
   QTT_OBS_DENSE = 2,     /* 2^N values: f[i1][i2][j1][j2][j3] row-major; N <= 26 */
   QTT_OBS_MEANS = 3,     /* 3 * 2^(K3+K4+K5) values: <1>(x), <Phi_1>(x), <Phi_2>(x); x row-major */
@@ -112,6 +133,17 @@ typedef enum {
                             (as doubles 0/1, MSB first per dimension), cap = n * N;
                             the first n entries are overwritten with the values */
   QTT_OBS_NVPP = 5,      /* 1 value: number of variables parameterising f (Eq. MPSdofs) */
+  QTT_OBS_ERRORS = 7,    /* needs moment_ref = 1.  6 values, the space averages that the error
+                            measures of Eqs. RMSE0 / RMSE1 take at one time sample:
+                            avg <Phi_1> - 1/2, avg <Phi_2> - 1/2,
+                            mean_x (<Phi_1>(x) - m_1(x))^2, mean_x (<Phi_2>(x) - m_2(x))^2
+                            (m_a: the moment-equation reference), avg <Phi_1> - avg <Phi_2>,
+                            mean_x (<1>(x) - 1)^2.  Over the time samples, E_t is the mean
+                            of the squares of the first, second and fifth value and E_tx the
+                            mean of the third, fourth and sixth; then Error_2b_up =
+                            sqrt((E_t[1] + E_t[2]) / 2), Error_2b_down = sqrt((E_tx[3] +
+                            E_tx[4]) / 2), Error_2c_up = sqrt(E_t[5]), Error_2c_down =
+                            sqrt(E_tx[6]) */
   QTT_OBS_TIMINGS = 6    /* 20 values: for the kernel classes FP64 GEMM, QR, eigensolver,
                             other, tensor-core GEMM (incl. operand packing), CUDA-core GEMM
                             of the operator-bond contractions: launches, total ms,
@@ -227,9 +259,12 @@ const char* qtt_version(void);
  *            (2^N x 2^N, N <= 12)
  *   31       the stage operator I + dt W_lin (2^N x 2^N, N <= 12)
  *   32       the composition-space factor of the mixing term,
- *            -dt Omega D1phi_a, for a = 1, 2: 2 x (M1 M2)^2 values
+ *            -dt Omega D1phi_a, for a = 1, 2: 2 x (M1 M2)^2 values (with sgs:
+ *            -dt D1phi_a, the rate then being the x factor of item 33)
+ *   33       sgs only: the encoded mixing rate Omega_mix(x), 2^(K3+K4+K5) values
  *   40       bond dimensions of the stage operator (N + 1 values)
  *   41       bond dimensions of the encoded initial PDF (N + 1 values)
+ *   42       sgs only: bond dimensions of the Omega_mix(x) train (K3+K4+K5+1 values)
  * Returns QTT_EINVAL for an unknown `which`, invalid params or cap too small.
  * ------------------------------------------------------------------- */
 qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, int64_t cap, int64_t* written);
@@ -237,7 +272,7 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
 /* Device self-checks of the kernel families on seeded random operands
  * (needs a GPU; no context).  The paper has no counterpart: these check the
  * implementation, not the method.  Values written (then one error-flag word):
- *   0  tensor-core GEMM: for 7 shapes x 4 modes (BF16X3, TF32, TF32X3, BF16)
+ *   0  tensor-core GEMM: for 7 shapes x 6 modes (BF16X3, TF32, TF32X3, BF16, BF16X6, BF16X10)
  *      max |C_tc - C_fp64| / max |C_fp64| (-1 when a shape is not supported)
  *   1  Householder QR: for 13 shapes x (FP64, FP32, FP32 followed by one
  *      FP64 Newton-Schulz step) the orthogonality max |Q^T Q - I| and the
@@ -256,8 +291,8 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
  *      a header (M, N, K, outer, inner, A transposed, B transposed, beta;
  *      alpha = 1.5), A, B and the initial C as stored (batch-major; row-major,
  *      or column-major when transposed), then C after each of the modes
- *      BF16X3, TF32, TF32X3, BF16, BF16X6 (NaN where a mode does not take
- *      the shape); four cases, about 9.1 million values
+ *      BF16X3, TF32, TF32X3, BF16, BF16X6, BF16X10 (NaN where a mode does
+ *      not take the shape); four cases, about 10.6 million values
  *   6  FP64 arithmetic throughput of the GPU: TFLOP/s of DFMA on the CUDA
  *      cores and of mma.sync m8n8k4 f64 (each the best of three launches of
  *      8 blocks of 256 threads per SM, 2 flops per FMA), the SM count and

@@ -17,9 +17,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libqtt_fp.so")
 QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENOCONV, QTT_ETIMEOUT, QTT_ENAN, QTT_ESTATE, QTT_EIO = range(9)
 STATUS_NAMES = ["QTT_OK", "QTT_EINVAL", "QTT_ENOMEM", "QTT_ECUDA", "QTT_ENOCONV", "QTT_ETIMEOUT", "QTT_ENAN",
                 "QTT_ESTATE", "QTT_EIO"]
-OBS_SCALARS, OBS_BONDS, OBS_DENSE, OBS_MEANS, OBS_POINTS, OBS_NVPP, OBS_TIMINGS = range(7)
+OBS_SCALARS, OBS_BONDS, OBS_DENSE, OBS_MEANS, OBS_POINTS, OBS_NVPP, OBS_TIMINGS, OBS_ERRORS = range(8)
 SCALAR_NAMES = ["time", "norm_avg", "mean1_avg", "mean2_avg", "phi11_avg", "phi22_avg", "phi12_avg", "R12", "Y12",
-                "product_J", "discarded_weight", "steps"]
+                "product_J", "discarded_weight", "steps", "norm2"]
 
 
 class QttError(RuntimeError):
@@ -61,6 +61,11 @@ class QttParams(C.Structure):
         ("flow", C.c_int32),
         ("u0", C.c_double),
         ("ic_kind", C.c_int32),
+        ("sgs", C.c_int32),
+        ("c_s", C.c_double),
+        ("c_omega", C.c_double),
+        ("delta_cells", C.c_double),
+        ("moment_ref", C.c_int32),
         ("stream", C.c_void_p),
     ]
 
@@ -140,6 +145,11 @@ def make_c_params(p: dict, stream=None):
     cp.flow = int(p.get("flow", 0))
     cp.u0 = float(p.get("u0", 1.0))
     cp.ic_kind = int(p.get("ic_kind", 0))
+    cp.sgs = int(p.get("sgs", 0))
+    cp.c_s = float(p.get("c_s", 0.11))
+    cp.c_omega = float(p.get("c_omega", 0.5))
+    cp.delta_cells = float(p.get("delta_cells", 3.0))
+    cp.moment_ref = int(p.get("moment_ref", 0))
     cp.stream = C.c_void_p(int(stream) if stream else 0)
     return cp, (comp, kk, ph, am, ik, iph, iam)
 

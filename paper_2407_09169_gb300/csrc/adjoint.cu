@@ -248,15 +248,12 @@ void Engine::grad_terms(const DevMps& a, const DevMps& f, const double* hf, doub
 
 std::vector<double> Engine::grad(int nsteps, int ckpt_every) {
   if (nsteps < 1) throw std::runtime_error("EINVAL: nsteps must be >= 1");
+  if (sgs_) throw std::runtime_error("EINVAL: the discrete adjoint is not available with the subgrid closures (sgs)");
   // The adjoint's products may grow the per-lane packing workspaces (freeing
   // the old ones), which captured step graphs point into: drop the graphs,
   // so that the next qtt_step captures them again.
   QTT_CUDA(cudaStreamSynchronize(st_));
-  for (int q = 0; q < 2; ++q)
-    if (graph_[q]) {
-      QTT_CUDA(cudaGraphExecDestroy(graph_[q]));
-      graph_[q] = nullptr;
-    }
+  drop_graphs();
   grad_setup();
   const int k = (ckpt_every < 1 || ckpt_every > nsteps) ? nsteps : ckpt_every;
   const int nseg = (nsteps + k - 1) / k;

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -96,6 +97,11 @@ bool to_params(const qtt_params* in, qtt::Params& p, std::string& err) {
   p.flow = in->flow;
   p.u0 = in->u0;
   p.ic_kind = in->ic_kind;
+  p.sgs = in->sgs;
+  p.c_s = in->c_s;
+  p.c_omega = in->c_omega;
+  p.delta_cells = in->delta_cells;
+  p.moment_ref = in->moment_ref;
   std::string why = qtt::validate(p);
   if (!why.empty()) {
     err = "EINVAL: " + why;
@@ -230,6 +236,95 @@ qtt_status qtt_grad(qtt_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* ou
   }
 }
 
+}  // extern "C"
+
+namespace {
+
+// One graph per step for a batch of contexts: once every context has
+// captured its two step graphs, the graph of each context's current parity
+// is embedded as an independent child node of one parent graph, which is
+// launched on a stream of the batch; the next step uses the parent graph of
+// the flipped parities.  Both parent graphs are built the first time a set
+// of contexts (engine ids, graph generations, parities) is stepped and kept
+// for the most recent set.
+struct BatchGraph {
+  std::vector<unsigned long long> ids;
+  std::vector<unsigned> gens;
+  std::vector<int> par0;  // parities the exec[0] graph was built for
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<cudaEvent_t> ctx_ev;
+  void release() {
+    for (cudaGraphExec_t& e : exec)
+      if (e) {
+        cudaGraphExecDestroy(e);
+        e = nullptr;
+      }
+  }
+};
+std::mutex g_batch_mu;
+BatchGraph g_batch;
+
+bool batch_build(qtt_ctx* const* ctxs, int32_t n) {
+  BatchGraph& B = g_batch;
+  B.release();
+  if (!B.st && cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (!B.ev && cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming) != cudaSuccess) return false;
+  while ((int32_t)B.ctx_ev.size() < n) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    B.ctx_ev.push_back(e);
+  }
+  B.ids.assign(n, 0);
+  B.gens.assign(n, 0);
+  B.par0.assign(n, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    const qtt::Engine& E = *ctxs[i]->eng;
+    B.ids[i] = E.id();
+    B.gens[i] = E.graph_generation();
+    B.par0[i] = E.parity();
+  }
+  for (int flip = 0; flip < 2; ++flip) {
+    cudaGraph_t parent = nullptr;
+    if (cudaGraphCreate(&parent, 0) != cudaSuccess) return false;
+    bool ok = true;
+    for (int32_t i = 0; i < n && ok; ++i) {
+      cudaGraphNode_t node;
+      ok = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0,
+                                      ctxs[i]->eng->graph_template(B.par0[i] ^ flip)) == cudaSuccess;
+    }
+    ok = ok && cudaGraphInstantiate(&B.exec[flip], parent, 0) == cudaSuccess;
+    cudaGraphDestroy(parent);
+    if (!ok) {
+      cudaGetLastError();
+      B.release();
+      return false;
+    }
+  }
+  return true;
+}
+
+// exec index for the contexts' current parities, or -1 when the cached
+// parent graphs do not describe this set of contexts
+int batch_match(qtt_ctx* const* ctxs, int32_t n) {
+  const BatchGraph& B = g_batch;
+  if ((int32_t)B.ids.size() != n || !B.exec[0] || !B.exec[1]) return -1;
+  int flip = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    const qtt::Engine& E = *ctxs[i]->eng;
+    if (B.ids[i] != E.id() || B.gens[i] != E.graph_generation()) return -1;
+    const int f = E.parity() ^ B.par0[i];
+    if (flip >= 0 && f != flip) return -1;
+    flip = f;
+  }
+  return flip;
+}
+
+}  // namespace
+
+extern "C" {
+
 qtt_status qtt_step_many(qtt_ctx* const* ctxs, int32_t n, int32_t nsteps, int32_t* failed) {
   if (failed) *failed = -1;
   if (n < 0 || nsteps < 0 || (n > 0 && !ctxs)) return QTT_EINVAL;
@@ -248,7 +343,47 @@ qtt_status qtt_step_many(qtt_ctx* const* ctxs, int32_t n, int32_t nsteps, int32_
   // step-major order: every context's step s is enqueued before any step s+1
   std::vector<int> bad(n, 0);
   std::vector<qtt_status> code(n, QTT_OK);
+  std::lock_guard<std::mutex> batch_lock(g_batch_mu);
+  bool on_batch = false;  // the batch stream holds work the contexts' streams have not waited for
+  auto leave_batch = [&]() {
+    if (!on_batch) return true;
+    on_batch = false;
+    if (cudaEventRecord(g_batch.ev, g_batch.st) != cudaSuccess) return false;
+    for (int32_t i = 0; i < n; ++i)
+      if (cudaStreamWaitEvent(ctxs[i]->eng->stream(), g_batch.ev, 0) != cudaSuccess) return false;
+    return true;
+  };
   for (int32_t s = 0; s < nsteps; ++s) {
+    bool all_ready = n > 1;
+    for (int32_t i = 0; i < n && all_ready; ++i) all_ready = !bad[i] && ctxs[i]->eng->step_graphs_ready();
+    if (all_ready) {
+      int flip = batch_match(ctxs, n);
+      if (flip < 0 && batch_build(ctxs, n)) flip = batch_match(ctxs, n);
+      if (flip >= 0) {
+        bool ok = true;
+        if (!on_batch) {  // the batch stream waits for every context's earlier work
+          for (int32_t i = 0; i < n && ok; ++i)
+            ok = cudaEventRecord(g_batch.ctx_ev[i], ctxs[i]->eng->stream()) == cudaSuccess &&
+                 cudaStreamWaitEvent(g_batch.st, g_batch.ctx_ev[i], 0) == cudaSuccess;
+        }
+        ok = ok && cudaGraphLaunch(g_batch.exec[flip], g_batch.st) == cudaSuccess;
+        if (ok) {
+          on_batch = true;
+          for (int32_t i = 0; i < n; ++i) ctxs[i]->eng->step_launched_externally();
+          continue;
+        }
+        cudaGetLastError();
+        g_batch.release();
+      }
+    }
+    if (!leave_batch()) {
+      for (int32_t i = 0; i < n; ++i) {
+        ctxs[i]->err = "CUDA error: ordering the contexts after the batch graph failed";
+        code[i] = QTT_ECUDA;
+        bad[i] = 1;
+      }
+      break;
+    }
     for (int32_t i = 0; i < n; ++i) {
       if (bad[i]) continue;
       try {
@@ -258,6 +393,13 @@ qtt_status qtt_step_many(qtt_ctx* const* ctxs, int32_t n, int32_t nsteps, int32_
         code[i] = classify(ctxs[i]->err);
         bad[i] = 1;
       }
+    }
+  }
+  if (!leave_batch()) {
+    for (int32_t i = 0; i < n; ++i) {
+      ctxs[i]->err = "CUDA error: ordering the contexts after the batch graph failed";
+      code[i] = QTT_ECUDA;
+      bad[i] = 1;
     }
   }
   qtt_status first = QTT_OK;
@@ -297,7 +439,7 @@ qtt_status qtt_observe(qtt_ctx* ctx, int32_t what, double* out, int64_t cap, int
     const int Kx = p.bits[2] + p.bits[3] + p.bits[4];
     switch (what) {
       case QTT_OBS_SCALARS: {
-        std::vector<double> v(12);
+        std::vector<double> v(13);
         E.scalars(v.data());
         return put(v, out, cap, written);
       }
@@ -356,6 +498,15 @@ qtt_status qtt_observe(qtt_ctx* ctx, int32_t what, double* out, int64_t cap, int
       }
       case QTT_OBS_TIMINGS:
         return put(E.timings(), out, cap, written);
+      case QTT_OBS_ERRORS: {
+        if (p.moment_ref != 1) {
+          ctx->err = "EINVAL: the error measures need a context made with moment_ref = 1";
+          return QTT_EINVAL;
+        }
+        std::vector<double> v(6);
+        E.error_sample(v.data());
+        return put(v, out, cap, written);
+      }
       default:
         ctx->err = "EINVAL: unknown observable";
         return QTT_EINVAL;
@@ -567,6 +718,12 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
     if (which == 41) {
       qtt::Model m = qtt::build_model(p);
       return put(std::vector<double>(m.f0.r.begin(), m.f0.r.end()), out, cap, written);
+    }
+    if (which == 33 || which == 42) {  // the encoded Omega_mix(x) (sgs), or its bonds
+      if (p.sgs != 1) return QTT_EINVAL;
+      qtt::Model m = qtt::build_model(p);
+      if (which == 42) return put(std::vector<double>(m.omega_x.r.begin(), m.omega_x.r.end()), out, cap, written);
+      return put(qtt::tt_dense(m.omega_x), out, cap, written);
     }
     return QTT_EINVAL;
   } catch (const std::exception& ex) {

@@ -31,6 +31,7 @@
 #include "gemm_tc.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -112,7 +113,10 @@ Chain DevMps::chain() const {
 
 static long long pow2(int e) { return e >= 62 ? (1LL << 62) : (1LL << e); }
 
+static std::atomic<unsigned long long> g_engine_ids{0};
+
 Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
+  id_ = ++g_engine_ids;
   if (st_ == nullptr) {
     // A stream of our own (blocking, so ordered with the legacy default
     // stream) instead of the legacy stream, which cannot be captured.
@@ -135,9 +139,17 @@ Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
   // because T_n R_{n+1} can be far smaller than |T_n| |R_{n+1}| (the stencils
   // cancel) and an error in R_{n+1} steers the range finder away from
   // T_n R_{n+1}; a bias of the sketch, on the other hand, only rescales it.
-  const int mode = p.precision == 1 ? TC_BF16X6 : p.precision == 2 ? TC_TF32 : p.precision == 3 ? TC_BF16X3 : -1;
+  const int mode = p.precision == 1   ? TC_BF16X6
+                   : p.precision == 2 ? TC_TF32
+                   : p.precision == 3 ? TC_BF16X3
+                   : p.precision == 4 ? TC_BF16X10
+                                      : -1;
   for (int& m : tc_mode_) m = mode;
-  if (p.precision == 1) tc_mode_[GEMM_SKETCH] = tc_mode_[GEMM_RANGE] = TC_TF32X3;
+  if (p.precision == 1 || p.precision == 4) tc_mode_[GEMM_SKETCH] = tc_mode_[GEMM_RANGE] = TC_TF32X3;
+  // BF16X10 keeps the operator-bond contractions (CUDA cores) in FP64: in
+  // FP32 alone they move the state by ~1e-5 over ten steps of the 2^4-point
+  // workload, far above what its sliced products leave.
+  small_fp32_ = p.precision >= 1 && p.precision <= 3;
   // The reduced forms re-orthonormalise the float QR's Q in FP64 (one
   // Newton-Schulz step).  The float Q's departure from orthonormality
   // (~1e-6) otherwise shows up as a drift of the mass <1>: -8.7e-5 against
@@ -150,6 +162,8 @@ Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
 Engine::~Engine() {
   for (cudaGraphExec_t& g : graph_)
     if (g) cudaGraphExecDestroy(g);
+  for (cudaGraph_t& g : graph_tmpl_)
+    if (g) cudaGraphDestroy(g);
   for (void* a : allocs_) cudaFree(a);
   for (void* w : pack_ws_)
     if (w) cudaFree(w);
@@ -243,7 +257,7 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
   if (small_gemm_fits(M, N, K, outer, inner)) {
     // operator-bond contractions: memory-bound, on the CUDA cores
     TimeScope ts(timer_, TM_SMALL, cur(), 2.0 * M * (double)N * K * outer * inner);
-    small_gemm(cur(), mode >= 0, M, N, K, outer, inner, alpha, A, B, beta, C);
+    small_gemm(cur(), mode >= 0 && small_fp32_, M, N, K, outer, inner, alpha, A, B, beta, C);
     return;
   }
   if (mode < 0) {
@@ -268,7 +282,7 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
   }
   const double fl = 2.0 * M * (double)N * K * outer * inner;
   if (timer_->on) {
-    static const double passes[5] = {3, 2, 6, 1, 6};  // indexed by TcMode, in bf16-pass units
+    static const double passes[6] = {3, 2, 6, 1, 6, 10};  // indexed by TcMode, in bf16-pass units
     tc_issued_flops_ += fl * passes[mode];
   }
   TimeScope ts(timer_, TM_TC, cur(), fl);
@@ -329,11 +343,39 @@ void Engine::init() {
     alloc_mps(wphi_[w], model_.wphi[w].r);
     upload_tt_mps(wphi_[w], model_.wphi[w], model_.wphi[w].r);
   }
+  sgs_ = p_.sgs == 1;
+  if (sgs_) {
+    const TT& ox = model_.omega_x;
+    alloc_mps(omx_, ox.r);
+    upload_tt_mps(omx_, ox, ox.r);
+    std::vector<int> hb(N + 1, 1);
+    hb[kphi_] = 2;
+    for (int n = kphi_ + 1; n < N; ++n) hb[n] = ox.r[n - kphi_] * D_[n];
+    alloc_mps(hk_, hb);
+  }
+  if (p_.moment_ref == 1) {
+    const size_t Mx = (size_t)1 << (p_.bits[2] + p_.bits[3] + p_.bits[4]);
+    mref_ = (double*)dalloc(2 * Mx * sizeof(double));
+    mtmp_ = (double*)dalloc(2 * Mx * sizeof(double));
+    ux_ = (double*)dalloc(3 * Mx * sizeof(double));
+    errs_ = (double*)dalloc(8 * sizeof(double));
+    std::vector<double> h(3 * Mx);
+    for (int i = 0; i < 3; ++i) {
+      const std::vector<double> ui = tt_dense(model_.u[i]);
+      std::copy(ui.begin(), ui.end(), h.begin() + i * Mx);
+    }
+    QTT_CUDA(cudaMemcpy(ux_, h.data(), 3 * Mx * sizeof(double), cudaMemcpyHostToDevice));
+    if (sgs_) {
+      const std::vector<double> g = subgrid_fields(p_, model_.u).gamma;
+      gx_ = (double*)dalloc(Mx * sizeof(double));
+      QTT_CUDA(cudaMemcpy(gx_, g.data(), Mx * sizeof(double), cudaMemcpyHostToDevice));
+    }
+  }
 
   // per-slot product bonds: slot 0, 3 identity, slot 1 linear, slot 2 mixing
   auto wslot = [&](int slot, int n) -> size_t {
     if (slot == 1) return (size_t)op_lin_.w[n];
-    if (slot == 2) return (size_t)(n <= kphi_ ? had_.w[n] : D_[n]);
+    if (slot == 2) return (size_t)(n <= kphi_ ? had_.w[n] : sgs_ ? hk_.b[n] : D_[n]);
     return 1;
   };
   const int nlo = exact_ ? nc_ + 1 : 1;
@@ -383,7 +425,12 @@ void Engine::init() {
     wchains_dev_ = (Chain*)dalloc(6 * sizeof(Chain));
     QTT_CUDA(cudaMemcpy(wchains_dev_, wc.data(), 6 * sizeof(Chain), cudaMemcpyHostToDevice));
   }
-  ws_elems_ = (size_t)8 << 20;
+  // Split-K partial tiles (FP64): a split product writes splits x M x N
+  // doubles, and the outputs of this context's products are a few max_bond^2;
+  // 512 max_bond^2 (capped at 8 Mi doubles, the size the chi = 128 chains
+  // use) leaves room for the splits the cost model picks, without holding
+  // 64 MB per lane in the small contexts of a batch.
+  ws_elems_ = std::min<size_t>((size_t)8 << 20, std::max<size_t>((size_t)1 << 18, (size_t)512 * max_bond_ * max_bond_));
   ws_ = (double*)dalloc(ws_elems_ * sizeof(double));
   // lanes for the terms' concurrent work (at most 2 terms in the first stage
   // and 3 (Heun) or 4 (midpoint) in the second)
@@ -451,7 +498,27 @@ void Engine::init() {
   }
   QTT_CUDA(cudaMemsetAsync(disc_, 0, sizeof(double) * 4, st_));
   QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int) * 4, st_));
+  if (mref_) {  // the reference starts from the initial <Phi_a>(x)
+    const size_t Mx = (size_t)1 << (p_.bits[2] + p_.bits[3] + p_.bits[4]);
+    double* tmp3 = (double*)dalloc(3 * Mx * sizeof(double));
+    means_dev(tmp3);
+    QTT_CUDA(cudaMemcpyAsync(mref_, tmp3 + Mx, 2 * Mx * sizeof(double), cudaMemcpyDeviceToDevice, st_));
+  }
   QTT_CUDA(cudaStreamSynchronize(st_));
+}
+
+void Engine::moment_ref_step() {
+  if (!mref_) return;
+  TimeScope ts(timer_, TM_OTHER, st_);
+  const int K[3] = {p_.bits[2], p_.bits[3], p_.bits[4]};
+  const double dt = p_.dt;
+  if (p_.rk_variant == 0) {  // Heun
+    moment_stage(st_, mref_, mref_, mtmp_, ux_, gx_, p_.gamma, K, dt, 1.0, 0.0, 1.0);
+    moment_stage(st_, mref_, mtmp_, mref_, ux_, gx_, p_.gamma, K, dt, 0.5, 0.5, 0.5);
+  } else {  // midpoint
+    moment_stage(st_, mref_, mref_, mtmp_, ux_, gx_, p_.gamma, K, dt, 1.0, 0.0, 0.5);
+    moment_stage(st_, mref_, mtmp_, mref_, ux_, gx_, p_.gamma, K, dt, 1.0, 0.0, 1.0);
+  }
 }
 
 void Engine::cond_means(const DevMps& f, double* v) {
@@ -465,6 +532,12 @@ void Engine::make_hfirst(const DevMps& f, double* v, double* hf) {
   // first x core of diag(<Phi_a>(x)): hf[a][s][b'] = sum_b v[a][b] A_kphi[b][s][b']
   const int bl = D_[kphi_], br = D_[kphi_ + 1];
   gemm64(2, 2 * br, bl, 1, 1, 1.0, mv(v, bl, 1), mv(f.core(kphi_), 2 * br, 1), 0.0, ov(hf, 2 * br, 1));
+}
+
+void Engine::mix_cores(const DevMps& f, const double* hf) {
+  if (!sgs_) return;
+  TimeScope ts(timer_, TM_OTHER, st_);
+  kron_diag_cores(st_, omx_.chain(), f.chain(), hk_.chain(), hf, kphi_);
 }
 
 void Engine::sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr,
@@ -568,6 +641,10 @@ Term Engine::term_mix(const DevMps* f, const double* hf, double scale) const {
   t.kind = 1;
   t.op = &had_;
   t.hfirst = hf;
+  if (sgs_) {  // diag(Omega_mix(x) <Phi_a>(x)): the Kronecker cores built by mix_cores
+    t.hsrc = &hk_;
+    t.hfirst = hk_.core(kphi_);
+  }
   t.kphi = kphi_;
   t.slot = 2;
   t.scale = scale;
@@ -746,24 +823,29 @@ void Engine::step_body() {
     // Heun: f* = f + dt L(f);  f_{n+1} = (f + f* + dt L(f*)) / 2
     cond_means(f_, v_[0]);
     make_hfirst(f_, v_[0], hf_[0]);
+    mix_cores(f_, hf_[0]);
     Term a[2] = {term_dense(1, &op_lin_, &f_, 1.0), term_mix(&f_, hf_[0], 1.0)};
     run_stage(a, 2, fs_, 0);
     cond_means(fs_, v_[1]);
     make_hfirst(fs_, v_[1], hf_[1]);
+    mix_cores(fs_, hf_[1]);
     Term b[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &fs_, 0.5), term_mix(&fs_, hf_[1], 0.5)};
     run_stage(b, 3, g_, 1);
   } else {
     // midpoint: f_h = f + dt/2 L(f);  f_{n+1} = f + dt L(f_h)
     cond_means(f_, v_[0]);
     make_hfirst(f_, v_[0], hf_[0]);
+    mix_cores(f_, hf_[0]);
     Term a[3] = {term_dense(0, &ident_, &f_, 0.5), term_dense(1, &op_lin_, &f_, 0.5), term_mix(&f_, hf_[0], 0.5)};
     run_stage(a, 3, fs_, 0);
     cond_means(fs_, v_[1]);
     make_hfirst(fs_, v_[1], hf_[1]);
+    mix_cores(fs_, hf_[1]);
     Term b[4] = {term_dense(0, &ident_, &f_, 1.0), term_dense(1, &op_lin_, &fs_, 1.0),
                  term_dense(3, &ident_, &fs_, -1.0), term_mix(&fs_, hf_[1], 1.0)};
     run_stage(b, 4, g_, 1);
   }
+  moment_ref_step();
   bump_counter(st_, dstep_);
 }
 
@@ -793,8 +875,36 @@ bool Engine::capture_step(int parity) {
   cudaGraph_t g = nullptr;
   if (cudaStreamEndCapture(st_, &g) != cudaSuccess || g == nullptr) return give_up(g);
   if (cudaGraphInstantiate(&graph_[parity], g, 0) != cudaSuccess) return give_up(g);
-  cudaGraphDestroy(g);
+  if (graph_tmpl_[parity]) cudaGraphDestroy(graph_tmpl_[parity]);
+  graph_tmpl_[parity] = g;  // kept for embedding into a batch graph
+  ++graph_gen_;
   return true;
+}
+
+void Engine::drop_graphs() {
+  for (int q = 0; q < 2; ++q) {
+    if (graph_[q]) {
+      QTT_CUDA(cudaGraphExecDestroy(graph_[q]));
+      graph_[q] = nullptr;
+    }
+    if (graph_tmpl_[q]) {
+      cudaGraphDestroy(graph_tmpl_[q]);
+      graph_tmpl_[q] = nullptr;
+    }
+  }
+  ++graph_gen_;
+}
+
+bool Engine::step_graphs_ready() const {
+  return graphs_ && warm_ && !timer_->on && graph_[0] && graph_[1] && graph_tmpl_[0] && graph_tmpl_[1];
+}
+
+void Engine::step_launched_externally() {
+  count_launches(graph_launches_[parity_]);
+  std::swap(f_, g_);
+  parity_ ^= 1;
+  time_ += p_.dt;
+  ++steps_;
 }
 
 void Engine::step(int nsteps) {
@@ -885,7 +995,7 @@ void Engine::xgram(const DevMps& f, double* E) {
   QTT_CUDA(cudaMemcpyAsync(E, cur, sizeof(double) * f.b[kphi_] * f.b[kphi_], cudaMemcpyDeviceToDevice, st_));
 }
 
-void Engine::scalars(double out[12]) {
+void Engine::scalars(double out[13]) {
   const int b = D_[kphi_];
   double* V = envout_;              // 6 x b weight environments
   double* u = V + 6 * (size_t)b;    // b
@@ -919,9 +1029,26 @@ void Engine::scalars(double out[12]) {
   out[9] = h[0] - h[1] - h[2];  // mean of <1 - phi1 - phi2>
   out[10] = discarded_last_;
   out[11] = (double)steps_;
+  out[12] = norm2();  // sum of f^2 over every grid cell
 }
 
 void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out) {
+  size_t rows = head_rows;
+  for (int n = n0; n < N_; ++n) rows *= 2;
+  double* d = nullptr;
+  QTT_CUDA(cudaMalloc(&d, sizeof(double) * rows));
+  try {
+    chain_dense_dev(f, n0, head, head_rows, d);
+    QTT_CUDA(cudaMemcpyAsync(out, d, sizeof(double) * rows, cudaMemcpyDeviceToHost, st_));
+    QTT_CUDA(cudaStreamSynchronize(st_));
+  } catch (...) {
+    cudaFree(d);
+    throw;
+  }
+  cudaFree(d);
+}
+
+void Engine::chain_dense_dev(const DevMps& f, int n0, const double* head, int head_rows, double* dout) {
   // rows = multi-index of the processed sites, columns = open bond; out gets head_rows * 2^(N - n0) values
   size_t rows = head_rows;
   for (int n = n0; n < N_; ++n) rows *= 2;
@@ -941,7 +1068,7 @@ void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_r
     bond = br;
   }
   QTT_CUDA(cudaGetLastError());
-  QTT_CUDA(cudaMemcpyAsync(out, a, sizeof(double) * R, cudaMemcpyDeviceToHost, st_));
+  QTT_CUDA(cudaMemcpyAsync(dout, a, sizeof(double) * R, cudaMemcpyDeviceToDevice, st_));
   QTT_CUDA(cudaStreamSynchronize(st_));
   cudaFree(a);
   cudaFree(b);
@@ -950,6 +1077,43 @@ void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_r
 void Engine::dense(double* out) {
   fill_value(st_, obsA_, 1, 1.0);
   chain_dense(f_, 0, obsA_, 1, out);
+}
+
+void Engine::means_dev(double* dout) {
+  const int b = D_[kphi_];
+  const size_t Mx = (size_t)1 << (p_.bits[2] + p_.bits[3] + p_.bits[4]);
+  const Chain fc = f_.chain();
+  for (int w = 0; w < 3; ++w) {
+    left_weight_env(st_, fc, wphi_[w].chain(), kphi_, max_bond_, envout_, b, envw_);
+    chain_dense_dev(f_, kphi_, envout_, 1, dout + w * Mx);
+  }
+}
+
+void Engine::error_sample(double* out) {
+  if (!mref_) throw std::runtime_error("EINVAL: the error measures need moment_ref = 1");
+  const size_t Mx = (size_t)1 << (p_.bits[2] + p_.bits[3] + p_.bits[4]);
+  double* fields = nullptr;
+  QTT_CUDA(cudaMalloc(&fields, 3 * Mx * sizeof(double)));
+  double acc[5] = {0, 0, 0, 0, 0};
+  try {
+    means_dev(fields);
+    QTT_CUDA(cudaMemsetAsync(errs_, 0, 5 * sizeof(double), st_));
+    error_sums(st_, fields, mref_, Mx, errs_);
+    QTT_CUDA(cudaGetLastError());
+    QTT_CUDA(cudaMemcpyAsync(acc, errs_, sizeof(acc), cudaMemcpyDeviceToHost, st_));
+    QTT_CUDA(cudaStreamSynchronize(st_));
+  } catch (...) {
+    cudaFree(fields);
+    throw;
+  }
+  cudaFree(fields);
+  const double n = (double)Mx, a1 = acc[3] / n, a2 = acc[4] / n;
+  out[0] = a1 - 0.5;
+  out[1] = a2 - 0.5;
+  out[2] = acc[0] / n;
+  out[3] = acc[1] / n;
+  out[4] = a1 - a2;
+  out[5] = acc[2] / n;
 }
 
 void Engine::means(double* out) {
@@ -990,10 +1154,15 @@ double Engine::overlap(const Engine& o) {
     const size_t ma = (size_t)std::max(A.b[n], A.b[n + 1]), mb = (size_t)std::max(B.b[n], B.b[n + 1]);
     need = std::max(need, ma * 2 * mb);
   }
-  double *e0 = nullptr, *e1 = nullptr, *x = nullptr;
-  QTT_CUDA(cudaMalloc(&e0, need * sizeof(double)));
-  QTT_CUDA(cudaMalloc(&e1, need * sizeof(double)));
-  QTT_CUDA(cudaMalloc(&x, need * sizeof(double)));
+  // the observable scratch (2 max_bond^2 doubles each) serves any pair of
+  // states no wider than this one; a wider partner gets buffers of its own
+  const bool own = need > (size_t)2 * max_bond_ * max_bond_;
+  double *e0 = obsA_, *e1 = obsB_, *x = obsX_;
+  if (own) {
+    QTT_CUDA(cudaMalloc(&e0, need * sizeof(double)));
+    QTT_CUDA(cudaMalloc(&e1, need * sizeof(double)));
+    QTT_CUDA(cudaMalloc(&x, need * sizeof(double)));
+  }
   fill_value(st_, e0, 1, 1.0);
   for (int n = 0; n < N_; ++n) {
     const int ba = A.b[n], bb = B.b[n], ba2 = A.b[n + 1], bb2 = B.b[n + 1];
@@ -1004,9 +1173,11 @@ double Engine::overlap(const Engine& o) {
   double r = 0;
   QTT_CUDA(cudaMemcpyAsync(&r, e0, sizeof(double), cudaMemcpyDeviceToHost, st_));
   QTT_CUDA(cudaStreamSynchronize(st_));
-  cudaFree(e0);
-  cudaFree(e1);
-  cudaFree(x);
+  if (own) {
+    cudaFree(e0);
+    cudaFree(e1);
+    cudaFree(x);
+  }
   return r;
 }
 

@@ -125,10 +125,12 @@ class Engine {
   void step(int nsteps);       // RK2 steps
   int check_status(std::string& msg);  // syncs; returns a qtt_status value
   // observables (host outputs)
-  void scalars(double out[12]);
+  void scalars(double out[13]);
   std::vector<int> bonds() const { return f_.b; }
   void dense(double* out);                     // 2^N values
   void means(double* out);                     // 3 * 2^Kx values
+  // the 6 space averages of one error sample (needs moment_ref, see QTT_OBS_ERRORS)
+  void error_sample(double* out);
   void points(const std::vector<unsigned char>& bits, int npts, double* out);
   // Point evaluation through the fixed device array of points_static.cu
   // (no allocation); inout holds npts x N 0/1 flags and receives the values.
@@ -147,6 +149,18 @@ class Engine {
   double discarded_last() const { return discarded_last_; }
   cudaStream_t stream() const { return st_; }
   void set_time(double t, long long s);
+  // Batched stepping (qtt_step_many): once both step graphs are captured, a
+  // caller may launch the captured step itself (embedded in a graph of its
+  // own) and then record the step here.  graph_template(q) is the captured
+  // graph of parity q (owned by the engine); graph_generation() changes
+  // whenever the engine drops or recaptures its graphs; id() is unique per
+  // engine in the process.
+  bool step_graphs_ready() const;
+  int parity() const { return parity_; }
+  cudaGraph_t graph_template(int q) const { return graph_tmpl_[q]; }
+  unsigned graph_generation() const { return graph_gen_; }
+  unsigned long long id() const { return id_; }
+  void step_launched_externally();
   // Discrete adjoint (gradient of J = avg_x (<1> - <Phi_1> - <Phi_2>) after
   // nsteps Heun steps from the initial PDF): out[0] = J, out[1..] = dJ/dtheta
   // for Omega, Da, gamma, each velocity mode amplitude and each IC mode
@@ -170,12 +184,14 @@ class Engine {
   void gemm64(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C);
   void cond_means(const DevMps& f, double* v);
   void make_hfirst(const DevMps& f, double* v, double* hf);
+  void mix_cores(const DevMps& f, const double* hf);  // sgs: the mixing term's Kronecker cores into hk_
   void sketch_site(const Term& t, int n, const double* Wn1, double* Wn, const double* Om, int Ll, int Lr, int role);
   void sketch_pass(Term* terms, int nt, int n_stop, const DevMps& om);  // right-to-left, sites N-1 .. n_stop+1
   void zip_site(const Term& t, int n, int r, const double* C, double* T, double alpha);
   void run_stage(Term* terms, int nterms, DevMps& out, int stage);
   void step_body();      // one RK2 step from f_ into g_ (launches only)
   bool capture_step(int parity);  // false: graphs unavailable, run eagerly
+  void drop_graphs();             // destroys the step graphs (the next steps recapture them)
   void run_stage_exact(Term* terms, int nterms, DevMps& out);
   void xgram(const DevMps& f, double* E);
   void gram_pass(const DevMps& g);
@@ -183,6 +199,10 @@ class Engine {
   Term term_dense(int slot, const DevOp* op, const DevMps* f, double scale) const;
   Term term_mix(const DevMps* f, const double* hf, double scale) const;
   void chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out);
+  // the same into device memory (dout holds head_rows * 2^(N - n0) doubles)
+  void chain_dense_dev(const DevMps& f, int n0, const double* head, int head_rows, double* dout);
+  void means_dev(double* dout);  // <1>, <Phi_1>, <Phi_2> over x into device memory
+  void moment_ref_step();        // one RK2 step of the first-moment reference (moment_ref)
   // adjoint (adjoint.cu)
   void grad_setup();
   void copy_mps(const DevMps& from, DevMps& to);
@@ -201,12 +221,20 @@ class Engine {
   int N_ = 0, kphi_ = 0, nc_ = 0;
   int prec_bits_ = 64;
   bool qr_refine_ = false;
+  bool small_fp32_ = false;  // operator-bond contractions on the CUDA cores in FP32
   bool exact_ = false;
   std::vector<void*> allocs_;
   std::vector<int> D_, ell_, rz_;
   DevMps f_, fs_, g_, mid_, omega_, wphi_[6];
   Chain* wchains_dev_ = nullptr;  // wphi_ chains on the device
   DevOp op_lin_, had_, ident_;
+  // subgrid closures: the Omega_mix(x) train over the x sites, and the
+  // mixing term's diagonal cores (f's x cores times it, built each stage)
+  DevMps omx_, hk_;
+  bool sgs_ = false;
+  // first-moment reference (moment_ref): m [2][Mx], a stage buffer, the
+  // velocity [3][Mx], gamma(x) [Mx] under sgs (else null), error sums [5]
+  double *mref_ = nullptr, *mtmp_ = nullptr, *ux_ = nullptr, *gx_ = nullptr, *errs_ = nullptr;
   // scratch
   double *Wslot_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<size_t> Woff_[5];
@@ -246,6 +274,9 @@ class Engine {
   // CUDA graphs of one step, indexed by which of the two state buffers is f_
   // (the step swaps them); captured after one step has run eagerly.
   cudaGraphExec_t graph_[2] = {nullptr, nullptr};
+  cudaGraph_t graph_tmpl_[2] = {nullptr, nullptr};  // the captured graphs (for embedding)
+  unsigned graph_gen_ = 0;
+  unsigned long long id_ = 0;
   int graph_launches_[2] = {0, 0};
   bool graphs_ = true, warm_ = false;
   int parity_ = 0;

@@ -204,6 +204,24 @@ void left_weight_envs(cudaStream_t st, const Chain& f, const Chain* wchains_dev,
 void right_ones_env(cudaStream_t st, const Chain& f, int n0, int max_bond, double* out, double* work);
 // Evaluates f at npts multi-indices given as bits[p * N + n] (one warp per
 // point); work holds npts * 2 * max_bond doubles.
+// Diagonal cores of the mixing term under the subgrid closures: the x cores
+// of f (the first one replaced by hf, [2][2][b], the conditional means
+// absorbed) times the x cores of the Omega_mix(x) train, site by site as a
+// Kronecker product: out_n[(o, h)][s][(o', h')] = Om_j[o][s][o'] F_n[h][s][h']
+// with j = n - kphi; out's bonds are the products of the two.
+void kron_diag_cores(cudaStream_t st, const Chain& om, const Chain& f, const Chain& out, const double* hf, int kphi);
+// One explicit RK2 stage of the first-moment equation Eq. FPMoms (S = 0) on
+// the dense x grid (x1 slowest, 2^K per dimension), both species at once:
+// out = a m0 + b m + c dt R(m), R(m) = -u . D1 m + div(g grad m) with
+// periodic CFD2 differences; g = null: the constant gamma times the compact
+// second difference, else the flux form with face values averaged from the
+// two neighbours.  m0 is read point-wise only, so out may be m0.
+void moment_stage(cudaStream_t st, const double* m0, const double* m, double* out, const double* u, const double* g,
+                  double gamma, const int K[3], double dt, double a, double b, double c);
+// The space sums of an error sample: acc[0..5) += (M1 - r1)^2, (M2 - r2)^2,
+// (N - 1)^2, M1, M2 over the x grid (fields [3][Mx] = <1>, <Phi_1>, <Phi_2>;
+// ref [2][Mx]); acc must be zeroed first.
+void error_sums(cudaStream_t st, const double* fields, const double* ref, size_t Mx, double* acc);
 void eval_points(cudaStream_t st, const Chain& f, int npts, const unsigned char* bits, int max_bond, double* out,
                  double* work);
 // flag[0] = 1 if any of the n entries is NaN or infinite.

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdlib>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace qtt {
@@ -249,6 +251,72 @@ __global__ void eval_points_kernel(Chain f, int npts, const unsigned char* bits,
   if (lane == 0) out[warp] = val;
 }
 
+__global__ void kron_diag_kernel(Chain om, Chain f, Chain out, const double* hf, int kphi) {
+  const int j = blockIdx.y, n = kphi + j;
+  const int ol = om.bond[j], orr = om.bond[j + 1];
+  const int fl = j == 0 ? 2 : f.bond[n], fr = f.bond[n + 1];
+  const double* F = j == 0 ? hf : f.core[n];
+  const double* O = om.core[j];
+  double* X = const_cast<double*>(out.core[n]);
+  const long long R = (long long)orr * fr;
+  const long long total = (long long)ol * fl * 2 * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e % R, rest = e / R;
+    const int s = (int)(rest & 1);
+    const long long r = rest >> 1;
+    const long long o = r / fl, h = r - o * fl, o2 = c / fr, h2 = c - o2 * fr;
+    X[e] = O[(o * 2 + s) * orr + o2] * F[(h * 2 + s) * fr + h2];
+  }
+}
+
+__global__ void moment_stage_kernel(const double* m0, const double* m, double* out, const double* u, const double* g,
+                                    double gamma, int K1, int K2, int K3, double dt, double a, double b, double c) {
+  const long long M1 = 1LL << K1, M2 = 1LL << K2, M3 = 1LL << K3, Mx = M1 * M2 * M3;
+  const long long st[3] = {M2 * M3, M3, 1};
+  const long long Md[3] = {M1, M2, M3};
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * Mx; e += (long long)gridDim.x * blockDim.x) {
+    const long long sp = e / Mx, x = e - sp * Mx;
+    const double* ms = m + sp * Mx;
+    const double mc = ms[x];
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const long long j = (x / st[i]) % Md[i];
+      const long long xp = x + (((j + 1) % Md[i]) - j) * st[i];
+      const long long xm = x + (((j + Md[i] - 1) % Md[i]) - j) * st[i];
+      const double h = two_pi / (double)Md[i];
+      r -= u[i * Mx + x] * (ms[xp] - ms[xm]) / (2.0 * h);
+      if (g) {
+        const double gp = 0.5 * (g[x] + g[xp]), gm = 0.5 * (g[xm] + g[x]);
+        r += (gp * (ms[xp] - mc) - gm * (mc - ms[xm])) / (h * h);
+      } else {
+        r += gamma * (ms[xp] - 2.0 * mc + ms[xm]) / (h * h);
+      }
+    }
+    out[e] = a * m0[e] + b * mc + c * dt * r;
+  }
+}
+
+__global__ void error_sums_kernel(const double* fields, const double* ref, long long Mx, double* acc) {
+  double v[5] = {0, 0, 0, 0, 0};
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < Mx; x += (long long)gridDim.x * blockDim.x) {
+    const double n = fields[x], m1 = fields[Mx + x], m2 = fields[2 * Mx + x];
+    const double d1 = m1 - ref[x], d2 = m2 - ref[Mx + x], dn = n - 1.0;
+    v[0] += d1 * d1;
+    v[1] += d2 * d2;
+    v[2] += dn * dn;
+    v[3] += m1;
+    v[4] += m2;
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, v[k]);
+  }
+}
+
 __global__ void finite_kernel(const double* p, size_t n, int* flag) {
   for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x)
     if (!isfinite(p[x])) {
@@ -368,6 +436,23 @@ void eval_points(cudaStream_t st, const Chain& f, int npts, const unsigned char*
   count_launches(1);
   eval_points_kernel<<<(npts + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
       f, npts, bits, max_bond, out, work);
+}
+void kron_diag_cores(cudaStream_t st, const Chain& om, const Chain& f, const Chain& out, const double* hf, int kphi) {
+  long long most = 1;
+  for (int j = 0; j < om.n; ++j) most = std::max<long long>(most, (long long)out.bond[kphi + j] * 2 * out.bond[kphi + j + 1]);
+  const unsigned bx = (unsigned)std::min<long long>(1024, (most + 255) / 256);
+  count_launches(1);
+  kron_diag_kernel<<<dim3(bx, (unsigned)om.n), 256, 0, st>>>(om, f, out, hf, kphi);
+}
+void moment_stage(cudaStream_t st, const double* m0, const double* m, double* out, const double* u, const double* g,
+                  double gamma, const int K[3], double dt, double a, double b, double c) {
+  const long long n = 2LL << (K[0] + K[1] + K[2]);
+  count_launches(1);
+  moment_stage_kernel<<<grid_for((size_t)n), 256, 0, st>>>(m0, m, out, u, g, gamma, K[0], K[1], K[2], dt, a, b, c);
+}
+void error_sums(cudaStream_t st, const double* fields, const double* ref, size_t Mx, double* acc) {
+  count_launches(1);
+  error_sums_kernel<<<grid_for(Mx), 256, 0, st>>>(fields, ref, (long long)Mx, acc);
 }
 void check_finite(cudaStream_t st, const double* p, size_t n, int* flag) {
   if (n) count_launches(1);

@@ -28,7 +28,7 @@ std::string validate(const Params& p) {
   if (p.chi_max < 1) e << "chi_max must be >= 1; ";
   if (p.chi_max > 4096) e << "chi_max > 4096 unsupported; ";
   if (!(p.svd_rel_tol >= 0.0) || p.svd_rel_tol >= 1.0) e << "svd_rel_tol must be in [0, 1); ";
-  if (p.precision < 0 || p.precision > 3) e << "unknown precision " << p.precision << "; ";
+  if (p.precision < 0 || p.precision > 4) e << "unknown precision " << p.precision << "; ";
   if (!(p.dt > 0.0) || !std::isfinite(p.dt)) e << "dt must be positive; ";
   if (!(p.ic_sigma > 0.0)) e << "ic_sigma must be positive; ";
   if (p.ic_kind == 2 ? !(p.ic_blend_width >= 0.0) : !(p.ic_blend_width > 0.0))
@@ -38,6 +38,15 @@ std::string validate(const Params& p) {
   if (!std::isfinite(p.u0)) e << "u0 must be finite; ";
   if (p.oversample < 0 || p.oversample > 256) e << "oversample outside 0..256; ";
   if (p.rk_variant != 0 && p.rk_variant != 1) e << "rk_variant must be 0 or 1; ";
+  if (p.sgs != 0 && p.sgs != 1) e << "sgs must be 0 or 1; ";
+  if (p.moment_ref != 0 && p.moment_ref != 1) e << "moment_ref must be 0 or 1; ";
+  if (p.moment_ref == 1 && p.bits[2] + p.bits[3] + p.bits[4] > 26) e << "moment_ref needs K3 + K4 + K5 <= 26; ";
+  if (p.sgs == 1) {
+    if (p.bits[2] + p.bits[3] + p.bits[4] > 18) e << "sgs needs K3 + K4 + K5 <= 18 (dense fields at set-up); ";
+    if (!(p.c_s >= 0.0) || !(p.c_omega >= 0.0) || !(p.delta_cells > 0.0) || !std::isfinite(p.c_s) ||
+        !std::isfinite(p.c_omega) || !std::isfinite(p.delta_cells))
+      e << "sgs needs c_s >= 0, c_omega >= 0, delta_cells > 0; ";
+  }
   for (const Mode& m : p.umodes) {
     if (m.comp < 0 || m.comp > 2) e << "velocity mode component outside 0..2; ";
     else if (m.k[m.comp] != 0) e << "velocity mode must have k[comp] = 0 (divergence-free); ";
@@ -358,6 +367,69 @@ static TT initial_pdf(const Params& p) {
   return f;
 }
 
+SubgridFields subgrid_fields(const Params& p, const TT* u3) {
+  // Eq. FP0's closures on the sampled velocity: strain rates by periodic CFD2
+  // differences, Smagorinsky diffusivity, LMSE mixing rate.
+  const int K[3] = {p.bits[2], p.bits[3], p.bits[4]};
+  const size_t M[3] = {(size_t)1 << K[0], (size_t)1 << K[1], (size_t)1 << K[2]};
+  const size_t Mx = M[0] * M[1] * M[2];
+  const double h[3] = {2.0 * kPi / (double)M[0], 2.0 * kPi / (double)M[1], 2.0 * kPi / (double)M[2]};
+  std::vector<double> u[3];
+  for (int i = 0; i < 3; ++i) u[i] = tt_dense(u3[i]);
+  const size_t stride[3] = {M[1] * M[2], M[2], 1};
+  auto neighbour = [&](size_t idx, int axis, int dir) {
+    const size_t j = (idx / stride[axis]) % M[axis];
+    const size_t jn = (j + M[axis] + (size_t)(dir + (int)M[axis])) % M[axis];
+    return idx + (jn - j) * stride[axis];  // unsigned wrap-around is exact modulo 2^64
+  };
+  auto deriv = [&](const std::vector<double>& F, int axis, size_t idx) {
+    return (F[neighbour(idx, axis, +1)] - F[neighbour(idx, axis, -1)]) / (2.0 * h[axis]);
+  };
+  SubgridFields out;
+  out.delta = p.delta_cells * std::cbrt(h[0] * h[1] * h[2]);
+  out.gamma.assign(Mx, p.gamma);
+  out.omega.assign(Mx, 0.0);
+  const double c = p.c_s * 0.5 * out.delta * out.delta;
+  for (size_t idx = 0; idx < Mx; ++idx) {
+    double s2 = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const double sij = deriv(u[i], j, idx) + deriv(u[j], i, idx);
+        s2 += sij * sij;
+      }
+    out.gamma[idx] += c * std::sqrt(s2);
+    out.omega[idx] = p.c_omega * out.gamma[idx] / (out.delta * out.delta);
+  }
+  return out;
+}
+
+// Tolerance of the TT encodings of the subgrid fields (their ranks grow
+// quickly below it; the fields then enter the dynamics at this level).
+static const double kFieldTol = 1e-12;
+
+// d/dx_dim [g d/dx_dim] in flux form (periodic): B diag(g_face) F with
+// F = (S+ - I) / h, B = (I - S-) / h and g_face(x) = (g(x) + g(x + h e_dim)) / 2.
+static TT flux_diffusion_op(const Params& p, const std::vector<double>& g, int dim) {
+  const int K[3] = {p.bits[2], p.bits[3], p.bits[4]};
+  const int Kx = K[0] + K[1] + K[2];
+  const size_t M[3] = {(size_t)1 << K[0], (size_t)1 << K[1], (size_t)1 << K[2]};
+  const size_t stride[3] = {M[1] * M[2], M[2], 1};
+  std::vector<double> face(g.size());
+  for (size_t idx = 0; idx < g.size(); ++idx) {
+    const size_t j = (idx / stride[dim]) % M[dim];
+    const size_t jn = (j + 1) % M[dim];
+    face[idx] = 0.5 * (g[idx] + g[idx + (jn - j) * stride[dim]]);
+  }
+  const double hh = 2.0 * kPi / (double)M[dim];
+  TT F = tt_add(op_shift(K[dim], +1, true), scaled(mpo_identity(K[dim]), -1.0));
+  TT B = tt_add(mpo_identity(K[dim]), scaled(op_shift(K[dim], -1, true), -1.0));
+  tt_scale(F, 1.0 / hh);
+  tt_scale(B, 1.0 / hh);
+  const TT diag = tt_kron(mpo_identity(p.bits[0] + p.bits[1]), mpo_diag(tt_from_vector(face, Kx, kFieldTol)));
+  TT op = mpo_mul(embed_op(p, tt_round(B, kTol, 0), 2 + dim), tt_round(mpo_mul(diag, embed_op(p, tt_round(F, kTol, 0), 2 + dim)), kTol, 0));
+  return tt_round(op, kTol, 0);
+}
+
 TT linear_operator(const Params& p, const TT* u3) {
   const int Kphi = p.bits[0] + p.bits[1];
   TT idphi = mpo_identity(Kphi);
@@ -367,7 +439,13 @@ TT linear_operator(const Params& p, const TT* u3) {
     W = have ? tt_round(tt_add(W, t), kTol, 0) : t;
     have = true;
   };
-  // transport and diffusion in x (periodic CFD2)
+  SubgridFields sg;
+  TT omega_x;
+  if (p.sgs == 1) {
+    sg = subgrid_fields(p, u3);
+    omega_x = tt_from_vector(sg.omega, p.bits[2] + p.bits[3] + p.bits[4], kFieldTol);
+  }
+  // transport and diffusion in x (periodic CFD2; flux form with gamma(x) under sgs)
   for (int i = 0; i < 3; ++i) {
     const int K = p.bits[2 + i];
     const double h = 2.0 * kPi / (double)(1 << K);
@@ -375,18 +453,28 @@ TT linear_operator(const Params& p, const TT* u3) {
     TT adv = mpo_mul(du, embed_op(p, op_d1_periodic(K, h), 2 + i));
     tt_scale(adv, -1.0);
     acc(tt_round(adv, kTol, 0));
-    if (p.gamma != 0.0) acc(scaled(embed_op(p, op_d2_periodic(K, h), 2 + i), p.gamma));
+    if (p.sgs == 1)
+      acc(flux_diffusion_op(p, sg.gamma, i));
+    else if (p.gamma != 0.0)
+      acc(scaled(embed_op(p, op_d2_periodic(K, h), 2 + i), p.gamma));
   }
   // composition drift (linear part) + reaction + artificial dissipation
   for (int a = 0; a < 2; ++a) {
     const int K = p.bits[a];
     const double h = 1.0 / (double)(1 << K);
-    TT c = scaled(phi_weight(p, a == 0 ? 1 : 0, a == 1 ? 1 : 0), p.omega);
-    c = tt_add(c, scaled(phi_weight(p, 1, 1), p.da));
     const double h12 = (1.0 / (double)(1 << p.bits[0])) * (1.0 / (double)(1 << p.bits[1]));
-    tt_scale(c, 1.0 / h12);  // phi_weight carries h1 h2
-    c = tt_round(c, kTol, 0);
-    TT dc = mpo_diag(tt_kron(c, ones_x(p)));
+    TT dc;
+    if (p.sgs == 1) {  // Omega_mix(x) phi_a + Da phi1 phi2
+      TT ca = scaled(phi_weight(p, a == 0 ? 1 : 0, a == 1 ? 1 : 0), 1.0 / h12);  // phi_weight carries h1 h2
+      TT cr = scaled(phi_weight(p, 1, 1), p.da / h12);
+      dc = mpo_diag(tt_round(tt_add(tt_kron(ca, omega_x), tt_kron(cr, ones_x(p))), kTol, 0));
+    } else {
+      TT c = scaled(phi_weight(p, a == 0 ? 1 : 0, a == 1 ? 1 : 0), p.omega);
+      c = tt_add(c, scaled(phi_weight(p, 1, 1), p.da));
+      tt_scale(c, 1.0 / h12);  // phi_weight carries h1 h2
+      c = tt_round(c, kTol, 0);
+      dc = mpo_diag(tt_kron(c, ones_x(p)));
+    }
     TT drift = mpo_mul(embed_op(p, op_d1_zero_sum(K, h), a), dc);
     acc(tt_round(drift, kTol, 0));
     if (p.d_phi != 0.0) acc(scaled(embed_op(p, op_d2_zero_sum(K, h), a), p.d_phi));
@@ -409,7 +497,11 @@ Model build_model(const Params& p) {
   TT d1a = tt_kron(op_d1_zero_sum(p.bits[0], 1.0 / (double)(1 << p.bits[0])), mpo_identity(p.bits[1]));
   TT d1b = tt_kron(mpo_identity(p.bits[0]), op_d1_zero_sum(p.bits[1], 1.0 / (double)(1 << p.bits[1])));
   m.had_phi = tt_stack_right(d1a, d1b);
-  tt_scale(m.had_phi, -p.dt * p.omega);
+  // the mixing rate: the constant Omega here, or the field Omega_mix(x) as
+  // the x factor of the mixing term (applied with the conditional means)
+  tt_scale(m.had_phi, -p.dt * (p.sgs == 1 ? 1.0 : p.omega));
+  if (p.sgs == 1)
+    m.omega_x = tt_from_vector(subgrid_fields(p, m.u).omega, p.bits[2] + p.bits[3] + p.bits[4], kFieldTol);
   const int ex[6][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {0, 2}, {1, 1}};
   for (int w = 0; w < 6; ++w) m.wphi[w] = phi_weight(p, ex[w][0], ex[w][1]);
   return m;

@@ -31,6 +31,9 @@ struct Params {
   int flow = 0;        // 0: shear + seeded modes; 1: jet through a Taylor-Green vortex (Eq. velField)
   double u0 = 1.0;     // velocity scale of flow 1
   int ic_kind = 0;     // 0: tanh blend in x2; 1: Gaussian step function in x1 (Eq. initPDF), smoothed
+  int sgs = 0;         // 1: gamma(x) = gamma + gamma_SGS(x) (Smagorinsky), Omega_mix(x) (LMSE)
+  double c_s = 0.11, c_omega = 0.5, delta_cells = 3.0;
+  int moment_ref = 0;  // 1: step the first-moment equation alongside (error measures)
   int N() const { return bits[0] + bits[1] + bits[2] + bits[3] + bits[4]; }
   int Kphi() const { return bits[0] + bits[1]; }
 };
@@ -45,7 +48,16 @@ struct Model {
   TT had_phi;   // -dt * Omega * [D1phi1 (+) D1phi2] over the phi sites, open right bond 2
   TT wphi[6];   // h1 h2 * {1, phi1, phi2, phi1^2, phi2^2, phi1 phi2} over the phi sites
   TT u[3];      // velocity components over the x sites (for checks)
+  TT omega_x;   // sgs: Omega_mix(x) over the x sites (the mixing term's x factor); empty otherwise
 };
+
+// sgs: gamma(x) = gamma + gamma_SGS(x) and Omega_mix(x) on the x grid
+// (x1 slowest), from the sampled velocity components.
+struct SubgridFields {
+  std::vector<double> gamma, omega;
+  double delta = 0.0;
+};
+SubgridFields subgrid_fields(const Params& p, const TT* u3);
 
 // Trains of the discrete adjoint of the Heun step (gradient of the mean
 // product J = avg_x (<1> - <Phi_1> - <Phi_2>), Eqs. 2 and spaceAvg).

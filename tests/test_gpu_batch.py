@@ -26,16 +26,22 @@ def _instances():
 
 
 def test_step_many_matches_separate_steps():
+    """The first steps run context by context (eager step, graph captures);
+    from then on one parent graph per step embeds every context's step graph.
+    Stepping one context alone in between changes the contexts' relative
+    parities, so the parent graphs are rebuilt; every state stays bitwise
+    equal to stepping the contexts one by one."""
     ps = _instances()
-    nsteps = 4
     batch = [pkg.qtt_init(p) for p in ps]
     alone = [pkg.qtt_init(p) for p in ps]
     try:
-        pkg.qtt_step_many(batch, nsteps)
-        for c in alone:
-            c.step(nsteps)
+        pkg.qtt_step_many(batch, 6)
+        batch[1].step(1)
+        pkg.qtt_step_many(batch, 3)
+        for i, c in enumerate(alone):
+            c.step(10 if i == 1 else 9)
         for a, b in zip(batch, alone):
-            assert a.scalars()["steps"] == nsteps
+            assert a.scalars()["steps"] == b.scalars()["steps"]
             assert a.compare(b) == 0.0
     finally:
         for c in batch + alone:

@@ -260,3 +260,93 @@ def test_truncated_moving_gaussian_against_oracle():
     err = rel_l2(got, oracle.solve(p, 10).ravel())
     print(f"\nmoving Gaussian, chi 64: initial {e0:.2e}, after 10 steps {err:.2e}, <1>-1 {s['norm_avg'] - 1:.1e}")
     assert e0 <= 1e-6 and err <= 1e-4 and abs(s["norm_avg"] - 1.0) <= 1e-6
+
+
+# --------------------------- subgrid closures (Eq. FP0: Smagorinsky, LMSE)
+def sgs_params(bits, chi=None, exact=True, **kw):
+    """The paper's flow case with gamma(x) = gamma + gamma_SGS(x) and Omega_mix(x),
+    dt from the fields' maxima (stability rule of the workloads)."""
+    p = workload.make_paper_params(**kw)
+    p.update(sgs=1, c_s=0.11, c_omega=0.5, delta_cells=3.0)
+    p["bits"] = list(bits)
+    g = oracle.make_grid(p["bits"])
+    gam, om = oracle.subgrid_fields(p, g, oracle.velocity_field(p, g))
+    p["dt"] = workload.cfl_dt(p["bits"], float(om.max()), p["da"], float(gam.max()), p["d_phi"],
+                              workload.velocity_bound(p))
+    N = sum(p["bits"])
+    if exact:
+        p.update(chi_max=2 ** (N // 2), svd_rel_tol=0.0, exact=1)
+    else:
+        p["chi_max"] = chi
+    return p
+
+
+@pytest.mark.parametrize("bits,da", [([2, 2, 2, 2, 2], 0.0), ([2, 2, 3, 2, 2], 1.2)])
+def test_subgrid_exact_mode_matches_oracle(bits, da):
+    """gamma(x) in flux form and Omega_mix(x) as the x factor of the mixing
+    term's diagonal cores (Kronecker product with f's x cores), untruncated:
+    the MPS path equals the oracle."""
+    p = sgs_params(bits, da=da)
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(4)
+        got = ctx.observe(pkg.OBS_DENSE)
+    err = rel_l2(got, oracle.solve(p, 4).ravel())
+    assert err <= 1e-10, err
+
+
+def test_subgrid_truncated_vs_oracle():
+    """2^4 points per dimension, chi 32, FP64, 8 steps of the paper's case with
+    the subgrid closures: error against the oracle, mass, the conditional mean."""
+    p = sgs_params([4] * 5, chi=32, exact=False)
+    ref = oracle.solve(p, 8)
+    o = oracle.observables(ref, oracle.make_grid(p["bits"]))
+    with pkg.qtt_init(p) as ctx:
+        ctx.step(8)
+        got = ctx.observe(pkg.OBS_DENSE)
+        s = ctx.scalars()
+    err = rel_l2(got, ref.ravel())
+    print(f"\nsubgrid closures, 2^4 chi 32, 8 steps: rel-L2 vs oracle {err:.2e}, <1>-1 {s['norm_avg'] - 1:.1e}, "
+          f"d<Phi1> {s['mean1_avg'] - o['mean1_avg']:.1e}")
+    assert err < 1e-4
+    assert abs(s["norm_avg"] - 1.0) < 1e-8
+    assert abs(s["mean1_avg"] - o["mean1_avg"]) < 1e-6
+
+
+@pytest.mark.parametrize("sgs", [0, 1])
+def test_error_measures_match_oracle(sgs):
+    """Eqs. RMSE0 / RMSE1 over 17 equally spaced time samples of the paper's
+    case (Da = 0, untruncated, 2^2 / 2^3 points per dimension): the library's
+    per-sample space averages (moment-equation reference stepped on the
+    device) aggregated as the header states, against oracle.error_measures on
+    the oracle's run and its 3-D moment-equation solution."""
+    bits = [2, 2, 3, 2, 2]
+    p = sgs_params(bits) if sgs else paper_exact_params(bits)
+    p["moment_ref"] = 1
+    per = 2  # steps between samples
+    g = oracle.make_grid(p["bits"])
+    u = oracle.velocity_field(p, g)
+    f = oracle.initial_pdf(p, g)
+    m1, m2 = oracle.conditional_means(f, g)
+    samples, exact, lib = [], [], []
+    with pkg.qtt_init(p) as ctx:
+        for k in range(17):
+            if k:
+                ctx.step(per)
+                for _ in range(per):
+                    f = oracle.rk2_step(f, g, u, p)
+                    m1 = oracle.moment_step(m1, g, u, p)
+                    m2 = oracle.moment_step(m2, g, u, p)
+            lib.append(ctx.observe(pkg.OBS_ERRORS))
+            samples.append(oracle.observables(f, g))
+            exact.append((m1.copy(), m2.copy()))
+    ref = oracle.error_measures(samples, exact)
+    v = np.array(lib)
+    Et = lambda c: float(np.mean(v[:, c] ** 2))
+    Etx = lambda c: float(np.mean(v[:, c]))
+    got = {"err_2b_up": math.sqrt((Et(0) + Et(1)) / 2), "err_2b_down": math.sqrt((Etx(2) + Etx(3)) / 2),
+           "err_2c_up": math.sqrt(Et(4)), "err_2c_down": math.sqrt(Etx(5))}
+    print("\n", {k: (f"{got[k]:.6e}", f"{ref[k]:.6e}") for k in got})
+    for k in ("err_2b_up", "err_2b_down", "err_2c_up"):
+        assert abs(got[k] - ref[k]) <= 1e-9 * max(ref[k], 1e-6), k
+    assert got["err_2c_down"] <= 1e-12 and ref["err_2c_down"] <= 1e-12  # <1> stays 1 point-wise
+    assert ref["err_2b_down"] > 1e-6  # the wall terms make the means leave the moment equation

@@ -206,3 +206,48 @@ def test_init_fails_loudly_without_gpu():
         pass
     with pytest.raises(pkg.QttError):
         pkg.qtt_init(_params([2, 2, 2, 2, 2]))
+
+
+# ---------------- subgrid closures (Eq. FP0: Smagorinsky gamma_SGS(x), LMSE Omega_mix(x))
+def _sgs(bits, **kw):
+    base = dict(sgs=1, c_s=0.11, c_omega=0.5, delta_cells=3.0)
+    base.update(kw)
+    return _paper(bits, **base)
+
+
+@pytest.mark.parametrize("bits,da", [([2, 2, 2, 2, 2], 0.0), ([2, 3, 2, 3, 2], 0.9)])
+def test_subgrid_stage_operator_reproduces_oracle_euler_step(bits, da):
+    """Under the subgrid closures the library's encodings -- the stage operator
+    (flux-form diffusion with gamma(x), Omega_mix(x) phi_a in the linear
+    drift), the composition-space factor -dt D1phi_a and the encoded
+    Omega_mix(x) -- assemble f + dt L(f) of the oracle for a random PDF, and
+    the encoded Omega_mix(x) equals the oracle's field."""
+    p = _sgs(bits, da=da, d_phi=0.01)
+    g = oracle.make_grid(bits)
+    u = oracle.velocity_field(p, g)
+    gam, om = oracle.subgrid_fields(p, g, u)
+    om_lib = pkg.qtt_host_dense(p, 33, om.size)
+    assert np.abs(om_lib - om.ravel()).max() <= 1e-11 * np.abs(om).max()
+    assert np.ptp(gam) > 1e-3 * gam.max()
+    rng = np.random.default_rng(9)
+    f = rng.random(g.shape)
+    ref = f + p["dt"] * oracle.rhs(f, g, u, p)
+    n = f.size
+    op = pkg.qtt_host_dense(p, 31, n * n).reshape(n, n)
+    Mphi = g.M[0] * g.M[1]
+    had = pkg.qtt_host_dense(p, 32, 2 * Mphi * Mphi).reshape(2, Mphi, Mphi)
+    m1, m2 = oracle.conditional_means(f, g)
+    fx = f.reshape(Mphi, -1)
+    out = op @ f.ravel()
+    for a, m in enumerate((m1, m2)):
+        out += (had[a] @ (fx * (om_lib * m.ravel())[None, :])).ravel()
+    assert np.linalg.norm(out - ref.ravel()) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_subgrid_rejects_large_grids_and_bad_constants():
+    p = _sgs([2, 2, 6, 6, 7])
+    with pytest.raises(pkg.QttError):
+        pkg.qtt_host_dense(p, 40, 64)
+    p = _sgs([2, 2, 2, 2, 2], c_omega=-1.0)
+    with pytest.raises(pkg.QttError):
+        pkg.qtt_host_dense(p, 40, 64)

@@ -25,7 +25,7 @@ import math
 
 import numpy as np
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "bf16x10": 4}
 
 WORKLOADS = {
     "small": dict(bits=4, chi_max=32, steps=50),
@@ -99,7 +99,7 @@ def make_params(workload: str = "small", seed: int = 0, precision: str = "fp64",
     p = dict(
         bits=[K] * 5,
         chi_max=w["chi_max"],
-        svd_rel_tol=1e-14 if precision == "fp64" else 1e-7,
+        svd_rel_tol=1e-14 if precision in ("fp64", "bf16x10") else 1e-7,
         precision=PRECISIONS[precision],
         omega=1.0,
         da=1.0,
