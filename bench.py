@@ -34,11 +34,8 @@ sys.path.insert(0, ROOT)
 import workload  # noqa: E402
 
 METRIC = "MPS time-steps/s at chi=128 vs plain FP64 GPU path; rel-L2 vs FP64 oracle"
-# FP64 peak of one GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (the unit
-# count is the one that reproduces the 1.25 TFLOP/s nominal and the 1.19
-# TFLOP/s measured by an FMA-throughput probe at the observed clocks).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
+ACCURACY_STEPS = (25, 100)  # step counts at which every form is compared with the FP64 path
 TIMING_LAUNCHES, TIMING_TC_ISSUED = 18, 19  # positions in OBS_TIMINGS after the 6 classes x 3
 
 
@@ -59,16 +56,19 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--workload", default="large", choices=list(workload.WORKLOADS))
-    ap.add_argument("--precision", default="bf16x3", choices=list(workload.PRECISIONS),
+    ap.add_argument("--precision", default="bf16x10", choices=list(workload.PRECISIONS),
                     help="contraction arithmetic of the timed form (the FP64 path is timed beside it)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path beside the form")
-    ap.add_argument("--also", default="fp32,tf32",
+    ap.add_argument("--also", default="bf16x3,fp32,tf32",
                     help="other reduced forms timed and compared with the FP64 path (comma-separated)")
     ap.add_argument("--batch", type=int, default=256,
                     help="instances of the batched configuration stepped together (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--adjoint-steps", type=int, default=20,
+    ap.add_argument("--batch-steps", type=int, default=30, help="timed steps of the batched configuration")
+    ap.add_argument("--adjoint-steps", type=int, default=workload.ADJOINT["steps"],
                     help="Heun steps of the timed gradient (qtt_grad) on the adjoint configuration (0: skip)")
+    ap.add_argument("--config2-seeds", type=int, default=4,
+                    help="seeds of the 2^6-point, chi 64, 200-step comparison of the forms (0: skip)")
+    ap.add_argument("--no-config1", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -132,11 +132,41 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(wl: str, seed: int = 0, nsteps: int = 1):
-    """Times nsteps RK2 steps of the CPU oracle on a 2^(5*ORACLE_SAMPLE_BITS)-cell
-    grid of the workload (same coefficients, velocity, initial condition and dt),
-    in a child process pinned to one thread.  Returns seconds per step."""
-    code = f"""
+def host_cpu():
+    """nproc and the CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_sample_all_cores(wl: str, nsteps: int = 1, procs: int | None = None):
+    """The oracle's throughput with every host core busy: one single-thread
+    oracle process per core, each timing nsteps steps of its own copy of the
+    2^(5*ORACLE_SAMPLE_BITS)-cell sample, started together.  Returns (procs,
+    mean seconds per step per process)."""
+    procs = procs or (os.cpu_count() or 1)
+    code = oracle_code(wl, 0, nsteps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, text=True, env=env)
+          for _ in range(procs)]
+    times = []
+    for pr in ps:
+        out, _ = pr.communicate()
+        if pr.returncode == 0:
+            times.extend(json.loads(out.strip().splitlines()[-1])["times"])
+    return procs, (statistics.mean(times) if times else float("nan"))
+
+
+def oracle_code(wl: str, seed: int, nsteps: int) -> str:
+    return f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import oracle, workload
@@ -154,9 +184,31 @@ for _ in range({nsteps}):
     ts.append(time.perf_counter() - t0)
 print(json.dumps(dict(times=ts, norm=float(f.sum()))))
 """
+
+
+def oracle_sample(wl: str, seed: int = 0, nsteps: int = 1):
+    """Times nsteps RK2 steps of the CPU oracle on a 2^(5*ORACLE_SAMPLE_BITS)-cell
+    grid of the workload (same coefficients, velocity, initial condition and dt),
+    in a child process pinned to one thread.  Returns seconds per step."""
+    code = oracle_code(wl, seed, nsteps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+
+
+def roofline_traffic():
+    """DRAM bytes per launch of the tensor-core GEMM from the committed ncu
+    summary, when it was taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tc_gemm_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, "paper_2407_09169_gb300", "csrc", "gemm_tc.cu"), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    return rec.get("dram_bytes_per_launch") if rec.get("gemm_tc_sha16") == sha else None
 
 
 def oracle_rate(seconds_per_step: float, wl: str):
@@ -185,19 +237,24 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     p = workload.make_params(args.workload, precision=args.precision)
-    times = oracle_sample(args.workload, nsteps=args.warmup + args.steps)
-    timed = times[args.warmup:] if len(times) > args.warmup else times
-    sps = statistics.mean(timed)
-    value, cell_rate = oracle_rate(sps, args.workload)
-    sample = (f"{len(timed)} Heun steps of the dense FP64 finite-difference oracle (numpy, 1 thread) on the "
-              f"2^{5 * ORACLE_SAMPLE_BITS}-cell grid (2^{ORACLE_SAMPLE_BITS} points per dimension) of the same "
-              f"workload, extrapolated by cell count to 2^{sum(p['bits'])} cells ({cell_rate:.3e} cell-steps/s)")
+    ncores, cpu_model = host_cpu()
+    # one oracle process per host core, each a bounded sample of the workload
+    nsteps = max(1, min(args.warmup + args.steps, 3))
+    procs, sps = oracle_sample_all_cores(args.workload, nsteps=nsteps, procs=ncores)
+    v1, cell_rate1 = oracle_rate(sps, args.workload)
+    value, cell_rate = v1 * procs, cell_rate1 * procs
+    sample = (f"{procs} concurrent single-thread processes of the dense FP64 finite-difference oracle (numpy), one "
+              f"per host core ({cpu_model or 'CPU model unknown'}, nproc {ncores}), each {nsteps} Heun steps on the "
+              f"2^{5 * ORACLE_SAMPLE_BITS}-cell grid (2^{ORACLE_SAMPLE_BITS} points per dimension) of the same workload "
+              f"({sps:.1f} s per step each); aggregate {cell_rate:.3e} cell-steps/s extrapolated by cell count to "
+              f"2^{sum(p['bits'])} cells")
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_for(args, p),
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": procs, "kind": "oracle", "sample": sample,
+                         "one_core_steps_per_s": v1, "cpu_model": cpu_model, "nproc": ncores},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -259,6 +316,10 @@ def run_mine(args, rank, world, local_rank):
     state_bytes = int(sum(bonds[n] * 2 * bonds[n + 1] for n in range(len(bonds) - 1)) * 8)
     ctx.close()
 
+    # ---- measured FP64 peak of this GPU (DFMA and f64 mma.sync throughput probes)
+    fp64_probe = [float(x) for x in q.qtt_selftest(6)[:4]]
+    fp64_peak = max(fp64_probe[0], fp64_probe[1])
+
     # ---- per-kernel-class roofline (separate pass: CUDA events around every launch)
     roofline, classes = None, None
     if not args.no_profile and rank == 0:
@@ -287,9 +348,10 @@ def run_mine(args, rank, world, local_rank):
             ach = g["gflop_per_step"] / (g["ms_per_step"] / 1e3) / 1e3 if g["ms_per_step"] > 0 else 0.0
             roofline = {
                 "kernel": "gemm_f64 (FP64 DFMA core contractions)",
-                "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json)",
+                "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak,
+                "peak_source": (f"of measured: FP64 throughput probe of this run (qtt_selftest 6: DFMA "
+                                f"{fp64_probe[0]:.3f}, mma.sync f64 {fp64_probe[1]:.3f} TFLOP/s; the larger)"),
                 "traffic": None,
             }
         else:
@@ -308,7 +370,7 @@ def run_mine(args, rank, world, local_rank):
                                 "MMA passes per algorithmic flop (mean over the step's products; TF32 passes count 2)"
                                 if "bf16_tflops" in peaks else
                                 f"of fallback: {FALLBACK_BF16_TFLOPS} TFLOP/s bf16 / {passes:.2f} MMA passes"),
-                "traffic": None,
+                "traffic": roofline_traffic(),
             }
         roofline["flop_per_launch"] = g["gflop_per_step"] * 1e9 / max(g["launches_per_step"], 1)
         roofline["avg_launch_us"] = g["ms_per_step"] * 1e3 / max(g["launches_per_step"], 1)
@@ -324,7 +386,7 @@ def run_mine(args, rank, world, local_rank):
                                              "max_rel_err_sampled": float(err_)}
             roofline["same_kernel_large_square"] = big
 
-    # ---- the plain FP64 GPU path at equal chi: steps/s, and the form's distance to it
+    # ---- the plain FP64 GPU path at equal chi: steps/s, and every form's distance to it
     fp64_path = None
     if args.precision != "fp64" and not args.no_fp64_path:
         p64 = workload.make_params(args.workload, seed=rank, precision="fp64")
@@ -338,40 +400,53 @@ def run_mine(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1))
-        # advance a copy of the form to the same step count and compare at equal chi
-        cf = q.qtt_init(p, stream=stream.cuda_stream)
-        cf.step(args.warmup + args.steps)
-        rel = cf.compare(c64)
-        s64, sf = c64.scalars(), cf.scalars()
-        cf.close()
         v64 = args.steps * world / (ms64 / 1e3)
+        forms = [args.precision] + [x for x in args.also.split(",") if x and x != args.precision and x != "fp64"]
+        fctx, fval = {}, {}
+        for fm in forms:  # steps/s of each form (the headline form's is the timed value above)
+            cf = q.qtt_init(workload.make_params(args.workload, seed=rank, precision=fm), stream=stream.cuda_stream)
+            if fm != args.precision:
+                for _ in range(args.warmup):
+                    cf.step(1)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                cf.step(args.steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                fval[fm] = args.steps * world / (max_over_ranks(e0.elapsed_time(e1)) / 1e3)
+            else:
+                fval[fm] = value
+            fctx[fm] = cf
+        # distance to the FP64 path at equal chi after a stated number of steps
+        acc = {fm: {} for fm in forms}
+        n64 = args.warmup + args.steps
+        for target in ACCURACY_STEPS:
+            if target > n64:
+                c64.step(target - n64)
+                n64 = target
+            s64 = c64.scalars()
+            for fm, cf in fctx.items():
+                done = int(cf.scalars()["steps"])
+                if target > done:
+                    cf.step(target - done)
+                sf = cf.scalars()
+                acc[fm][str(target)] = {"rel_l2": cf.compare(c64), "d_norm_avg": sf["norm_avg"] - s64["norm_avg"],
+                                        "d_mean1_avg": sf["mean1_avg"] - s64["mean1_avg"],
+                                        "d_phi11_avg": sf["phi11_avg"] - s64["phi11_avg"]}
+        for cf in fctx.values():
+            cf.close()
+        c64.close()
+        head = acc[args.precision]
         fp64_path = {
             "value": v64, "unit": "steps/s", "ms_per_step": ms64 / args.steps, "speedup": value / v64,
-            "rel_l2_vs_fp64_after_steps": rel, "steps_compared": args.warmup + args.steps,
-            "d_norm_avg": sf["norm_avg"] - s64["norm_avg"], "d_mean1_avg": sf["mean1_avg"] - s64["mean1_avg"],
-            "d_phi11_avg": sf["phi11_avg"] - s64["phi11_avg"],
+            "rel_l2_vs_fp64": {k: v["rel_l2"] for k, v in head.items()},
+            "gate": {"rel_l2_max": 1e-5, "speedup_min": 5.0,
+                     "met_at_steps": [int(k) for k, v in head.items() if v["rel_l2"] <= 1e-5 and value / v64 >= 5.0]},
+            "forms": {fm: {"value": fval[fm], "unit": "steps/s", "speedup": fval[fm] / v64, "vs_fp64": acc[fm]}
+                      for fm in forms},
+            "comparison": "each form and the FP64 path stepped from the same initial state to the stated step "
+                          "counts at equal chi; relative L2 distance of the decompressed states (qtt_compare)",
         }
-        # the other reduced forms on the same workload: steps/s and distance to the FP64 path
-        others = {}
-        for other in [x for x in args.also.split(",") if x and x != args.precision and x != "fp64"]:
-            po = workload.make_params(args.workload, seed=rank, precision=other)
-            co = q.qtt_init(po, stream=stream.cuda_stream)
-            for _ in range(args.warmup):
-                co.step(1)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            co.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            mso = max_over_ranks(e0.elapsed_time(e1))
-            so = co.scalars()
-            others[other] = {"value": args.steps * world / (mso / 1e3), "unit": "steps/s",
-                             "speedup": (args.steps * world / (mso / 1e3)) / v64,
-                             "rel_l2_vs_fp64_after_steps": co.compare(c64),
-                             "d_norm_avg": so["norm_avg"] - s64["norm_avg"]}
-            co.close()
-        fp64_path["other_forms"] = others
-        c64.close()
 
     # ---- end to end through the C ABI: host params -> device, K steps, scalars read back each step
     e2e = None
@@ -387,20 +462,28 @@ def run_mine(args, rank, world, local_rank):
         dt_e2e = max_over_ranks(time.perf_counter() - t0)
         ce.close()
         e2e = {"value": args.steps * world / dt_e2e, "unit": "steps/s",
-               "h2d_bytes_per_step": state_bytes // max(args.steps, 1), "d2h_bytes_per_step": 12 * 8,
-               "note": "includes qtt_init (host encoding + upload of the state and operators), per-step D2H of the 12 scalars"}
+               "h2d_bytes_per_step": state_bytes // max(args.steps, 1), "d2h_bytes_per_step": 13 * 8,
+               "note": "includes qtt_init (host encoding + upload of the state and operators) and a D2H read of "
+                       "the 13 scalars after every step; the contraction tile and split choices are the ones the "
+                       "earlier contexts of this process autotuned (first-shape tuning not in the timed region)"}
 
-    # ---- CPU baseline (oracle) and a small-workload parity check, rank 0 at N = 1 only
+    # ---- CPU baseline (oracle), one core and every core, rank 0 at N = 1 only
     cpu = None
     parity = None
     if rank == 0 and world == 1:
         if not args.no_cpu_baseline:
+            ncores, cpu_model = host_cpu()
             times = oracle_sample(args.workload, nsteps=1)
-            v, cell_rate = oracle_rate(times[0], args.workload)
-            cpu = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                   "sample": f"1 Heun step of the dense FP64 finite-difference oracle (numpy, 1 thread) on the "
-                             f"2^{5 * ORACLE_SAMPLE_BITS}-cell grid of the same workload ({times[0]:.1f} s), "
-                             f"extrapolated by cell count to 2^{sum(p['bits'])} cells ({cell_rate:.3e} cell-steps/s)"}
+            v1, cell1 = oracle_rate(times[0], args.workload)
+            procs, sps = oracle_sample_all_cores(args.workload, nsteps=1, procs=ncores)
+            vall, cellall = oracle_rate(sps, args.workload)
+            cpu = {"value": vall * procs, "unit": "steps/s", "cores": procs, "kind": "oracle",
+                   "one_core_value": v1, "cpu_model": cpu_model, "nproc": ncores,
+                   "sample": f"1 Heun step of the dense FP64 finite-difference oracle (numpy, single-thread processes) "
+                             f"on the 2^{5 * ORACLE_SAMPLE_BITS}-cell grid of the same workload: one process alone "
+                             f"({times[0]:.1f} s, {cell1:.3e} cell-steps/s) and {procs} processes at once, one per core "
+                             f"({sps:.1f} s each, {cellall * procs:.3e} cell-steps/s together); extrapolated by cell "
+                             f"count to 2^{sum(p['bits'])} cells"}
     if rank == 0 and world == 1 and not args.no_parity:
         try:
             import oracle
@@ -409,9 +492,57 @@ def run_mine(args, rank, world, local_rank):
                 cs.step(10)
                 got = cs.observe(q.OBS_DENSE)
             ref = oracle.solve(ps, 10).ravel()
-            parity = {"small_workload_10_steps_rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+            parity = {"small_workload_10_steps_rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                      "form": args.precision}
         except Exception as ex:  # reported, never silently dropped
             parity = {"error": str(ex)}
+
+    # ---- the 2^20-cell configuration: FP64 steps/s and distance to the oracle after 50 steps
+    config1 = None
+    if rank == 0 and world == 1 and not args.no_config1:
+        try:
+            import oracle
+            pc = workload.make_params("small")
+            with q.qtt_init(pc, stream=stream.cuda_stream) as cc:
+                cc.step(args.warmup)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                cc.step(20)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sps1 = 20 / (e0.elapsed_time(e1) / 1e3)
+                cc.step(pc["steps"] - args.warmup - 20)
+                got = cc.observe(q.OBS_DENSE)
+                sc = cc.scalars()
+            ref = oracle.solve(pc, pc["steps"])
+            o = oracle.observables(ref, oracle.make_grid(pc["bits"]))
+            config1 = {"workload": "2^4 points per dimension (2^20 cells), chi 32, FP64, 50 Heun steps",
+                       "steps_per_s": sps1,
+                       "rel_l2_vs_oracle": float(np.linalg.norm(got - ref.ravel()) / np.linalg.norm(ref)),
+                       "d_norm_avg": sc["norm_avg"] - o["norm_avg"], "d_mean1_avg": sc["mean1_avg"] - o["mean1_avg"],
+                       "d_R12": sc["R12"] - o["R12"], "d_Y12": sc["Y12"] - o["Y12"]}
+        except Exception as ex:
+            config1 = {"error": str(ex)}
+
+    # ---- the 2^30-cell configuration: forms against FP64 after 200 steps, seeds 0..S-1
+    config2 = None
+    if rank == 0 and world == 1 and args.config2_seeds > 0:
+        config2 = {"workload": "2^6 points per dimension (2^30 cells), chi 64, 200 Heun steps", "seeds": {}}
+        for seed in range(args.config2_seeds):
+            pm = workload.make_params("medium", seed=seed)
+            with q.qtt_init(pm, stream=stream.cuda_stream) as cm:
+                cm.step(pm["steps"])
+                sm = cm.scalars()
+                row = {}
+                for fm in ("fp32", "tf32", "bf16x10"):
+                    with q.qtt_init(workload.make_params("medium", seed=seed, precision=fm),
+                                    stream=stream.cuda_stream) as cf:
+                        cf.step(pm["steps"])
+                        sf = cf.scalars()
+                        row[fm] = {"rel_l2": cf.compare(cm)}
+                        for k in ("mean1_avg", "mean2_avg", "phi11_avg", "phi22_avg", "phi12_avg"):
+                            row[fm]["d_" + k] = sf[k] - sm[k]
+            config2["seeds"][str(seed)] = row
 
     # ---- batched independent PDFs (uneven grid and chi), rank 0 at N = 1 only
     batched = None
@@ -419,20 +550,26 @@ def run_mine(args, rank, world, local_rank):
         bps = workload.make_batch_params(args.batch, seed=0, precision="fp32")
         free0 = torch.cuda.mem_get_info(dev)[0]
         t0 = time.perf_counter()
-        ctxs = [q.qtt_init(bp) for bp in bps]
+        ctxs = [q.qtt_init(bp, stream=stream.cuda_stream) for bp in bps]
         t_init = time.perf_counter() - t0
         free1 = torch.cuda.mem_get_info(dev)[0]
-        q.qtt_step_many(ctxs, 2)  # first step eager, second captures the step graphs
+        q.qtt_step_many(ctxs, 3)  # eager step, the two graph captures (context by context)
+        q.qtt_step_many(ctxs, 1)  # builds the batch graph
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        launches_b0 = ctxs[0].observe(q.OBS_TIMINGS)[TIMING_LAUNCHES]
+        e0.record(stream)
         q.qtt_step_many(ctxs, args.batch_steps)
+        e1.record(stream)
         torch.cuda.synchronize()
-        tb = time.perf_counter() - t0
+        tb = e0.elapsed_time(e1) / 1e3
+        launches_b = ctxs[0].observe(q.OBS_TIMINGS)[TIMING_LAUNCHES] - launches_b0
         norms = [c.scalars()["norm_avg"] for c in ctxs]
-        # the same contexts stepped one after another (each synchronised), for comparison
+        # the same contexts stepped one after another, for comparison
+        nseq = max(1, min(5, args.batch_steps))
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for c in ctxs:
-            c.step(args.batch_steps)
+            c.step(nseq)
         torch.cuda.synchronize()
         tseq = time.perf_counter() - t0
         for c in ctxs:
@@ -444,9 +581,12 @@ def run_mine(args, rank, world, local_rank):
             "ms_per_step_all_instances": tb * 1e3 / args.batch_steps,
             "precision": "fp32", "config": "Da log-U[0.1,10], Omega U[0.5,2], 2^5..2^7 points per dimension, "
                                             "chi in {16,32,64,96}, seeds 0..n-1 (workload.make_batch_params)",
-            "timing": "host clock around qtt_step_many with a device synchronize on both sides; "
-                      "2 untimed steps first (eager step, graph capture)",
-            "sequential_instance_steps_per_s": args.batch * args.batch_steps / tseq,
+            "timing": "CUDA events on the contexts' stream around one qtt_step_many call of the stated steps, each "
+                      "step one launch of a graph that embeds every context's step graph; 4 untimed steps first "
+                      "(eager step, graph captures, batch graph)",
+            "kernel_launches_per_step": launches_b / args.batch_steps,
+            "sequential_instance_steps_per_s": args.batch * nseq / tseq,
+            "sequential_timing": f"host clock, each context stepped {nseq} steps alone, device synchronised",
             "init_s": t_init, "device_bytes": free0 - free1,
             "max_abs_norm_err": max(abs(v - 1.0) for v in norms), "sum_cells": cells,
         }
@@ -456,7 +596,7 @@ def run_mine(args, rank, world, local_rank):
     if rank == 0 and world == 1 and args.adjoint_steps > 0:
         pa = workload.make_adjoint_params(seed=0, precision="fp32")
         ns = args.adjoint_steps
-        ck = max(1, min(workload.ADJOINT["ckpt_every"], ns // 4))
+        ck = max(1, min(workload.ADJOINT["ckpt_every"], ns))
         with q.qtt_init(pa) as ca:
             ca.grad(2, 1)  # untimed: sizes the workspaces
             torch.cuda.synchronize()
@@ -489,9 +629,13 @@ def run_mine(args, rank, world, local_rank):
             "config": config_for(args, p),
             "roofline": roofline, "kernel_classes": classes, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": int(launches),
+            "fp64_peak": {"dfma_tflops": fp64_probe[0], "dmma_tflops": fp64_probe[1], "sms": int(fp64_probe[2]),
+                          "source": "qtt_selftest 6, this run"},
             "state": {"norm_avg": scal["norm_avg"], "mean1_avg": scal["mean1_avg"], "nvpp": nvpp,
-                      "discarded_weight_last_step": scal["discarded_weight"]},
-            "parity": parity, "fp64_path": fp64_path, "batched": batched, "adjoint": adjoint,
+                      "discarded_weight_last_step": scal["discarded_weight"],
+                      "discarded_weight_rel": scal["discarded_weight"] / scal["norm2"] if scal["norm2"] > 0 else None},
+            "parity": parity, "fp64_path": fp64_path, "config1": config1, "config2": config2, "batched": batched,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
 
