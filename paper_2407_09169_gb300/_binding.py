@@ -204,8 +204,8 @@ class Context:
         Kx = sum(self.params["bits"][2:])
         if out is None:
             if cap is None:
-                cap = {OBS_SCALARS: 12, OBS_BONDS: self.N + 1, OBS_DENSE: 2 ** self.N, OBS_MEANS: 3 * 2 ** Kx,
-                       OBS_NVPP: 1, OBS_TIMINGS: 20}[what]
+                cap = {OBS_SCALARS: len(SCALAR_NAMES), OBS_BONDS: self.N + 1, OBS_DENSE: 2 ** self.N,
+                       OBS_MEANS: 3 * 2 ** Kx, OBS_NVPP: 1, OBS_TIMINGS: 20, OBS_ERRORS: 6}[what]
             out = np.zeros(cap, dtype=np.float64)
         written = C.c_int64(0)
         _check(load_library().qtt_observe(self._handle(), int(what), out.ctypes.data_as(C.POINTER(C.c_double)),
