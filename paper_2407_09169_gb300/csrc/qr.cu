@@ -746,11 +746,13 @@ __global__ void __launch_bounds__(512) qr64_cluster_kernel(int m, int n, int P, 
     const uint32_t vb = qr64_mapa(V0 + slot * 32 * RPL * 8, owner);
     const double t = qr64_ld_remote(qr64_mapa(T0 + slot * 8, owner));
     if (t == 0.0) continue;
-    double v[RPL], d = 0.0;
+    double v[RPL], dp[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < RPL; ++k) v[k] = qr64_ld_remote(vb + (lane + 32 * k) * 8);
+    // three independent partial sums: the FP64 chain is a third as long
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) d = fma(v[k], X[k], d);
+    for (int k = 0; k < RPL; ++k) dp[k % 3] = fma(v[k], X[k], dp[k % 3]);
+    double d = dp[0] + (dp[1] + dp[2]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     const double f = -t * d;
@@ -759,27 +761,35 @@ __global__ void __launch_bounds__(512) qr64_cluster_kernel(int m, int n, int P, 
   }
   if (alive) {
     // reflector of column c: v = (x - beta e_c) / (x_c - beta) on rows >= c
-    double s = 0.0, a = 0.0;
+    double sp[3] = {0.0, 0.0, 0.0}, a = 0.0;
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
       const int i = lane + 32 * k;
-      if (i > c) s = fma(X[k], X[k], s);
-      if (i == c) a = X[k];
+      if (i > c) sp[k % 3] = fma(X[k], X[k], sp[k % 3]);
+      if (i == c) a = X[k];  // only lane c % 32 holds row c
     }
+    double s = sp[0] + (sp[1] + sp[2]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-    }
-    double t = 0.0, v0 = 1.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    a = __shfl_sync(0xffffffffu, a, c & 31);
+    double t = 0.0, v0 = 1.0, rv0 = 0.0;
     if (s != 0.0) {
       const double mu = sqrt(fma(a, a, s));
       const double beta = a <= 0.0 ? mu : -mu;
-      t = (beta - a) / beta;
       v0 = a - beta;  // |v0| >= mu >= |x_i|
+      // one division for both reciprocals: r = 1 / (beta v0), 1/beta = v0 r,
+      // 1/v0 = beta r (two divisions where |beta v0| >= mu^2 could underflow)
+      const double bv = beta * v0;
+      if (fabs(bv) > 1e-290) {
+        const double r = 1.0 / bv;
+        t = -v0 * (v0 * r);  // (beta - a) / beta
+        rv0 = beta * r;
+      } else {
+        t = (beta - a) / beta;
+        rv0 = 1.0 / v0;
+      }
     }
     double* vc = V + (size_t)w * 32 * RPL;
-    const double rv0 = t != 0.0 ? 1.0 / v0 : 0.0;
     const bool tiny = fabs(v0) < 1e-300;
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
