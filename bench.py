@@ -417,13 +417,18 @@ def run_mine(args, rank, world, local_rank):
             else:
                 fval[fm] = value
             fctx[fm] = cf
-        # distance to the FP64 path at equal chi after a stated number of steps
+        # distance to the FP64 path at equal chi after a stated number of steps,
+        # beside the FP64 path's own floor (its initial condition moved by one ulp)
         acc = {fm: {} for fm in forms}
         n64 = args.warmup + args.steps
+        c64u = q.qtt_init(dict(p64, ic_sigma=math.nextafter(p64["ic_sigma"], 1.0)), stream=stream.cuda_stream)
+        c64u.step(n64)
+        floor = {}
         for target in ACCURACY_STEPS:
             if target > n64:
-                c64.step(target - n64)
+                q.qtt_step_many([c64, c64u], target - n64)
                 n64 = target
+            floor[str(target)] = c64u.compare(c64)
             s64 = c64.scalars()
             for fm, cf in fctx.items():
                 done = int(cf.scalars()["steps"])
@@ -436,16 +441,20 @@ def run_mine(args, rank, world, local_rank):
         for cf in fctx.values():
             cf.close()
         c64.close()
+        c64u.close()
         head = acc[args.precision]
         fp64_path = {
             "value": v64, "unit": "steps/s", "ms_per_step": ms64 / args.steps, "speedup": value / v64,
             "rel_l2_vs_fp64": {k: v["rel_l2"] for k, v in head.items()},
+            "fp64_one_ulp_floor": floor,
             "gate": {"rel_l2_max": 1e-5, "speedup_min": 5.0,
                      "met_at_steps": [int(k) for k, v in head.items() if v["rel_l2"] <= 1e-5 and value / v64 >= 5.0]},
             "forms": {fm: {"value": fval[fm], "unit": "steps/s", "speedup": fval[fm] / v64, "vs_fp64": acc[fm]}
                       for fm in forms},
             "comparison": "each form and the FP64 path stepped from the same initial state to the stated step "
-                          "counts at equal chi; relative L2 distance of the decompressed states (qtt_compare)",
+                          "counts at equal chi; relative L2 distance of the decompressed states (qtt_compare); "
+                          "fp64_one_ulp_floor: the FP64 path against itself from an initial condition moved by "
+                          "one ulp (ic_sigma), the reproducibility the truncation to chi leaves",
         }
 
     # ---- end to end through the C ABI: host params -> device, K steps, scalars read back each step
@@ -527,13 +536,20 @@ def run_mine(args, rank, world, local_rank):
     # ---- the 2^30-cell configuration: forms against FP64 after 200 steps, seeds 0..S-1
     config2 = None
     if rank == 0 and world == 1 and args.config2_seeds > 0:
-        config2 = {"workload": "2^6 points per dimension (2^30 cells), chi 64, 200 Heun steps", "seeds": {}}
+        config2 = {"workload": "2^6 points per dimension (2^30 cells), chi 64, 200 Heun steps; fp64_one_ulp: the "
+                               "FP64 path from an initial condition moved by one ulp (ic_sigma), its own floor",
+                   "seeds": {}}
         for seed in range(args.config2_seeds):
             pm = workload.make_params("medium", seed=seed)
             with q.qtt_init(pm, stream=stream.cuda_stream) as cm:
                 cm.step(pm["steps"])
                 sm = cm.scalars()
                 row = {}
+                # the FP64 path's own reproducibility: its initial condition moved by one ulp
+                pu = dict(pm, ic_sigma=math.nextafter(pm["ic_sigma"], 1.0))
+                with q.qtt_init(pu, stream=stream.cuda_stream) as cu:
+                    cu.step(pm["steps"])
+                    row["fp64_one_ulp"] = {"rel_l2": cu.compare(cm)}
                 for fm in ("fp32", "tf32", "bf16x10"):
                     with q.qtt_init(workload.make_params("medium", seed=seed, precision=fm),
                                     stream=stream.cuda_stream) as cf:
