@@ -221,7 +221,8 @@ class Engine {
   int N_ = 0, kphi_ = 0, nc_ = 0;
   int prec_bits_ = 64;
   bool qr_refine_ = false;
-  bool small_fp32_ = false;  // operator-bond contractions on the CUDA cores in FP32
+  bool small_fp32_ = false;         // operator-bond contractions on the CUDA cores in FP32
+  bool small_sketch_fp32_ = false;  // those of the sketch pass in FP32
   bool exact_ = false;
   std::vector<void*> allocs_;
   std::vector<int> D_, ell_, rz_;
