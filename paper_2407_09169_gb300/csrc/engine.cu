@@ -1009,6 +1009,21 @@ void Engine::scalars(double out[13]) {
   left_weight_envs(st_, fc, wchains_dev_, 6, kphi_, max_bond_, V, b, b);
   right_ones_env(st_, fc, kphi_, max_bond_, u, envw_);
   xgram(f_, E);
+  // |f|^2 = sum_bb' G[b][b'] E[b][b'], G the Gram of the phi part (left to right)
+  {
+    fill_value(st_, obsA_, 1, 1.0);
+    double* G = obsA_;
+    double* Gn = obsB_;
+    for (int n = 0; n < kphi_; ++n) {
+      const int bl = f_.b[n], br = f_.b[n + 1];
+      gemm64(bl, 2 * br, bl, 1, 1, 1.0, mv(G, bl, 1), mv(f_.core(n), 2LL * br, 1), 0.0, ov(obsX_, 2LL * br, 1));
+      gemm64(br, br, 2 * bl, 1, 1, 1.0, mv(f_.core(n), 1, br), mv(obsX_, br, 1), 0.0, ov(Gn, br, 1));
+      std::swap(G, Gn);
+    }
+    gemm64(1, 1, b * b, 1, 1, 1.0, mv(G, (long long)b * b, 1), mv(E, 1, 1), 0.0, ov(obsX_, 1, 1));
+  }
+  double n2 = 0.0;
+  QTT_CUDA(cudaMemcpyAsync(&n2, obsX_, sizeof(double), cudaMemcpyDeviceToHost, st_));
   gemm64(6, 1, b, 1, 1, 1.0, mv(V, b, 1), mv(u, 1, 1), 0.0, ov(res, 1, 1));                 // <w> sums
   gemm64(1, b, b, 1, 1, 1.0, mv(V + b, b, 1), mv(E, b, 1), 0.0, ov(res + 6, b, 1));           // v1^T E
   gemm64(1, 1, b, 1, 1, 1.0, mv(res + 6, b, 1), mv(V + 2 * (size_t)b, 1, 1), 0.0, ov(res + 6 + b, 1, 1));
@@ -1033,7 +1048,7 @@ void Engine::scalars(double out[13]) {
   out[9] = h[0] - h[1] - h[2];  // mean of <1 - phi1 - phi2>
   out[10] = discarded_last_;
   out[11] = (double)steps_;
-  out[12] = norm2();  // sum of f^2 over every grid cell
+  out[12] = n2;  // sum of f^2 over every grid cell
 }
 
 void Engine::chain_dense(const DevMps& f, int n0, const double* head, int head_rows, double* out) {

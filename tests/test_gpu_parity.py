@@ -61,9 +61,12 @@ def test_exact_mode_observables_match_oracle():
         s = ctx.scalars()
         means = ctx.observe(pkg.OBS_MEANS)
     g = oracle.make_grid(p["bits"])
-    o = oracle.observables(oracle.solve(p, 3), g)
+    fo = oracle.solve(p, 3)
+    o = oracle.observables(fo, g)
     for k in ("norm_avg", "mean1_avg", "mean2_avg", "phi11_avg", "phi22_avg", "phi12_avg", "R12", "Y12", "product_J"):
         assert abs(s[k] - o[k]) <= 1e-11 * max(1.0, abs(o[k])), (k, s[k], o[k])
+    n2 = float(np.sum(fo * fo))
+    assert abs(s["norm2"] - n2) <= 1e-11 * n2
     Mx = g.M[2] * g.M[3] * g.M[4]
     assert np.abs(means[:Mx] - o["norm"].ravel()).max() < 1e-11
     assert np.abs(means[Mx:2 * Mx] - o["mean1"].ravel()).max() < 1e-11
