@@ -190,8 +190,12 @@ qtt_status qtt_grad(qtt_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* ou
  * steps one PDF): advances each of ctxs[0..n) by nsteps steps, enqueueing the
  * work of every context before synchronising any of them, so that contexts
  * on different streams (a context created with stream NULL owns one) run
- * concurrently on the GPU.  After a context's first step every step is one
- * CUDA-graph launch, so the host cost is about n launches per step.  The
+ * concurrently on the GPU.  Once every context has captured its step graphs
+ * (after its first three steps), each step is one launch of a graph that
+ * embeds every context's step graph as an independent node; it is built the
+ * first time a set of contexts is stepped together and rebuilt when the set,
+ * a context's graphs or the contexts' relative step parity change (the
+ * contexts must belong to the current device).  The
  * contexts may differ in grid, chi, coefficients and precision; a context
  * must not appear twice.  Returns QTT_OK, or the status of the first context
  * (lowest index) that failed, whose index goes to *failed (-1 when none;
