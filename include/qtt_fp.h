@@ -55,8 +55,10 @@ typedef enum {
  * operator bond <= 32 run on the CUDA cores (FP32 in those three forms).
  * BF16X10: the products carrying the state as 4 x 4 exact bf16 slices cut
  * from the FP64 mantissa (10 slice products, exact FP32 accumulation,
- * ~2^-31 of the row maxima), the sketch products hi/lo TF32, the
- * operator-bond contractions in FP64. */
+ * ~2^-31 of the row maxima), except those of the mixing term (O(dt): its
+ * product errors reach the state scaled by dt Omega), which take the 3 x 3
+ * slices of FP32; the sketch products hi/lo TF32, the operator-bond
+ * contractions that carry the state in FP64, those of the sketch in FP32. */
 typedef enum { QTT_FP64 = 0, QTT_FP32 = 1, QTT_TF32 = 2, QTT_BF16X3 = 3, QTT_BF16X10 = 4 } qtt_precision;
 
 typedef struct {

@@ -146,6 +146,17 @@ Engine::Engine(const Params& p, cudaStream_t stream) : p_(p), st_(stream) {
                                       : -1;
   for (int& m : tc_mode_) m = mode;
   if (p.precision == 1 || p.precision == 4) tc_mode_[GEMM_SKETCH] = tc_mode_[GEMM_RANGE] = TC_TF32X3;
+  // BF16X10 takes the mixing term's state products (projection and zip-up of
+  // the term kind 1, the Hadamard product with the conditional means) in
+  // BF16X6.  The term is dt Omega D1phi[(phi - <Phi>) f], of size
+  // ~dt Omega |phi - <Phi>| / sigma ~ 4e-3 |f| on the 2^8-point workload, so
+  // its products' error (~2^-24 of their operands' row and column maxima)
+  // reaches the state ~250 times smaller, at the level BF16X10 leaves on the
+  // other terms.  Measured on that workload against the FP64 path after
+  // 25 / 100 / 250 steps: 8.3e-7 / 4.1e-6 / 5.3e-6 (all products in BF16X10:
+  // 1.0e-6 / 1.9e-6 / 5.4e-6), 6% shorter steps; TF32X3 there gives
+  // 9.4e-6 / 2.6e-5 / 5.0e-5.
+  tc_mode_[GEMM_MIX] = p.precision == 4 ? TC_BF16X6 : tc_mode_[GEMM_STATE];
   // BF16X10 keeps the operator-bond contractions (CUDA cores) that carry the
   // state in FP64: in FP32 they move the state by ~1e-5 over ten steps of the
   // 2^4-point workload, far above what its sliced products leave.  Those of
@@ -260,7 +271,7 @@ void Engine::gemm(int M, int N, int K, int outer, int inner, double alpha, MatVi
   if (small_gemm_fits(M, N, K, outer, inner)) {
     // operator-bond contractions: memory-bound, on the CUDA cores
     TimeScope ts(timer_, TM_SMALL, cur(), 2.0 * M * (double)N * K * outer * inner);
-    small_gemm(cur(), mode >= 0 && (small_fp32_ || (small_sketch_fp32_ && role != GEMM_STATE)), M, N, K, outer,
+    small_gemm(cur(), mode >= 0 && (small_fp32_ || (small_sketch_fp32_ && role != GEMM_STATE && role != GEMM_MIX)), M, N, K, outer,
                inner, alpha, A, B, beta, C);
     return;
   }
@@ -614,17 +625,18 @@ void Engine::zip_site(const Term& t, int n, int r, const double* C, double* T, d
   const double* A = t.A(n);
   double* P = lane_p_[lane_];
   // P[(rho,w)][(s',a')] = sum_a C[(rho,w)][a] A[a][(s',a')]
-  gemm(r * wl, 2 * br, bl, 1, 1, 1.0, mv(C, bl, 1), mv(A, 2LL * br, 1), 0.0, ov(P, 2LL * br, 1));
+  const int role = t.kind == 1 ? GEMM_MIX : GEMM_STATE;
+  gemm(r * wl, 2 * br, bl, 1, 1, 1.0, mv(C, bl, 1), mv(A, 2LL * br, 1), 0.0, ov(P, 2LL * br, 1), role);
   if (!t.diag(n)) {
     // T[(rho,s)][(w',a')] = sum_{(w,s')} Wt[s][w'][(w,s')] P[rho][(w,s')][a']
     const double* Wt = t.op->Wt(n);
     gemm(wr, br, 2 * wl, r, 2, alpha, mv(Wt, 2LL * wl, 1, 0, (long long)wr * 2 * wl),
-         mv(P, br, 1, 2LL * wl * br, 0), 0.0, ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
+         mv(P, br, 1, 2LL * wl * br, 0), 0.0, ov(T, br, 1, 2LL * wr * br, (long long)wr * br), role);
   } else {
     const double* H = t.H(n);
     // T[(rho,s)][(h',a')] = sum_h H[h][s][h'] P[(rho,h)][(s,a')]
     gemm(wr, br, wl, r, 2, alpha, mv(H, 1, 2LL * wr, 0, wr), mv(P, 2LL * br, 1, (long long)wl * 2 * br, br), 0.0,
-         ov(T, br, 1, 2LL * wr * br, (long long)wr * br));
+         ov(T, br, 1, 2LL * wr * br, (long long)wr * br), role);
   }
 }
 
@@ -685,7 +697,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
       const Term& t = terms[i];
       if (project)  // C_i = Q^T T_i at the previous site
         gemm(rn, (int)t.B(n), 2 * r, 1, 1, 1.0, mv(mid_.core(n - 1), 1, rn), mv(T_[t.slot], t.B(n), 1), 0.0,
-             ov(C_[t.slot], t.B(n), 1));
+             ov(C_[t.slot], t.B(n), 1), t.kind == 1 ? GEMM_MIX : GEMM_STATE);
       zip_site(t, n, rs, C_[t.slot], T_[t.slot], n == 0 ? t.scale : 1.0);
       if (range) {
         const int L = ell_[n + 1];

@@ -53,7 +53,7 @@ struct DevOp {
 // Arithmetic classes of the contractions (each precision form maps them to a
 // tensor-core mode): products carrying the state, products of the random
 // sketch environments, and state times sketch (the range finder's Y).
-enum GemmRole { GEMM_STATE = 0, GEMM_SKETCH = 1, GEMM_RANGE = 2 };
+enum GemmRole { GEMM_STATE = 0, GEMM_SKETCH = 1, GEMM_RANGE = 2, GEMM_MIX = 3 };
 
 // One summand c * Op * f of a stage.  kind 0: dense MPO over all sites;
 // kind 1: mixing Hadamard term -- dense composition-space MPO on the phi
@@ -177,7 +177,8 @@ class Engine {
   void upload_tt_mps(DevMps& m, const TT& t, const std::vector<int>& bonds);
   // Contraction in the context's precision form (tensor cores for the reduced forms).
   // role: GEMM_STATE (products that carry the state), GEMM_SKETCH (products
-  // of the random sketch environments), GEMM_RANGE (state times sketch)
+  // of the random sketch environments), GEMM_RANGE (state times sketch),
+  // GEMM_MIX (state products of the mixing term, which is O(dt))
   void gemm(int M, int N, int K, int outer, int inner, double alpha, MatView A, MatView B, double beta, OutView C,
             int role = 0);
   // FP64 product (Gram matrices, norms, masses, observables).
@@ -269,7 +270,7 @@ class Engine {
   cudaStream_t cur() const { return lane_st_[lane_]; }
   void fork_lanes(int n);  // lanes 1..n wait for st_
   void join_lanes(int n);  // st_ waits for lanes 1..n
-  int tc_mode_[3] = {-1, -1, -1};  // per GEMM role; -1: FP64 kernel
+  int tc_mode_[4] = {-1, -1, -1, -1};  // per GEMM role; -1: FP64 kernel
   int max_bond_ = 1;
   unsigned long long* dstep_ = nullptr;  // device copy of the step count (sketch draws)
   // CUDA graphs of one step, indexed by which of the two state buffers is f_
