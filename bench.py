@@ -35,6 +35,7 @@ import workload  # noqa: E402
 
 METRIC = "MPS time-steps/s at chi=128 vs plain FP64 GPU path; rel-L2 vs FP64 oracle"
 FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
+LATE_STEPS = 10  # steps timed after the last accuracy point
 ACCURACY_STEPS = (25, 100)  # step counts at which every form is compared with the FP64 path
 TIMING_LAUNCHES, TIMING_TC_ISSUED = 18, 19  # positions in OBS_TIMINGS after the 6 classes x 3
 
@@ -438,6 +439,21 @@ def run_mine(args, rank, world, local_rank):
                 acc[fm][str(target)] = {"rel_l2": cf.compare(c64), "d_norm_avg": sf["norm_avg"] - s64["norm_avg"],
                                         "d_mean1_avg": sf["mean1_avg"] - s64["mean1_avg"],
                                         "d_phi11_avg": sf["phi11_avg"] - s64["phi11_avg"]}
+        # steps/s further into the run: the bond eigensolves take more QL
+        # sweeps once the state fills its bonds (the Gram matrices of the
+        # early, low-rank states deflate at once), so the step lengthens
+        # along the run; timed on the same contexts right after the last
+        # accuracy point
+        def time_steps(c, k):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c.step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return k * world / (max_over_ranks(e0.elapsed_time(e1)) / 1e3)
+
+        late64 = time_steps(c64, LATE_STEPS)
+        late = {fm: time_steps(cf, LATE_STEPS) for fm, cf in fctx.items()}
         for cf in fctx.values():
             cf.close()
         c64.close()
@@ -451,6 +467,9 @@ def run_mine(args, rank, world, local_rank):
                      "met_at_steps": [int(k) for k, v in head.items() if v["rel_l2"] <= 1e-5 and value / v64 >= 5.0]},
             "forms": {fm: {"value": fval[fm], "unit": "steps/s", "speedup": fval[fm] / v64, "vs_fp64": acc[fm]}
                       for fm in forms},
+            "later_in_run": {"window": f"steps {n64 + 1}-{n64 + LATE_STEPS} from the initial condition (CUDA events)",
+                             "fp64": late64,
+                             "forms": {fm: {"value": late[fm], "speedup": late[fm] / late64} for fm in forms}},
             "comparison": "each form and the FP64 path stepped from the same initial state to the stated step "
                           "counts at equal chi; relative L2 distance of the decompressed states (qtt_compare); "
                           "fp64_one_ulp_floor: the FP64 path against itself from an initial condition moved by "
