@@ -7,20 +7,23 @@
 //
 // Three kernels, so that the FP64 work does not all sit on one SM:
 //   1. eig_tridiag_ql (one block): Householder reduction to tridiagonal form
-//      (matrix in shared memory when it fits, lower-triangle updates), then
-//      the implicit-shift QL iteration on (d, e) run by warp 0 (one lane
-//      carries the rotation chain; lanes of warps 1 and 2 apply each rotation
-//      to e and d and record it in a list of every sweep's rotations), and a
-//      stable descending order of the eigenvalues;
-//   2. eig_apply_rotations (one thread per row of the eigenvector matrix Z of
-//      the tridiagonal problem, over several blocks): replays the rotation
-//      list on its row;
+//      (matrix in shared memory when it fits, lower-triangle updates); for
+//      single-precision problems it then runs the implicit-shift QL iteration
+//      on (d, e) in warp 0 (one lane carries the rotation chain; lanes of
+//      warps 1 and 2 apply each rotation to e and d and record it in a list
+//      of every sweep's rotations) and a stable descending order of the
+//      eigenvalues;
+//   2. FP64: eig_dc (one block), divide and conquer on (d, e) (below), which
+//      also orders the eigenvalues; single precision: eig_apply_rotations
+//      (one thread per row of the eigenvector matrix Z of the tridiagonal
+//      problem, over several blocks), which replays the rotation list on its
+//      row;
 //   3. eig_back_transform (one warp per kept eigenvector): applies the
 //      Householder reflectors, U[:, r] = H_0 ... H_{n-3} Z[:, order[r]].
-// Every loop is bounded; the QL iteration stops after 60 sweeps per
-// eigenvalue (or when the rotation list is full), and the two QL lanes wait
-// on each other for at most about a second; both report through the status
-// word (bits 2 and 8).
+// Every loop is bounded; a QL iteration stops after 60 sweeps per
+// eigenvalue (or when the rotation list is full), a secular root after 100
+// steps, and the two QL lanes wait on each other for at most about a second;
+// both report through the status word (bits 2 and 8).
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -53,17 +56,10 @@ __device__ T warp_sum_e(T v) {
 
 __device__ __forceinline__ double rhyp(double a, double b) { return rhypot(a, b); }
 __device__ __forceinline__ float rhyp(float a, float b) { return rhypotf(a, b); }
-// 1 / sqrt(a^2 + b^2) on the QL recurrence's dependency chain: the plain
-// reciprocal square root of the sum of squares (fewer dependent operations
-// than the scaled rhypot) while the sum stays inside the normal range, else
-// the scaled form.
-__device__ __forceinline__ double rhyp_fast(double a, double b) {
-  const double q = fma(a, a, b * b);
-  // normal range test on the exponent bits (integer pipe): 2^-996 .. 2^996
-  const int ex = (__double2hiint(q) >> 20) & 0x7ff;
-  return (ex > 27 && ex < 2019) ? rsqrt(q) : rhypot(a, b);
-}
-// the same with b^2 given (b2 = b * b, computed off the chain)
+// 1 / sqrt(a^2 + b^2) on the QL recurrence's dependency chain, with b^2
+// given (b2 = b * b, computed off the chain): the plain reciprocal square
+// root of the sum of squares (fewer dependent operations than the scaled
+// rhypot) while the sum stays inside the normal range, else the scaled form.
 __device__ __forceinline__ double rhyp_fast_sq(double a, double b, double b2) {
   const double q = fma(a, a, b2);
   const int ex = (__double2hiint(q) >> 20) & 0x7ff;
@@ -71,10 +67,6 @@ __device__ __forceinline__ double rhyp_fast_sq(double a, double b, double b2) {
 }
 __device__ __forceinline__ float rhyp_fast_sq(float a, float b, float b2) {
   const float q = fmaf(a, a, b2);
-  return (q > 1e-35f && q < 1e35f) ? rsqrtf(q) : rhypotf(a, b);
-}
-__device__ __forceinline__ float rhyp_fast(float a, float b) {
-  const float q = fmaf(a, a, b * b);
   return (q > 1e-35f && q < 1e35f) ? rsqrtf(q) : rhypotf(a, b);
 }
 
@@ -128,13 +120,15 @@ __device__ inline int ql_wait_change(volatile int* w, int seen, volatile int* ab
   }
 }
 
-// Work layout, in elements of T: A n*n | Z n*n | rot_c R | rot_s R; then
-// ints: seg_lo S | seg_hi S | seg_off S | order n | nseg.  R = 4 n^2 + 64 n
+// Work layout, in elements of T: A n*n | Z n*n | rot_c R | rot_s R | (divide
+// and conquer) U n*n | V n*n | vectors 10 n; then ints: seg_lo S | seg_hi S |
+// seg_off S | order n | nseg 4 | (divide and conquer) 6 n.  R = 4 n^2 + 64 n
 // rotations, S = 60 n sweeps.
 struct EigLayout {
   size_t A, Z, rc, rs, R, S;
+  size_t dcU, dcV, dcv;
   size_t ints_off;  // bytes
-  size_t seg_lo, seg_hi, seg_off, order, nseg;
+  size_t seg_lo, seg_hi, seg_off, order, nseg, dci;
   size_t bytes;
 };
 
@@ -148,20 +142,24 @@ __host__ __device__ EigLayout eig_layout(int n) {
   L.Z = nn;
   L.rc = 2 * nn;
   L.rs = L.rc + L.R;
-  L.ints_off = (L.rs + L.R) * sizeof(T);
+  L.dcU = L.rs + L.R;
+  L.dcV = L.dcU + nn;
+  L.dcv = L.dcV + nn;
+  L.ints_off = (L.dcv + 10 * (size_t)n) * sizeof(T);
   L.ints_off = (L.ints_off + 15) & ~(size_t)15;
   L.seg_lo = 0;
   L.seg_hi = L.S;
   L.seg_off = 2 * L.S;
   L.order = 3 * L.S;
   L.nseg = 3 * L.S + n;
-  L.bytes = L.ints_off + (3 * L.S + n + 4) * sizeof(int);
+  L.dci = L.nseg + 4;
+  L.bytes = L.ints_off + (L.dci + 6 * (size_t)n) * sizeof(int);
   return L;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* __restrict__ probs, int use_smem,
-                                                              int* status) {
+                                                              int* status, int dc) {
   const EigProblem P = probs[blockIdx.x];
   const int n = P.n;
   if (n <= 0) return;
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   __shared__ T d[EIG_MAXN], e[EIG_MAXN], vb[EIG_MAXN], pb[EIG_MAXN], wb[EIG_MAXN], tauv[EIG_MAXN];
   __shared__ T s_tau, s_v0, s_K;
   __shared__ int ql_ctl[8];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = TRI_THREADS / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // row stride of the working copy: n + 1 in shared memory (rows of
   // consecutive threads then fall on different banks), n in global memory
@@ -301,6 +299,13 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
     else if (c == i) W[L.A + x] = tauv[i];
   }
 
+  if (dc) {  // the tridiagonal (d, e) for eig_dc, which finds its eigenpairs
+    for (int i = tid; i < n; i += TRI_THREADS) {
+      W[L.dcv + i] = d[i];
+      W[L.dcv + n + i] = e[i];
+    }
+    return;
+  }
   // ---- implicit QL with a Wilkinson-type shift, rotations recorded per sweep.
   // Warp 0 runs it: the search for the next negligible off-diagonal (32
   // entries per ballot) and the shift of the trailing diagonal are spread over
@@ -501,6 +506,456 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_tridiag_ql(const EigProblem* 
   for (int r = tid; r < n; r += TRI_THREADS) lam[r] = (double)d[order[r]];
 }
 
+// ---------------------------------------------------------------------------
+// Divide and conquer on the tridiagonal (FP64): the QL chain above issues one
+// dependent FP64 rotation after another, about 1.7k cycles each on this GPU,
+// and a full 136 x 136 spectrum takes ~10k of them plus their replay on Z.
+// Here the tridiagonal T is cut recursively in halves (Cuppen):
+//   T = diag(T1, T2) + beta (e_a + e_b)(e_a + e_b)^T,  beta = T[a][b] at the
+// cut, T1's last and T2's first diagonal entries minus beta;
+// leaves of at most DC_LEAF rows are solved by the implicit QL iteration in
+// one warp each (every lane runs the same scalar recurrence and rotates its
+// own row of Z), and two solved halves T1 = Q1 D1 Q1^T, T2 = Q2 D2 Q2^T are
+// merged by the eigen-decomposition of D + rho z z^T, z = (last row of Q1,
+// first row of Q2): deflation of the negligible components of z and of
+// (nearly) equal poles by plane rotations, one root of the secular equation
+// 1 + rho sum_i z_i^2 / (d_i - lambda) = 0 per remaining pole (a rational
+// model of each side's poles, safeguarded by the bracket), eigenvector
+// components from the recomputed z of Gu and Eisenstat (orthogonal vectors
+// from computed roots), and the product of the block-diagonal Q with the
+// merged vectors.  One block per problem; every loop is bounded.
+constexpr int DC_LEAF = 32;
+constexpr int DC_SECULAR_ITERS = 100;
+
+// Eigenpairs of the leaf (d[0..m), e[0..m-1)) in place (d <- eigenvalues, e
+// overwritten: a copy, e[m - 1] is set to 0), rotating the columns c0 .. c0 +
+// m - 1 of rows c0 .. c0 + m - 1 of Z (row stride ldz) from the identity; one
+// warp, lane r owns row c0 + r.
+__device__ void dc_leaf_ql(double* d, double* e, int m, double* Z, int ldz, int c0, int lane, int* status) {
+  const double eps = Eps<double>::v();
+  double* zrow = Z + (size_t)(c0 + (lane < m ? lane : 0)) * ldz + c0;
+  if (lane < m) zrow[lane] = 1.0;
+  if (lane == 0) e[m - 1] = 0.0;
+  __syncwarp();
+  double f = 0.0, tst1 = 0.0;
+  for (int l = 0; l < m; ++l) {
+    const double hl = fabs(d[l]) + fabs(e[l]);
+    tst1 = hl > tst1 ? hl : tst1;
+    for (int iter = 0;; ++iter) {
+      int mm = l;
+      while (mm < m - 1 && fabs(e[mm]) > eps * tst1) ++mm;
+      if (mm == l) break;
+      if (iter >= QL_MAX_SWEEPS) {
+        if (lane == 0) atomicOr(status, 2);
+        break;
+      }
+      const double g0 = d[l];
+      double p = (d[l + 1] - g0) / (2.0 * e[l]);
+      double r = hypot(p, 1.0);
+      if (p < 0) r = -r;
+      const double dl0 = e[l] / (p + r), dl1 = e[l] * (p + r);
+      const double h0 = g0 - dl0;
+      __syncwarp();
+      if (lane == 0) {
+        d[l] = dl0;
+        d[l + 1] = dl1;
+      }
+      for (int i = l + 2 + lane; i < m; i += 32) d[i] -= h0;
+      __syncwarp();
+      f += h0;
+      p = d[mm];
+      double c = 1.0, c2 = 1.0, c3 = 1.0, s = 0.0, s2 = 0.0;
+      const double el1 = e[l + 1];
+      for (int i = mm - 1; i >= l; --i) {
+        c3 = c2;
+        c2 = c;
+        s2 = s;
+        const double ei = e[i], di = d[i];
+        const double g = c * ei, h = c * p;
+        r = hypot(p, ei);
+        const double ei1 = s * r, rinv = 1.0 / r;
+        s = ei * rinv;
+        c = p * rinv;
+        p = c * di - s * g;
+        const double di1 = h + s * (c * g + s * di);
+        __syncwarp();
+        if (lane == 0) {
+          e[i + 1] = ei1;
+          d[i + 1] = di1;
+        }
+        if (lane < m) {
+          const double zi = zrow[i], zi1 = zrow[i + 1];
+          zrow[i + 1] = s * zi + c * zi1;
+          zrow[i] = c * zi - s * zi1;
+        }
+        __syncwarp();
+      }
+      p = -s * s2 * c3 * el1 * e[l] / dl1;
+      __syncwarp();
+      if (lane == 0) {
+        e[l] = s * p;
+        d[l] = c * p;
+      }
+      __syncwarp();
+      if (!(fabs(e[l]) > eps * tst1)) break;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      d[l] += f;
+      e[l] = 0.0;
+    }
+    __syncwarp();
+  }
+}
+
+// The root of 1 + rho sum_q z2[q] / (p[q] - lambda) (rho > 0, p increasing,
+// kk poles) in (p[i], p[i + 1]), or above p[kk - 1] for i = kk - 1, as
+// lambda = p[j] + tau with j the pole nearer to the root, so that the
+// differences p[q] - lambda = (p[q] - p[j]) - tau keep their relative
+// accuracy.  Each step fits psi (the poles <= i) by q / (p_i - tau) + const
+// and phi (the others) by s / (p_{i+1} - tau) + const through their values
+// and slopes, and takes the model's root inside the bracket.
+__device__ void dc_secular(const double* pole, const double* z2, double zsum, double rho, int i, int kk, int* jout,
+                           double* tout) {
+  const double eps = Eps<double>::v();
+  const bool last = i == kk - 1;
+  const double lo = pole[i], hi = last ? pole[i] + rho * zsum : pole[i + 1];
+  const double mid = 0.5 * (lo + hi);
+  double fmid = 1.0;
+  for (int q = 0; q < kk; ++q) fmid += rho * z2[q] / (pole[q] - mid);
+  const int j = (!last && fmid < 0) ? i + 1 : i;
+  const double org = pole[j];
+  double a = lo - org, b = hi - org;
+  if (fmid < 0) a = fmax(a, mid - org);
+  else b = fmin(b, mid - org);
+  double tau = 0.5 * (a + b);
+  for (int it = 0; it < DC_SECULAR_ITERS; ++it) {
+    double psi = 0, dpsi = 0, phi = 0, dphi = 0;
+    for (int q = 0; q < kk; ++q) {
+      const double inv = 1.0 / ((pole[q] - org) - tau);
+      const double t = z2[q] * inv;
+      if (q <= i) {
+        psi += t;
+        dpsi += t * inv;
+      } else {
+        phi += t;
+        dphi += t * inv;
+      }
+    }
+    const double f = 1.0 + rho * (psi + phi);
+    if (fabs(f) <= 8.0 * kk * eps * (1.0 + rho * (fabs(psi) + fabs(phi)))) break;
+    if (f < 0) a = fmax(a, tau);
+    else b = fmin(b, tau);
+    const double di = (pole[i] - org) - tau;
+    const double qq = rho * dpsi * di * di;
+    double c = f - qq / di;
+    double eta;
+    if (last) {
+      eta = c != 0.0 ? di + qq / c : 0.5 * (a + b) - tau;
+    } else {
+      const double di1 = (pole[i + 1] - org) - tau;
+      const double ss = rho * dphi * di1 * di1;
+      c -= ss / di1;
+      // c (di - eta)(di1 - eta) + qq (di1 - eta) + ss (di - eta) = 0
+      const double A = c, B = -(c * (di + di1) + qq + ss), C = c * di * di1 + qq * di1 + ss * di;
+      eta = 0.5 * (di + di1);
+      if (fabs(A) < 1e-300) {
+        if (B != 0.0) eta = -C / B;
+      } else {
+        const double sq = sqrt(fmax(B * B - 4.0 * A * C, 0.0));
+        const double den = B > 0 ? -B - sq : -B + sq;
+        double r1 = den != 0.0 ? den / (2.0 * A) : 0.5 * (di + di1);
+        double r2 = (r1 != 0.0) ? C / (A * r1) : 0.5 * (di + di1);
+        if (di < r1 && r1 < di1) eta = r1;
+        else if (di < r2 && r2 < di1) eta = r2;
+      }
+    }
+    double tn = tau + eta;
+    if (!(a < tn && tn < b)) tn = 0.5 * (a + b);
+    if (!(a < tn && tn < b)) break;  // the bracket is down to adjacent doubles
+    const bool done = fabs(tn - tau) <= 4.0 * eps * fabs(tn);
+    tau = tn;
+    if (done) break;
+  }
+  *jout = j;
+  *tout = tau;
+}
+
+__global__ void __launch_bounds__(TRI_THREADS) eig_dc(const EigProblem* __restrict__ probs, int* status) {
+  const EigProblem P = probs[blockIdx.x];
+  const int n = P.n;
+  if (n <= 0) return;
+  double* __restrict__ lam = P.lam;
+  unsigned char* work = P.work;
+  const EigLayout L = eig_layout<double>(n);
+  double* W = (double*)work;
+  int* I = (int*)(work + L.ints_off);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TRI_THREADS / 32;
+  double* Z = W + L.Z;     // n x n, row = coordinate, column = eigenvector
+  double* U = W + L.dcU;   // merge scratch, stride n
+  double* V = W + L.dcV;   // merge scratch, stride n
+  double* vd = W + L.dcv;  // diagonal, then eigenvalues
+  double* ve = vd + n;     // off-diagonal (ve[i] couples i, i + 1)
+  double* pk = ve + n;     // merge: poles (then the kept, ascending)
+  double* zk = pk + n;     // merge: z (then the kept z^2)
+  double* ds = zk + n;     // merge: poles in ascending order
+  double* zs = ds + n;     // merge: z in the same order
+  double* tau = zs + n;    // merge: root offsets
+  double* zh = tau + n;    // merge: recomputed z
+  double* rcs = zh + n;    // merge: deflation rotations (c, s)
+  double* rss = rcs + n;
+  int* order = I + L.order;
+  int* perm = I + L.dci;   // merge: sorted position -> local coordinate
+  int* jr = perm + n;      // merge: root origin pole; deflation flags before
+  int* kept = jr + n;      // merge: sorted positions of the kept poles
+  int* rl = kept + n;      // merge: deflation rotation pairs
+  int* ri = rl + n;
+  int* act = ri + n;       // merge: columns that are not a copy of one column of Q
+  __shared__ int s_kk, s_nrot;
+  __shared__ double s_red[NW], s_rho, s_zsum;
+  __shared__ double s_ld[NW][DC_LEAF], s_le[NW][DC_LEAF];
+
+  int depth = 0;
+  while (((n + (1 << depth) - 1) >> depth) > DC_LEAF) ++depth;
+  // Cuppen cuts of every level: the two diagonal entries beside each cut lose beta
+  if (tid == 0)
+    for (int dd = 0; dd < depth; ++dd)
+      for (int q = 0; q < (1 << dd); ++q) {
+        const int sp = ((2 * q + 1) * n) >> (dd + 1);
+        const double beta = ve[sp - 1];
+        vd[sp - 1] -= beta;
+        vd[sp] -= beta;
+      }
+  for (size_t x = tid; x < (size_t)n * n; x += TRI_THREADS) Z[x] = 0.0;
+  __syncthreads();
+  // leaves, one warp each, on copies of (d, e) in shared memory (the entry of
+  // e at a cut is the coupling its merge needs)
+  for (int q = warp; q < (1 << depth); q += NW) {
+    const int s0 = (q * n) >> depth, s1 = ((q + 1) * n) >> depth, m = s1 - s0;
+    if (lane < m) {
+      s_ld[warp][lane] = vd[s0 + lane];
+      s_le[warp][lane] = ve[s0 + lane];
+    }
+    __syncwarp();
+    dc_leaf_ql(s_ld[warp], s_le[warp], m, Z, n, s0, lane, status);
+    if (lane < m) vd[s0 + lane] = s_ld[warp][lane];
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // merges, bottom-up; the whole block on one merge at a time
+  for (int dd = depth - 1; dd >= 0; --dd) {
+    for (int q = 0; q < (1 << dd); ++q) {
+      const int s0 = (q * n) >> dd, s1 = ((q + 1) * n) >> dd, sp = ((2 * q + 1) * n) >> (dd + 1);
+      const int k = s1 - s0, n1 = sp - s0;
+      const double beta = ve[sp - 1];
+      const double sgn = beta < 0 ? -1.0 : 1.0;
+      // poles (sign-flipped for beta < 0) and z = (last row of Q1, first row of Q2)
+      double part = 0.0;
+      for (int j = tid; j < k; j += TRI_THREADS) {
+        pk[j] = sgn * vd[s0 + j];
+        const double zj = j < n1 ? Z[(size_t)(sp - 1) * n + s0 + j] : Z[(size_t)sp * n + s0 + j];
+        zk[j] = zj;
+        part += zj * zj;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) s_red[warp] = part;
+      __syncthreads();
+      if (tid == 0) {
+        double z2 = 0.0;
+        for (int w = 0; w < NW; ++w) z2 += s_red[w];
+        s_rho = fabs(beta) * z2;
+        s_red[0] = sqrt(z2);
+      }
+      __syncthreads();
+      const double rho = s_rho, zn = s_red[0];
+      // ascending order of the poles (stable)
+      for (int j = tid; j < k; j += TRI_THREADS) {
+        const double pj = pk[j];
+        int rank = 0;
+        for (int t = 0; t < k; ++t) {
+          const double pt = pk[t];
+          rank += (pt < pj) || (pt == pj && t < j);
+        }
+        perm[rank] = j;
+      }
+      __syncthreads();
+      for (int r = tid; r < k; r += TRI_THREADS) {
+        ds[r] = pk[perm[r]];
+        zs[r] = zn > 0.0 ? zk[perm[r]] / zn : 0.0;
+      }
+      __syncthreads();
+      // deflation (one thread): negligible rho z_i, and pairs of poles whose
+      // rotation onto one z component leaves an off-diagonal below tol
+      if (tid == 0) {
+        double dmax = 0.0;
+        for (int r = 0; r < k; ++r) dmax = fmax(dmax, fabs(ds[r]));
+        const double tol = 8.0 * Eps<double>::v() * fmax(dmax, rho);
+        int nrot = 0, last = -1;
+        for (int r = 0; r < k; ++r) {
+          jr[r] = 0;
+          if (fabs(rho * zs[r]) <= tol) {
+            jr[r] = 1;
+            continue;
+          }
+          if (last >= 0) {
+            const double t = hypot(zs[last], zs[r]);
+            const double c = zs[last] / t, s = zs[r] / t;
+            if (fabs((ds[r] - ds[last]) * c * s) <= tol) {
+              const double dl = ds[last], dr = ds[r];
+              zs[r] = t;
+              zs[last] = 0.0;
+              ds[r] = dl * c * c + dr * s * s;
+              ds[last] = dl * s * s + dr * c * c;
+              jr[last] = 1;
+              rl[nrot] = last;
+              ri[nrot] = r;
+              rcs[nrot] = c;
+              rss[nrot] = s;
+              ++nrot;
+            }
+          }
+          last = r;
+        }
+        int kk = 0;
+        for (int r = 0; r < k; ++r) {
+          act[r] = !jr[r] ? 1 : 0;
+          if (!jr[r]) kept[kk++] = r;
+        }
+        for (int t = 0; t < nrot; ++t) act[rl[t]] = act[ri[t]] = 1;
+        s_kk = kk;
+        s_nrot = nrot;
+      }
+      __syncthreads();
+      const int kk = s_kk, nrot = s_nrot;
+      // the kept poles in ascending order (a rotation may have moved one by <= tol)
+      for (int m = tid; m < kk; m += TRI_THREADS) {
+        const double pm = ds[kept[m]];
+        int rank = 0;
+        for (int t = 0; t < kk; ++t) {
+          const double pt = ds[kept[t]];
+          rank += (pt < pm) || (pt == pm && t < m);
+        }
+        jr[rank] = kept[m];  // jr as scratch (flags are no longer needed)
+      }
+      __syncthreads();
+      for (int m = tid; m < kk; m += TRI_THREADS) kept[m] = jr[m];
+      __syncthreads();
+      double zpart = 0.0;
+      for (int m = tid; m < kk; m += TRI_THREADS) {
+        pk[m] = ds[kept[m]];
+        const double zm = zs[kept[m]];
+        zk[m] = zm * zm;
+        zh[m] = zm;  // its sign, for the recomputed z
+        zpart += zm * zm;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) zpart += __shfl_xor_sync(0xffffffffu, zpart, o);
+      if (lane == 0) s_red[warp] = zpart;
+      __syncthreads();
+      if (tid == 0) {
+        double zsum = 0.0;
+        for (int w = 0; w < NW; ++w) zsum += s_red[w];
+        s_zsum = zsum;
+      }
+      __syncthreads();
+      // one root per kept pole
+      for (int m = tid; m < kk; m += TRI_THREADS) dc_secular(pk, zk, s_zsum, rho, m, kk, jr + m, tau + m);
+      __syncthreads();
+      // recomputed z (Gu-Eisenstat): zhat_m^2 = prod_i (lambda_i - p_m) / (rho prod_{i != m} (p_i - p_m))
+      for (int m = tid; m < kk; m += TRI_THREADS) {
+        const double pm = pk[m];
+        double v = -((pm - pk[jr[m]]) - tau[m]) / rho;
+        for (int t = 0; t < kk; ++t)
+          if (t != m) v *= -((pm - pk[jr[t]]) - tau[t]) / (pk[t] - pm);
+        const double a = sqrt(fabs(v));
+        zh[m] = zh[m] < 0 ? -a : a;
+      }
+      __syncthreads();
+      // vectors of the kept part: U[m][i] = zhat_m / (p_m - lambda_i), columns normalised
+      for (size_t x = tid; x < (size_t)kk * kk; x += TRI_THREADS) {
+        const int m = (int)(x / kk), i = (int)(x - (size_t)m * kk);
+        U[(size_t)m * n + i] = zh[m] / ((pk[m] - pk[jr[i]]) - tau[i]);
+      }
+      __syncthreads();
+      for (int i = tid; i < kk; i += TRI_THREADS) {
+        double s2 = 0.0;
+        for (int m = 0; m < kk; ++m) s2 += U[(size_t)m * n + i] * U[(size_t)m * n + i];
+        const double inv = 1.0 / sqrt(s2);
+        for (int m = 0; m < kk; ++m) U[(size_t)m * n + i] *= inv;
+      }
+      __syncthreads();
+      // V (sorted coordinates): identity on the deflated positions, U on the
+      // kept ones; then the deflation rotations, last first; eigenvalues
+      for (size_t x = tid; x < (size_t)k * k; x += TRI_THREADS) {
+        const int r = (int)(x / k), c = (int)(x - (size_t)r * k);
+        V[(size_t)r * n + c] = r == c ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      for (size_t x = tid; x < (size_t)kk * kk; x += TRI_THREADS) {
+        const int m = (int)(x / kk), i = (int)(x - (size_t)m * kk);
+        V[(size_t)kept[m] * n + kept[i]] = U[(size_t)m * n + i];
+      }
+      __syncthreads();
+      for (int c = tid; c < k; c += TRI_THREADS) {
+        for (int t = nrot - 1; t >= 0; --t) {
+          const int a = rl[t], b = ri[t];
+          const double cc = rcs[t], ss = rss[t];
+          const double va = V[(size_t)a * n + c], vb = V[(size_t)b * n + c];
+          V[(size_t)a * n + c] = -ss * va + cc * vb;
+          V[(size_t)b * n + c] = cc * va + ss * vb;
+        }
+      }
+      __syncthreads();
+      // rows back to the local coordinates: U[perm[r]][c] = V[r][c]
+      for (size_t x = tid; x < (size_t)k * k; x += TRI_THREADS) {
+        const int r = (int)(x / k), c = (int)(x - (size_t)r * k);
+        U[(size_t)perm[r] * n + c] = V[(size_t)r * n + c];
+      }
+      __syncthreads();
+      // Z block <- blockdiag(Q1, Q2) U (through V); a column deflated without a
+      // rotation is the unit vector of its pole, so Q's column perm[c] itself
+      for (size_t x = tid; x < (size_t)k * k; x += TRI_THREADS) {
+        const int r = (int)(x / k), c = (int)(x - (size_t)r * k);
+        const double* zr = Z + (size_t)(s0 + r) * n + s0;
+        if (!act[c]) {
+          V[(size_t)r * n + c] = zr[perm[c]];
+          continue;
+        }
+        const int j0 = r < n1 ? 0 : n1, j1 = r < n1 ? n1 : k;
+        double acc = 0.0;
+        for (int j = j0; j < j1; ++j) acc += zr[j] * U[(size_t)j * n + c];
+        V[(size_t)r * n + c] = acc;
+      }
+      __syncthreads();
+      for (size_t x = tid; x < (size_t)k * k; x += TRI_THREADS) {
+        const int r = (int)(x / k), c = (int)(x - (size_t)r * k);
+        Z[(size_t)(s0 + r) * n + s0 + c] = V[(size_t)r * n + c];
+      }
+      // eigenvalue of column c (sorted position c): the root of the kept pole
+      // there, or the (rotated) deflated pole itself
+      for (int c = tid; c < k; c += TRI_THREADS) vd[s0 + c] = sgn * ds[c];
+      __syncthreads();
+      for (int m = tid; m < kk; m += TRI_THREADS) vd[s0 + kept[m]] = sgn * (pk[jr[m]] + tau[m]);
+      __syncthreads();
+    }
+  }
+  // stable descending order of the eigenvalues
+  for (int i = tid; i < n; i += TRI_THREADS) {
+    const double di = vd[i];
+    int rank = 0;
+    for (int q = 0; q < n; ++q) {
+      const double dq = vd[q];
+      rank += (dq > di) || (dq == di && q < i);
+    }
+    order[rank] = i;
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += TRI_THREADS) lam[r] = vd[order[r]];
+}
+
 // Row `row` of Z (eigenvectors of the tridiagonal matrix as columns) starts as
 // e_row and receives every recorded rotation in order.
 template <typename T>
@@ -575,11 +1030,18 @@ void eig_launch(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nma
     cudaFuncSetAttribute(eig_tridiag_ql<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
     attr = true;
   }
+  // FP64 problems: tridiagonalisation, then divide and conquer; float ones
+  // keep the QL iteration and the replay of its rotations
+  constexpr bool dc = sizeof(T) == sizeof(double);
   count_launches(kmax > 0 ? 3 : 2);
-  eig_tridiag_ql<T><<<nprob, TRI_THREADS, use_smem ? smem_A : 0, st>>>(probs_dev, use_smem, status);
-  const int rows_per_block = 32;
-  eig_apply_rotations<T><<<dim3((nmax + rows_per_block - 1) / rows_per_block, nprob), rows_per_block, 0, st>>>(
-      probs_dev);
+  eig_tridiag_ql<T><<<nprob, TRI_THREADS, use_smem ? smem_A : 0, st>>>(probs_dev, use_smem, status, dc ? 1 : 0);
+  if constexpr (dc) {
+    eig_dc<<<nprob, TRI_THREADS, 0, st>>>(probs_dev, status);
+  } else {
+    const int rows_per_block = 32;
+    eig_apply_rotations<T><<<dim3((nmax + rows_per_block - 1) / rows_per_block, nprob), rows_per_block, 0, st>>>(
+        probs_dev);
+  }
   if (kmax > 0) {
     const int warps = 4;
     eig_back_transform<T><<<dim3((kmax + warps - 1) / warps, nprob), 32 * warps, (size_t)warps * nmax * sizeof(T),
