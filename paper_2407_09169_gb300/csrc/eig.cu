@@ -26,8 +26,6 @@
 // both report through the status word (bits 2 and 8).
 #include <cuda_runtime.h>
 
-#include <algorithm>
-
 #include "kernels.cuh"
 
 namespace qtt {
@@ -123,13 +121,12 @@ __device__ inline int ql_wait_change(volatile int* w, int seen, volatile int* ab
 }
 
 // Work layout, in elements of T: A n*n | Z n*n | rot_c R | rot_s R | (divide
-// and conquer) U n*n | V n*n | vectors 10 n | (its cluster variant) 8 n*n;
-// then ints: seg_lo S | seg_hi S |
+// and conquer) U n*n | V n*n | vectors 10 n; then ints: seg_lo S | seg_hi S |
 // seg_off S | order n | nseg 4 | (divide and conquer) 6 n.  R = 4 n^2 + 64 n
 // rotations, S = 60 n sweeps.
 struct EigLayout {
   size_t A, Z, rc, rs, R, S;
-  size_t dcU, dcV, dcv, dcc;
+  size_t dcU, dcV, dcv;
   size_t ints_off;  // bytes
   size_t seg_lo, seg_hi, seg_off, order, nseg, dci;
   size_t bytes;
@@ -148,8 +145,7 @@ __host__ __device__ EigLayout eig_layout(int n) {
   L.dcU = L.rs + L.R;
   L.dcV = L.dcU + nn;
   L.dcv = L.dcV + nn;
-  L.dcc = L.dcv + 10 * (size_t)n;  // cluster variant: U, V per CTA (4 CTAs)
-  L.ints_off = (L.dcc + 8 * nn) * sizeof(T);
+  L.ints_off = (L.dcv + 10 * (size_t)n) * sizeof(T);
   L.ints_off = (L.ints_off + 15) & ~(size_t)15;
   L.seg_lo = 0;
   L.seg_hi = L.S;
@@ -964,397 +960,6 @@ __global__ void __launch_bounds__(TRI_THREADS) eig_dc(const EigProblem* __restri
 }
 
 
-// ---------------------------------------------------------------------------
-// The same divide and conquer over a cluster of DCC CTAs per problem (n <=
-// DCC_MAXN), for four SMs' FP64 pipes instead of one: leaf q and its rows of
-// Z belong to CTA q % DCC, which keeps them in shared memory; every CTA holds
-// the vectors of the merge (poles, z, deflation, sort) and computes them
-// redundantly; the roots of the secular equation and the recomputed z are
-// split over the CTAs (root m on CTA m % DCC) and gathered through
-// distributed shared memory; each CTA forms the merged eigenvectors of the
-// small problem in its own scratch and multiplies its own rows of Z.
-constexpr int DCC = 4;
-constexpr int DCC_MAXN = 256;
-
-__device__ __forceinline__ uint32_t dcc_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void dcc_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t dcc_mapa(const void* local, uint32_t rank) {
-  uint32_t r;
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ double dcc_ld_f64(const double* local, uint32_t rank) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dcc_mapa(local, rank)) : "memory");
-  return v;
-}
-__device__ __forceinline__ int dcc_ld_s32(const int* local, uint32_t rank) {
-  int v;
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dcc_mapa(local, rank)) : "memory");
-  return v;
-}
-
-// dynamic shared memory of eig_dc_cluster (in doubles, then ints)
-struct DccSmem {
-  int rows;  // owned rows of Z (at most)
-  size_t zs, tmp, vec, ints, bytes;
-};
-__host__ __device__ inline int dcc_depth(int n) {
-  int depth = 0;
-  while (((n + (1 << depth) - 1) >> depth) > DC_LEAF) ++depth;
-  return depth;
-}
-__host__ __device__ inline DccSmem dcc_smem(int n) {
-  DccSmem S;
-  const int depth = dcc_depth(n), nleaf = 1 << depth;
-  const int leaf_max = (n + nleaf - 1) / nleaf;
-  S.rows = ((nleaf + DCC - 1) / DCC) * leaf_max;
-  S.zs = 0;
-  S.tmp = (size_t)S.rows * n;                  // owned rows of Z, full width
-  S.vec = S.tmp + (size_t)(TRI_THREADS / 32) * n;  // a row per warp
-  S.ints = S.vec + 12 * (size_t)n;            // 12 vectors of n doubles
-  S.bytes = S.ints * 8 + 7 * (size_t)n * 4;   // 7 vectors of n ints
-  return S;
-}
-
-__global__ void __launch_bounds__(TRI_THREADS) eig_dc_cluster(const EigProblem* __restrict__ probs, int* status) {
-  const int rank = (int)dcc_rank();
-  const EigProblem P = probs[blockIdx.x / DCC];
-  const int n = P.n;
-  if (n <= 0) return;  // the same for every CTA of the cluster
-  double* __restrict__ lam = P.lam;
-  unsigned char* work = P.work;
-  const EigLayout L = eig_layout<double>(n);
-  double* W = (double*)work;
-  int* I = (int*)(work + L.ints_off);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = TRI_THREADS / 32;
-  const DccSmem S = dcc_smem(n);
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  double* sm = (double*)dyn_smem;
-  double* Zs = sm + S.zs;    // owned rows of Z (local row li), full width n
-  double* tmp = sm + S.tmp;  // one row per warp
-  double* vd = sm + S.vec;   // diagonal, then eigenvalues (every CTA)
-  double* ve = vd + n;
-  double* pk = ve + n;
-  double* zk = pk + n;
-  double* ds = zk + n;
-  double* zs = ds + n;
-  double* tau = zs + n;
-  double* zh = tau + n;
-  double* rcs = zh + n;
-  double* rss = rcs + n;
-  double* tau_own = rss + n;  // roots this CTA computed (m % DCC == rank)
-  double* zh_own = tau_own + n;
-  int* perm = (int*)(sm + S.ints);
-  int* jr = perm + n;
-  int* kept = jr + n;
-  int* rl = kept + n;
-  int* ri = rl + n;
-  int* act = ri + n;
-  int* jr_own = act + n;
-  double* U = W + L.dcc + (size_t)rank * 2 * n * n;  // this CTA's scratch, stride n
-  double* V = U + (size_t)n * n;
-  __shared__ int s_kk, s_nrot;
-  __shared__ double s_red[NW], s_rho, s_zsum, s_zn;
-  __shared__ double s_ld[NW][DC_LEAF], s_le[NW][DC_LEAF];
-
-  const int depth = dcc_depth(n), nleaf = 1 << depth;
-  // leaf of a row, and the local row of an owned row
-  auto leaf_of = [&](int r) {
-    int q = 0;
-    while (q + 1 < nleaf && (((q + 1) * n) >> depth) <= r) ++q;
-    return q;
-  };
-  auto local_row = [&](int r) {
-    const int q = leaf_of(r), own = q % DCC;
-    int base = 0;
-    for (int t = own; t < q; t += DCC) base += (((t + 1) * n) >> depth) - ((t * n) >> depth);
-    return base + (r - ((q * n) >> depth));
-  };
-
-  for (int i = tid; i < n; i += TRI_THREADS) {
-    vd[i] = W[L.dcv + i];
-    ve[i] = W[L.dcv + n + i];
-  }
-  for (size_t x = tid; x < (size_t)S.rows * n; x += TRI_THREADS) Zs[x] = 0.0;
-  __syncthreads();
-  if (tid == 0)
-    for (int dd = 0; dd < depth; ++dd)
-      for (int q = 0; q < (1 << dd); ++q) {
-        const int sp = ((2 * q + 1) * n) >> (dd + 1);
-        const double beta = ve[sp - 1];
-        vd[sp - 1] -= beta;
-        vd[sp] -= beta;
-      }
-  __syncthreads();
-  // this CTA's leaves, one warp each
-  {
-    int base = 0, slot = 0;
-    for (int q = rank; q < nleaf; q += DCC, ++slot) {
-      const int s0 = (q * n) >> depth, s1 = ((q + 1) * n) >> depth, m = s1 - s0;
-      if (slot % NW == warp) {
-        if (lane < m) {
-          s_ld[warp][lane] = vd[s0 + lane];
-          s_le[warp][lane] = ve[s0 + lane];
-        }
-        __syncwarp();
-        dc_leaf_ql(s_ld[warp], s_le[warp], m, Zs + (size_t)base * n + s0, n, lane, status);
-        if (lane < m) vd[s0 + lane] = s_ld[warp][lane];
-        __syncwarp();
-      }
-      base += m;
-    }
-  }
-  dcc_sync();
-  // every leaf's eigenvalues from its owner
-  for (int i = tid; i < n; i += TRI_THREADS) {
-    const int own = leaf_of(i) % DCC;
-    if (own != rank) vd[i] = dcc_ld_f64(vd + i, (uint32_t)own);
-  }
-  __syncthreads();
-
-  for (int dd = depth - 1; dd >= 0; --dd) {
-    for (int q = 0; q < (1 << dd); ++q) {
-      const int s0 = (q * n) >> dd, s1 = ((q + 1) * n) >> dd, sp = ((2 * q + 1) * n) >> (dd + 1);
-      const int k = s1 - s0, n1 = sp - s0;
-      const double beta = ve[sp - 1];
-      const double sgn = beta < 0 ? -1.0 : 1.0;
-      const int ra = sp - 1, rb = sp;  // the rows holding z
-      const int oa = leaf_of(ra) % DCC, ob = leaf_of(rb) % DCC;
-      const int la = local_row(ra), lb = local_row(rb);
-      double part = 0.0;
-      for (int j = tid; j < k; j += TRI_THREADS) {
-        pk[j] = sgn * vd[s0 + j];
-        const double zj = j < n1 ? dcc_ld_f64(Zs + (size_t)la * n + s0 + j, (uint32_t)oa)
-                                 : dcc_ld_f64(Zs + (size_t)lb * n + s0 + j, (uint32_t)ob);
-        zk[j] = zj;
-        part += zj * zj;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) s_red[warp] = part;
-      __syncthreads();
-      if (tid == 0) {
-        double z2 = 0.0;
-        for (int w = 0; w < NW; ++w) z2 += s_red[w];
-        s_rho = fabs(beta) * z2;
-        s_zn = sqrt(z2);
-      }
-      __syncthreads();
-      const double rho = s_rho, zn = s_zn;
-      for (int j = tid; j < k; j += TRI_THREADS) {
-        const double pj = pk[j];
-        int rk = 0;
-        for (int t = 0; t < k; ++t) {
-          const double pt = pk[t];
-          rk += (pt < pj) || (pt == pj && t < j);
-        }
-        perm[rk] = j;
-      }
-      __syncthreads();
-      for (int r = tid; r < k; r += TRI_THREADS) {
-        ds[r] = pk[perm[r]];
-        zs[r] = zn > 0.0 ? zk[perm[r]] / zn : 0.0;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double dmax = 0.0;
-        for (int r = 0; r < k; ++r) dmax = fmax(dmax, fabs(ds[r]));
-        const double tol = 8.0 * Eps<double>::v() * fmax(dmax, rho);
-        int nrot = 0, last = -1;
-        for (int r = 0; r < k; ++r) {
-          jr[r] = 0;
-          if (fabs(rho * zs[r]) <= tol) {
-            jr[r] = 1;
-            continue;
-          }
-          const double zl = last >= 0 ? zs[last] : 0.0, zr = zs[r];
-          if (last >= 0 && fabs((ds[r] - ds[last]) * zl * zr) <= tol * (zl * zl + zr * zr)) {
-            const double t = hypot(zl, zr);
-            const double c = zl / t, s = zr / t;
-            const double dl = ds[last], dr = ds[r];
-            zs[r] = t;
-            zs[last] = 0.0;
-            ds[r] = dl * c * c + dr * s * s;
-            ds[last] = dl * s * s + dr * c * c;
-            jr[last] = 1;
-            rl[nrot] = last;
-            ri[nrot] = r;
-            rcs[nrot] = c;
-            rss[nrot] = s;
-            ++nrot;
-          }
-          last = r;
-        }
-        int kk = 0;
-        for (int r = 0; r < k; ++r) {
-          act[r] = !jr[r] ? 1 : 0;
-          if (!jr[r]) kept[kk++] = r;
-        }
-        for (int t = 0; t < nrot; ++t) act[rl[t]] = act[ri[t]] = 1;
-        s_kk = kk;
-        s_nrot = nrot;
-      }
-      __syncthreads();
-      const int kk = s_kk, nrot = s_nrot;
-      for (int m = tid; m < kk; m += TRI_THREADS) {
-        const double pm = ds[kept[m]];
-        int rk = 0;
-        for (int t = 0; t < kk; ++t) {
-          const double pt = ds[kept[t]];
-          rk += (pt < pm) || (pt == pm && t < m);
-        }
-        jr[rk] = kept[m];
-      }
-      __syncthreads();
-      for (int m = tid; m < kk; m += TRI_THREADS) kept[m] = jr[m];
-      __syncthreads();
-      double zpart = 0.0;
-      for (int m = tid; m < kk; m += TRI_THREADS) {
-        pk[m] = ds[kept[m]];
-        const double zm = zs[kept[m]];
-        zk[m] = zm * zm;
-        zpart += zm * zm;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) zpart += __shfl_xor_sync(0xffffffffu, zpart, o);
-      if (lane == 0) s_red[warp] = zpart;
-      __syncthreads();
-      if (tid == 0) {
-        double zsum = 0.0;
-        for (int w = 0; w < NW; ++w) zsum += s_red[w];
-        s_zsum = zsum;
-      }
-      __syncthreads();
-      // this CTA's roots, then every root from its owner
-      for (int m = rank + DCC * tid; m < kk; m += DCC * TRI_THREADS)
-        dc_secular(pk, zk, s_zsum, rho, m, kk, jr_own + m, tau_own + m);
-      dcc_sync();
-      for (int m = tid; m < kk; m += TRI_THREADS) {
-        const uint32_t own = (uint32_t)(m % DCC);
-        jr[m] = dcc_ld_s32(jr_own + m, own);
-        tau[m] = dcc_ld_f64(tau_own + m, own);
-      }
-      __syncthreads();
-      for (int m = rank + DCC * tid; m < kk; m += DCC * TRI_THREADS) {
-        const double pm = pk[m];
-        double v = -((pm - pk[jr[m]]) - tau[m]) / rho;
-        for (int t = 0; t < kk; ++t)
-          if (t != m) v *= -((pm - pk[jr[t]]) - tau[t]) / (pk[t] - pm);
-        const double a = sqrt(fabs(v));
-        zh_own[m] = zs[kept[m]] < 0 ? -a : a;
-      }
-      dcc_sync();
-      for (int m = tid; m < kk; m += TRI_THREADS) zh[m] = dcc_ld_f64(zh_own + m, (uint32_t)(m % DCC));
-      __syncthreads();
-      // the merged vectors of the small problem, in this CTA's scratch
-      for (size_t x = tid; x < (size_t)kk * kk; x += TRI_THREADS) {
-        const int m = (int)(x / kk), i = (int)(x - (size_t)m * kk);
-        U[(size_t)m * n + i] = zh[m] / ((pk[m] - pk[jr[i]]) - tau[i]);
-      }
-      __syncthreads();
-      for (int i = tid; i < kk; i += TRI_THREADS) {
-        double s2 = 0.0;
-        for (int m = 0; m < kk; ++m) s2 += U[(size_t)m * n + i] * U[(size_t)m * n + i];
-        const double inv = 1.0 / sqrt(s2);
-        for (int m = 0; m < kk; ++m) U[(size_t)m * n + i] *= inv;
-      }
-      __syncthreads();
-      for (size_t x = tid; x < (size_t)k * k; x += TRI_THREADS) {
-        const int r = (int)(x / k), c = (int)(x - (size_t)r * k);
-        V[(size_t)r * n + c] = r == c ? 1.0 : 0.0;
-      }
-      __syncthreads();
-      for (size_t x = tid; x < (size_t)kk * kk; x += TRI_THREADS) {
-        const int m = (int)(x / kk), i = (int)(x - (size_t)m * kk);
-        V[(size_t)kept[m] * n + kept[i]] = U[(size_t)m * n + i];
-      }
-      __syncthreads();
-      for (int c = tid; c < k; c += TRI_THREADS) {
-        if (!act[c]) continue;
-        for (int t = nrot - 1; t >= 0; --t) {
-          const int a = rl[t], b = ri[t];
-          const double cc = rcs[t], ss = rss[t];
-          const double va = V[(size_t)a * n + c], vb = V[(size_t)b * n + c];
-          V[(size_t)a * n + c] = -ss * va + cc * vb;
-          V[(size_t)b * n + c] = cc * va + ss * vb;
-        }
-      }
-      __syncthreads();
-      for (size_t x = tid; x < (size_t)k * k; x += TRI_THREADS) {
-        const int r = (int)(x / k), c = (int)(x - (size_t)r * k);
-        U[(size_t)perm[r] * n + c] = V[(size_t)r * n + c];
-      }
-      __syncthreads();
-      // this CTA's rows of the merged block: row <- row (Q1 or Q2 part) x U;
-      // a warp per row through its row buffer
-      {
-        int slot = 0, base = 0;
-        for (int ql = rank; ql < nleaf; ql += DCC) {
-          const int l0 = (ql * n) >> depth, l1 = ((ql + 1) * n) >> depth;
-          if (l0 >= s0 && l1 <= s1) {
-            for (int r = l0; r < l1; ++r, ++slot) {
-              if (slot % NW != warp) continue;
-              double* zr = Zs + (size_t)(base + (r - l0)) * n + s0;
-              const int j0 = r - s0 < n1 ? 0 : n1, j1 = r - s0 < n1 ? n1 : k;
-              double* tr = tmp + (size_t)warp * n;
-              for (int c = lane; c < k; c += 32) {
-                if (!act[c]) {
-                  tr[c] = zr[perm[c]];
-                  continue;
-                }
-                double acc = 0.0;
-                for (int j = j0; j < j1; ++j) acc += zr[j] * U[(size_t)j * n + c];
-                tr[c] = acc;
-              }
-              __syncwarp();
-              for (int c = lane; c < k; c += 32) zr[c] = tr[c];
-              __syncwarp();
-            }
-          }
-          base += l1 - l0;
-        }
-      }
-      for (int c = tid; c < k; c += TRI_THREADS) vd[s0 + c] = sgn * ds[c];
-      __syncthreads();
-      for (int m = tid; m < kk; m += TRI_THREADS) vd[s0 + kept[m]] = sgn * (pk[jr[m]] + tau[m]);
-      dcc_sync();  // rows and the roots' buffers are read remotely by the next merge
-    }
-  }
-  // eigenvalue order (every CTA the same), this CTA's rows of Z to the work area
-  int* order = I + L.order;
-  for (int i = tid; i < n; i += TRI_THREADS) {
-    const double di = vd[i];
-    int rk = 0;
-    for (int q = 0; q < n; ++q) {
-      const double dq = vd[q];
-      rk += (dq > di) || (dq == di && q < i);
-    }
-    if (rank == 0) order[rk] = i;
-    if (rank == 0) lam[rk] = di;
-  }
-  {
-    int base = 0;
-    for (int ql = rank; ql < nleaf; ql += DCC) {
-      const int l0 = (ql * n) >> depth, l1 = ((ql + 1) * n) >> depth;
-      for (size_t x = tid; x < (size_t)(l1 - l0) * n; x += TRI_THREADS) {
-        const int r = (int)(x / n), c = (int)(x - (size_t)r * n);
-        W[L.Z + (size_t)(l0 + r) * n + c] = Zs[(size_t)(base + r) * n + c];
-      }
-      base += l1 - l0;
-    }
-  }
-  dcc_sync();  // no CTA leaves while another may still read its shared memory
-}
-
 // Row `row` of Z (eigenvectors of the tridiagonal matrix as columns) starts as
 // e_row and receives every recorded rotation in order.
 template <typename T>
@@ -1420,47 +1025,6 @@ __global__ void eig_back_transform(const EigProblem* __restrict__ probs) {
   for (int i = lane; i < n; i += 32) U[(size_t)i * k + warp] = (double)zr[i];
 }
 
-// The cluster variant of the divide and conquer for problems up to DCC_MAXN;
-// false (nothing launched) where the GPU or the size does not take it.
-bool launch_dc_cluster(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nmax, int* status) {
-  if (nmax > DCC_MAXN || nprob <= 0) return false;
-  size_t smem = 0;  // the largest layout of any size up to nmax (it is not monotonic in n)
-  for (int m = 1; m <= nmax; ++m) smem = std::max(smem, dcc_smem(m).bytes);
-  static int ok = -1;
-  static size_t smem_set = 0;
-  if (smem > smem_set) {
-    if (cudaFuncSetAttribute(eig_dc_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    smem_set = smem;
-    ok = -1;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nprob * DCC));
-  cfg.blockDim = dim3(TRI_THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = DCC;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (ok < 0) {
-    int nclusters = 0;
-    ok = (cudaOccupancyMaxActiveClusters(&nclusters, eig_dc_cluster, &cfg) == cudaSuccess && nclusters > 0) ? 1 : 0;
-    cudaGetLastError();
-  }
-  if (!ok) return false;
-  if (cudaLaunchKernelEx(&cfg, eig_dc_cluster, probs_dev, status) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return true;
-}
-
 template <typename T>
 void eig_launch(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nmax, int kmax, int* status) {
   const size_t smem_A = (size_t)nmax * (nmax + 1) * sizeof(T);  // row stride n + 1 in shared memory
@@ -1476,7 +1040,7 @@ void eig_launch(cudaStream_t st, const EigProblem* probs_dev, int nprob, int nma
   count_launches(kmax > 0 ? 3 : 2);
   eig_tridiag_ql<T><<<nprob, TRI_THREADS, use_smem ? smem_A : 0, st>>>(probs_dev, use_smem, status, dc ? 1 : 0);
   if constexpr (dc) {
-    if (!launch_dc_cluster(st, probs_dev, nprob, nmax, status)) eig_dc<<<nprob, TRI_THREADS, 0, st>>>(probs_dev, status);
+    eig_dc<<<nprob, TRI_THREADS, 0, st>>>(probs_dev, status);
   } else {
     const int rows_per_block = 32;
     eig_apply_rotations<T><<<dim3((nmax + rows_per_block - 1) / rows_per_block, nprob), rows_per_block, 0, st>>>(
