@@ -185,19 +185,44 @@ std::vector<double> run_selftest(int which) {
       }
     }
   } else if (which == 2) {
-    const int sizes[] = {136, 64, 7, 1, 200};
-    for (int n : sizes) {
-      // G = X X^T with a graded spectrum (columns scaled by 10^(-6 i / n))
+    // (size, spectrum): 0 G = X diag(10^(-6 k / n)) X^T (X Gaussian); with Q
+    // orthonormal (Gram-Schmidt of a Gaussian X on the host) G = Q diag(w) Q^T
+    // for 1: w_k = 10^(-6 k / 20) for k < 20 and 0 beyond (rank 20), 2: w_k =
+    // 1/2 for k < 40 (a 40-fold eigenvalue) and 1 + k / n beyond, 3: w_k =
+    // 10^(-30 k / n) (graded far below the double precision of the largest)
+    const int cases[][2] = {{136, 0}, {64, 0}, {7, 0}, {1, 0}, {200, 0}, {136, 1}, {136, 2}, {136, 3}, {200, 1}, {200, 3}};
+    for (const auto& cs : cases) {
+      const int n = cs[0], kind = cs[1];
       std::vector<double> x((size_t)n * n);
       DBuf X((size_t)n * n), G((size_t)n * n), U((size_t)n * n), L(n), W(eig_work_bytes(n, 64) / 8 + 64);
-      fill_gaussian(st, X.p, (size_t)n * n, 1.0, 4242 + n, 6);
+      fill_gaussian(st, X.p, (size_t)n * n, 1.0, 4242 + n + 1000 * kind, 6);
       if (cudaStreamSynchronize(st) != cudaSuccess) throw std::runtime_error("CUDA error: selftest eig");
       x = down(X.p, (size_t)n * n);
+      std::vector<double> w(n);
+      for (int k = 0; k < n; ++k)
+        w[k] = kind == 0   ? std::pow(10.0, -6.0 * k / n)
+               : kind == 1 ? (k < 20 ? std::pow(10.0, -6.0 * k / 20) : 0.0)
+               : kind == 2 ? (k < 40 ? 0.5 : 1.0 + (double)k / n)
+                           : std::pow(10.0, -30.0 * k / n);
+      if (kind != 0) {  // columns of x orthonormal (modified Gram-Schmidt, twice)
+        for (int pass = 0; pass < 2; ++pass)
+          for (int k = 0; k < n; ++k) {
+            for (int j = 0; j < k; ++j) {
+              double d = 0;
+              for (int i = 0; i < n; ++i) d += x[(size_t)i * n + j] * x[(size_t)i * n + k];
+              for (int i = 0; i < n; ++i) x[(size_t)i * n + k] -= d * x[(size_t)i * n + j];
+            }
+            double nr = 0;
+            for (int i = 0; i < n; ++i) nr += x[(size_t)i * n + k] * x[(size_t)i * n + k];
+            nr = std::sqrt(nr);
+            for (int i = 0; i < n; ++i) x[(size_t)i * n + k] /= nr;
+          }
+      }
       std::vector<double> g((size_t)n * n, 0.0);
       for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
           double s = 0;
-          for (int k = 0; k < n; ++k) s += x[(size_t)i * n + k] * x[(size_t)j * n + k] * std::pow(10.0, -6.0 * k / n);
+          for (int k = 0; k < n; ++k) s += x[(size_t)i * n + k] * x[(size_t)j * n + k] * w[k];
           g[(size_t)i * n + j] = s;
         }
       if (cudaMemcpy(G.p, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
