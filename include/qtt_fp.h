@@ -283,12 +283,12 @@ qtt_status qtt_host_dense(const qtt_params* params, int32_t which, double* out, 
  *   1  Householder QR: for 13 shapes x (FP64, FP32, FP32 followed by one
  *      FP64 Newton-Schulz step) the orthogonality max |Q^T Q - I| and the
  *      projection residual ||Y - Q Q^T Y|| / ||Y||
- *   2  eigensolver: for 10 (size, spectrum) cases x (FP64, FP32)
+ *   2  eigensolver: for 11 (size, spectrum) cases x (FP64, FP32)
  *      max |G U - U diag(lam)| / max |G|, max |U^T U - I| and 1 if the
  *      eigenvalues are not descending; cases (136, 64, 7, 1, 200 with the
  *      graded spectrum 10^(-6 k / n)), then (136, rank 20), (136, a 40-fold
  *      eigenvalue), (136, graded to 1e-30), (200, rank 20), (200, graded to
- *      1e-30)
+ *      1e-30), (520, graded)
  *   3  accumulation bias of the tensor-core GEMM: positive operands, K = 32,
  *      256, 2048, modes (TF32X3, BF16X3), accumulation (one FP32 accumulator,
  *      FP64 sum of per-k-block accumulators): mean signed and max relative error

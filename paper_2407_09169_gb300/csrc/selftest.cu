@@ -190,7 +190,7 @@ std::vector<double> run_selftest(int which) {
     // for 1: w_k = 10^(-6 k / 20) for k < 20 and 0 beyond (rank 20), 2: w_k =
     // 1/2 for k < 40 (a 40-fold eigenvalue) and 1 + k / n beyond, 3: w_k =
     // 10^(-30 k / n) (graded far below the double precision of the largest)
-    const int cases[][2] = {{136, 0}, {64, 0}, {7, 0}, {1, 0}, {200, 0}, {136, 1}, {136, 2}, {136, 3}, {200, 1}, {200, 3}};
+    const int cases[][2] = {{136, 0}, {64, 0}, {7, 0}, {1, 0}, {200, 0}, {136, 1}, {136, 2}, {136, 3}, {200, 1}, {200, 3}, {520, 0}};
     for (const auto& cs : cases) {
       const int n = cs[0], kind = cs[1];
       std::vector<double> x((size_t)n * n);

@@ -50,13 +50,14 @@ def test_householder_qr():
 
 
 def test_eigensolver():
-    """Ten (size, spectrum) cases: the graded Gram matrices at n = 136, 64, 7,
-    1, 200, and, with orthonormal eigenvectors, rank 20, a 40-fold eigenvalue
-    and a spectrum graded to 1e-30 (the deflation paths of the FP64 divide and
-    conquer: negligible z components, equal poles rotated together, roots far
-    below the largest eigenvalue's precision)."""
+    """Eleven (size, spectrum) cases: the graded Gram matrices at n = 136, 64,
+    7, 1, 200, and, with orthonormal eigenvectors, rank 20, a 40-fold
+    eigenvalue and a spectrum graded to 1e-30 (the deflation paths of the FP64
+    divide and conquer: negligible z components, equal poles rotated together,
+    roots far below the largest eigenvalue's precision), and n = 520 (five
+    merge levels; the tridiagonalisation in global memory)."""
     v = np.array(pkg.qtt_selftest(2)[:-1]).reshape(-1, 2, 3)  # case, precision, (res, orth, order)
-    assert v.shape[0] == 10
+    assert v.shape[0] == 11
     for case in v:
         (r64, o64, ord64), (r32, o32, ord32) = case
         assert r64 < 1e-12 and o64 < 1e-12 and ord64 == 0
