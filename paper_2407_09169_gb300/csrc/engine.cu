@@ -752,7 +752,7 @@ void Engine::run_stage(Term* terms, int nt, DevMps& out, int stage) {
   // 3. SVD truncation of every bond to chi.  The state is left-orthonormal,
   // so the squared singular values at bond n are the eigenvalues of the
   // Gram matrix R_n of its right part.  All R_n come from one right-to-left
-  // FP64 contraction pass; all bond eigensolves run in one batched launch;
+  // FP64 contraction pass; all bond eigensolves run in one batched pass;
   // the projectors U_n U_n^T are then inserted into every core independently.
   gram_pass(mid_);
   if (!trunc_bonds_.empty()) {
@@ -985,7 +985,7 @@ int Engine::check_status(std::string& msg) {
     return 5;  // QTT_ETIMEOUT
   }
   if (h[0] & 2) {
-    msg = "eigen-decomposition hit its QL sweep cap";
+    msg = "a QL iteration of the eigen-decomposition hit its sweep cap";
     QTT_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), st_));
     return 4;  // QTT_ENOCONV
   }

@@ -135,13 +135,14 @@ void qr_thin(cudaStream_t st, int m, int n, const double* A, double* Qout, void*
 
 // Symmetric eigen-decomposition of an n x n row-major matrix G (n <= 1024).
 // Eigenvalues descending in lam[0..n); eigenvectors of the leading k in the
-// columns of U (n x k, row-major).  Computed in float or double; work must
-// hold eig_work_bytes(n, prec_bits) bytes.  *status |= 2 when the QL
-// iteration hits its cap.
+// columns of U (n x k, row-major).  Computed in float (Householder
+// tridiagonalisation, implicit QL) or double (tridiagonalisation, divide and
+// conquer with QL on its leaves); work must hold eig_work_bytes(n, prec_bits)
+// bytes.  *status |= 2 when a QL iteration hits its cap.
 size_t eig_work_bytes(int n, int prec_bits);  // plus 256 + sizeof(EigProblem) for eig_sym
 void eig_sym(cudaStream_t st, int n, int k, const double* G, double* U, double* lam, void* work, int prec_bits,
              int* status);
-// Many independent problems in one launch (one block per problem); the
+// Many independent problems in one pass (one block per problem); the
 // descriptors live in device memory, nmax / kmax bound every n / k.
 struct EigProblem {
   int n = 0, k = 0;
