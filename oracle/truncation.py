@@ -10,12 +10,15 @@ decomposition ("Matrix product state algorithm").  The reading taken here
 N binary sites stored as the vector X[i_1 ... i_N] (site 1 most significant),
 X_(n) its unfolding at cut n (2^n rows, 2^(N-n) columns) and Pi_n the
 orthogonal projector onto the k_n leading left singular vectors of X_(n)
-(k_n = min(chi, #{sigma > tol sigma_1})), acting on the first n sites,
+(k_n = min(chi, #{sigma > tol sigma_1}), singular values at or below their
+FP64 rounding counting as zero), acting on the first n sites,
 
     T(X) = Pi_1 Pi_2 ... Pi_{N-1} X          (Pi_{N-1} applied first).
 
 Where the leading subspaces are separated from the rest (sigma_k > sigma_{k+1}
-at every cut) T is differentiable, and its adjoint applied to a cotangent
+at every cut, and, where k_n is below chi, the rank held by tol against the
+small singular values a perturbation creates) T is differentiable, and its
+adjoint applied to a cotangent
 Ybar (the vector-Jacobian product) is the sum of
 
 * the part with the projectors held fixed: Pi_{N-1} ... Pi_1 Ybar;
@@ -31,8 +34,8 @@ Ybar (the vector-Jacobian product) is the sum of
   (lambda_i - lambda_j) / ((lambda_i - lambda_j)^2 + eps^2) that keeps the
   gaps finite where eigenvalues meet.
 
-Plain numpy FP64; eigenpairs by numpy.linalg.eigh, sizes kept small (the
-unfoldings of up to ~2^12 entries).
+Plain numpy FP64; singular values and vectors by numpy.linalg.svd of each
+unfolding, sizes kept small (tensors of up to ~2^12 entries).
 """
 from __future__ import annotations
 
@@ -45,18 +48,26 @@ def unfold(X, N: int, n: int):
 
 
 def _cut_eig(X, N: int, n: int):
-    """All eigenpairs of X_(n) X_(n)^T, eigenvalues in descending order."""
+    """All eigenpairs of X_(n) X_(n)^T in descending order, from the SVD of
+    X_(n): the squared singular values padded with zeros, and the full set of
+    left singular vectors (null space included); also the singular values."""
     A = unfold(X, N, n)
-    lam, U = np.linalg.eigh(A @ A.T)
-    return lam[::-1].copy(), U[:, ::-1].copy()
+    U, s, _ = np.linalg.svd(A, full_matrices=True)
+    lam = np.zeros(A.shape[0])
+    lam[: s.size] = s * s
+    return lam, U, s
 
 
-def kept_count(lam, chi: int, tol: float) -> int:
-    """min(chi, #{sigma_i > tol sigma_1}) with sigma = sqrt(lam)."""
-    lam = np.clip(lam, 0.0, None)
-    if lam.size == 0 or lam[0] <= 0.0:
+def kept_count(sigma, chi: int, tol: float, shape) -> int:
+    """min(chi, #{sigma_i > tol sigma_1}) for the singular values sigma of a
+    matrix of the given shape; a singular value at or below its FP64 rounding,
+    max(shape) * eps * sigma_1, is zero, so tol = 0 keeps the numerical rank."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    if sigma.size == 0 or sigma[0] <= 0.0:
         return 0
-    return int(min(chi, np.count_nonzero(np.sqrt(lam) > tol * np.sqrt(lam[0]))))
+    floor = max(shape) * np.finfo(np.float64).eps * sigma[0]
+    resolved = sigma > floor
+    return int(min(chi, np.count_nonzero(resolved & (sigma > tol * sigma[0]))))
 
 
 def projectors(X, N: int, chi: int, tol: float = 0.0):
@@ -64,8 +75,8 @@ def projectors(X, N: int, chi: int, tol: float = 0.0):
     left singular vectors, their count and all eigenpairs of X_(n) X_(n)^T."""
     out = {}
     for n in range(1, N):
-        lam, U = _cut_eig(X, N, n)
-        k = kept_count(lam, chi, tol)
+        lam, U, sigma = _cut_eig(X, N, n)
+        k = kept_count(sigma, chi, tol, (2 ** n, 2 ** (N - n)))
         out[n] = (U[:, :k], k, lam, U)
     return out
 

@@ -111,3 +111,31 @@ def test_lorentzian_broadening_tends_to_the_exact_backward():
     errs = [np.abs(tr.truncate_vjp(X, Yb, N, chi, eps=e * lam1) - exact).max() for e in (1e-2, 1e-4, 1e-6)]
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] <= 1e-6 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_vjp_at_frozen_rank_below_chi(seed):
+    """A tensor train of bond 3 with chi = 5 and tol = 1e-4: the kept count at
+    its rank-3 cuts is the rank, held by tol against the O(h) singular values a
+    perturbation adds, and the backward runs through the null-space term alone
+    there; central differences with h small against tol sigma_1 agree."""
+    rng = np.random.default_rng(40 + seed)
+    N, chi, tol = 8, 5, 1e-4
+    X = _random_tt(N, 3, rng)
+    P = tr.projectors(X, N, chi, tol)
+    assert [P[n][1] for n in range(1, N)] == [2, 3, 3, 3, 3, 3, 2]
+    for n in range(1, N):
+        s = np.linalg.svd(tr.unfold(X, N, n), compute_uv=False)
+        assert s[P[n][1] - 1] > 100 * tol * s[0]
+    Yb = rng.standard_normal(2 ** N)
+    g = tr.truncate_vjp(X, Yb, N, chi, tol)
+    h = 1e-8 * np.abs(X).max()
+    for _ in range(3):
+        D = rng.standard_normal(2 ** N)
+        fd = (Yb @ tr.truncate(X + h * D, N, chi, tol) - Yb @ tr.truncate(X - h * D, N, chi, tol)) / (2 * h)
+        assert abs(fd - g @ D) <= 1e-5 * max(abs(fd), 1.0), (fd, g @ D)
+    # tol = 0 keeps the numerical rank: rounding-level singular values are zeros
+    P0 = tr.projectors(X, N, chi, 0.0)
+    assert [P0[n][1] for n in range(1, N)] == [2, 3, 3, 3, 3, 3, 2]
+    g0 = tr.truncate_vjp(X, Yb, N, chi, 0.0)
+    assert np.abs(g0 - g).max() <= 1e-10 * np.abs(g).max()
