@@ -188,6 +188,42 @@ qtt_status qtt_step(qtt_ctx* ctx, int32_t nsteps);
  * (rk_variant 0). */
 qtt_status qtt_grad(qtt_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* out, int64_t cap, int64_t* written);
 
+/* Backward of the bond truncation (the derivative of the SVD rounding of
+ * section "Matrix product state algorithm"), context-free, on the device.
+ * The truncation is the simultaneous one of every bond that the stages use:
+ * T(X) = Pi_1 ... Pi_{N-1} X, Pi_n the orthogonal projector onto the k_n
+ * leading left singular vectors of X's unfolding at cut n (first n sites
+ * against the rest), k_n = min(chi, #{lambda_i > max(tol^2, 1e-24)
+ * lambda_0}) over the eigenvalues lambda of the cut's right Gram.  The call
+ * returns (dT/dX)^T ybar, exact where every kept eigenvalue is separated
+ * from the discarded ones; eps > 0 replaces each 1 / (lambda_i - lambda_j)
+ * by its Lorentzian broadening (lambda_i - lambda_j) / ((lambda_i -
+ * lambda_j)^2 + eps^2) (eps in the units of lambda, i.e. of |X|^2).
+ *   N       number of binary sites, 2 .. 64
+ *   rx      host array of N + 1 bonds of x (rx[0] = rx[N] = 1, rx[n] <= 1024,
+ *           rx[n] <= 2 rx[n-1])
+ *   x       device array: the N cores of X, core n being [rx[n]][2][rx[n+1]]
+ *           row-major (site 1, the most significant index, first), stored
+ *           one after another; cores 0 .. N-2 left-orthonormal (each
+ *           (2 rx[n]) x rx[n+1] matrix has orthonormal columns), which is not
+ *           checked: otherwise the result is not the derivative
+ *   sy, ybar  the cotangent as a train of any bonds sy (<= 1024), same layout
+ *   xbar    device array receiving the result as a train of bonds 1,
+ *           2 rx[1], ..., 2 rx[N-1], 1 in the same layout: site 1 [Q_1 D_1],
+ *           site n [[Q_n D_n], [0 Q_n]], site N [[E], [x's last core]]; cap
+ *           is its room in doubles, *written the count used
+ *   kept    host array receiving the N - 1 kept counts k_n
+ *   stream  CUDA stream (NULL: the legacy default stream); the call
+ *           allocates and frees its work space and synchronises the stream
+ * Returns QTT_EINVAL for bad sizes or pointers (no device work done; the
+ * message names the check), QTT_ECUDA on a CUDA failure, QTT_ESTATE when the
+ * eigen-decomposition reports a failure.  The paper rounds with an SVD but
+ * does not differentiate it; this is the backward a discrete adjoint through
+ * the truncated steps would use. */
+qtt_status qtt_truncate_vjp(int32_t N, const int32_t* rx, const double* x, const int32_t* sy, const double* ybar,
+                            int32_t chi, double tol, double eps, double* xbar, int64_t cap, int64_t* written,
+                            int32_t* kept, void* stream);
+
 /* Batched stepping of independent PDFs (no counterpart in the paper, which
  * steps one PDF): advances each of ctxs[0..n) by nsteps steps, enqueueing the
  * work of every context before synchronising any of them, so that contexts

@@ -99,8 +99,11 @@ def load_library(path: str | None = None):
     lib.qtt_version.restype = C.c_char_p
     lib.qtt_host_dense.argtypes = [P(QttParams), C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
     lib.qtt_selftest.argtypes = [C.c_int32, P(C.c_double), C.c_int64, P(C.c_int64)]
+    lib.qtt_truncate_vjp.argtypes = [C.c_int32, P(C.c_int32), C.c_void_p, P(C.c_int32), C.c_void_p, C.c_int32,
+                                     C.c_double, C.c_double, C.c_void_p, C.c_int64, P(C.c_int64), P(C.c_int32),
+                                     C.c_void_p]
     for fn in ("qtt_init", "qtt_step", "qtt_step_many", "qtt_grad", "qtt_observe", "qtt_compare", "qtt_save", "qtt_load", "qtt_host_dense",
-               "qtt_selftest"):
+               "qtt_selftest", "qtt_truncate_vjp"):
         getattr(lib, fn).restype = C.c_int
     _lib = lib
     return lib
@@ -327,3 +330,33 @@ def qtt_selftest(which: int, cap: int = 4096) -> np.ndarray:
     written = C.c_int64(0)
     _check(lib.qtt_selftest(int(which), out.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(written)), None)
     return out[: written.value]
+
+
+def _device_ptr(t, name: str) -> int:
+    """Device address of a contiguous float64 CUDA tensor (or a raw int)."""
+    if isinstance(t, int):
+        return t
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+        raise QttError(QTT_EINVAL, f"{name} must be a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def qtt_truncate_vjp(rx, x, sy, ybar, chi: int, tol: float, eps: float, xbar, cap: int, stream=None):
+    """Backward of the bond truncation (see include/qtt_fp.h): x, ybar, xbar
+    are device buffers (CUDA tensors or addresses), rx and sy the bond lists.
+    Returns (doubles written, kept counts)."""
+    lib = load_library()
+    rx = [int(v) for v in rx]
+    sy = [int(v) for v in sy]
+    N = len(rx) - 1
+    if len(sy) != N + 1:
+        raise QttError(QTT_EINVAL, "rx and sy must have the same length")
+    rxa = (C.c_int32 * len(rx))(*rx)
+    sya = (C.c_int32 * len(sy))(*sy)
+    kept = (C.c_int32 * max(N - 1, 1))()
+    written = C.c_int64(0)
+    st = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    _check(lib.qtt_truncate_vjp(N, rxa, C.c_void_p(_device_ptr(x, "x")), sya, C.c_void_p(_device_ptr(ybar, "ybar")),
+                                int(chi), float(tol), float(eps), C.c_void_p(_device_ptr(xbar, "xbar")), int(cap),
+                                C.byref(written), kept, st), None)
+    return written.value, [kept[i] for i in range(N - 1)]

@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqtt_fp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["host_tt.cpp", "cross.cpp", "model.cpp", "capi.cpp", "gemm_f64.cu", "gemm_tc.cu", "gemm_small.cu", "qr.cu", "eig.cu",
-           "misc.cu", "engine.cu", "adjoint.cu", "selftest.cu", "points_static.cu"]
+           "misc.cu", "engine.cu", "adjoint.cu", "selftest.cu", "points_static.cu", "trunc_vjp.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", ARCH, "-I" + INCLUDE]
 

@@ -755,6 +755,46 @@ qtt_status qtt_observe_points_noalloc(qtt_ctx* ctx, double* inout, int64_t cap, 
   }
 }
 
+qtt_status qtt_truncate_vjp(int32_t N, const int32_t* rx, const double* x, const int32_t* sy, const double* ybar,
+                            int32_t chi, double tol, double eps, double* xbar, int64_t cap, int64_t* written,
+                            int32_t* kept, void* stream) {
+  if (written) *written = 0;
+  try {
+    if (N < 2 || N > 64) throw std::runtime_error("EINVAL: N must be in [2, 64]");
+    if (!rx || !sy || !x || !ybar || !xbar || !kept) throw std::runtime_error("EINVAL: a pointer argument is NULL");
+    if (rx[0] != 1 || rx[N] != 1 || sy[0] != 1 || sy[N] != 1)
+      throw std::runtime_error("EINVAL: the end bonds of both trains must be 1");
+    for (int n = 1; n < N; ++n) {
+      if (rx[n] < 1 || sy[n] < 1) throw std::runtime_error("EINVAL: a bond is below 1");
+      if (rx[n] > 1024 || sy[n] > 1024) throw std::runtime_error("EINVAL: a bond is above 1024");
+      if (rx[n] > 2 * rx[n - 1])
+        throw std::runtime_error("EINVAL: rx[n] > 2 rx[n-1]: the cores of x cannot be left-orthonormal");
+    }
+    if (chi < 1) throw std::runtime_error("EINVAL: chi < 1");
+    if (!(tol >= 0.0) || !(eps >= 0.0) || !std::isfinite(tol) || !std::isfinite(eps))
+      throw std::runtime_error("EINVAL: tol and eps must be finite and >= 0");
+    std::vector<int> r(rx, rx + N + 1), s(sy, sy + N + 1);
+    const size_t need = qtt::truncate_vjp_out_elems(N, r.data());
+    if (cap < 0 || (size_t)cap < need)
+      throw std::runtime_error("EINVAL: xbar has room for " + std::to_string(cap) + " doubles, " +
+                               std::to_string(need) + " are needed");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      throw std::runtime_error("CUDA: no usable CUDA device");
+    }
+    std::vector<int> k((size_t)(N - 1), 0);
+    qtt::truncate_vjp((cudaStream_t)stream, N, r.data(), x, s.data(), ybar, chi, tol, eps, xbar, k.data());
+    for (int n = 0; n + 1 < N; ++n) kept[n] = k[(size_t)n];
+    if (written) *written = (int64_t)need;
+    g_init_err.clear();
+    return QTT_OK;
+  } catch (const std::exception& ex) {
+    g_init_err = ex.what();
+    return classify(g_init_err);
+  }
+}
+
 qtt_status qtt_selftest(int32_t which, double* out, int64_t cap, int64_t* written) {
   if (written) *written = 0;
   try {

@@ -301,4 +301,15 @@ class Engine {
   size_t pp_elems_ = 0;
 };
 
+// Backward of the simultaneous bond truncation in tensor-train form
+// (trunc_vjp.cu).  x: N cores [rx[n]][2][rx[n+1]] concatenated in site order,
+// the first N-1 left-orthonormal; ybar: N cores of bonds sy; xbar receives
+// the vector-Jacobian product as a train of bonds 1, 2 rx[1], ..,
+// 2 rx[N-1], 1 (truncate_vjp_out_elems doubles); kept[0..N-1) the kept
+// counts min(chi, #{lambda_i > max(tol^2, 1e-24) lambda_0}) of the right
+// Grams.  Device pointers; synchronises st; throws on failure.
+size_t truncate_vjp_out_elems(int N, const int* rx);
+void truncate_vjp(cudaStream_t st, int N, const int* rx, const double* x, const int* sy, const double* ybar, int chi,
+                  double tol, double eps, double* xbar, int* kept);
+
 }  // namespace qtt
