@@ -212,6 +212,69 @@ def roofline_traffic():
     return rec.get("dram_bytes_per_launch") if rec.get("gemm_tc_sha16") == sha else None
 
 
+def truncate_vjp_flops(r, s, k):
+    """Algorithmic FP64 flops of one qtt_truncate_vjp call: 2 M N K for every
+    product the pass issues (bonds r of X, s of the cotangent, kept counts
+    k[1..N-1]), and per cut the eigen-decomposition's Householder
+    tridiagonalisation (4/3 n^3) and back-transformation (2 n^3)."""
+    N = len(r) - 1
+    g = 2 * r[N - 1] * r[N - 1] * 2
+    for n in range(N - 1, 1, -1):
+        g += 2 * (2 * r[n - 1]) * r[n] * r[n] + 2 * r[n - 1] * r[n - 1] * (2 * r[n])
+    for n in range(1, N):
+        g += 2 * r[n] * r[n] * k[n]
+        g += 2 * r[n - 1] * (2 * s[n]) * s[n - 1] + 2 * r[n] * s[n] * (2 * r[n - 1]) + 2 * r[n] * s[n] * r[n]
+    g += 2 * r[N - 1] * 2 * s[N - 1] + 2 * s[N - 1] * r[N - 1] * 2
+    for n in range(2, N):
+        g += 2 * (2 * r[n - 1]) * r[n] * r[n]
+    for n in range(N - 1, 1, -1):
+        g += 2 * (2 * s[n - 1]) * r[n] * s[n] + 2 * s[n - 1] * r[n - 1] * (2 * r[n])
+    for n in range(1, N):
+        rl, rr, sr, kk = r[n - 1], r[n], s[n], k[n]
+        nd = rr - kk
+        g += 2 * (2 * rl) * rr * sr + 2 * rr * rr * (2 * rl) + 2 * rr * rr * kk
+        if kk and nd:
+            g += 2 * nd * rr * rr + 2 * nd * kk * rr + 2 * rr * kk * nd + 2 * rr * rr * kk
+        g += 2 * (2 * rl) * rr * rr + 2 * rr * rr * (2 * rl) + 2 * (2 * rl) * rr * rr
+    e = sum((4.0 / 3.0) * r[n] ** 3 + 2.0 * r[n] ** 3 for n in range(1, N))
+    return float(g), float(e)
+
+
+def truncate_vjp_bench(q, torch, stream, nsites, ell, chi, fp64_peak, calls=3):
+    """Times qtt_truncate_vjp at a step's sizes (inputs from
+    workload.make_truncation_trains: X of bond ell in the zip-up's
+    left-orthonormal form, the cotangent of bond chi); CUDA events on the
+    bench stream around `calls` calls after one untimed call."""
+    r, xh, sb, yh = workload.make_truncation_trains(nsites, ell, chi)
+    xd = torch.from_numpy(xh).cuda()
+    yd = torch.from_numpy(yh).cuda()
+    ro = [1] + [2 * v for v in r[1:-1]] + [1]
+    cap = sum(ro[n] * 2 * ro[n + 1] for n in range(nsites))
+    out = torch.empty(cap, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    _, kept = q.qtt_truncate_vjp(r, xd, sb, yd, chi, 1e-14, 0.0, out, cap, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(calls):
+        q.qtt_truncate_vjp(r, xd, sb, yd, chi, 1e-14, 0.0, out, cap, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / calls
+    g, e = truncate_vjp_flops(r, sb, [0] + list(kept))
+    ach = (g + e) / (ms * 1e-3) / 1e12
+    return {
+        "config": f"{nsites} sites, X bond {ell} (random isometries, Gaussian last core), cotangent bond {chi}, "
+                  f"chi {chi}, tol 1e-14, eps 0",
+        "ms_per_call": ms, "kept_min": int(min(kept)), "kept_max": int(max(kept)),
+        "gemm_gflop": g / 1e9, "eig_gflop": e / 1e9,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": ach / fp64_peak, "peak_source": "of measured: FP64 DFMA (qtt_selftest 6, this run)"},
+        "timing": f"CUDA events on the bench stream around {calls} calls after one untimed call; each call "
+                  "includes its work-space allocation, one host read of the eigenvalues and a stream synchronize",
+    }
+
+
 def oracle_rate(seconds_per_step: float, wl: str):
     cells_sample = 2 ** (5 * ORACLE_SAMPLE_BITS)
     cells_full = 2 ** (5 * workload.WORKLOADS[wl]["bits"])
@@ -655,6 +718,13 @@ def run_mine(args, rank, world, local_rank):
                       "device synchronize on both sides, after an untimed 2-step call",
         }
 
+    # ---- backward of the bond truncation (qtt_truncate_vjp) at this workload's sizes, rank 0 at N = 1 only
+    tvjp = None
+    if rank == 0 and world == 1:
+        nsites = int(sum(p["bits"]))
+        tvjp = truncate_vjp_bench(q, torch, stream, nsites, int(p["chi_max"]) + int(p.get("oversample", 8)),
+                                  int(p["chi_max"]), fp64_peak)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -670,7 +740,7 @@ def run_mine(args, rank, world, local_rank):
                       "discarded_weight_last_step": scal["discarded_weight"],
                       "discarded_weight_rel": scal["discarded_weight"] / scal["norm2"] if scal["norm2"] > 0 else None},
             "parity": parity, "fp64_path": fp64_path, "config1": config1, "config2": config2, "batched": batched,
-            "adjoint": adjoint,
+            "adjoint": adjoint, "truncate_vjp": tvjp,
         }
         print(json.dumps(line), flush=True)
 

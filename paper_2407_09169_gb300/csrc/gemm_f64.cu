@@ -324,6 +324,18 @@ void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double
   }
 }
 
+void gemm_f64_tiles16(cudaStream_t st, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
+                      OutView C) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0 || M > 65535 * 16) {  // empty contraction, or more row tiles than grid.y holds
+    gemm_f64(st, M, N, K, 1, 1, alpha, A, B, beta, C, nullptr, 0);
+    return;
+  }
+  count_launches(1);
+  launch_pdl(gemm_f64_t16_kernel, dim3((N + 15) / 16, (M + 15) / 16, 1), dim3(256), 0, st, M, N, K, 1, alpha, A, B,
+             beta, C);
+}
+
 void newton_schulz_step(cudaStream_t st, int m, int n, const double* Q, double* G, double* out) {
   if (m <= 0 || n <= 0) return;
   count_launches(2);

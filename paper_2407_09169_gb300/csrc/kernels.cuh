@@ -117,6 +117,12 @@ __device__ __forceinline__ double eval_point_warp(const Chain& f, BitFn bit, dou
 void gemm_f64(cudaStream_t st, int M, int N, int K, int outer, int inner, double alpha, MatView A,
               MatView B, double beta, OutView C, double* ws, size_t ws_elems);
 int gemm_split_k(int M, int N, int K, int batch);
+// One product (no batch) on 16 x 16 output tiles, whatever its shape: for
+// the small and skinny products of short chains, where a 64 x 64 tile would
+// issue mostly masked FP64 work (each k is summed in the same order as by
+// gemm_f64, so the results are the same).
+void gemm_f64_tiles16(cudaStream_t st, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
+                      OutView C);
 // C = alpha * sum_k ws[b][k] + beta * C: the fixed-order reduction of split-K partial tiles.
 void splitk_reduce(cudaStream_t st, int M, int N, int inner, int splitk, int batch, double alpha, const double* ws,
                    double beta, OutView C);

@@ -130,9 +130,12 @@ OutView outm(double* p, long long ld) {
   return v;
 }
 
-// C (M x N, leading dimension N) = alpha A B + beta C, one product.
+// C (M x N, leading dimension N) = alpha A B + beta C, one product on 16 x 16
+// output tiles: the products here are at most a few hundred on a side and
+// many are skinny (the discarded block is often a few columns), where a
+// 64 x 64 tile would spend most of the scarce FP64 issue on masked rows.
 void mm(cudaStream_t st, int M, int N, int K, double alpha, MatView A, MatView B, double beta, double* Cp) {
-  gemm_f64(st, M, N, K, 1, 1, alpha, A, B, beta, outm(Cp, N), nullptr, 0);
+  gemm_f64_tiles16(st, M, N, K, alpha, A, B, beta, outm(Cp, N));
 }
 
 struct DevBuf {

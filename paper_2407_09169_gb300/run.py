@@ -2,10 +2,14 @@
 
     python -m paper_2407_09169_gb300.run --workload large --precision fp32 --steps 1
     python -m paper_2407_09169_gb300.run --adjoint --precision fp32 --steps 4 --ckpt 2
+    python -m paper_2407_09169_gb300.run --workload large --truncate-vjp --steps 2
 
 Builds the library if needed, creates a context for the named workload
 (workload.WORKLOADS, or --paper for the paper's flow case at that grid and
-chi), advances it and prints the scalar observables as one JSON line.  Used
+chi), advances it and prints the scalar observables as one JSON line; with
+--truncate-vjp it instead calls the backward of the bond truncation --steps
+times on trains of the workload's sizes (workload.make_truncation_trains:
+bond chi_max + 8 in left-orthonormal form, cotangent bond chi_max).  Used
 as the profiled command of the ncu summaries (with QTT_GRAPHS=0 every step
 runs eagerly, so every kernel launch appears individually).
 """
@@ -36,9 +40,26 @@ def main(argv=None):
     ap.add_argument("--adjoint", action="store_true",
                     help="run qtt_grad on the adjoint configuration (workload.make_adjoint_params) instead")
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval of --adjoint")
+    ap.add_argument("--truncate-vjp", action="store_true",
+                    help="call qtt_truncate_vjp --steps times at the workload's sizes instead")
     args = ap.parse_args(argv)
     qbuild.build()
     w = workload.WORKLOADS[args.workload]
+    if args.truncate_vjp:
+        import torch
+        nsites, chi = 5 * w["bits"], w["chi_max"]
+        r, xh, sy, yh = workload.make_truncation_trains(nsites, chi + 8, chi, seed=args.seed + 11)
+        xd, yd = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+        cap = sum((1 if n == 0 else 2 * r[n]) * 2 * (1 if n == nsites - 1 else 2 * r[n + 1]) for n in range(nsites))
+        out = torch.empty(cap, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, kept = q.qtt_truncate_vjp(r, xd, sy, yd, chi, 1e-14, 0.0, out, cap)
+        torch.cuda.synchronize()
+        print(json.dumps({"sites": nsites, "bond": chi + 8, "chi": chi, "kept": kept, "calls": args.steps,
+                          "wall_s": time.perf_counter() - t0}))
+        return
     if args.adjoint:
         p = workload.make_adjoint_params(seed=args.seed, precision=args.precision)
         t0 = time.perf_counter()

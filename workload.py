@@ -172,3 +172,19 @@ def make_adjoint_params(seed: int = 0, precision: str = "fp32") -> dict:
                     precision=precision)
     p["icmodes"] = draw_ic_modes(seed, ADJOINT["n_ic"])
     return p
+
+
+def make_truncation_trains(nsites: int, ell: int, chi: int, seed: int = 11):
+    """Inputs of the truncation backward at a step's sizes: X as nsites cores
+    [r_n][2][r_{n+1}] with r_n = min(2^n, 2^(nsites-n), ell), the first
+    nsites-1 random isometries (orthonormal columns of a Gaussian matrix, the
+    form the zip-up leaves) and a Gaussian last core; the cotangent as a
+    Gaussian train of bonds min(2^n, 2^(nsites-n), chi).  Returns (r, x, s, y)
+    with x and y the cores flattened one after another."""
+    rng = np.random.default_rng(seed)
+    r = [min(2 ** n, 2 ** (nsites - n), ell) for n in range(nsites + 1)]
+    s = [min(2 ** n, 2 ** (nsites - n), chi) for n in range(nsites + 1)]
+    xc = [np.linalg.qr(rng.standard_normal((2 * r[n], r[n + 1])))[0] for n in range(nsites - 1)]
+    xc.append(rng.standard_normal((2 * r[nsites - 1], 1)))
+    yc = [rng.standard_normal(s[n] * 2 * s[n + 1]) for n in range(nsites)]
+    return r, np.concatenate([c.ravel() for c in xc]), s, np.concatenate(yc)
