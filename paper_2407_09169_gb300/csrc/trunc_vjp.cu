@@ -43,6 +43,7 @@ namespace qtt {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kCutStreams = 4;  // streams the per-cut cores are spread over
 
 int grid_for(long long total) {
   long long b = (total + kThreads - 1) / kThreads;
@@ -138,6 +139,28 @@ void mm(cudaStream_t st, int M, int N, int K, double alpha, MatView A, MatView B
   gemm_f64_tiles16(st, M, N, K, alpha, A, B, beta, outm(Cp, N));
 }
 
+// Streams and events of one call, destroyed on every path out of it.
+struct Streams {
+  std::vector<cudaStream_t> s;
+  std::vector<cudaEvent_t> ev;
+  void make(int ns, int nev) {
+    for (int i = 0; i < ns; ++i) {
+      cudaStream_t x;
+      QTT_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      s.push_back(x);
+    }
+    for (int i = 0; i < nev; ++i) {
+      cudaEvent_t e;
+      QTT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ev.push_back(e);
+    }
+  }
+  ~Streams() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaStream_t x : s) cudaStreamDestroy(x);
+  }
+};
+
 struct DevBuf {
   void* p = nullptr;
   ~DevBuf() {
@@ -203,9 +226,11 @@ void truncate_vjp(cudaStream_t st, int N, const int* rx, const double* x, const 
   }
   for (int n = 0; n < N; ++n) eO[n] = take((size_t)(r[n] * s[n]));
   const size_t lastO = take((size_t)(2 * r[N - 1]));
-  enum { T_A, T_G, T_H, T_S, T_VF, T_AM, T_B1, T_B, T_C1, T_GAM, T_U, T_GA, T_COUNT };
-  size_t tO[T_COUNT];
-  for (int t = 0; t < T_COUNT; ++t) tO[t] = take(tmax);
+  const size_t taO = take(tmax), trO = take(tmax);
+  enum { T_G, T_H, T_S, T_VF, T_AM, T_B1, T_B, T_C1, T_GAM, T_U, T_GA, T_COUNT };
+  size_t tO[kCutStreams][T_COUNT];
+  for (int c = 0; c < kCutStreams; ++c)
+    for (int t = 0; t < T_COUNT; ++t) tO[c][t] = take(tmax);
   const size_t ndbl = off;
 
   // byte work area: eigensolver work per cut, descriptors, status
@@ -228,8 +253,8 @@ void truncate_vjp(cudaStream_t st, int N, const int* rx, const double* x, const 
   int* status = (int*)(B + statO);
   QTT_CUDA(cudaMemsetAsync(W, 0, ndbl * sizeof(double), st));
   QTT_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-  double* T[T_COUNT];
-  for (int t = 0; t < T_COUNT; ++t) T[t] = W + tO[t];
+  double* const TA = W + taO;
+  double* const TR = W + trO;
 
   // right Grams: G_{N-1} = C C^T, G_{n-1} = sum_i Q_n[:, i, :] G_n Q_n[:, i, :]^T
   {
@@ -238,8 +263,8 @@ void truncate_vjp(cudaStream_t st, int N, const int* rx, const double* x, const 
   }
   for (int n = N - 1; n >= 2; --n) {
     const long long rl = r[n - 1], rr = r[n];
-    mm(st, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(Xs(n), rr, 1), mat(W + gO[n], rr, 1), 0.0, T[T_A]);
-    mm(st, (int)rl, (int)rl, (int)(2 * rr), 1.0, mat(T[T_A], 2 * rr, 1), mat(Xs(n), 1, 2 * rr), 0.0, W + gO[n - 1]);
+    mm(st, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(Xs(n), rr, 1), mat(W + gO[n], rr, 1), 0.0, TA);
+    mm(st, (int)rl, (int)rl, (int)(2 * rr), 1.0, mat(TA, 2 * rr, 1), mat(Xs(n), 1, 2 * rr), 0.0, W + gO[n - 1]);
   }
 
   // all eigenpairs of every right Gram, one block per cut
@@ -291,75 +316,101 @@ void truncate_vjp(cudaStream_t st, int N, const int* rx, const double* x, const 
     mm(st, (int)rr, (int)rr, k[(size_t)n], 1.0, mat(U, rr, 1), mat(U, 1, rr), 0.0, W + pO[n]);
   }
 
+  // the two environment sweeps run side by side, then the cuts over
+  // kCutStreams streams; events order them after the projectors and before
+  // the end of the call
+  Streams ss;
+  ss.make(2 + kCutStreams, 3 + kCutStreams);
+  cudaStream_t sl_st = ss.s[0], sr_st = ss.s[1];
+  cudaEvent_t ev_p = ss.ev[0], ev_l = ss.ev[1], ev_r = ss.ev[2];
+  QTT_CUDA(cudaEventRecord(ev_p, st));
+  QTT_CUDA(cudaStreamWaitEvent(sl_st, ev_p, 0));
+  QTT_CUDA(cudaStreamWaitEvent(sr_st, ev_p, 0));
+
   // left environments
-  fill_value(st, W + eO[0], 1, 1.0);
+  fill_value(sl_st, W + eO[0], 1, 1.0);
   for (int n = 1; n < N; ++n) {
     const long long rl = r[n - 1], rr = r[n], sl = s[n - 1], sr = s[n];
-    mm(st, (int)rl, (int)(2 * sr), (int)sl, 1.0, mat(W + eO[n - 1], sl, 1), mat(Ys(n), 2 * sr, 1), 0.0,
+    mm(sl_st, (int)rl, (int)(2 * sr), (int)sl, 1.0, mat(W + eO[n - 1], sl, 1), mat(Ys(n), 2 * sr, 1), 0.0,
        W + yhO[n]);
-    mm(st, (int)rr, (int)sr, (int)(2 * rl), 1.0, mat(Xs(n), 1, rr), mat(W + yhO[n], sr, 1), 0.0, T[T_A]);
-    mm(st, (int)rr, (int)sr, (int)rr, 1.0, mat(W + pO[n], rr, 1), mat(T[T_A], sr, 1), 0.0, W + eO[n]);
+    mm(sl_st, (int)rr, (int)sr, (int)(2 * rl), 1.0, mat(Xs(n), 1, rr), mat(W + yhO[n], sr, 1), 0.0, TA);
+    mm(sl_st, (int)rr, (int)sr, (int)rr, 1.0, mat(W + pO[n], rr, 1), mat(TA, sr, 1), 0.0, W + eO[n]);
   }
   {
     const long long rl = r[N - 1], sl = s[N - 1];
-    mm(st, (int)rl, 2, (int)sl, 1.0, mat(W + eO[N - 1], sl, 1), mat(Ys(N), 2, 1), 0.0, W + lastO);
+    mm(sl_st, (int)rl, 2, (int)sl, 1.0, mat(W + eO[N - 1], sl, 1), mat(Ys(N), 2, 1), 0.0, W + lastO);
   }
+  QTT_CUDA(cudaEventRecord(ev_l, sl_st));
 
   // right environments against X's projected right part
   for (int n = 2; n < N; ++n) {
     const long long rl = r[n - 1], rr = r[n];
-    mm(st, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(Xs(n), rr, 1), mat(W + pO[n], rr, 1), 0.0, W + qpO[n]);
+    mm(sr_st, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(Xs(n), rr, 1), mat(W + pO[n], rr, 1), 0.0, W + qpO[n]);
   }
   {
     const long long rl = r[N - 1], sl = s[N - 1];
-    mm(st, (int)sl, (int)rl, 2, 1.0, mat(Ys(N), 2, 1), mat(Xs(N), 1, 2), 0.0, W + rO[N - 1]);
+    mm(sr_st, (int)sl, (int)rl, 2, 1.0, mat(Ys(N), 2, 1), mat(Xs(N), 1, 2), 0.0, W + rO[N - 1]);
   }
   for (int n = N - 1; n >= 2; --n) {
     const long long rl = r[n - 1], rr = r[n], sl = s[n - 1], sr = s[n];
-    mm(st, (int)(2 * sl), (int)rr, (int)sr, 1.0, mat(Ys(n), sr, 1), mat(W + rO[n], rr, 1), 0.0, T[T_A]);
-    mm(st, (int)sl, (int)rl, (int)(2 * rr), 1.0, mat(T[T_A], 2 * rr, 1), mat(W + qpO[n], 1, 2 * rr), 0.0,
+    mm(sr_st, (int)(2 * sl), (int)rr, (int)sr, 1.0, mat(Ys(n), sr, 1), mat(W + rO[n], rr, 1), 0.0, TR);
+    mm(sr_st, (int)sl, (int)rl, (int)(2 * rr), 1.0, mat(TR, 2 * rr, 1), mat(W + qpO[n], 1, 2 * rr), 0.0,
        W + rO[n - 1]);
+  }
+  QTT_CUDA(cudaEventRecord(ev_r, sr_st));
+  for (int c = 0; c < kCutStreams; ++c) {
+    QTT_CUDA(cudaStreamWaitEvent(ss.s[2 + c], ev_l, 0));
+    QTT_CUDA(cudaStreamWaitEvent(ss.s[2 + c], ev_r, 0));
   }
 
   // one delta core per cut, written into the output train with X's cores
   for (int n = 1; n < N; ++n) {
+    const int c = (n - 1) % kCutStreams;
+    cudaStream_t cs = ss.s[2 + c];
+    double* T[T_COUNT];
+    for (int t = 0; t < T_COUNT; ++t) T[t] = W + tO[c][t];
     const long long rl = r[n - 1], rr = r[n], sr = s[n];
     const int kk = k[(size_t)n], nd = (int)rr - kk;
     const double* U = W + uO[n];
     const double* L = W + lO[n];
     const double* Q = Xs(n);
-    mm(st, (int)(2 * rl), (int)rr, (int)sr, 1.0, mat(W + yhO[n], sr, 1), mat(W + rO[n], rr, 1), 0.0, T[T_G]);
-    mm(st, (int)rr, (int)rr, (int)(2 * rl), 1.0, mat(Q, 1, rr), mat(T[T_G], rr, 1), 0.0, T[T_H]);
+    mm(cs, (int)(2 * rl), (int)rr, (int)sr, 1.0, mat(W + yhO[n], sr, 1), mat(W + rO[n], rr, 1), 0.0, T[T_G]);
+    mm(cs, (int)rr, (int)rr, (int)(2 * rl), 1.0, mat(Q, 1, rr), mat(T[T_G], rr, 1), 0.0, T[T_H]);
     count_launches(1);
-    sym_sum_kernel<<<grid_for(rr * rr), kThreads, 0, st>>>((int)rr, T[T_H], T[T_S]);
+    sym_sum_kernel<<<grid_for(rr * rr), kThreads, 0, cs>>>((int)rr, T[T_H], T[T_S]);
     if (kk > 0) {
       count_launches(1);
-      scale_kept_kernel<<<grid_for(rr * kk), kThreads, 0, st>>>((int)rr, kk, U, (int)rr, L, eps, T[T_VF]);
+      scale_kept_kernel<<<grid_for(rr * kk), kThreads, 0, cs>>>((int)rr, kk, U, (int)rr, L, eps, T[T_VF]);
     }
-    mm(st, (int)rr, (int)rr, kk, 1.0, mat(T[T_VF], kk, 1), mat(U, 1, rr), 0.0, T[T_AM]);
+    mm(cs, (int)rr, (int)rr, kk, 1.0, mat(T[T_VF], kk, 1), mat(U, 1, rr), 0.0, T[T_AM]);
     if (kk > 0 && nd > 0) {
-      mm(st, nd, (int)rr, (int)rr, 1.0, mat(U + kk, 1, rr), mat(T[T_S], rr, 1), 0.0, T[T_B1]);
-      mm(st, nd, kk, (int)rr, 1.0, mat(T[T_B1], rr, 1), mat(U, rr, 1), 0.0, T[T_B]);
+      mm(cs, nd, (int)rr, (int)rr, 1.0, mat(U + kk, 1, rr), mat(T[T_S], rr, 1), 0.0, T[T_B1]);
+      mm(cs, nd, kk, (int)rr, 1.0, mat(T[T_B1], rr, 1), mat(U, rr, 1), 0.0, T[T_B]);
       count_launches(1);
-      gap_scale_kernel<<<grid_for((long long)nd * kk), kThreads, 0, st>>>(nd, kk, L, eps, T[T_B]);
-      mm(st, (int)rr, kk, nd, 1.0, mat(U + kk, rr, 1), mat(T[T_B], kk, 1), 0.0, T[T_C1]);
-      mm(st, (int)rr, (int)rr, kk, 1.0, mat(T[T_C1], kk, 1), mat(U, 1, rr), 0.0, T[T_GAM]);
+      gap_scale_kernel<<<grid_for((long long)nd * kk), kThreads, 0, cs>>>(nd, kk, L, eps, T[T_B]);
+      mm(cs, (int)rr, kk, nd, 1.0, mat(U + kk, rr, 1), mat(T[T_B], kk, 1), 0.0, T[T_C1]);
+      mm(cs, (int)rr, (int)rr, kk, 1.0, mat(T[T_C1], kk, 1), mat(U, 1, rr), 0.0, T[T_GAM]);
       count_launches(1);
-      sym_sum_kernel<<<grid_for(rr * rr), kThreads, 0, st>>>((int)rr, T[T_GAM], T[T_U]);
+      sym_sum_kernel<<<grid_for(rr * rr), kThreads, 0, cs>>>((int)rr, T[T_GAM], T[T_U]);
     } else {
-      QTT_CUDA(cudaMemsetAsync(T[T_U], 0, (size_t)(rr * rr) * sizeof(double), st));
+      QTT_CUDA(cudaMemsetAsync(T[T_U], 0, (size_t)(rr * rr) * sizeof(double), cs));
     }
     // gA = g A;  u = Gamma + Gamma^T - Q^T gA;  delta = gA + Q u
-    mm(st, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(T[T_G], rr, 1), mat(T[T_AM], rr, 1), 0.0, T[T_GA]);
-    mm(st, (int)rr, (int)rr, (int)(2 * rl), -1.0, mat(Q, 1, rr), mat(T[T_GA], rr, 1), 1.0, T[T_U]);
-    mm(st, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(Q, rr, 1), mat(T[T_U], rr, 1), 1.0, T[T_GA]);
+    mm(cs, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(T[T_G], rr, 1), mat(T[T_AM], rr, 1), 0.0, T[T_GA]);
+    mm(cs, (int)rr, (int)rr, (int)(2 * rl), -1.0, mat(Q, 1, rr), mat(T[T_GA], rr, 1), 1.0, T[T_U]);
+    mm(cs, (int)(2 * rl), (int)rr, (int)rr, 1.0, mat(Q, rr, 1), mat(T[T_U], rr, 1), 1.0, T[T_GA]);
     const long long ocore = (n == 1 ? 1 : 2 * rl) * 2 * (2 * rr);
     count_launches(1);
-    assemble_core_kernel<<<grid_for(ocore), kThreads, 0, st>>>((int)rl, (int)rr, n == 1 ? 1 : 0, Q, T[T_GA],
+    assemble_core_kernel<<<grid_for(ocore), kThreads, 0, cs>>>((int)rl, (int)rr, n == 1 ? 1 : 0, Q, T[T_GA],
                                                                  xbar + oo[n]);
   }
+  QTT_CUDA(cudaStreamWaitEvent(st, ev_l, 0));
   count_launches(1);
   assemble_last_kernel<<<1, kThreads, 0, st>>>((int)r[N - 1], W + lastO, Xs(N), xbar + oo[N]);
+  for (int c = 0; c < kCutStreams; ++c) {
+    QTT_CUDA(cudaEventRecord(ss.ev[3 + c], ss.s[2 + c]));
+    QTT_CUDA(cudaStreamWaitEvent(st, ss.ev[3 + c], 0));
+  }
   QTT_CUDA(cudaGetLastError());
   QTT_CUDA(cudaStreamSynchronize(st));
 }
