@@ -198,7 +198,10 @@ qtt_status qtt_grad(qtt_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* ou
  * returns (dT/dX)^T ybar, exact where every kept eigenvalue is separated
  * from the discarded ones; eps > 0 replaces each 1 / (lambda_i - lambda_j)
  * by its Lorentzian broadening (lambda_i - lambda_j) / ((lambda_i -
- * lambda_j)^2 + eps^2) (eps in the units of lambda, i.e. of |X|^2).
+ * lambda_j)^2 + eps^2) (eps in the units of lambda, i.e. of |X|^2).  A kept
+ * eigenvalue near the Gram's FP64 rounding (lambda_k below ~1e-12 lambda_0)
+ * makes the exact weight 1 / lambda_k of the null-space part amplify that
+ * rounding: pass tol >= 1e-7 or eps >= 1e-8 lambda_0 for such spectra.
  *   N       number of binary sites, 2 .. 64
  *   rx      host array of N + 1 bonds of x (rx[0] = rx[N] = 1, rx[n] <= 1024,
  *           rx[n] <= 2 rx[n-1])
