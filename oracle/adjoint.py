@@ -37,12 +37,25 @@ What it computes (plain FP64 numpy):
       dJ/db_m   = <dJ/df_0, g cos(q_m . x + p_m)>.
   The time step is held fixed (it is an input, not a function of theta).
 
+* With the bond truncation in the step (``solve_truncated``,
+  ``gradient_truncated``): each stage's sum is truncated as the stages of the
+  MPS algorithm are, f* = T(f + dt L(f)) and f_{n+1} = T((f + f* + dt L(f*)) / 2),
+  T the simultaneous truncation of every bond of the dense state read as a
+  train of N binary sites (module truncation).  The backward passes each
+  cotangent through T's vector-Jacobian product first:
+      lambda2 = T'(X2)^T lambda,  mu = T'(X1)^T (lambda2 + dt L'(f*)^T lambda2) / 2,
+      dJ/df_n = lambda2 / 2 + mu + dt L'(f_n)^T mu,
+  with the parameter terms taken against lambda2 and mu.
+
 Parity status: pinned in ``tests/test_oracle_adjoint.py`` against the
 forward oracle -- the transpose identity <lambda, L'(f) v> = <L'(f)^T lambda, v>
 with L'(f) v from central differences of fd.rhs (exact for a quadratic map),
 dL/dtheta against central differences of fd.rhs in theta (exact: L is affine
 in each parameter), and the whole gradient against central differences of
-J(theta) through fd.solve.
+J(theta) through fd.solve.  The truncated gradient is pinned in
+``tests/test_oracle_truncated_gradient.py`` against central differences of J
+through solve_truncated, in a configuration whose kept and discarded
+eigenvalues are separated at every stage.
 """
 from __future__ import annotations
 
@@ -51,9 +64,10 @@ import copy
 import numpy as np
 
 from . import fd
+from . import truncation
 
 __all__ = ["param_names", "objective", "objective_gradient", "rhs_transpose", "rhs_param_derivative",
-           "gradient", "fd_gradient", "with_param"]
+           "gradient", "fd_gradient", "with_param", "solve_truncated", "gradient_truncated"]
 
 
 def param_names(params):
@@ -239,3 +253,59 @@ def fd_gradient(params, nsteps, names=None, rel_h=1e-4):
         jm = objective(fd.solve(with_param(params, n, v - h), nsteps), grid)
         out.append((jp - jm) / (2.0 * h))
     return np.array(out)
+
+
+def solve_truncated(params, nsteps, chi, tol=0.0):
+    """nsteps Heun steps with both stage sums truncated to chi (module
+    truncation, the state read as a train of sum(bits) binary sites, site
+    order phi1, phi2, x1, x2, x3, most significant bit first); returns the
+    dense final state."""
+    grid = fd.make_grid(params["bits"])
+    u = fd.velocity_field(params, grid)
+    N = int(sum(params["bits"]))
+    dt = params["dt"]
+    f = fd.initial_pdf(params, grid)
+    shape = f.shape
+    for _ in range(int(nsteps)):
+        fs = truncation.truncate((f + dt * fd.rhs(f, grid, u, params)).ravel(), N, chi, tol).reshape(shape)
+        f = truncation.truncate((0.5 * (f + fs + dt * fd.rhs(fs, grid, u, params))).ravel(), N, chi,
+                                tol).reshape(shape)
+    return f
+
+
+def gradient_truncated(params, nsteps, chi, tol=0.0, eps=0.0):
+    """(J, dJ/dtheta) through solve_truncated (module docstring), theta in the
+    order of param_names(params); eps broadens the truncation's gaps."""
+    if params.get("rk_variant", 0) != 0:
+        raise ValueError("the adjoint is written for the Heun scheme")
+    grid = fd.make_grid(params["bits"])
+    u = fd.velocity_field(params, grid)
+    ops = _Ops(grid)
+    N = int(sum(params["bits"]))
+    dt = params["dt"]
+    f = fd.initial_pdf(params, grid)
+    shape = f.shape
+    traj = []
+    for _ in range(int(nsteps)):
+        X1 = f + dt * fd.rhs(f, grid, u, params)
+        fs = truncation.truncate(X1.ravel(), N, chi, tol).reshape(shape)
+        X2 = 0.5 * (f + fs + dt * fd.rhs(fs, grid, u, params))
+        traj.append((f, X1, fs, X2))
+        f = truncation.truncate(X2.ravel(), N, chi, tol).reshape(shape)
+    J = objective(f, grid)
+    names = param_names(params)
+    dyn = [n for n in names if not n.startswith("icmode")]
+    g = dict.fromkeys(names, 0.0)
+    lam = objective_gradient(grid)
+    for f, X1, fs, X2 in reversed(traj):
+        lam2 = truncation.truncate_vjp(X2.ravel(), lam.ravel(), N, chi, tol, eps).reshape(shape)
+        pre = 0.5 * (lam2 + dt * rhs_transpose(fs, lam2, grid, u, params, ops))
+        mu = truncation.truncate_vjp(X1.ravel(), pre.ravel(), N, chi, tol, eps).reshape(shape)
+        for n in dyn:
+            g[n] += 0.5 * dt * float(np.sum(lam2 * rhs_param_derivative(fs, grid, u, params, n, ops)))
+            g[n] += dt * float(np.sum(mu * rhs_param_derivative(f, grid, u, params, n, ops)))
+        lam = 0.5 * lam2 + mu + dt * rhs_transpose(f, mu, grid, u, params, ops)
+    for n in names:
+        if n.startswith("icmode"):
+            g[n] = float(np.sum(lam * _ic_derivative(params, grid, n)))
+    return J, np.array([g[n] for n in names])
