@@ -281,7 +281,9 @@ qtt_status qtt_observe_points_noalloc(qtt_ctx* ctx, double* inout, int64_t cap, 
 
 void qtt_destroy(qtt_ctx* ctx);
 
-/* Last error message of ctx (or of the last failed qtt_init when ctx is NULL). */
+/* Last error message of ctx; with ctx NULL, that of the calling thread's last
+ * failed call that takes no context (qtt_init, qtt_truncate_vjp,
+ * qtt_host_dense, qtt_selftest). */
 const char* qtt_last_error(const qtt_ctx* ctx);
 
 /* Library version string. */
