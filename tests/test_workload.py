@@ -21,3 +21,22 @@ def test_batch_params_ranges_and_seeding():
     # every grid size and chi is drawn
     assert {p["bits"][0] for p in a} == {5, 6, 7}
     assert {p["chi_max"] for p in a} == {16, 32, 64, 96}
+
+
+def test_truncation_trains_are_left_orthonormal():
+    """The inputs of the truncation backward's timing: bonds min(2^n, 2^(N-n),
+    ell) and min(.., chi), the first N-1 cores of X with orthonormal columns
+    (the precondition of qtt_truncate_vjp), seeded."""
+    N, ell, chi = 12, 20, 16
+    r, x, s, y = workload.make_truncation_trains(N, ell, chi)
+    assert r == [min(2 ** n, 2 ** (N - n), ell) for n in range(N + 1)]
+    assert s == [min(2 ** n, 2 ** (N - n), chi) for n in range(N + 1)]
+    assert x.size == sum(r[n] * 2 * r[n + 1] for n in range(N))
+    assert y.size == sum(s[n] * 2 * s[n + 1] for n in range(N))
+    off = 0
+    for n in range(N - 1):
+        Q = x[off: off + r[n] * 2 * r[n + 1]].reshape(2 * r[n], r[n + 1])
+        assert np.abs(Q.T @ Q - np.eye(r[n + 1])).max() < 1e-13
+        off += r[n] * 2 * r[n + 1]
+    r2, x2, _, y2 = workload.make_truncation_trains(N, ell, chi)
+    assert np.array_equal(x, x2) and np.array_equal(y, y2)
